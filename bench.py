@@ -1,0 +1,322 @@
+"""Benchmark: LiDAR rays/s on the 128-channel, 2048-azimuth (262,144 beams)
+sensor over the ~1.04M-triangle terrain + objects scene.
+
+One step = one pass of the whole per-beam path for one frame: ray generation,
+closest-hit traversal, surface attributes, incidence angle, reflectance lerp,
+Philox range noise, cut-offs, intensity and the ordered compaction of the
+kept returns into a point cloud.  The BVH is built once per scene (timed
+separately, reported as build_ms).  L2 is flushed (256 MiB write) before every
+timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(brute force, OpenMP) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LiDAR rays/sec (128-ch, 1M-tri scene) & roofline %; fwd+bwd vs plain fwd ms"
+UNIT = "rays/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+HBM_FALLBACK_GBS = 6800.0
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_FALLBACK_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lidar_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def fp32_peak_tflops(torch, sm_mhz):
+    props = torch.cuda.get_device_properties(0)
+    return props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import synth
+    from paper_2208_10295_gb300 import Lidar
+    from paper_2208_10295_gb300.build import build as build_lib
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    build_lib()
+    dev = torch.device("cuda", local_rank)
+    w = synth.cfg1()
+    # weak scaling: rank r casts its own frames along the trajectory (no data-path collective)
+    w3 = synth.cfg3(n_frames=max(world, 1))
+    frames = w.frames.copy()
+    if world > 1:
+        frames = w3.frames[rank:rank + 1].copy()
+    L = Lidar(local_rank)
+    stream = L.stream
+    scene = L.build_scene(w.scene.verts, w.scene.tris, w.scene.mat, w.scene.inst)
+    L.set_sensor(0, w.sensors[0])
+    table = L.build_tables(torch.tensor(w.params, device=dev))
+    L.set_materials(table)
+    if args.tune:
+        from paper_2208_10295_gb300.tune import autotune
+        autotune(L, scene, frames, w.seed)
+    n_beams = L.total_beams(frames)
+    build_ms = scene.info()["build_ms"]
+    pts = L.alloc_points(n_beams)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        L.cast_into(scene, frames, w.seed, None, pts)
+
+    # ---- whole-step timing (cast + compaction), L2 flushed before each step
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    st = L.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}")
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_points = int(pts["count"].item())
+
+    # ---- dominant kernel alone (the cast kernel, dense valid flags out)
+    dense = L.alloc_beams(n_beams, ("valid",))
+    k_ms = []
+    for i in range(args.steps + 3):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        L.cast_into(scene, frames, w.seed, dense)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            k_ms.append(s0.elapsed_time(s1))
+    kernel_ms = statistics.mean(k_ms)
+
+    # ---- end to end through host buffers: pose in, point cloud out
+    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in pts.items()}
+    e2e_ms = []
+    bo_total = 0
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.cast_into(scene, frames, w.seed, None, pts)   # copies the host frame array in
+        host["count"].copy_(pts["count"], non_blocking=True)
+        stream.synchronize()
+        c = int(host["count"].item())
+        for k in ("xyz", "range", "intensity", "normal", "material", "instance", "beam", "frame"):
+            host[k][:c].copy_(pts[k][:c], non_blocking=True)
+        stream.synchronize()
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+            bo_total += 8 + c * (12 + 4 + 4 + 12 + 2 + 4 + 4 + 4)
+    e2e_step_ms = statistics.mean(e2e_ms)
+
+    # ---- algorithmic work of one launch (instrumented run of the same kernel)
+    counters = L.count_work(scene, frames, w.seed)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return None
+    peaks, peaks_src = load_peaks()
+    clocks = clk.summary()
+    rays_total = n_beams * args.steps * world
+    value = rays_total / (total_ms / 1e3)
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    uniq_bytes = counters["unique_node_bytes"] + counters["unique_tri_bytes"] + counters["io_bytes"]
+    visit_bytes = counters["node_visits"] * 64 + counters["tri_tests"] * 48 + counters["io_bytes"]
+    achieved = uniq_bytes / (kernel_ms / 1e3) / 1e9
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
+    flops = counters["node_visits"] * 2 * 24 + counters["tri_tests"] * 40
+    alu_tf = flops / (kernel_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "cfg1: 128-ch x 2048 az (262,144 beams) over 1,036,288-tri terrain+objects "
+                               "scene, one frame per step incl. ordered compaction",
+                   "beams_per_step_per_gpu": n_beams, "tris": int(w.scene.n_tris),
+                   "l2": "flushed (256 MiB write) before every timed step", "build_ms": build_ms,
+                   "points_per_step": n_points, "launch": L.launch_config()},
+        "gpu_launches": 4 * args.steps,
+        "e2e": {"value": n_beams / (e2e_step_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 56,
+                "d2h_bytes_per_step": bo_total / args.steps},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "peak_source": f"{peaks_src} hbm_gbs (STREAM-style copy)",
+                     "bytes_per_launch": uniq_bytes, "kernel": "k_cast", "kernel_ms": kernel_ms},
+        "work_per_ray": {k: v / n_beams for k, v in counters.items()},
+        "visit_bytes_per_s_GBps": visit_bytes / (kernel_ms / 1e3) / 1e9,
+        "alu": {"achieved_tflops": alu_tf, "peak_tflops": fp32_peak_tflops(torch, sm_mhz),
+                "frac": alu_tf / fp32_peak_tflops(torch, sm_mhz)},
+        "clocks": clocks,
+    }
+    if world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, args)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return line
+
+
+def cpu_baseline(w, args, n_beams=None):
+    import oracle
+    oracle.build()
+    nb = n_beams or args.cpu_beams
+    sensor = w.sensors[0]
+    rng = np.random.default_rng(123)
+    beams = np.sort(rng.choice(sensor.n_beams, nb, replace=False)).astype(np.int64)
+    samples = (np.zeros(nb, np.int64), beams)
+    T = oracle.build_tables(w.params)
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    oracle.cast(w.scene, w.sensors, w.frames, T, w.seed, samples=samples, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": nb / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nb} seeded beams of the same frame (brute force FP64 over all {w.scene.n_tris} tris), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import synth
+    w = synth.cfg1()
+    for _ in range(args.warmup):
+        cpu_baseline(w, args, n_beams=64)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, args, n_beams=args.ref_beams))
+    total = time.perf_counter() - t0
+    nb = args.ref_beams * args.steps
+    value = nb / total
+    cb = vals[-1]
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "cfg1: 128-ch x 2048 az over 1,036,288-tri scene; each step a bounded "
+                                   f"sample of {args.ref_beams} beams"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": f"{args.ref_beams} seeded beams per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-beams", type=int, default=2048)
+    ap.add_argument("--ref-beams", type=int, default=256)
+    ap.add_argument("--tune", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,280 @@
+/*
+ * lidar.h — C ABI of the GB300 per-beam LiDAR return-generation library.
+ *
+ * The operation is the per-beam model of "Physical LiDAR Simulation in
+ * Real-Time Engine" (Jansen, Huebel, Steckel, 2022), Sec. II:
+ *   - beam pattern: spherical beam coordinates (azimuth theta_i, elevation
+ *     phi_j) from the sensor's horizontal/vertical FOV (Sec. II-A);
+ *   - range: distance to the first surface along the beam (Sec. II-A; found
+ *     here by ray casting a triangle BVH instead of sampling a depth pass),
+ *     with additive Gaussian range noise scaled by a noise factor (Sec. II-A);
+ *   - labels: per-point instance ID (Sec. II-B) and material ID (Sec. II-C);
+ *   - reflectance: Lambertian R(theta) = R(0) cos(theta) (Eq. 4), generalised
+ *     to a per-material 91-entry table over incidence angle 0..90 degrees that
+ *     is interpolated linearly (Sec. III); theta is the angle between the beam
+ *     and the surface normal (Sec. II-C);
+ *   - capability model: R_L(d) = R_L,max / d_max * d (Eq. 5); a point is kept
+ *     iff R_L(d) <= R and d <= d_max, d including the noise (Sec. II-D).
+ *
+ * Conventions
+ *   - Every pointer named *_dev is a device pointer on the context's device;
+ *     every other pointer is host memory.  All device arrays passed in are
+ *     owned by the caller and must stay valid until the work that uses them has
+ *     completed on the context stream.  The library owns only what it returns
+ *     through an opaque handle (context, scene) and its internal scratch.
+ *   - Calls are asynchronous on the context's CUDA stream unless stated.
+ *     Argument errors are detected on the host and returned immediately as
+ *     LIDAR_EINVAL with a message in lidar_last_error().  Errors found by a
+ *     kernel (capacity, traversal stack, bounded waits) are recorded in a
+ *     device status word and returned by lidar_sync_status().
+ *   - Floating point: all per-beam arithmetic is FP32.
+ */
+#ifndef LIDAR_H
+#define LIDAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lidar_ctx lidar_ctx;
+typedef struct lidar_scene lidar_scene;
+
+typedef enum {
+    LIDAR_OK = 0,
+    LIDAR_EINVAL = -1,    /* bad argument (host-side check) */
+    LIDAR_ENOMEM = -2,    /* device or host allocation failed */
+    LIDAR_ECUDA = -3,     /* a CUDA runtime call failed */
+    LIDAR_ESTATE = -4,    /* call not valid in the current state (e.g. no sensor in a slot) */
+    LIDAR_ESTACK = -5,    /* BVH deeper than the traversal stack */
+    LIDAR_ETIMEOUT = -6,  /* a bounded device-side wait gave up */
+    LIDAR_ECAPACITY = -7  /* point output capacity exceeded; count holds the needed size */
+} lidar_status;
+
+#define LIDAR_NO_HIT 0xFFFFFFFFu
+#define LIDAR_TABLE_SIZE 91      /* reflectance entries per material: 0..90 degrees, 1-degree grid */
+#define LIDAR_MAX_SENSORS 16
+#define LIDAR_MAX_SUBRAYS 8
+
+/* ------------------------------------------------------------------ context */
+
+/* Creates a context on `device` that enqueues all work on `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  The caller keeps
+ * ownership of the stream.  *out receives the handle; free with lidar_destroy. */
+lidar_status lidar_create(int device, void* cuda_stream, lidar_ctx** out);
+
+/* Releases the context, its sensors, its scratch and every scene still alive
+ * that it created.  Synchronises the context stream first. */
+void lidar_destroy(lidar_ctx* ctx);
+
+/* Thread-local, NUL-terminated message describing the last failed call on
+ * this thread ("" if none).  Valid until the next call on this thread. */
+const char* lidar_last_error(void);
+
+/* Synchronises the context stream, then returns and clears the device status
+ * word (LIDAR_OK, LIDAR_ECAPACITY, LIDAR_ESTACK or LIDAR_ETIMEOUT). */
+lidar_status lidar_sync_status(lidar_ctx* ctx);
+
+/* ------------------------------------------------------------------- scene */
+
+/* Builds a linear BVH (Karras 2012: 63-bit Morton codes of triangle centroids,
+ * radix sort, hierarchy from key prefixes, bottom-up exact FP32 box refit)
+ * over a triangle mesh and copies the triangles, in leaf order, into a
+ * library-owned layout.
+ *   verts_dev        float32 [n_verts][3], metres, world frame
+ *   tris_dev         uint32  [n_tris][3], vertex indices (< n_verts)
+ *   tri_material_dev uint16  [n_tris], material ID (row of the reflectance table;
+ *                    IDs >= the table's row count use the last row)
+ *   tri_instance_dev uint32  [n_tris], instance label reported per point
+ * n_tris may be 0 (every beam misses).  The input arrays are only read during
+ * the call.  This call synchronises the stream to report build errors
+ * (LIDAR_EINVAL for an out-of-range vertex index, LIDAR_ESTACK if the tree is
+ * deeper than the traversal stack). */
+lidar_status lidar_scene_build(lidar_ctx* ctx, const float* verts_dev, int64_t n_verts,
+                               const uint32_t* tris_dev, int64_t n_tris,
+                               const uint16_t* tri_material_dev, const uint32_t* tri_instance_dev,
+                               lidar_scene** out);
+
+void lidar_scene_free(lidar_scene* scene);
+
+typedef struct {
+    int64_t n_tris;
+    int64_t n_nodes;       /* internal nodes (n_tris - 1, or 1 for a single triangle) */
+    int32_t max_depth;     /* longest root-to-leaf path, in internal nodes */
+    int64_t device_bytes;  /* bytes held by the scene on the device */
+    double build_ms;       /* device time of the last build, CUDA events */
+} lidar_scene_info;
+
+lidar_status lidar_get_scene_info(const lidar_scene* scene, lidar_scene_info* out);
+
+/* Exports the built hierarchy for validation (host buffers, may be NULL):
+ * nodes [n_nodes][16] float32 bit patterns in the device layout, and the
+ * leaf-order -> original triangle index map [n_tris].  Synchronises. */
+lidar_status lidar_scene_export(const lidar_scene* scene, float* nodes_host, uint32_t* leaf_tri_host);
+
+/* ----------------------------------------------------------------- sensors */
+
+/* One sensor (Sec. II-A beam configuration, Sec. II-D capability model).
+ * Beam b has azimuth az_rad[b] (from +x towards +y in the sensor frame) and
+ * elevation el_rad[b] (from the x-y plane towards +z); its unit direction
+ * (cos el cos az, cos el sin az, sin el) is evaluated in FP64 on the host and
+ * rounded once to FP32.  Ranges in metres; reflectances as fractions. */
+typedef struct {
+    int64_t n_beams;
+    const double* az_rad;      /* host, [n_beams] */
+    const double* el_rad;      /* host, [n_beams] */
+    float r_min, r_max;        /* returns outside [r_min, r_max] are dropped (nearer hits still occlude) */
+    float d_max;               /* capability model maximum range (Eq. 5) */
+    float RL_max;              /* reflectance needed at d_max (Eq. 5) */
+    float sigma;               /* range-noise standard deviation (Sec. II-A noise factor) */
+    float gain;                /* intensity gain g: I = g R (r_ref/d)^p */
+    float range_exp;           /* p; 0 reproduces the paper's reflectance intensity */
+    float r_ref;
+    float divergence_rad;      /* full beam divergence; sampled by n_subrays rays, strongest return kept */
+    int32_t n_subrays;         /* 1..LIDAR_MAX_SUBRAYS */
+} lidar_sensor_desc;
+
+/* Installs a sensor in slot [0, LIDAR_MAX_SENSORS).  Copies the beam
+ * directions to the device (synchronously; the host arrays may be freed on
+ * return) and computes the slot's ray-order permutation. */
+lidar_status lidar_set_sensor(lidar_ctx* ctx, int32_t slot, const lidar_sensor_desc* desc);
+
+/* Replaces the intensity gain g of an installed sensor (the differentiable
+ * sensor constant of the adjoint); everything else in the slot is kept. */
+lidar_status lidar_set_sensor_gain(lidar_ctx* ctx, int32_t slot, float gain);
+
+/* Copies the slot's FP32 sensor-frame beam directions to host_out [n_beams][3]. */
+lidar_status lidar_get_beam_dirs(lidar_ctx* ctx, int32_t slot, float* host_out);
+
+/* --------------------------------------------------------------- materials */
+
+/* Reflectance tables from per-material parameters (a, s, w) [M][3]:
+ *   T[m][k] = a_m cos(k deg) + s_m exp(-k^2 / (2 w_m^2)),  k = 0..90,
+ * i.e. Eq. 4's Lambertian term with R(0) = a_m plus a specular lobe of height
+ * s_m and width w_m degrees.  table_dev: float32 [M][91]. */
+lidar_status lidar_build_tables(lidar_ctx* ctx, const float* params_dev, int32_t n_materials,
+                                float* table_dev);
+
+/* Chain rule of lidar_build_tables: grad_params_dev [M][3] = dL/d(a, s, w)
+ * given grad_table_dev [M][91] = dL/dT (overwrites grad_params_dev). */
+lidar_status lidar_build_tables_backward(lidar_ctx* ctx, const float* params_dev,
+                                         const float* grad_table_dev, int32_t n_materials,
+                                         float* grad_params_dev);
+
+/* Selects the reflectance table [n_materials][91] used by later casts and
+ * backward passes.  The table is read in place (not copied). */
+lidar_status lidar_set_materials(lidar_ctx* ctx, const float* table_dev, int32_t n_materials);
+
+/* -------------------------------------------------------------------- cast */
+
+/* One frame: sensor slot, frame number (part of the noise counter) and the
+ * sensor-to-world pose as a row-major 3x4 [R | t] (56 bytes, no padding). */
+typedef struct {
+    int32_t sensor;
+    int32_t frame;
+    float pose[12];
+} lidar_frame;
+
+/* Dense per-beam results.  Frame k's beams occupy the index range
+ * [off_k, off_k + n_beams(sensor_k)), off_k = sum of n_beams over frames < k.
+ * Every array is optional (NULL = not written) and has one entry per beam
+ * (normal: 3).  The tape used by lidar_cast_backward is {valid, mat,
+ * theta_deg, rf}. */
+typedef struct {
+    uint8_t* valid;       /* 1 if the return is kept */
+    uint32_t* tri;        /* original index of the hit triangle, LIDAR_NO_HIT on a miss */
+    float* t;             /* hit distance along the beam before noise (+inf on a miss) */
+    float* range;         /* noisy range d = t + sigma z */
+    float* intensity;     /* I = g R (r_ref/d)^p (0 on a miss) */
+    float* normal;        /* [3] face normal facing the sensor, sensor frame */
+    uint16_t* mat;        /* material of the hit triangle */
+    uint32_t* inst;       /* instance of the hit triangle */
+    uint8_t* sub;         /* chosen sub-ray (strongest valid return) */
+    float* theta_deg;     /* incidence angle in degrees */
+    float* rf;            /* range factor (r_ref/d)^p */
+} lidar_beams;
+
+/* Compacted point cloud: kept returns in (frame, beam) order.  All arrays
+ * optional; one entry per point (xyz, normal: 3). */
+typedef struct {
+    int64_t capacity;
+    float* xyz;           /* [3] d * beam direction, sensor frame */
+    float* range;
+    float* intensity;
+    float* normal;        /* [3] sensor frame */
+    uint16_t* material;
+    uint32_t* instance;
+    uint32_t* beam;       /* beam index within its sensor pattern */
+    uint32_t* frame;      /* index of the frame in the frames array */
+} lidar_points;
+
+/* Casts every beam of every frame against `scene`.
+ *   frames_host  [n_frames] host array, copied during the call
+ *   seed         noise key: the draw for (beam b, frame f, sensor s, sub-ray k)
+ *                is Philox4x64-10 with key (seed, 0) and counter
+ *                (b, f | s << 32, k, 0), Box-Muller on its first two words
+ *   beams        dense output (may be NULL)
+ *   points       compacted output (may be NULL); n_points_dev (device int64)
+ *                receives the number of kept returns, which may exceed the
+ *                capacity: then only `capacity` points are written and the
+ *                status word records LIDAR_ECAPACITY.
+ * Requires a material table (lidar_set_materials) and a sensor in every slot
+ * the frames name. */
+lidar_status lidar_cast(lidar_ctx* ctx, const lidar_scene* scene, const lidar_frame* frames_host,
+                        int32_t n_frames, uint64_t seed, const lidar_beams* beams,
+                        const lidar_points* points, int64_t* n_points_dev);
+
+/* Adjoint of the intensity with the hits and masks of the forward pass held
+ * fixed.  For every beam b with tape valid[b] = 1 and grad_I_dev[b] = dL/dI_b:
+ *   dL/dT[m][i]   += g rf (1 - f) dL/dI,   dL/dT[m][i+1] += g rf f dL/dI,
+ *   dL/dg         += rf R dL/dI,
+ * with i = min(floor(theta), 89), f = theta - i, R the interpolated table
+ * value and g = gain.  grad_table_dev [M][91] and grad_gain_dev [1] are
+ * accumulated into (not overwritten).  Accumulation uses 64-bit fixed point,
+ * so the result is bit-reproducible run to run. */
+lidar_status lidar_cast_backward(lidar_ctx* ctx, int64_t n_beams, const lidar_beams* tape, float gain,
+                                 const float* grad_I_dev, float* grad_table_dev, float* grad_gain_dev);
+
+/* Fused mean-squared-error variant: dL/dI_b = 2 (I_b - I*_b) / N over the
+ * beams valid in both the tape and target_valid_dev, N their count.  Writes
+ * loss_dev [1] (overwritten) and accumulates grad_table_dev, grad_gain_dev. */
+lidar_status lidar_cast_backward_mse(lidar_ctx* ctx, int64_t n_beams, const lidar_beams* tape, float gain,
+                                     const float* target_I_dev, const uint8_t* target_valid_dev,
+                                     float* loss_dev, float* grad_table_dev, float* grad_gain_dev);
+
+/* ----------------------------------------------------------- instrumentation */
+
+/* Work of one cast, counted by an instrumented instantiation of the same
+ * traversal kernel (not the timed one): BVH nodes fetched, triangles tested,
+ * and how many distinct nodes and triangles were touched.  Used to state the
+ * algorithmic bytes and flops behind the roofline. */
+typedef struct {
+    uint64_t rays;           /* traced rays (beams x sub-rays) */
+    uint64_t node_visits;    /* 64-byte node fetches */
+    uint64_t tri_tests;      /* 48-byte triangle fetches + watertight tests */
+    uint64_t unique_nodes;   /* distinct nodes fetched */
+    uint64_t unique_tris;    /* distinct triangles fetched */
+} lidar_work_counts;
+
+/* Runs the cast of lidar_cast (dense valid flags only) with counting enabled
+ * and returns the totals.  Synchronises. */
+lidar_status lidar_count_work(lidar_ctx* ctx, const lidar_scene* scene, const lidar_frame* frames_host,
+                              int32_t n_frames, uint64_t seed, lidar_work_counts* out);
+
+/* --------------------------------------------------------------- launch tuning */
+
+typedef struct {
+    int32_t block_threads;   /* threads per block of the cast kernel (multiple of 32, <= 1024) */
+    int32_t blocks_per_sm;   /* persistent blocks per SM */
+    int32_t tile_rays;       /* rays a block takes from the work queue at a time */
+    int32_t ray_order;       /* 0 = beam order, 1 = Morton order of beam directions */
+} lidar_launch_config;
+
+lidar_status lidar_get_launch_config(lidar_ctx* ctx, lidar_launch_config* out);
+lidar_status lidar_set_launch_config(lidar_ctx* ctx, const lidar_launch_config* cfg);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIDAR_H */

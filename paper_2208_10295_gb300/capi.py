@@ -1,0 +1,166 @@
+"""ctypes binding of include/lidar.h: the same names, argument marshalling only.
+
+Every function here forwards to the compiled CUDA library; nothing computes on
+the host.  A missing library raises immediately (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblidar.so")
+
+LIDAR_OK = 0
+LIDAR_EINVAL = -1
+LIDAR_ENOMEM = -2
+LIDAR_ECUDA = -3
+LIDAR_ESTATE = -4
+LIDAR_ESTACK = -5
+LIDAR_ETIMEOUT = -6
+LIDAR_ECAPACITY = -7
+STATUS_NAMES = {0: "LIDAR_OK", -1: "LIDAR_EINVAL", -2: "LIDAR_ENOMEM", -3: "LIDAR_ECUDA", -4: "LIDAR_ESTATE",
+                -5: "LIDAR_ESTACK", -6: "LIDAR_ETIMEOUT", -7: "LIDAR_ECAPACITY"}
+
+LIDAR_NO_HIT = 0xFFFFFFFF
+LIDAR_TABLE_SIZE = 91
+LIDAR_MAX_SENSORS = 16
+LIDAR_MAX_SUBRAYS = 8
+
+c_vp = ctypes.c_void_p
+
+
+class LidarError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class lidar_scene_info(ctypes.Structure):
+    _fields_ = [("n_tris", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("max_depth", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double)]
+
+
+class lidar_sensor_desc(ctypes.Structure):
+    _fields_ = [("n_beams", ctypes.c_int64), ("az_rad", c_vp), ("el_rad", c_vp),
+                ("r_min", ctypes.c_float), ("r_max", ctypes.c_float), ("d_max", ctypes.c_float),
+                ("RL_max", ctypes.c_float), ("sigma", ctypes.c_float), ("gain", ctypes.c_float),
+                ("range_exp", ctypes.c_float), ("r_ref", ctypes.c_float), ("divergence_rad", ctypes.c_float),
+                ("n_subrays", ctypes.c_int32)]
+
+
+class lidar_frame(ctypes.Structure):
+    _fields_ = [("sensor", ctypes.c_int32), ("frame", ctypes.c_int32), ("pose", ctypes.c_float * 12)]
+
+
+class lidar_beams(ctypes.Structure):
+    _fields_ = [(n, c_vp) for n in ("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst", "sub",
+                                    "theta_deg", "rf")]
+
+
+class lidar_points(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64)] + [(n, c_vp) for n in ("xyz", "range", "intensity", "normal",
+                                                                      "material", "instance", "beam", "frame")]
+
+
+class lidar_work_counts(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("rays", "node_visits", "tri_tests", "unique_nodes", "unique_tris")]
+
+
+class lidar_launch_config(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("tile_rays", ctypes.c_int32), ("ray_order", ctypes.c_int32)]
+
+
+assert ctypes.sizeof(lidar_frame) == 56
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes); restype None means lidar_status checked by _call
+_PROTOS = [
+    ("lidar_create", ctypes.c_int, [ctypes.c_int, c_vp, ctypes.POINTER(c_vp)]),
+    ("lidar_destroy", None, [c_vp]),
+    ("lidar_last_error", ctypes.c_char_p, []),
+    ("lidar_sync_status", ctypes.c_int, [c_vp]),
+    ("lidar_scene_build", ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, c_vp, ctypes.c_int64, c_vp, c_vp,
+                                         ctypes.POINTER(c_vp)]),
+    ("lidar_scene_free", None, [c_vp]),
+    ("lidar_get_scene_info", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_scene_info)]),
+    ("lidar_scene_export", ctypes.c_int, [c_vp, c_vp, c_vp]),
+    ("lidar_set_sensor", ctypes.c_int, [c_vp, ctypes.c_int32, ctypes.POINTER(lidar_sensor_desc)]),
+    ("lidar_set_sensor_gain", ctypes.c_int, [c_vp, ctypes.c_int32, ctypes.c_float]),
+    ("lidar_get_beam_dirs", ctypes.c_int, [c_vp, ctypes.c_int32, c_vp]),
+    ("lidar_build_tables", ctypes.c_int, [c_vp, c_vp, ctypes.c_int32, c_vp]),
+    ("lidar_build_tables_backward", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, c_vp]),
+    ("lidar_set_materials", ctypes.c_int, [c_vp, c_vp, ctypes.c_int32]),
+    ("lidar_cast", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
+                                  ctypes.POINTER(lidar_beams), ctypes.POINTER(lidar_points), c_vp]),
+    ("lidar_cast_backward", ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.POINTER(lidar_beams), ctypes.c_float,
+                                           c_vp, c_vp, c_vp]),
+    ("lidar_cast_backward_mse", ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.POINTER(lidar_beams),
+                                               ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    ("lidar_count_work", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.POINTER(lidar_work_counts)]),
+    ("lidar_get_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
+    ("lidar_set_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
+]
+
+EXPORTED = [p[0] for p in _PROTOS]
+
+
+def load(path: str = None):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
+            L = ctypes.CDLL(p)
+            for name, res, args in _PROTOS:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return load().lidar_last_error().decode(errors="replace")
+
+
+def check(status: int, what: str = ""):
+    if status != LIDAR_OK:
+        raise LidarError(status, f"{what}: {last_error()}")
+    return status
+
+
+def _fwd(name):
+    def f(*args):
+        return getattr(load(), name)(*args)
+    f.__name__ = name
+    return f
+
+
+lidar_create = _fwd("lidar_create")
+lidar_destroy = _fwd("lidar_destroy")
+lidar_last_error = _fwd("lidar_last_error")
+lidar_sync_status = _fwd("lidar_sync_status")
+lidar_scene_build = _fwd("lidar_scene_build")
+lidar_scene_free = _fwd("lidar_scene_free")
+lidar_get_scene_info = _fwd("lidar_get_scene_info")
+lidar_scene_export = _fwd("lidar_scene_export")
+lidar_set_sensor = _fwd("lidar_set_sensor")
+lidar_set_sensor_gain = _fwd("lidar_set_sensor_gain")
+lidar_get_beam_dirs = _fwd("lidar_get_beam_dirs")
+lidar_build_tables = _fwd("lidar_build_tables")
+lidar_build_tables_backward = _fwd("lidar_build_tables_backward")
+lidar_set_materials = _fwd("lidar_set_materials")
+lidar_cast = _fwd("lidar_cast")
+lidar_cast_backward = _fwd("lidar_cast_backward")
+lidar_cast_backward_mse = _fwd("lidar_cast_backward_mse")
+lidar_count_work = _fwd("lidar_count_work")
+lidar_get_launch_config = _fwd("lidar_get_launch_config")
+lidar_set_launch_config = _fwd("lidar_set_launch_config")

@@ -1,0 +1,318 @@
+// Linear BVH build (Karras, "Maximizing Parallelism in the Construction of
+// BVHs, Octrees, and k-d Trees", HPG 2012), hand-written:
+//   1. centroid bounds (block reduction + ordered-int atomics), index check
+//   2. 63-bit Morton keys of the triangle centroids (21 bits per axis)
+//   3. stable radix sort of (key, triangle index)
+//   4. leaf-ordered triangle gather (vertices + original index, material, instance)
+//   5. internal nodes from the longest common key prefixes (ties on equal keys
+//      broken by the leaf index), parent links
+//   6. bottom-up refit: each leaf climbs; the second thread to reach a node
+//      writes both child boxes (exact FP32 min/max, no rounding) and the node
+//      height; the first stops.  The root height bounds the traversal stack.
+#include "common.cuh"
+
+namespace lidar {
+namespace {
+
+constexpr int kBuildThreads = 256;
+
+__device__ __forceinline__ int float_to_ordered(float f)
+{
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+
+__device__ __forceinline__ float ordered_to_float(int i)
+{
+    return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF);
+}
+
+__device__ __forceinline__ float3 load_vert(const float* v, uint32_t i)
+{
+    return make_float3(v[3 * (int64_t)i], v[3 * (int64_t)i + 1], v[3 * (int64_t)i + 2]);
+}
+
+__global__ void k_init_bounds(int* bounds)
+{
+    if (threadIdx.x < 3) bounds[threadIdx.x] = float_to_ordered(INFINITY);
+    else if (threadIdx.x < 6) bounds[threadIdx.x] = float_to_ordered(-INFINITY);
+}
+
+__device__ __forceinline__ float3 centroid(float3 a, float3 b, float3 c)
+{
+    const float k = 1.0f / 3.0f;
+    return make_float3((a.x + b.x + c.x) * k, (a.y + b.y + c.y) * k, (a.z + b.z + c.z) * k);
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_centroid_bounds(const float* __restrict__ verts,
+                                                                   int64_t n_verts,
+                                                                   const uint32_t* __restrict__ tris,
+                                                                   int64_t n, int* bounds, int* status)
+{
+    float lo[3] = {INFINITY, INFINITY, INFINITY};
+    float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t a = tris[3 * i], b = tris[3 * i + 1], c = tris[3 * i + 2];
+        if ((int64_t)a >= n_verts || (int64_t)b >= n_verts || (int64_t)c >= n_verts) {
+            raise_status(status, ST_INDEX);
+            continue;
+        }
+        float3 ct = centroid(load_vert(verts, a), load_vert(verts, b), load_vert(verts, c));
+        lo[0] = fminf(lo[0], ct.x); lo[1] = fminf(lo[1], ct.y); lo[2] = fminf(lo[2], ct.z);
+        hi[0] = fmaxf(hi[0], ct.x); hi[1] = fmaxf(hi[1], ct.y); hi[2] = fmaxf(hi[2], ct.z);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_down_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_down_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&bounds[k], float_to_ordered(lo[k]));
+            atomicMax(&bounds[3 + k], float_to_ordered(hi[k]));
+        }
+    }
+}
+
+// spread the low 21 bits of x so that bit i lands on bit 3i
+__device__ __forceinline__ uint64_t spread3(uint64_t x)
+{
+    x &= 0x1FFFFFull;
+    x = (x | (x << 32)) & 0x001F00000000FFFFull;
+    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t quantize21(float v, float lo, float inv_ext)
+{
+    float q = (v - lo) * inv_ext * 2097151.0f;
+    q = fminf(fmaxf(q, 0.0f), 2097151.0f);
+    return (uint32_t)q;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_morton(const float* __restrict__ verts,
+                                                          const uint32_t* __restrict__ tris, int64_t n,
+                                                          int64_t n_verts, const int* __restrict__ bounds,
+                                                          uint64_t* __restrict__ keys,
+                                                          uint32_t* __restrict__ vals)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float lo[3], inv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = ordered_to_float(bounds[k]);
+        float ext = ordered_to_float(bounds[3 + k]) - lo[k];
+        inv[k] = ext > 0.0f ? 1.0f / ext : 0.0f;
+    }
+    uint32_t a = tris[3 * i], b = tris[3 * i + 1], c = tris[3 * i + 2];
+    uint64_t key = 0;
+    if ((int64_t)a < n_verts && (int64_t)b < n_verts && (int64_t)c < n_verts) {
+        float3 ct = centroid(load_vert(verts, a), load_vert(verts, b), load_vert(verts, c));
+        key = (spread3(quantize21(ct.x, lo[0], inv[0])) << 2) | (spread3(quantize21(ct.y, lo[1], inv[1])) << 1) |
+              spread3(quantize21(ct.z, lo[2], inv[2]));
+    }
+    keys[i] = key;
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_gather(const float* __restrict__ verts, int64_t n_verts,
+                                                          const uint32_t* __restrict__ tris,
+                                                          const uint16_t* __restrict__ mat,
+                                                          const uint32_t* __restrict__ inst,
+                                                          const uint32_t* __restrict__ order, int64_t n,
+                                                          float4* __restrict__ tris_out,
+                                                          uint32_t* __restrict__ leaf_tri)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t t = order[i];
+    uint32_t a = tris[3 * (int64_t)t], b = tris[3 * (int64_t)t + 1], c = tris[3 * (int64_t)t + 2];
+    if ((int64_t)a >= n_verts || (int64_t)b >= n_verts || (int64_t)c >= n_verts) a = b = c = 0;
+    float3 va = load_vert(verts, a), vb = load_vert(verts, b), vc = load_vert(verts, c);
+    tris_out[3 * i + 0] = make_float4(va.x, va.y, va.z, __int_as_float((int)t));
+    tris_out[3 * i + 1] = make_float4(vb.x, vb.y, vb.z, __int_as_float((int)(mat ? mat[t] : 0)));
+    tris_out[3 * i + 2] = make_float4(vc.x, vc.y, vc.z, __int_as_float((int)(inst ? inst[t] : 0)));
+    leaf_tri[i] = t;
+}
+
+// length of the common prefix of keys i and j; -1 outside [0, n)
+__device__ __forceinline__ int delta(const uint64_t* __restrict__ keys, int64_t n, int64_t i, int64_t j)
+{
+    if (j < 0 || j >= n) return -1;
+    uint64_t a = keys[i], b = keys[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_karras(const uint64_t* __restrict__ keys, int64_t n,
+                                                          float4* __restrict__ nodes,
+                                                          int* __restrict__ parent_node,
+                                                          int* __restrict__ parent_leaf)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    // direction of the node's key range
+    const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(keys, n, i, i - d);
+    // exponential then binary search for the far end of the range
+    int64_t lmax = 2;
+    while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    const int64_t j = i + l * d;
+    const int dnode = delta(keys, n, i, j);
+    // split: last position of the range that still shares more than dnode bits with i
+    int64_t s = 0;
+    int64_t step = l;
+    do {
+        step = (step + 1) >> 1;
+        if (delta(keys, n, i, i + (s + step) * d) > dnode) s += step;
+    } while (step > 1);
+    const int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    int left, right;
+    if (lo == gamma) {
+        left = ~(int)gamma;
+        parent_leaf[gamma] = (int)i;
+    } else {
+        left = (int)gamma;
+        parent_node[gamma] = (int)i;
+    }
+    if (hi == gamma + 1) {
+        right = ~(int)(gamma + 1);
+        parent_leaf[gamma + 1] = (int)i;
+    } else {
+        right = (int)(gamma + 1);
+        parent_node[gamma + 1] = (int)i;
+    }
+    nodes[4 * i + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.0f, 0.0f);
+    if (i == 0) parent_node[0] = -1;
+}
+
+struct Box {
+    float lo[3], hi[3];
+};
+
+__device__ __forceinline__ Box leaf_box(const float4* __restrict__ tris, int leaf)
+{
+    float4 a = tris[3 * (int64_t)leaf], b = tris[3 * (int64_t)leaf + 1], c = tris[3 * (int64_t)leaf + 2];
+    Box r;
+    r.lo[0] = fminf(a.x, fminf(b.x, c.x)); r.hi[0] = fmaxf(a.x, fmaxf(b.x, c.x));
+    r.lo[1] = fminf(a.y, fminf(b.y, c.y)); r.hi[1] = fmaxf(a.y, fmaxf(b.y, c.y));
+    r.lo[2] = fminf(a.z, fminf(b.z, c.z)); r.hi[2] = fmaxf(a.z, fmaxf(b.z, c.z));
+    return r;
+}
+
+__device__ __forceinline__ Box node_box(const float4* node_boxes, int node)
+{
+    float4 lo = __ldcg(&node_boxes[2 * (int64_t)node]);
+    float4 hi = __ldcg(&node_boxes[2 * (int64_t)node + 1]);
+    Box r;
+    r.lo[0] = lo.x; r.lo[1] = lo.y; r.lo[2] = lo.z;
+    r.hi[0] = hi.x; r.hi[1] = hi.y; r.hi[2] = hi.z;
+    return r;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_refit(const float4* __restrict__ tris, int64_t n,
+                                                         float4* nodes, float4* node_boxes, int* heights,
+                                                         const int* __restrict__ parent_node,
+                                                         const int* __restrict__ parent_leaf, int* visits,
+                                                         int* max_height)
+{
+    int64_t leaf = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (leaf >= n) return;
+    int p = parent_leaf[leaf];
+    while (p >= 0) {
+        __threadfence();
+        if (atomicAdd(&visits[p], 1) == 0) return;  // the sibling subtree is not finished yet
+        __threadfence();
+        float4 n3 = __ldcg(&nodes[4 * (int64_t)p + 3]);
+        int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+        Box L = cl < 0 ? leaf_box(tris, ~cl) : node_box(node_boxes, cl);
+        Box R = cr < 0 ? leaf_box(tris, ~cr) : node_box(node_boxes, cr);
+        int hl = cl < 0 ? 0 : __ldcg(&heights[cl]);
+        int hr = cr < 0 ? 0 : __ldcg(&heights[cr]);
+        nodes[4 * (int64_t)p + 0] = make_float4(L.lo[0], L.hi[0], L.lo[1], L.hi[1]);
+        nodes[4 * (int64_t)p + 1] = make_float4(R.lo[0], R.hi[0], R.lo[1], R.hi[1]);
+        nodes[4 * (int64_t)p + 2] = make_float4(L.lo[2], L.hi[2], R.lo[2], R.hi[2]);
+        node_boxes[2 * (int64_t)p] = make_float4(fminf(L.lo[0], R.lo[0]), fminf(L.lo[1], R.lo[1]),
+                                                 fminf(L.lo[2], R.lo[2]), 0.0f);
+        node_boxes[2 * (int64_t)p + 1] = make_float4(fmaxf(L.hi[0], R.hi[0]), fmaxf(L.hi[1], R.hi[1]),
+                                                     fmaxf(L.hi[2], R.hi[2]), 0.0f);
+        int h = 1 + max(hl, hr);
+        heights[p] = h;
+        if (p == 0) atomicMax(max_height, h);
+        p = parent_node[p];
+    }
+}
+
+// a single triangle: one root whose right child box is empty
+__global__ void k_single(const float4* __restrict__ tris, float4* nodes, int* max_height)
+{
+    Box L = leaf_box(tris, 0);
+    nodes[0] = make_float4(L.lo[0], L.hi[0], L.lo[1], L.hi[1]);
+    nodes[1] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+    nodes[2] = make_float4(L.lo[2], L.hi[2], INFINITY, -INFINITY);
+    nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), 0.0f, 0.0f);
+    *max_height = 1;
+}
+
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+size_t build_scratch_bytes(int64_t n)
+{
+    return align256(n * sizeof(uint64_t)) + align256(n * sizeof(uint32_t)) + align256(n * sizeof(int)) * 4 +
+           align256((size_t)n * 2 * sizeof(float4)) + align256(64) + radix_sort_scratch_bytes(n);
+}
+
+cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, const uint32_t* tris,
+                       const uint16_t* mat, const uint32_t* inst, int64_t n, float4* nodes_out,
+                       float4* tris_out, uint32_t* leaf_tri_out, int* status, int* max_height_dev,
+                       void* scratch, size_t scratch_bytes)
+{
+    if (n == 0) return cudaSuccess;
+    if (scratch_bytes < build_scratch_bytes(n)) return cudaErrorInvalidValue;
+    char* p = (char*)scratch;
+    uint64_t* keys = (uint64_t*)p; p += align256(n * sizeof(uint64_t));
+    uint32_t* vals = (uint32_t*)p; p += align256(n * sizeof(uint32_t));
+    int* parent_node = (int*)p; p += align256(n * sizeof(int));
+    int* parent_leaf = (int*)p; p += align256(n * sizeof(int));
+    int* visits = (int*)p; p += align256(n * sizeof(int));
+    int* heights = (int*)p; p += align256(n * sizeof(int));
+    float4* node_boxes = (float4*)p; p += align256((size_t)n * 2 * sizeof(float4));
+    int* bounds = (int*)p; p += align256(64);
+    void* sort_scratch = p;
+    size_t sort_bytes = scratch_bytes - (size_t)(p - (char*)scratch);
+
+    const int blocks = (int)((n + kBuildThreads - 1) / kBuildThreads);
+    k_init_bounds<<<1, 32, 0, s>>>(bounds);
+    const int red_blocks = blocks < 2048 ? blocks : 2048;
+    k_centroid_bounds<<<red_blocks, kBuildThreads, 0, s>>>(verts, n_verts, tris, n, bounds, status);
+    k_morton<<<blocks, kBuildThreads, 0, s>>>(verts, tris, n, n_verts, bounds, keys, vals);
+    cudaError_t e = radix_sort_pairs_u64(s, keys, vals, n, 63, sort_scratch, sort_bytes);
+    if (e != cudaSuccess) return e;
+    k_gather<<<blocks, kBuildThreads, 0, s>>>(verts, n_verts, tris, mat, inst, vals, n, tris_out, leaf_tri_out);
+    cudaMemsetAsync(max_height_dev, 0, sizeof(int), s);
+    if (n == 1) {
+        k_single<<<1, 1, 0, s>>>(tris_out, nodes_out, max_height_dev);
+        return cudaGetLastError();
+    }
+    const int iblocks = (int)((n - 1 + kBuildThreads - 1) / kBuildThreads);
+    k_karras<<<iblocks, kBuildThreads, 0, s>>>(keys, n, nodes_out, parent_node, parent_leaf);
+    cudaMemsetAsync(visits, 0, n * sizeof(int), s);
+    k_refit<<<blocks, kBuildThreads, 0, s>>>(tris_out, n, nodes_out, node_boxes, heights, parent_node, parent_leaf,
+                                             visits, max_height_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace lidar

@@ -1,0 +1,397 @@
+// Per-beam return generation: one persistent kernel takes tiles of beams from
+// a global work counter (tiles ordered by frame, then by position in the
+// sensor's ray order), and for every beam runs
+//   ray generation -> closest-hit BVH traversal -> surface attributes ->
+//   incidence angle -> reflectance lerp -> Philox range noise -> cut-offs ->
+//   intensity -> strongest of the sub-rays
+// writing a dense per-beam record.  A second stage compacts the kept returns
+// in (frame, beam) order.
+#include "common.cuh"
+#include "philox.cuh"
+#include "trace.cuh"
+
+namespace lidar {
+namespace {
+
+struct BeamResult {
+    float t, range, intensity, theta_deg, rf;
+    float nx, ny, nz;   // world frame, facing the sensor
+    uint32_t tri, inst;
+    uint32_t mat;
+    int valid;
+};
+
+// Everything after the closest hit for one ray (Sec. II-A..II-D).
+__device__ __forceinline__ void shade(const SceneDev& S, const HitRec& h, const RayW& r, const SensorDev& sd,
+                                      const TableDev& T, uint64_t seed, uint32_t beam, uint32_t frame,
+                                      uint32_t sensor, uint32_t sub, BeamResult& out)
+{
+    if (h.leaf < 0) {
+        out.t = INFINITY;
+        out.range = INFINITY;
+        out.intensity = 0.0f;
+        out.theta_deg = 0.0f;
+        out.rf = 0.0f;
+        out.nx = out.ny = out.nz = 0.0f;
+        out.tri = LIDAR_NO_HIT;
+        out.inst = 0;
+        out.mat = 0;
+        out.valid = 0;
+        return;
+    }
+    const float4 a = __ldg(&S.tris[3 * (int64_t)h.leaf]);
+    const float4 b = __ldg(&S.tris[3 * (int64_t)h.leaf + 1]);
+    const float4 c = __ldg(&S.tris[3 * (int64_t)h.leaf + 2]);
+    // face normal, turned towards the sensor
+    const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+    const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+    float nx = e1y * e2z - e1z * e2y;
+    float ny = e1z * e2x - e1x * e2z;
+    float nz = e1x * e2y - e1y * e2x;
+    const float inl = rsqrtf(nx * nx + ny * ny + nz * nz);
+    nx *= inl; ny *= inl; nz *= inl;
+    float dn = r.dx * nx + r.dy * ny + r.dz * nz;
+    if (dn > 0.0f) { nx = -nx; ny = -ny; nz = -nz; dn = -dn; }
+    // incidence angle between beam and normal (Sec. II-C)
+    const float cx = r.dy * nz - r.dz * ny, cy = r.dz * nx - r.dx * nz, cz = r.dx * ny - r.dy * nx;
+    const float theta = atan2f(sqrtf(cx * cx + cy * cy + cz * cz), fabsf(dn));
+    const float theta_deg = theta * 57.295779513082320876798f;
+    // reflectance: linear interpolation of the material's 1-degree table (Eq. 4, Sec. III)
+    uint32_t m = (uint32_t)__float_as_int(b.w);
+    const uint32_t mrow = m < (uint32_t)T.n_mat ? m : (uint32_t)(T.n_mat - 1);
+    int i = (int)theta_deg;
+    if (i > LIDAR_TABLE_SIZE - 2) i = LIDAR_TABLE_SIZE - 2;
+    const float f = theta_deg - (float)i;
+    const float* row = T.table + (int64_t)mrow * LIDAR_TABLE_SIZE;
+    const float R0 = __ldg(&row[i]), R1 = __ldg(&row[i + 1]);
+    const float R = R0 * (1.0f - f) + R1 * f;
+    // range with Gaussian noise (Sec. II-A)
+    const float z = range_noise_normal(seed, beam, frame, sensor, sub);
+    const float d = h.t + sd.sigma * z;
+    // capability model (Eq. 5) and range limits
+    const float RLd = __fdiv_rn(__fmul_rn(sd.RL_max, d), sd.d_max);
+    const int valid = (d >= sd.r_min) && (d <= sd.r_max) && (d <= sd.d_max) && (RLd <= R);
+    const float rf = (sd.range_exp == 0.0f) ? 1.0f : powf(sd.r_ref / d, sd.range_exp);
+    out.t = h.t;
+    out.range = d;
+    out.intensity = sd.gain * R * rf;
+    out.theta_deg = theta_deg;
+    out.rf = rf;
+    out.nx = nx; out.ny = ny; out.nz = nz;
+    out.tri = h.idx;
+    out.inst = (uint32_t)__float_as_int(c.w);
+    out.mat = m;
+    out.valid = valid;
+}
+
+__device__ __forceinline__ int find_frame(const int64_t* __restrict__ prefix, int n_frames, int64_t tile)
+{
+    int lo = 0, hi = n_frames - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&prefix[mid]) <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(1024) k_cast(SceneDev S, const SensorDev* __restrict__ sensors,
+                                               const FrameDev* __restrict__ frames, int n_frames,
+                                               const int64_t* __restrict__ tile_prefix, int64_t n_tiles,
+                                               TableDev T, uint64_t seed, BeamsOut out, int* status,
+                                               unsigned long long* work_counter, int tile_rays, WorkCount wc)
+{
+    __shared__ int64_t s_tile;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(work_counter, 1ull);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= n_tiles) return;
+        const int fi = find_frame(tile_prefix, n_frames, tile);
+        const FrameDev& fr = frames[fi];
+        const SensorDev& sd = sensors[fr.sensor];
+        for (int j = threadIdx.x; j < tile_rays; j += blockDim.x) {
+            const int64_t pos = (tile - tile_prefix[fi]) * tile_rays + j;
+            if (pos >= sd.n_beams) break;
+            const uint32_t beam = sd.order ? __ldg(&sd.order[pos]) : (uint32_t)pos;
+            const float d0 = __ldg(&sd.dirs[3 * (int64_t)beam]);
+            const float d1 = __ldg(&sd.dirs[3 * (int64_t)beam + 1]);
+            const float d2 = __ldg(&sd.dirs[3 * (int64_t)beam + 2]);
+            const RayW beam_ray = world_ray(fr.pose, d0, d1, d2);
+            BeamResult best;
+            int best_sub = 0;
+            float best_I = -1.0f;
+            for (int k = 0; k < sd.n_sub; ++k) {
+                RayW r = beam_ray;
+                if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
+                const RayPre p = prepare_ray(r);
+                HitRec h;
+                if (!trace_closest<kCount>(S, p, sd.t_max, h, &wc)) raise_status(status, ST_STACK);
+                BeamResult res;
+                shade(S, h, r, sd, T, seed, beam, (uint32_t)fr.frame, (uint32_t)fr.sensor, (uint32_t)k, res);
+                if (k == 0) best = res;
+                if (res.valid && res.intensity > best_I) {
+                    best_I = res.intensity;
+                    best = res;
+                    best_sub = k;
+                }
+            }
+            const int64_t o = fr.beam_offset + beam;
+            if (out.valid) out.valid[o] = (uint8_t)best.valid;
+            if (out.tri) out.tri[o] = best.tri;
+            if (out.t) out.t[o] = best.t;
+            if (out.range) out.range[o] = best.range;
+            if (out.intensity) out.intensity[o] = best.intensity;
+            if (out.normal) {
+                // into the sensor frame: n_s = R^T n_w
+                const float* P = fr.pose;
+                out.normal[3 * o + 0] = P[0] * best.nx + P[4] * best.ny + P[8] * best.nz;
+                out.normal[3 * o + 1] = P[1] * best.nx + P[5] * best.ny + P[9] * best.nz;
+                out.normal[3 * o + 2] = P[2] * best.nx + P[6] * best.ny + P[10] * best.nz;
+            }
+            if (out.mat) out.mat[o] = (uint16_t)best.mat;
+            if (out.inst) out.inst[o] = best.inst;
+            if (out.sub) out.sub[o] = (uint8_t)best_sub;
+            if (out.theta_deg) out.theta_deg[o] = best.theta_deg;
+            if (out.rf) out.rf[o] = best.rf;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ compaction
+
+constexpr int kCompactThreads = 256;
+constexpr int kCompactItems = 16;
+constexpr int kCompactTile = kCompactThreads * kCompactItems;
+
+__global__ void __launch_bounds__(kCompactThreads) k_count_valid(const uint8_t* __restrict__ valid, int64_t n,
+                                                                 uint32_t* __restrict__ counts)
+{
+    const int64_t base = (int64_t)blockIdx.x * kCompactTile;
+    uint32_t c = 0;
+    for (int i = threadIdx.x; i < kCompactTile; i += kCompactThreads) {
+        int64_t idx = base + i;
+        if (idx < n) c += valid[idx] ? 1u : 0u;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    __shared__ uint32_t s[kCompactThreads / 32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kCompactThreads / 32; ++w) t += s[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of the tile counts (one block); writes the total
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t* __restrict__ counts, int64_t n,
+                                                     int64_t* __restrict__ offsets, int64_t* total)
+{
+    __shared__ int64_t s_sum[1024];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = (int64_t)threadIdx.x * per;
+    const int64_t hi = min(lo + per, n);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += counts[i];
+    s_sum[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int64_t v = (threadIdx.x >= (unsigned)off) ? s_sum[threadIdx.x - off] : 0;
+        __syncthreads();
+        s_sum[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = (threadIdx.x == 0) ? 0 : s_sum[threadIdx.x - 1];
+    for (int64_t i = lo; i < hi; ++i) {
+        offsets[i] = run;
+        run += counts[i];
+    }
+    if (threadIdx.x == blockDim.x - 1 && total) *total = s_sum[blockDim.x - 1];
+}
+
+__device__ __forceinline__ int frame_of_index(const FrameDev* __restrict__ frames, int n_frames, int64_t idx)
+{
+    int lo = 0, hi = n_frames - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (frames[mid].beam_offset <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kCompactThreads) k_scatter_points(
+    const SensorDev* __restrict__ sensors, const FrameDev* __restrict__ frames, int n_frames, int64_t n,
+    BeamsOut dense, const int64_t* __restrict__ tile_offsets, lidar_points pts, int* status)
+{
+    __shared__ uint32_t s_warp[kCompactThreads / 32];
+    __shared__ int64_t s_run;
+    const int64_t base = (int64_t)blockIdx.x * kCompactTile;
+    if (threadIdx.x == 0) s_run = tile_offsets[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int it = 0; it < kCompactItems; ++it) {
+        const int64_t idx = base + (int64_t)it * kCompactThreads + threadIdx.x;
+        const bool v = idx < n && dense.valid[idx];
+        const uint32_t bal = __ballot_sync(0xffffffffu, v);
+        if (lane == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < kCompactThreads / 32; ++w) {
+            const uint32_t c = s_warp[w];
+            if (w < warp) before += c;
+            total += c;
+        }
+        const int64_t pos = s_run + before + __popc(bal & ((1u << lane) - 1u));
+        if (v) {
+            if (pos < pts.capacity) {
+                const int fi = frame_of_index(frames, n_frames, idx);
+                const FrameDev& fr = frames[fi];
+                const uint32_t beam = (uint32_t)(idx - fr.beam_offset);
+                const float d = dense.range[idx];
+                if (pts.xyz) {
+                    const float* dir = sensors[fr.sensor].dirs + 3 * (int64_t)beam;
+                    pts.xyz[3 * pos + 0] = d * dir[0];
+                    pts.xyz[3 * pos + 1] = d * dir[1];
+                    pts.xyz[3 * pos + 2] = d * dir[2];
+                }
+                if (pts.range) pts.range[pos] = d;
+                if (pts.intensity) pts.intensity[pos] = dense.intensity[idx];
+                if (pts.normal) {
+                    pts.normal[3 * pos + 0] = dense.normal[3 * idx + 0];
+                    pts.normal[3 * pos + 1] = dense.normal[3 * idx + 1];
+                    pts.normal[3 * pos + 2] = dense.normal[3 * idx + 2];
+                }
+                if (pts.material) pts.material[pos] = dense.mat[idx];
+                if (pts.instance) pts.instance[pos] = dense.inst[idx];
+                if (pts.beam) pts.beam[pos] = beam;
+                if (pts.frame) pts.frame[pos] = (uint32_t)fi;
+            } else {
+                raise_status(status, ST_CAPACITY);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_run += total;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ ray order
+
+// Octahedral map of a unit direction to [0,1]^2 (Praun & Hoppe 2003), then a
+// 32-bit Morton code of the two 16-bit coordinates.
+__device__ __forceinline__ uint32_t spread2(uint32_t x)
+{
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+__global__ void k_dir_keys(const float* __restrict__ dirs, int n, uint32_t* keys, uint32_t* vals)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x = dirs[3 * i], y = dirs[3 * i + 1], z = dirs[3 * i + 2];
+    const float s = fabsf(x) + fabsf(y) + fabsf(z);
+    x /= s; y /= s; z /= s;
+    float u = x, v = y;
+    if (z < 0.0f) {
+        u = (1.0f - fabsf(y)) * (x >= 0.0f ? 1.0f : -1.0f);
+        v = (1.0f - fabsf(x)) * (y >= 0.0f ? 1.0f : -1.0f);
+    }
+    const uint32_t qu = (uint32_t)fminf(fmaxf((u * 0.5f + 0.5f) * 65535.0f, 0.0f), 65535.0f);
+    const uint32_t qv = (uint32_t)fminf(fmaxf((v * 0.5f + 0.5f) * 65535.0f, 0.0f), 65535.0f);
+    keys[i] = (spread2(qu) << 1) | spread2(qv);
+    vals[i] = (uint32_t)i;
+}
+
+}  // namespace
+
+cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* sensors_dev,
+                        const FrameDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
+                        int64_t n_tiles, TableDev table, uint64_t seed, BeamsOut out, int* status,
+                        unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
+                        const WorkCount* count)
+{
+    if (n_tiles == 0) return cudaSuccess;
+    cudaMemsetAsync(work_counter, 0, sizeof(unsigned long long), s);
+    int64_t grid = (int64_t)num_sms * cfg.blocks_per_sm;
+    if (grid > n_tiles) grid = n_tiles;
+    if (count) {
+        k_cast<true><<<(unsigned)grid, cfg.block_threads, 0, s>>>(scene, sensors_dev, frames_dev, n_frames,
+                                                                  tile_prefix_dev, n_tiles, table, seed, out,
+                                                                  status, work_counter, cfg.tile_rays, *count);
+    } else {
+        k_cast<false><<<(unsigned)grid, cfg.block_threads, 0, s>>>(scene, sensors_dev, frames_dev, n_frames,
+                                                                   tile_prefix_dev, n_tiles, table, seed, out,
+                                                                   status, work_counter, cfg.tile_rays,
+                                                                   WorkCount{nullptr, nullptr, nullptr});
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_popcount(const uint32_t* __restrict__ bits, int64_t n_words, unsigned long long* total)
+{
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_words; i += (int64_t)gridDim.x * blockDim.x)
+        c += __popc(bits[i]);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(total, c);
+}
+}  // namespace
+
+cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_words, unsigned long long* total)
+{
+    if (n_words == 0) return cudaSuccess;
+    k_popcount<<<256, 256, 0, s>>>(bits, n_words, total);
+    return cudaGetLastError();
+}
+
+size_t compact_scratch_bytes(int64_t n)
+{
+    const int64_t tiles = (n + kCompactTile - 1) / kCompactTile;
+    return ((tiles * sizeof(uint32_t) + 255) / 256) * 256 + ((tiles * sizeof(int64_t) + 255) / 256) * 256 + 256;
+}
+
+cudaError_t launch_compact(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev,
+                           int n_frames, int64_t n, const uint8_t* valid, BeamsOut dense,
+                           const lidar_points& pts, int64_t* n_points_dev, int* status, void* scratch,
+                           size_t scratch_bytes)
+{
+    if (scratch_bytes < compact_scratch_bytes(n)) return cudaErrorInvalidValue;
+    const int64_t tiles = (n + kCompactTile - 1) / kCompactTile;
+    if (tiles == 0) {
+        if (n_points_dev) cudaMemsetAsync(n_points_dev, 0, sizeof(int64_t), s);
+        return cudaGetLastError();
+    }
+    char* p = (char*)scratch;
+    uint32_t* counts = (uint32_t*)p;
+    p += ((tiles * sizeof(uint32_t) + 255) / 256) * 256;
+    int64_t* offsets = (int64_t*)p;
+    k_count_valid<<<(unsigned)tiles, kCompactThreads, 0, s>>>(valid, n, counts);
+    k_scan_tiles<<<1, 1024, 0, s>>>(counts, tiles, offsets, n_points_dev);
+    k_scatter_points<<<(unsigned)tiles, kCompactThreads, 0, s>>>(sensors_dev, frames_dev, n_frames, n, dense,
+                                                                 offsets, pts, status);
+    return cudaGetLastError();
+}
+
+size_t ray_order_scratch_bytes(int64_t n)
+{
+    return ((n * sizeof(uint32_t) + 255) / 256) * 256 + radix_sort_scratch_bytes(n);
+}
+
+cudaError_t launch_ray_order(cudaStream_t s, const float* dirs, int n, uint32_t* order, void* scratch,
+                             size_t scratch_bytes)
+{
+    if (n == 0) return cudaSuccess;
+    uint32_t* keys = (uint32_t*)scratch;
+    char* rest = (char*)scratch + ((n * sizeof(uint32_t) + 255) / 256) * 256;
+    k_dir_keys<<<(n + 255) / 256, 256, 0, s>>>(dirs, n, keys, order);
+    return radix_sort_pairs_u32(s, keys, order, n, 32, rest, scratch_bytes - (rest - (char*)scratch));
+}
+
+}  // namespace lidar

@@ -1,0 +1,160 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/lidar.h"
+
+namespace lidar {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+
+#define LIDAR_CHECK_ARG(cond, msg)              \
+    do {                                        \
+        if (!(cond)) {                          \
+            ::lidar::set_error(msg);            \
+            return LIDAR_EINVAL;                \
+        }                                       \
+    } while (0)
+
+#define LIDAR_CUDA(call)                                                                      \
+    do {                                                                                      \
+        cudaError_t _e = (call);                                                              \
+        if (_e != cudaSuccess) {                                                              \
+            ::lidar::set_error(std::string(#call) + ": " + cudaGetErrorString(_e));           \
+            return _e == cudaErrorMemoryAllocation ? LIDAR_ENOMEM : LIDAR_ECUDA;              \
+        }                                                                                     \
+    } while (0)
+
+// device status word codes (first error wins)
+enum : int { ST_OK = 0, ST_CAPACITY = 1, ST_STACK = 2, ST_TIMEOUT = 3, ST_INDEX = 4 };
+
+__device__ __forceinline__ void raise_status(int* status, int code)
+{
+    atomicCAS(status, ST_OK, code);
+}
+
+// ------------------------------------------------------------------ scene layout
+//
+// BVH node (64 bytes, four 16-byte loads): both children's boxes live in the
+// parent so one fetch decides both children.
+//   n0 = (L.lo.x, L.hi.x, L.lo.y, L.hi.y)
+//   n1 = (R.lo.x, R.hi.x, R.lo.y, R.hi.y)
+//   n2 = (L.lo.z, L.hi.z, R.lo.z, R.hi.z)
+//   n3 = (left, right, -, -) as int bits; child >= 0: internal node, child < 0:
+//        leaf ~child = position in the leaf-ordered triangle array.
+// Triangle (48 bytes, three 16-byte loads), leaf order:
+//   v0.xyz, w = original triangle index (bits)
+//   v1.xyz, w = material (bits)
+//   v2.xyz, w = instance (bits)
+constexpr int kTraversalStack = 64;
+
+struct SceneDev {
+    const float4* nodes;     // [n_nodes * 4]
+    const float4* tris;      // [n_tris * 3]
+    int64_t n_tris;
+    int64_t n_nodes;
+};
+
+// ------------------------------------------------------------------ sensors
+
+struct SensorDev {
+    const float* dirs;        // [n_beams][3], sensor frame
+    const uint32_t* order;    // ray order permutation [n_beams] (beam processed at position j)
+    int32_t n_beams;
+    int32_t n_sub;
+    float r_min, r_max, d_max, RL_max, sigma, gain, range_exp, r_ref;
+    float t_max;              // search range end: min(r_max, d_max) + 9 sigma
+    float alpha[LIDAR_MAX_SUBRAYS], beta[LIDAR_MAX_SUBRAYS];
+};
+
+struct FrameDev {
+    int32_t sensor;
+    int32_t frame;
+    int64_t beam_offset;      // first dense index of this frame
+    float pose[12];
+};
+
+struct TableDev {
+    const float* table;       // [n_mat][91]
+    int32_t n_mat;
+};
+
+struct BeamsOut {
+    uint8_t* valid;
+    uint32_t* tri;
+    float* t;
+    float* range;
+    float* intensity;
+    float* normal;
+    uint16_t* mat;
+    uint32_t* inst;
+    uint8_t* sub;
+    float* theta_deg;
+    float* rf;
+};
+
+struct LaunchCfg {
+    int block_threads;
+    int blocks_per_sm;
+    int tile_rays;
+    int ray_order;
+};
+
+// ------------------------------------------------------------------ kernel launchers
+
+// build.cu
+struct BuildScratch;
+cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, const uint32_t* tris,
+                       const uint16_t* mat, const uint32_t* inst, int64_t n_tris, float4* nodes_out,
+                       float4* tris_out, uint32_t* leaf_tri_out, int* status, int* max_depth_dev,
+                       void* scratch, size_t scratch_bytes);
+size_t build_scratch_bytes(int64_t n_tris);
+
+// sort.cu: stable LSD radix sort of (key, value) pairs, keys of `key_bits` bits
+size_t radix_sort_scratch_bytes(int64_t n);
+cudaError_t radix_sort_pairs_u64(cudaStream_t s, uint64_t* keys, uint32_t* vals, int64_t n, int key_bits,
+                                 void* scratch, size_t scratch_bytes);
+cudaError_t radix_sort_pairs_u32(cudaStream_t s, uint32_t* keys, uint32_t* vals, int64_t n, int key_bits,
+                                 void* scratch, size_t scratch_bytes);
+
+// cast.cu
+// Instrumentation of the traversal (work counted per launch, not timed).
+struct WorkCount {
+    unsigned long long* totals;   // [0] node visits, [1] triangle tests
+    uint32_t* node_bits;          // one bit per internal node touched
+    uint32_t* leaf_bits;          // one bit per triangle tested
+};
+cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* sensors_dev,
+                        const FrameDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
+                        int64_t n_tiles, TableDev table, uint64_t seed, BeamsOut out, int* status,
+                        unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
+                        const WorkCount* count = nullptr);
+cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_words, unsigned long long* total);
+cudaError_t launch_compact(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev,
+                           int n_frames, int64_t n_beams_total, const uint8_t* valid, BeamsOut dense,
+                           const lidar_points& pts, int64_t* n_points_dev, int* status, void* scratch,
+                           size_t scratch_bytes);
+size_t compact_scratch_bytes(int64_t n_beams_total);
+cudaError_t launch_ray_order(cudaStream_t s, const float* dirs, int n_beams, uint32_t* order,
+                             void* scratch, size_t scratch_bytes);
+size_t ray_order_scratch_bytes(int64_t n_beams);
+
+// adjoint.cu
+cudaError_t launch_build_tables(cudaStream_t s, const float* params, int M, float* table);
+cudaError_t launch_build_tables_backward(cudaStream_t s, const float* params, const float* grad_table, int M,
+                                         float* grad_params);
+cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid, const uint16_t* mat,
+                                 const float* theta_deg, const float* rf, TableDev table, float gain,
+                                 const float* grad_I, const float* target_I, const uint8_t* target_valid,
+                                 float* loss, float* grad_table, float* grad_gain, void* scratch,
+                                 size_t scratch_bytes);
+size_t backward_scratch_bytes(int M);
+
+}  // namespace lidar

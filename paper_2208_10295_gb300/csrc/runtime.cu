@@ -1,0 +1,673 @@
+// C ABI implementation: context, scenes, sensors, materials, cast and adjoint
+// entry points.  Host code validates arguments, owns device buffers and
+// enqueues the kernels of build.cu, cast.cu and adjoint.cu on the context
+// stream.
+#include <math.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lidar {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// Host-side allocation fault injection for tests: LIDAR_FAULT_ALLOC_AT=n makes
+// the n-th device allocation of the process (1-based) fail with ENOMEM.
+static std::mutex g_alloc_mu;
+static long g_alloc_count = 0;
+
+static cudaError_t dev_alloc(void** p, size_t bytes)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        ++g_alloc_count;
+        const char* f = getenv("LIDAR_FAULT_ALLOC_AT");
+        if (f && atol(f) == g_alloc_count) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    if (bytes == 0) bytes = 16;
+    return cudaMalloc(p, bytes);
+}
+
+struct SensorSlot {
+    bool set = false;
+    int64_t n_beams = 0;
+    float* dirs_dev = nullptr;
+    uint32_t* order_dev = nullptr;
+    SensorDev dev{};
+};
+
+}  // namespace lidar
+
+using namespace lidar;
+
+struct lidar_scene {
+    lidar_ctx* ctx = nullptr;
+    float4* nodes = nullptr;
+    float4* tris = nullptr;
+    uint32_t* leaf_tri = nullptr;
+    int64_t n_tris = 0;
+    int64_t n_nodes = 0;
+    int max_depth = 0;
+    double build_ms = 0.0;
+    int64_t bytes = 0;
+};
+
+struct lidar_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int* status_dev = nullptr;
+    unsigned long long* work_counter = nullptr;
+    int* aux_dev = nullptr;  // scratch ints (build height)
+    SensorSlot slots[LIDAR_MAX_SENSORS];
+    SensorDev* sensors_dev = nullptr;
+    TableDev table{nullptr, 0};
+    FrameDev* frames_dev = nullptr;
+    int64_t* tile_prefix_dev = nullptr;
+    size_t frames_cap = 0;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    LaunchCfg cfg{128, 8, 128, 1};
+    std::set<lidar_scene*> scenes;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+lidar_status ensure_scratch(lidar_ctx* c, size_t bytes)
+{
+    if (c->scratch_bytes >= bytes) return LIDAR_OK;
+    if (c->scratch) {
+        LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+        cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    size_t want = bytes + bytes / 4;
+    LIDAR_CUDA(dev_alloc(&c->scratch, want));
+    c->scratch_bytes = want;
+    return LIDAR_OK;
+}
+
+lidar_status upload_sensor_slot(lidar_ctx* c, int slot)
+{
+    SensorDev d = c->slots[slot].dev;
+    if (c->cfg.ray_order == 0) d.order = nullptr;
+    LIDAR_CUDA(cudaMemcpyAsync(c->sensors_dev + slot, &d, sizeof(SensorDev), cudaMemcpyHostToDevice, c->stream));
+    LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    return LIDAR_OK;
+}
+
+lidar_status status_from_word(int w)
+{
+    switch (w) {
+    case ST_OK: return LIDAR_OK;
+    case ST_CAPACITY: set_error("point output capacity exceeded"); return LIDAR_ECAPACITY;
+    case ST_STACK: set_error("BVH traversal stack overflow"); return LIDAR_ESTACK;
+    case ST_TIMEOUT: set_error("a bounded device wait timed out"); return LIDAR_ETIMEOUT;
+    case ST_INDEX: set_error("triangle vertex index out of range"); return LIDAR_EINVAL;
+    default: set_error("unknown device status"); return LIDAR_ECUDA;
+    }
+}
+
+BeamsOut to_beams_out(const lidar_beams* b)
+{
+    BeamsOut o{};
+    if (!b) return o;
+    o.valid = b->valid; o.tri = b->tri; o.t = b->t; o.range = b->range; o.intensity = b->intensity;
+    o.normal = b->normal; o.mat = b->mat; o.inst = b->inst; o.sub = b->sub; o.theta_deg = b->theta_deg;
+    o.rf = b->rf;
+    return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lidar_last_error(void) { return g_last_error.c_str(); }
+
+lidar_status lidar_create(int device, void* cuda_stream, lidar_ctx** out)
+{
+    LIDAR_CHECK_ARG(out != nullptr, "lidar_create: out is NULL");
+    *out = nullptr;
+    int n_dev = 0;
+    LIDAR_CUDA(cudaGetDeviceCount(&n_dev));
+    LIDAR_CHECK_ARG(device >= 0 && device < n_dev, "lidar_create: no such device");
+    DeviceGuard g(device);
+    lidar_ctx* c = new lidar_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    void* p = nullptr;
+    cudaError_t e = dev_alloc(&p, 256);
+    if (e != cudaSuccess) {
+        delete c;
+        set_error("lidar_create: device allocation failed");
+        return LIDAR_ENOMEM;
+    }
+    c->status_dev = (int*)p;
+    c->work_counter = (unsigned long long*)((char*)p + 64);
+    c->aux_dev = (int*)((char*)p + 128);
+    e = dev_alloc((void**)&c->sensors_dev, sizeof(SensorDev) * LIDAR_MAX_SENSORS);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        delete c;
+        set_error("lidar_create: device allocation failed");
+        return LIDAR_ENOMEM;
+    }
+    cudaMemsetAsync(p, 0, 256, c->stream);
+    cudaMemsetAsync(c->sensors_dev, 0, sizeof(SensorDev) * LIDAR_MAX_SENSORS, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaFree(p);
+        cudaFree(c->sensors_dev);
+        delete c;
+        set_error("lidar_create: stream synchronisation failed");
+        return LIDAR_ECUDA;
+    }
+    *out = c;
+    return LIDAR_OK;
+}
+
+void lidar_scene_free(lidar_scene* s)
+{
+    if (!s) return;
+    DeviceGuard g(s->ctx->device);
+    cudaStreamSynchronize(s->ctx->stream);
+    cudaFree(s->nodes);
+    cudaFree(s->tris);
+    cudaFree(s->leaf_tri);
+    s->ctx->scenes.erase(s);
+    delete s;
+}
+
+void lidar_destroy(lidar_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    std::set<lidar_scene*> sc = c->scenes;
+    for (lidar_scene* s : sc) lidar_scene_free(s);
+    for (auto& sl : c->slots) {
+        cudaFree(sl.dirs_dev);
+        cudaFree(sl.order_dev);
+    }
+    cudaFree(c->sensors_dev);
+    cudaFree(c->frames_dev);
+    cudaFree(c->tile_prefix_dev);
+    cudaFree(c->scratch);
+    cudaFree(c->status_dev);
+    delete c;
+}
+
+lidar_status lidar_sync_status(lidar_ctx* c)
+{
+    LIDAR_CHECK_ARG(c != nullptr, "lidar_sync_status: ctx is NULL");
+    DeviceGuard g(c->device);
+    LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    int w = 0;
+    LIDAR_CUDA(cudaMemcpy(&w, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    LIDAR_CUDA(cudaMemset(c->status_dev, 0, sizeof(int)));
+    return status_from_word(w);
+}
+
+lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts, const uint32_t* tris,
+                               int64_t n_tris, const uint16_t* mat, const uint32_t* inst, lidar_scene** out)
+{
+    LIDAR_CHECK_ARG(c != nullptr && out != nullptr, "lidar_scene_build: ctx/out is NULL");
+    *out = nullptr;
+    LIDAR_CHECK_ARG(n_tris >= 0 && n_verts >= 0, "lidar_scene_build: negative size");
+    LIDAR_CHECK_ARG(n_tris < (int64_t)1 << 31, "lidar_scene_build: more than 2^31 - 1 triangles");
+    LIDAR_CHECK_ARG(n_tris == 0 || (verts && tris && n_verts > 0),
+                    "lidar_scene_build: verts/tris must be non-NULL for a non-empty mesh");
+    DeviceGuard g(c->device);
+    lidar_scene* s = new lidar_scene();
+    s->ctx = c;
+    s->n_tris = n_tris;
+    s->n_nodes = n_tris == 0 ? 0 : (n_tris == 1 ? 1 : n_tris - 1);
+    auto fail = [&](lidar_status st) {
+        cudaFree(s->nodes);
+        cudaFree(s->tris);
+        cudaFree(s->leaf_tri);
+        delete s;
+        return st;
+    };
+    if (n_tris > 0) {
+        if (dev_alloc((void**)&s->nodes, (size_t)s->n_nodes * 4 * sizeof(float4)) != cudaSuccess ||
+            dev_alloc((void**)&s->tris, (size_t)n_tris * 3 * sizeof(float4)) != cudaSuccess ||
+            dev_alloc((void**)&s->leaf_tri, (size_t)n_tris * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("lidar_scene_build: device allocation failed");
+            return fail(LIDAR_ENOMEM);
+        }
+        s->bytes = s->n_nodes * 64 + n_tris * 48 + n_tris * 4;
+        lidar_status st = ensure_scratch(c, build_scratch_bytes(n_tris));
+        if (st != LIDAR_OK) return fail(st);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, c->stream);
+        cudaError_t e = build_lbvh(c->stream, verts, n_verts, tris, mat, inst, n_tris, s->nodes, s->tris,
+                                   s->leaf_tri, c->status_dev, c->aux_dev, c->scratch, c->scratch_bytes);
+        cudaEventRecord(e1, c->stream);
+        if (e != cudaSuccess) {
+            set_error(std::string("lidar_scene_build: ") + cudaGetErrorString(e));
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(LIDAR_ECUDA);
+        }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            set_error("lidar_scene_build: stream synchronisation failed");
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(LIDAR_ECUDA);
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        s->build_ms = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        int w = 0, h = 0;
+        cudaMemcpy(&w, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&h, c->aux_dev, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaMemset(c->status_dev, 0, sizeof(int));
+        s->max_depth = h;
+        if (w != ST_OK) return fail(status_from_word(w));
+        if (h > kTraversalStack) {
+            set_error("lidar_scene_build: BVH height " + std::to_string(h) + " exceeds the traversal stack (" +
+                      std::to_string(kTraversalStack) + ")");
+            return fail(LIDAR_ESTACK);
+        }
+    }
+    c->scenes.insert(s);
+    *out = s;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_get_scene_info(const lidar_scene* s, lidar_scene_info* out)
+{
+    LIDAR_CHECK_ARG(s != nullptr && out != nullptr, "lidar_get_scene_info: NULL argument");
+    out->n_tris = s->n_tris;
+    out->n_nodes = s->n_nodes;
+    out->max_depth = s->max_depth;
+    out->device_bytes = s->bytes;
+    out->build_ms = s->build_ms;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_scene_export(const lidar_scene* s, float* nodes_host, uint32_t* leaf_tri_host)
+{
+    LIDAR_CHECK_ARG(s != nullptr, "lidar_scene_export: scene is NULL");
+    DeviceGuard g(s->ctx->device);
+    LIDAR_CUDA(cudaStreamSynchronize(s->ctx->stream));
+    if (nodes_host && s->n_nodes)
+        LIDAR_CUDA(cudaMemcpy(nodes_host, s->nodes, (size_t)s->n_nodes * 64, cudaMemcpyDeviceToHost));
+    if (leaf_tri_host && s->n_tris)
+        LIDAR_CUDA(cudaMemcpy(leaf_tri_host, s->leaf_tri, (size_t)s->n_tris * 4, cudaMemcpyDeviceToHost));
+    return LIDAR_OK;
+}
+
+lidar_status lidar_set_sensor(lidar_ctx* c, int32_t slot, const lidar_sensor_desc* d)
+{
+    LIDAR_CHECK_ARG(c != nullptr && d != nullptr, "lidar_set_sensor: NULL argument");
+    LIDAR_CHECK_ARG(slot >= 0 && slot < LIDAR_MAX_SENSORS, "lidar_set_sensor: slot out of range");
+    LIDAR_CHECK_ARG(d->n_beams > 0 && d->n_beams < (int64_t)1 << 31, "lidar_set_sensor: n_beams out of range");
+    LIDAR_CHECK_ARG(d->az_rad && d->el_rad, "lidar_set_sensor: az_rad/el_rad are NULL");
+    LIDAR_CHECK_ARG(d->n_subrays >= 1 && d->n_subrays <= LIDAR_MAX_SUBRAYS, "lidar_set_sensor: n_subrays out of range");
+    LIDAR_CHECK_ARG(d->r_min >= 0.0f && d->r_max > d->r_min, "lidar_set_sensor: need 0 <= r_min < r_max");
+    LIDAR_CHECK_ARG(d->d_max > 0.0f && d->RL_max >= 0.0f, "lidar_set_sensor: need d_max > 0, RL_max >= 0");
+    LIDAR_CHECK_ARG(d->sigma >= 0.0f && isfinite(d->sigma), "lidar_set_sensor: sigma must be finite, >= 0");
+    LIDAR_CHECK_ARG(d->divergence_rad >= 0.0f && d->divergence_rad < 0.1f, "lidar_set_sensor: divergence out of range");
+    DeviceGuard g(c->device);
+    const int64_t n = d->n_beams;
+    // FP32 unit directions from the FP64 spherical coordinates
+    std::vector<float> dirs((size_t)n * 3);
+    for (int64_t b = 0; b < n; ++b) {
+        const double ce = cos(d->el_rad[b]);
+        dirs[3 * b + 0] = (float)(ce * cos(d->az_rad[b]));
+        dirs[3 * b + 1] = (float)(ce * sin(d->az_rad[b]));
+        dirs[3 * b + 2] = (float)sin(d->el_rad[b]);
+    }
+    SensorSlot& sl = c->slots[slot];
+    if (sl.set) {
+        LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+        cudaFree(sl.dirs_dev);
+        cudaFree(sl.order_dev);
+        sl = SensorSlot();
+    }
+    if (dev_alloc((void**)&sl.dirs_dev, n * 3 * sizeof(float)) != cudaSuccess ||
+        dev_alloc((void**)&sl.order_dev, n * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(sl.dirs_dev);
+        sl = SensorSlot();
+        set_error("lidar_set_sensor: device allocation failed");
+        return LIDAR_ENOMEM;
+    }
+    LIDAR_CUDA(cudaMemcpyAsync(sl.dirs_dev, dirs.data(), n * 3 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    lidar_status st = ensure_scratch(c, ray_order_scratch_bytes(n));
+    if (st != LIDAR_OK) return st;
+    LIDAR_CUDA(launch_ray_order(c->stream, sl.dirs_dev, (int)n, sl.order_dev, c->scratch, c->scratch_bytes));
+    SensorDev& sd = sl.dev;
+    sd.dirs = sl.dirs_dev;
+    sd.order = sl.order_dev;
+    sd.n_beams = (int32_t)n;
+    sd.n_sub = d->n_subrays;
+    sd.r_min = d->r_min; sd.r_max = d->r_max; sd.d_max = d->d_max; sd.RL_max = d->RL_max;
+    sd.sigma = d->sigma; sd.gain = d->gain; sd.range_exp = d->range_exp; sd.r_ref = d->r_ref;
+    sd.t_max = fminf(d->r_max, d->d_max) + 9.0f * d->sigma;
+    // sub-ray offsets: ray 0 is the beam, rays 1..n-1 on the cone of half-angle divergence/2
+    const double rad = tan(0.5 * (double)d->divergence_rad);
+    for (int k = 0; k < LIDAR_MAX_SUBRAYS; ++k) {
+        sd.alpha[k] = 0.0f;
+        sd.beta[k] = 0.0f;
+    }
+    for (int k = 1; k < d->n_subrays; ++k) {
+        const double a = 2.0 * M_PI * (double)(k - 1) / (double)(d->n_subrays - 1);
+        sd.alpha[k] = (float)(rad * cos(a));
+        sd.beta[k] = (float)(rad * sin(a));
+    }
+    sl.n_beams = n;
+    sl.set = true;
+    return upload_sensor_slot(c, slot);
+}
+
+lidar_status lidar_set_sensor_gain(lidar_ctx* c, int32_t slot, float gain)
+{
+    LIDAR_CHECK_ARG(c != nullptr, "lidar_set_sensor_gain: ctx is NULL");
+    LIDAR_CHECK_ARG(slot >= 0 && slot < LIDAR_MAX_SENSORS, "lidar_set_sensor_gain: slot out of range");
+    LIDAR_CHECK_ARG(isfinite(gain), "lidar_set_sensor_gain: gain must be finite");
+    if (!c->slots[slot].set) {
+        set_error("lidar_set_sensor_gain: no sensor in this slot");
+        return LIDAR_ESTATE;
+    }
+    DeviceGuard g(c->device);
+    c->slots[slot].dev.gain = gain;
+    return upload_sensor_slot(c, slot);
+}
+
+lidar_status lidar_get_beam_dirs(lidar_ctx* c, int32_t slot, float* host_out)
+{
+    LIDAR_CHECK_ARG(c != nullptr && host_out != nullptr, "lidar_get_beam_dirs: NULL argument");
+    LIDAR_CHECK_ARG(slot >= 0 && slot < LIDAR_MAX_SENSORS, "lidar_get_beam_dirs: slot out of range");
+    if (!c->slots[slot].set) {
+        set_error("lidar_get_beam_dirs: no sensor in this slot");
+        return LIDAR_ESTATE;
+    }
+    DeviceGuard g(c->device);
+    LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    LIDAR_CUDA(cudaMemcpy(host_out, c->slots[slot].dirs_dev, c->slots[slot].n_beams * 3 * sizeof(float),
+                          cudaMemcpyDeviceToHost));
+    return LIDAR_OK;
+}
+
+lidar_status lidar_build_tables(lidar_ctx* c, const float* params, int32_t M, float* table)
+{
+    LIDAR_CHECK_ARG(c != nullptr, "lidar_build_tables: ctx is NULL");
+    LIDAR_CHECK_ARG(M >= 0 && (M == 0 || (params && table)), "lidar_build_tables: bad arguments");
+    DeviceGuard g(c->device);
+    LIDAR_CUDA(launch_build_tables(c->stream, params, M, table));
+    return LIDAR_OK;
+}
+
+lidar_status lidar_build_tables_backward(lidar_ctx* c, const float* params, const float* grad_table, int32_t M,
+                                         float* grad_params)
+{
+    LIDAR_CHECK_ARG(c != nullptr, "lidar_build_tables_backward: ctx is NULL");
+    LIDAR_CHECK_ARG(M >= 0 && (M == 0 || (params && grad_table && grad_params)),
+                    "lidar_build_tables_backward: bad arguments");
+    DeviceGuard g(c->device);
+    LIDAR_CUDA(launch_build_tables_backward(c->stream, params, grad_table, M, grad_params));
+    return LIDAR_OK;
+}
+
+lidar_status lidar_set_materials(lidar_ctx* c, const float* table, int32_t M)
+{
+    LIDAR_CHECK_ARG(c != nullptr, "lidar_set_materials: ctx is NULL");
+    LIDAR_CHECK_ARG(table != nullptr && M > 0 && M <= 65536, "lidar_set_materials: need a table with 1..65536 rows");
+    c->table.table = table;
+    c->table.n_mat = M;
+    return LIDAR_OK;
+}
+
+// shared front half of the cast entry points
+static lidar_status prepare_frames(lidar_ctx* c, const lidar_frame* frames, int32_t n_frames, int64_t* n_beams_total,
+                                   int64_t* n_tiles)
+{
+    LIDAR_CHECK_ARG(frames != nullptr && n_frames > 0, "lidar_cast: need at least one frame");
+    std::vector<FrameDev> fd((size_t)n_frames);
+    std::vector<int64_t> prefix((size_t)n_frames);
+    int64_t off = 0, tiles = 0;
+    const int tr = c->cfg.tile_rays;
+    for (int32_t k = 0; k < n_frames; ++k) {
+        const int s = frames[k].sensor;
+        if (s < 0 || s >= LIDAR_MAX_SENSORS || !c->slots[s].set) {
+            set_error("lidar_cast: frame " + std::to_string(k) + " names an empty sensor slot");
+            return LIDAR_ESTATE;
+        }
+        for (int j = 0; j < 12; ++j)
+            LIDAR_CHECK_ARG(isfinite(frames[k].pose[j]), "lidar_cast: non-finite pose");
+        fd[k].sensor = s;
+        fd[k].frame = frames[k].frame;
+        fd[k].beam_offset = off;
+        memcpy(fd[k].pose, frames[k].pose, sizeof(fd[k].pose));
+        prefix[k] = tiles;
+        off += c->slots[s].n_beams;
+        tiles += (c->slots[s].n_beams + tr - 1) / tr;
+    }
+    if ((size_t)n_frames > c->frames_cap) {
+        LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+        cudaFree(c->frames_dev);
+        cudaFree(c->tile_prefix_dev);
+        c->frames_dev = nullptr;
+        c->tile_prefix_dev = nullptr;
+        c->frames_cap = 0;
+        if (dev_alloc((void**)&c->frames_dev, n_frames * sizeof(FrameDev)) != cudaSuccess ||
+            dev_alloc((void**)&c->tile_prefix_dev, n_frames * sizeof(int64_t)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("lidar_cast: device allocation failed");
+            return LIDAR_ENOMEM;
+        }
+        c->frames_cap = n_frames;
+    }
+    // pageable source: the copy is staged before the call returns
+    LIDAR_CUDA(cudaMemcpyAsync(c->frames_dev, fd.data(), n_frames * sizeof(FrameDev), cudaMemcpyHostToDevice,
+                               c->stream));
+    LIDAR_CUDA(cudaMemcpyAsync(c->tile_prefix_dev, prefix.data(), n_frames * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, c->stream));
+    *n_beams_total = off;
+    *n_tiles = tiles;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
+                        uint64_t seed, const lidar_beams* beams, const lidar_points* points, int64_t* n_points_dev)
+{
+    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr, "lidar_cast: ctx/scene is NULL");
+    LIDAR_CHECK_ARG(scene->ctx == c, "lidar_cast: scene belongs to another context");
+    if (c->table.table == nullptr) {
+        set_error("lidar_cast: no material table (lidar_set_materials)");
+        return LIDAR_ESTATE;
+    }
+    LIDAR_CHECK_ARG(beams != nullptr || points != nullptr, "lidar_cast: nothing to write (beams and points NULL)");
+    LIDAR_CHECK_ARG(points == nullptr || points->capacity >= 0, "lidar_cast: negative capacity");
+    DeviceGuard g(c->device);
+    int64_t n_total = 0, n_tiles = 0;
+    lidar_status st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles);
+    if (st != LIDAR_OK) return st;
+    BeamsOut out = to_beams_out(beams);
+    // compaction reads the dense records: provide the ones the points need
+    std::vector<void*> tmp;
+    char* dense_base = nullptr;
+    size_t dense_bytes = 0;
+    if (points) {
+        const bool need_valid = out.valid == nullptr, need_range = out.range == nullptr;
+        const bool need_int = out.intensity == nullptr, need_norm = points->normal && out.normal == nullptr;
+        const bool need_mat = points->material && out.mat == nullptr, need_inst = points->instance && out.inst == nullptr;
+        auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+        dense_bytes = (need_valid ? al(n_total) : 0) + (need_range ? al(4 * n_total) : 0) +
+                      (need_int ? al(4 * n_total) : 0) + (need_norm ? al(12 * n_total) : 0) +
+                      (need_mat ? al(2 * n_total) : 0) + (need_inst ? al(4 * n_total) : 0);
+        size_t comp = compact_scratch_bytes(n_total);
+        st = ensure_scratch(c, dense_bytes + comp);
+        if (st != LIDAR_OK) return st;
+        char* p = (char*)c->scratch;
+        dense_base = p;
+        if (need_valid) { out.valid = (uint8_t*)p; p += al(n_total); }
+        if (need_range) { out.range = (float*)p; p += al(4 * n_total); }
+        if (need_int) { out.intensity = (float*)p; p += al(4 * n_total); }
+        if (need_norm) { out.normal = (float*)p; p += al(12 * n_total); }
+        if (need_mat) { out.mat = (uint16_t*)p; p += al(2 * n_total); }
+        if (need_inst) { out.inst = (uint32_t*)p; p += al(4 * n_total); }
+    }
+    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes};
+    LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, c->frames_dev, n_frames, c->tile_prefix_dev, n_tiles,
+                           c->table, seed, out, c->status_dev, c->work_counter, c->cfg, c->num_sms));
+    if (points) {
+        char* comp = dense_base + dense_bytes;
+        LIDAR_CUDA(launch_compact(c->stream, c->sensors_dev, c->frames_dev, n_frames, n_total, out.valid, out,
+                                  *points, n_points_dev, c->status_dev, comp,
+                                  c->scratch_bytes - dense_bytes));
+    }
+    return LIDAR_OK;
+}
+
+static lidar_status backward_common(lidar_ctx* c, int64_t n, const lidar_beams* tape, float gain,
+                                    const float* grad_I, const float* target_I, const uint8_t* target_valid,
+                                    float* loss, float* grad_table, float* grad_gain)
+{
+    LIDAR_CHECK_ARG(c != nullptr && tape != nullptr, "lidar_cast_backward: ctx/tape is NULL");
+    LIDAR_CHECK_ARG(n >= 0, "lidar_cast_backward: negative beam count");
+    LIDAR_CHECK_ARG(n == 0 || (tape->valid && tape->mat && tape->theta_deg && tape->rf),
+                    "lidar_cast_backward: tape needs valid, mat, theta_deg and rf");
+    if (c->table.table == nullptr) {
+        set_error("lidar_cast_backward: no material table (lidar_set_materials)");
+        return LIDAR_ESTATE;
+    }
+    DeviceGuard g(c->device);
+    lidar_status st = ensure_scratch(c, backward_scratch_bytes(c->table.n_mat));
+    if (st != LIDAR_OK) return st;
+    LIDAR_CUDA(launch_cast_backward(c->stream, n, tape->valid, tape->mat, tape->theta_deg, tape->rf, c->table, gain,
+                                    grad_I, target_I, target_valid, loss, grad_table, grad_gain, c->scratch,
+                                    c->scratch_bytes));
+    return LIDAR_OK;
+}
+
+lidar_status lidar_cast_backward(lidar_ctx* c, int64_t n, const lidar_beams* tape, float gain, const float* grad_I,
+                                 float* grad_table, float* grad_gain)
+{
+    LIDAR_CHECK_ARG(n == 0 || grad_I != nullptr, "lidar_cast_backward: grad_I is NULL");
+    return backward_common(c, n, tape, gain, grad_I, nullptr, nullptr, nullptr, grad_table, grad_gain);
+}
+
+lidar_status lidar_cast_backward_mse(lidar_ctx* c, int64_t n, const lidar_beams* tape, float gain,
+                                     const float* target_I, const uint8_t* target_valid, float* loss,
+                                     float* grad_table, float* grad_gain)
+{
+    LIDAR_CHECK_ARG(n == 0 || (target_I != nullptr && target_valid != nullptr),
+                    "lidar_cast_backward_mse: targets are NULL");
+    return backward_common(c, n, tape, gain, nullptr, target_I, target_valid, loss, grad_table, grad_gain);
+}
+
+lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
+                              uint64_t seed, lidar_work_counts* out)
+{
+    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr && out != nullptr, "lidar_count_work: NULL argument");
+    LIDAR_CHECK_ARG(scene->ctx == c, "lidar_count_work: scene belongs to another context");
+    if (c->table.table == nullptr) {
+        set_error("lidar_count_work: no material table (lidar_set_materials)");
+        return LIDAR_ESTATE;
+    }
+    DeviceGuard g(c->device);
+    int64_t n_total = 0, n_tiles = 0;
+    lidar_status st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles);
+    if (st != LIDAR_OK) return st;
+    const int64_t node_words = (scene->n_nodes + 31) / 32 + 1, leaf_words = (scene->n_tris + 31) / 32 + 1;
+    const size_t bytes = 64 + (node_words + leaf_words) * 4 + ((n_total + 255) / 256) * 256;
+    st = ensure_scratch(c, bytes);
+    if (st != LIDAR_OK) return st;
+    char* p = (char*)c->scratch;
+    unsigned long long* totals = (unsigned long long*)p;
+    uint32_t* node_bits = (uint32_t*)(p + 64);
+    uint32_t* leaf_bits = node_bits + node_words;
+    uint8_t* valid = (uint8_t*)(leaf_bits + leaf_words);
+    LIDAR_CUDA(cudaMemsetAsync(p, 0, 64 + (node_words + leaf_words) * 4, c->stream));
+    WorkCount wc{totals, node_bits, leaf_bits};
+    BeamsOut dense{};
+    dense.valid = valid;
+    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes};
+    LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, c->frames_dev, n_frames, c->tile_prefix_dev, n_tiles,
+                           c->table, seed, dense, c->status_dev, c->work_counter, c->cfg, c->num_sms, &wc));
+    LIDAR_CUDA(launch_popcount(c->stream, node_bits, node_words, totals + 2));
+    LIDAR_CUDA(launch_popcount(c->stream, leaf_bits, leaf_words, totals + 3));
+    unsigned long long h[4];
+    LIDAR_CUDA(cudaMemcpyAsync(h, totals, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    uint64_t rays = 0;
+    for (int32_t k = 0; k < n_frames; ++k) {
+        const SensorSlot& sl = c->slots[frames[k].sensor];
+        rays += (uint64_t)sl.n_beams * (uint64_t)sl.dev.n_sub;
+    }
+    out->rays = rays;
+    out->node_visits = h[0];
+    out->tri_tests = h[1];
+    out->unique_nodes = h[2];
+    out->unique_tris = h[3];
+    return LIDAR_OK;
+}
+
+lidar_status lidar_get_launch_config(lidar_ctx* c, lidar_launch_config* out)
+{
+    LIDAR_CHECK_ARG(c != nullptr && out != nullptr, "lidar_get_launch_config: NULL argument");
+    out->block_threads = c->cfg.block_threads;
+    out->blocks_per_sm = c->cfg.blocks_per_sm;
+    out->tile_rays = c->cfg.tile_rays;
+    out->ray_order = c->cfg.ray_order;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_set_launch_config(lidar_ctx* c, const lidar_launch_config* cfg)
+{
+    LIDAR_CHECK_ARG(c != nullptr && cfg != nullptr, "lidar_set_launch_config: NULL argument");
+    LIDAR_CHECK_ARG(cfg->block_threads >= 32 && cfg->block_threads <= 1024 && cfg->block_threads % 32 == 0,
+                    "lidar_set_launch_config: block_threads must be a multiple of 32 in [32, 1024]");
+    LIDAR_CHECK_ARG(cfg->blocks_per_sm >= 1 && cfg->blocks_per_sm <= 64, "lidar_set_launch_config: blocks_per_sm in [1, 64]");
+    LIDAR_CHECK_ARG(cfg->tile_rays >= 1 && cfg->tile_rays <= (1 << 20), "lidar_set_launch_config: tile_rays in [1, 2^20]");
+    LIDAR_CHECK_ARG(cfg->ray_order == 0 || cfg->ray_order == 1, "lidar_set_launch_config: ray_order is 0 or 1");
+    DeviceGuard g(c->device);
+    c->cfg.block_threads = cfg->block_threads;
+    c->cfg.blocks_per_sm = cfg->blocks_per_sm;
+    c->cfg.tile_rays = cfg->tile_rays;
+    c->cfg.ray_order = cfg->ray_order;
+    for (int s = 0; s < LIDAR_MAX_SENSORS; ++s)
+        if (c->slots[s].set) {
+            lidar_status st = upload_sensor_slot(c, s);
+            if (st != LIDAR_OK) return st;
+        }
+    return LIDAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,252 @@
+// Device-side ray geometry: world ray, sub-rays, robust box test, watertight
+// triangle test and closest-hit BVH traversal.  Shared by the cast kernel and
+// the brute-force debug kernel so both use bit-identical arithmetic.
+#pragma once
+#include "common.cuh"
+
+namespace lidar {
+
+constexpr float kTEps = 1e-4f;
+// Conservative slab test (Ize, "Robust BVH Ray Traversal", JCGT 2013): the far
+// slab distance is scaled by 1 + 2 gamma_3, gamma_3 = 3u / (1 - 3u), u = 2^-24;
+// rounded up here to 1 + 2^-21.
+constexpr float kFarScale = 1.0f + 4.76837158203125e-07f;
+// pruning against the current closest hit keeps a slightly wider margin
+constexpr float kBestScale = 1.0f + 9.5367431640625e-07f;
+
+struct RayW {
+    float ox, oy, oz;
+    float dx, dy, dz;
+};
+
+// World ray: o = pose translation, d_w[r] = fma(R[r][2], d2, fma(R[r][1], d1, R[r][0] * d0)).
+__device__ __forceinline__ RayW world_ray(const float* pose, float d0, float d1, float d2)
+{
+    RayW r;
+    r.dx = __fmaf_rn(pose[2], d2, __fmaf_rn(pose[1], d1, __fmul_rn(pose[0], d0)));
+    r.dy = __fmaf_rn(pose[6], d2, __fmaf_rn(pose[5], d1, __fmul_rn(pose[4], d0)));
+    r.dz = __fmaf_rn(pose[10], d2, __fmaf_rn(pose[9], d1, __fmul_rn(pose[8], d0)));
+    r.ox = pose[3];
+    r.oy = pose[7];
+    r.oz = pose[11];
+    return r;
+}
+
+// Sub-ray k of a beam: k = 0 is the beam; otherwise, with u = (d x z)/|d x z|
+// (d x x when |d x z| < 1e-3), v = d x u: w = (d + alpha u) + beta v,
+// direction w / |w|.  Every operation is rounded as written (no contraction).
+__device__ __forceinline__ void subray_dir(float& dx, float& dy, float& dz, float alpha, float beta)
+{
+    const float n2 = __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dx, dx));
+    float c0, c1, c2;
+    if (__fsqrt_rn(n2) >= 1e-3f) {
+        c0 = dy; c1 = -dx; c2 = 0.0f;
+    } else {
+        c0 = 0.0f; c1 = dz; c2 = -dy;
+    }
+    const float cc = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
+    const float s = __fsqrt_rn(cc);
+    const float u0 = __fdiv_rn(c0, s), u1 = __fdiv_rn(c1, s), u2 = __fdiv_rn(c2, s);
+    const float v0 = __fsub_rn(__fmul_rn(dy, u2), __fmul_rn(dz, u1));
+    const float v1 = __fsub_rn(__fmul_rn(dz, u0), __fmul_rn(dx, u2));
+    const float v2 = __fsub_rn(__fmul_rn(dx, u1), __fmul_rn(dy, u0));
+    const float w0 = __fadd_rn(__fadd_rn(dx, __fmul_rn(alpha, u0)), __fmul_rn(beta, v0));
+    const float w1 = __fadd_rn(__fadd_rn(dy, __fmul_rn(alpha, u1)), __fmul_rn(beta, v1));
+    const float w2 = __fadd_rn(__fadd_rn(dz, __fmul_rn(alpha, u2)), __fmul_rn(beta, v2));
+    const float ww = __fadd_rn(__fadd_rn(__fmul_rn(w0, w0), __fmul_rn(w1, w1)), __fmul_rn(w2, w2));
+    const float sw = __fsqrt_rn(ww);
+    dx = __fdiv_rn(w0, sw);
+    dy = __fdiv_rn(w1, sw);
+    dz = __fdiv_rn(w2, sw);
+}
+
+// Per-ray constants of the watertight test (Woop, Benthin, Wald, "Watertight
+// Ray/Triangle Intersection", JCGT 2013) and of the slab test.
+struct RayPre {
+    float ox, oy, oz;
+    float ix, iy, iz;     // correctly rounded reciprocals of the direction
+    int kx, ky, kz;       // kz: dominant axis; (kx, ky) keep the winding
+    float Sx, Sy, Sz;     // shear constants
+};
+
+__device__ __forceinline__ float sel3(float a, float b, float c, int k)
+{
+    return k == 0 ? a : (k == 1 ? b : c);
+}
+
+__device__ __forceinline__ RayPre prepare_ray(const RayW& r)
+{
+    RayPre p;
+    p.ox = r.ox; p.oy = r.oy; p.oz = r.oz;
+    p.ix = __frcp_rn(r.dx);
+    p.iy = __frcp_rn(r.dy);
+    p.iz = __frcp_rn(r.dz);
+    const float ax = fabsf(r.dx), ay = fabsf(r.dy), az = fabsf(r.dz);
+    int kz = (ax > ay) ? ((ax > az) ? 0 : 2) : ((ay > az) ? 1 : 2);
+    int kx = kz + 1; if (kx == 3) kx = 0;
+    int ky = kx + 1; if (ky == 3) ky = 0;
+    const float dkz = sel3(r.dx, r.dy, r.dz, kz);
+    if (dkz < 0.0f) { int t = kx; kx = ky; ky = t; }
+    p.kx = kx; p.ky = ky; p.kz = kz;
+    p.Sx = __fdiv_rn(sel3(r.dx, r.dy, r.dz, kx), dkz);
+    p.Sy = __fdiv_rn(sel3(r.dx, r.dy, r.dz, ky), dkz);
+    p.Sz = __frcp_rn(dkz);
+    return p;
+}
+
+struct HitRec {
+    float t;
+    float cull;       // t * kBestScale: boxes entering beyond this are pruned
+    uint32_t idx;     // original triangle index (ties: lowest wins)
+    int leaf;         // leaf position, -1 for no hit
+};
+
+// Watertight, two-sided ray/triangle test; updates `h` when the triangle is
+// closer (or equally close with a lower original index).
+__device__ __forceinline__ void intersect_triangle(const float4* __restrict__ tris, int leaf, const RayPre& p,
+                                                   float t_max, HitRec& h)
+{
+    const float4 a = __ldg(&tris[3 * (int64_t)leaf]);
+    const float4 b = __ldg(&tris[3 * (int64_t)leaf + 1]);
+    const float4 c = __ldg(&tris[3 * (int64_t)leaf + 2]);
+    const float A0 = __fsub_rn(a.x, p.ox), A1 = __fsub_rn(a.y, p.oy), A2 = __fsub_rn(a.z, p.oz);
+    const float B0 = __fsub_rn(b.x, p.ox), B1 = __fsub_rn(b.y, p.oy), B2 = __fsub_rn(b.z, p.oz);
+    const float C0 = __fsub_rn(c.x, p.ox), C1 = __fsub_rn(c.y, p.oy), C2 = __fsub_rn(c.z, p.oz);
+    const float Akz = sel3(A0, A1, A2, p.kz), Bkz = sel3(B0, B1, B2, p.kz), Ckz = sel3(C0, C1, C2, p.kz);
+    const float Ax = __fmaf_rn(-p.Sx, Akz, sel3(A0, A1, A2, p.kx));
+    const float Ay = __fmaf_rn(-p.Sy, Akz, sel3(A0, A1, A2, p.ky));
+    const float Bx = __fmaf_rn(-p.Sx, Bkz, sel3(B0, B1, B2, p.kx));
+    const float By = __fmaf_rn(-p.Sy, Bkz, sel3(B0, B1, B2, p.ky));
+    const float Cx = __fmaf_rn(-p.Sx, Ckz, sel3(C0, C1, C2, p.kx));
+    const float Cy = __fmaf_rn(-p.Sy, Ckz, sel3(C0, C1, C2, p.ky));
+    // edge functions, antisymmetric under swapping the edge's end points
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        // exact products in double decide edge cases consistently
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return;
+    const float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.0f) return;
+    const float Az = __fmul_rn(p.Sz, Akz), Bz = __fmul_rn(p.Sz, Bkz), Cz = __fmul_rn(p.Sz, Ckz);
+    const float T = __fmaf_rn(W, Cz, __fmaf_rn(V, Bz, __fmul_rn(U, Az)));
+    const float t = __fdiv_rn(T, det);
+    if (!(t > kTEps && t <= t_max)) return;
+    const uint32_t idx = (uint32_t)__float_as_int(a.w);
+    if (t < h.t || (t == h.t && idx < h.idx)) {
+        h.t = t;
+        h.idx = idx;
+        h.leaf = leaf;
+        h.cull = t * kBestScale;
+    }
+}
+
+// Slab test of the two child boxes of one node.  Entry and exit planes are
+// chosen by the sign of the direction (not by min/max of the two slab
+// distances): a ray parallel to an axis and lying exactly in a box plane gives
+// 0 * inf = NaN there, which fmaxf/fminf then ignore, leaving that axis
+// unconstrained as it should be for a ray inside the closed slab.
+__device__ __forceinline__ float slab_t(float plane, float o, float inv)
+{
+    return __fmul_rn(__fsub_rn(plane, o), inv);
+}
+
+__device__ __forceinline__ void child_boxes(const float4 n0, const float4 n1, const float4 n2, const RayPre& p,
+                                            float cull, bool& hitL, bool& hitR, float& tL, float& tR)
+{
+    const bool nx = p.ix < 0.0f, ny = p.iy < 0.0f, nz = p.iz < 0.0f;
+    const float lex = slab_t(nx ? n0.y : n0.x, p.ox, p.ix), lxx = slab_t(nx ? n0.x : n0.y, p.ox, p.ix);
+    const float ley = slab_t(ny ? n0.w : n0.z, p.oy, p.iy), lxy = slab_t(ny ? n0.z : n0.w, p.oy, p.iy);
+    const float lez = slab_t(nz ? n2.y : n2.x, p.oz, p.iz), lxz = slab_t(nz ? n2.x : n2.y, p.oz, p.iz);
+    const float rex = slab_t(nx ? n1.y : n1.x, p.ox, p.ix), rxx = slab_t(nx ? n1.x : n1.y, p.ox, p.ix);
+    const float rey = slab_t(ny ? n1.w : n1.z, p.oy, p.iy), rxy = slab_t(ny ? n1.z : n1.w, p.oy, p.iy);
+    const float rez = slab_t(nz ? n2.w : n2.z, p.oz, p.iz), rxz = slab_t(nz ? n2.z : n2.w, p.oz, p.iz);
+    const float lnear = fmaxf(fmaxf(lex, ley), fmaxf(lez, kTEps));
+    const float lfar = fminf(fminf(lxx, lxy), lxz) * kFarScale;
+    const float rnear = fmaxf(fmaxf(rex, rey), fmaxf(rez, kTEps));
+    const float rfar = fminf(fminf(rxx, rxy), rxz) * kFarScale;
+    hitL = lnear <= fminf(lfar, cull);
+    hitR = rnear <= fminf(rfar, cull);
+    tL = lnear;
+    tR = rnear;
+}
+
+// Closest hit in (kTEps, t_max] by BVH traversal with a per-thread stack of
+// deferred far children.  Returns false if the stack would overflow (the
+// build refuses trees deeper than the stack, so this does not happen).
+template <bool kCount = false>
+__device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p, float t_max, HitRec& h,
+                                              const WorkCount* wc = nullptr)
+{
+    unsigned long long n_nodes = 0, n_tris = 0;
+    h.t = t_max;
+    h.cull = t_max * kBestScale;
+    h.idx = 0xFFFFFFFFu;
+    h.leaf = -1;
+    if (S.n_tris == 0) return true;
+    int2 stack[kTraversalStack];
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        if (kCount) {
+            ++n_nodes;
+            atomicOr(&wc->node_bits[node >> 5], 1u << (node & 31));
+        }
+        const float4 n0 = __ldg(&S.nodes[4 * (int64_t)node + 0]);
+        const float4 n1 = __ldg(&S.nodes[4 * (int64_t)node + 1]);
+        const float4 n2 = __ldg(&S.nodes[4 * (int64_t)node + 2]);
+        const float4 n3 = __ldg(&S.nodes[4 * (int64_t)node + 3]);
+        bool hitL, hitR;
+        float tL, tR;
+        child_boxes(n0, n1, n2, p, h.cull, hitL, hitR, tL, tR);
+        const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+        if (hitL && cl < 0) {
+            if (kCount) {
+                ++n_tris;
+                atomicOr(&wc->leaf_bits[(~cl) >> 5], 1u << ((~cl) & 31));
+            }
+            intersect_triangle(S.tris, ~cl, p, t_max, h);
+            hitL = false;
+        }
+        if (hitR && cr < 0) {
+            if (kCount) {
+                ++n_tris;
+                atomicOr(&wc->leaf_bits[(~cr) >> 5], 1u << ((~cr) & 31));
+            }
+            intersect_triangle(S.tris, ~cr, p, t_max, h);
+            hitR = false;
+        }
+        hitL = hitL && tL <= h.cull;
+        hitR = hitR && tR <= h.cull;
+        if (hitL && hitR) {
+            const bool lfirst = tL <= tR;
+            if (sp >= kTraversalStack) return false;
+            stack[sp++] = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? tR : tL));
+            node = lfirst ? cl : cr;
+            continue;
+        }
+        if (hitL) { node = cl; continue; }
+        if (hitR) { node = cr; continue; }
+        bool found = false;
+        while (sp > 0) {
+            const int2 e = stack[--sp];
+            if (__int_as_float(e.y) <= h.cull) {
+                node = e.x;
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+    if (kCount) {
+        atomicAdd(&wc->totals[0], n_nodes);
+        atomicAdd(&wc->totals[1], n_tris);
+    }
+    return true;
+}
+
+}  // namespace lidar

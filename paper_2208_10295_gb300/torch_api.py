@@ -1,0 +1,277 @@
+"""PyTorch-facing wrapper over the C ABI: tensors in, tensors out.
+
+Only argument marshalling happens here (device pointers, struct packing,
+the current CUDA stream); every step of the per-beam model runs in the CUDA
+library.  `LidarCast` is a torch.autograd.Function whose backward calls the
+library's adjoint kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import capi as C
+
+FRAME_DTYPE = np.dtype([("sensor", np.int32), ("frame", np.int32), ("pose", np.float32, (12,))])
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _frames_array(frames):
+    fr = np.ascontiguousarray(frames)
+    if fr.dtype != FRAME_DTYPE:
+        fr = fr.astype(FRAME_DTYPE)
+    return fr
+
+
+class Scene:
+    def __init__(self, lidar, handle, n_tris):
+        self._lidar = lidar
+        self.handle = handle
+        self.n_tris = n_tris
+
+    def info(self):
+        info = C.lidar_scene_info()
+        C.check(C.lidar_get_scene_info(self.handle, ctypes.byref(info)), "lidar_get_scene_info")
+        return {k: getattr(info, k) for k, _ in info._fields_}
+
+    def export(self):
+        info = self.info()
+        nodes = np.zeros((max(info["n_nodes"], 1), 16), np.float32)
+        leaf = np.zeros(max(self.n_tris, 1), np.uint32)
+        C.check(C.lidar_scene_export(self.handle, nodes.ctypes.data_as(ctypes.c_void_p),
+                                     leaf.ctypes.data_as(ctypes.c_void_p)), "lidar_scene_export")
+        return nodes[:info["n_nodes"]], leaf[:self.n_tris]
+
+    def free(self):
+        if self.handle is not None and self._lidar.handle is not None:
+            C.lidar_scene_free(self.handle)
+        self.handle = None
+
+
+class Lidar:
+    """One library context bound to a CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream = None):
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        C.check(C.lidar_create(device, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "lidar_create")
+        self.handle = h
+        self.n_beams = {}
+        self.gains = {}
+        self._keep = []
+        self._table = None
+
+    def close(self):
+        if self.handle is not None:
+            C.lidar_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------- scene
+    def build_scene(self, verts, tris, mat=None, inst=None) -> Scene:
+        verts = torch.as_tensor(verts, dtype=torch.float32, device=self.device).contiguous()
+        tris = torch.as_tensor(np.asarray(tris).astype(np.int32) if isinstance(tris, np.ndarray) else tris,
+                               device=self.device).to(torch.int32).contiguous()
+        n = tris.shape[0]
+        mat_t = None if mat is None else torch.as_tensor(np.asarray(mat).astype(np.int16), device=self.device)
+        inst_t = None if inst is None else torch.as_tensor(np.asarray(inst).astype(np.int32), device=self.device)
+        h = ctypes.c_void_p()
+        C.check(C.lidar_scene_build(self.handle, _ptr(verts), verts.shape[0], _ptr(tris), n, _ptr(mat_t),
+                                    _ptr(inst_t), ctypes.byref(h)), "lidar_scene_build")
+        return Scene(self, h, n)
+
+    # ----------------------------------------------------------- sensors
+    def set_sensor(self, slot: int, spec):
+        az = np.ascontiguousarray(spec.az_rad, dtype=np.float64)
+        el = np.ascontiguousarray(spec.el_rad, dtype=np.float64)
+        d = C.lidar_sensor_desc(az.size, az.ctypes.data, el.ctypes.data, spec.r_min, spec.r_max, spec.d_max,
+                                spec.RL_max, spec.sigma, spec.gain, spec.range_exp, spec.r_ref,
+                                spec.divergence_rad, spec.n_subrays)
+        C.check(C.lidar_set_sensor(self.handle, slot, ctypes.byref(d)), "lidar_set_sensor")
+        self.n_beams[slot] = az.size
+        self.gains[slot] = float(np.float32(spec.gain))
+
+    def set_sensor_gain(self, slot: int, gain: float):
+        C.check(C.lidar_set_sensor_gain(self.handle, slot, float(gain)), "lidar_set_sensor_gain")
+        self.gains[slot] = float(np.float32(gain))
+
+    def beam_dirs(self, slot: int) -> np.ndarray:
+        out = np.zeros((self.n_beams[slot], 3), np.float32)
+        C.check(C.lidar_get_beam_dirs(self.handle, slot, out.ctypes.data_as(ctypes.c_void_p)), "lidar_get_beam_dirs")
+        return out
+
+    # ----------------------------------------------------------- materials
+    def build_tables(self, params: torch.Tensor) -> torch.Tensor:
+        params = params.to(self.device, torch.float32).contiguous()
+        M = params.shape[0]
+        table = torch.empty((M, C.LIDAR_TABLE_SIZE), dtype=torch.float32, device=self.device)
+        C.check(C.lidar_build_tables(self.handle, _ptr(params), M, _ptr(table)), "lidar_build_tables")
+        return table
+
+    def build_tables_backward(self, params: torch.Tensor, grad_table: torch.Tensor) -> torch.Tensor:
+        params = params.to(self.device, torch.float32).contiguous()
+        grad_table = grad_table.to(self.device, torch.float32).contiguous()
+        out = torch.empty_like(params)
+        C.check(C.lidar_build_tables_backward(self.handle, _ptr(params), _ptr(grad_table), params.shape[0],
+                                              _ptr(out)), "lidar_build_tables_backward")
+        return out
+
+    def set_materials(self, table: torch.Tensor):
+        table = table.to(self.device, torch.float32).contiguous()
+        C.check(C.lidar_set_materials(self.handle, _ptr(table), table.shape[0]), "lidar_set_materials")
+        self._table = table  # the library reads it in place: keep it alive
+
+    # ----------------------------------------------------------- cast
+    def total_beams(self, frames) -> int:
+        fr = _frames_array(frames)
+        return int(sum(self.n_beams[int(s)] for s in fr["sensor"]))
+
+    def alloc_beams(self, n: int, fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst",
+                                          "sub", "theta_deg", "rf")):
+        dt = {"valid": torch.uint8, "tri": torch.int32, "t": torch.float32, "range": torch.float32,
+              "intensity": torch.float32, "normal": torch.float32, "mat": torch.int16, "inst": torch.int32,
+              "sub": torch.uint8, "theta_deg": torch.float32, "rf": torch.float32}
+        out = {}
+        for f in fields:
+            shape = (n, 3) if f == "normal" else (n,)
+            out[f] = torch.empty(shape, dtype=dt[f], device=self.device)
+        return out
+
+    def alloc_points(self, capacity: int):
+        return {"xyz": torch.empty((capacity, 3), dtype=torch.float32, device=self.device),
+                "range": torch.empty(capacity, dtype=torch.float32, device=self.device),
+                "intensity": torch.empty(capacity, dtype=torch.float32, device=self.device),
+                "normal": torch.empty((capacity, 3), dtype=torch.float32, device=self.device),
+                "material": torch.empty(capacity, dtype=torch.int16, device=self.device),
+                "instance": torch.empty(capacity, dtype=torch.int32, device=self.device),
+                "beam": torch.empty(capacity, dtype=torch.int32, device=self.device),
+                "frame": torch.empty(capacity, dtype=torch.int32, device=self.device),
+                "count": torch.zeros(1, dtype=torch.int64, device=self.device)}
+
+    @staticmethod
+    def beams_struct(b):
+        s = C.lidar_beams()
+        for name, _ in s._fields_:
+            t = b.get(name) if b is not None else None
+            setattr(s, name, None if t is None else t.data_ptr())
+        return s
+
+    @staticmethod
+    def points_struct(p):
+        s = C.lidar_points()
+        s.capacity = p["xyz"].shape[0] if p.get("xyz") is not None else p["range"].shape[0]
+        for name, _ in s._fields_[1:]:
+            t = p.get(name)
+            setattr(s, name, None if t is None else t.data_ptr())
+        return s
+
+    def cast_into(self, scene: Scene, frames, seed: int, beams=None, points=None):
+        fr = _frames_array(frames)
+        bs = self.beams_struct(beams) if beams is not None else None
+        ps = self.points_struct(points) if points is not None else None
+        st = C.lidar_cast(self.handle, scene.handle, fr.ctypes.data_as(ctypes.c_void_p), len(fr),
+                          ctypes.c_uint64(seed), ctypes.byref(bs) if bs is not None else None,
+                          ctypes.byref(ps) if ps is not None else None,
+                          _ptr(points["count"]) if points is not None else None)
+        C.check(st, "lidar_cast")
+
+    def cast(self, scene: Scene, frames, seed: int, dense=True, points_capacity=None):
+        """Returns (beams dict, points dict or None)."""
+        n = self.total_beams(frames)
+        beams = self.alloc_beams(n) if dense else None
+        points = self.alloc_points(points_capacity) if points_capacity is not None else None
+        self.cast_into(scene, frames, seed, beams, points)
+        return beams, points
+
+    def sync_status(self) -> int:
+        return C.lidar_sync_status(self.handle)
+
+    # ----------------------------------------------------------- adjoint
+    def cast_backward(self, tape, gain: float, grad_I: torch.Tensor, grad_table: torch.Tensor,
+                      grad_gain: torch.Tensor):
+        n = tape["valid"].shape[0]
+        ts = self.beams_struct(tape)
+        C.check(C.lidar_cast_backward(self.handle, n, ctypes.byref(ts), float(gain), _ptr(grad_I.contiguous()),
+                                      _ptr(grad_table), _ptr(grad_gain)), "lidar_cast_backward")
+
+    def cast_backward_mse(self, tape, gain: float, target_I, target_valid, loss, grad_table, grad_gain):
+        n = tape["valid"].shape[0]
+        ts = self.beams_struct(tape)
+        C.check(C.lidar_cast_backward_mse(self.handle, n, ctypes.byref(ts), float(gain), _ptr(target_I),
+                                          _ptr(target_valid), _ptr(loss), _ptr(grad_table), _ptr(grad_gain)),
+                "lidar_cast_backward_mse")
+
+    def count_work(self, scene: Scene, frames, seed: int):
+        """Work of one cast (instrumented kernel): node fetches, triangle tests,
+        distinct nodes/triangles touched, and the bytes they stand for."""
+        fr = _frames_array(frames)
+        wc = C.lidar_work_counts()
+        C.check(C.lidar_count_work(self.handle, scene.handle, fr.ctypes.data_as(ctypes.c_void_p), len(fr),
+                                   ctypes.c_uint64(seed), ctypes.byref(wc)), "lidar_count_work")
+        d = {k: int(getattr(wc, k)) for k, _ in wc._fields_}
+        d["unique_node_bytes"] = d["unique_nodes"] * 64
+        d["unique_tri_bytes"] = d["unique_tris"] * 48
+        # per ray: beam direction and ray-order index in, one valid byte out
+        d["io_bytes"] = d["rays"] * (12 + 4 + 1)
+        return d
+
+    # ----------------------------------------------------------- tuning
+    def launch_config(self):
+        c = C.lidar_launch_config()
+        C.check(C.lidar_get_launch_config(self.handle, ctypes.byref(c)), "lidar_get_launch_config")
+        return {k: getattr(c, k) for k, _ in c._fields_}
+
+    def set_launch_config(self, **kw):
+        cur = self.launch_config()
+        cur.update(kw)
+        c = C.lidar_launch_config(**cur)
+        C.check(C.lidar_set_launch_config(self.handle, ctypes.byref(c)), "lidar_set_launch_config")
+
+
+class LidarCast(torch.autograd.Function):
+    """Intensities of every beam as a differentiable function of the material
+    parameters (a, s, w) [M,3] and the sensor gain, with hits and masks held
+    fixed from the forward pass (the per-beam model of Sec. II with the
+    table builder in front of it)."""
+
+    @staticmethod
+    def forward(ctx, params, gain, lidar: Lidar, scene: Scene, frames, seed: int, slot: int):
+        table = lidar.build_tables(params.detach())
+        lidar.set_materials(table)
+        lidar.set_sensor_gain(slot, float(gain.detach().cpu()))
+        n = lidar.total_beams(frames)
+        tape = lidar.alloc_beams(n, ("valid", "intensity", "mat", "theta_deg", "rf"))
+        lidar.cast_into(scene, frames, seed, tape)
+        ctx.lidar, ctx.tape, ctx.table, ctx.slot = lidar, tape, table, slot
+        ctx.save_for_backward(params.detach(), gain.detach())
+        I = tape["intensity"].clone()
+        ctx.mark_non_differentiable(tape["valid"])
+        return I, tape["valid"]
+
+    @staticmethod
+    def backward(ctx, grad_I, _grad_valid):
+        params, gain = ctx.saved_tensors
+        lidar = ctx.lidar
+        lidar.set_materials(ctx.table)
+        gT = torch.zeros_like(ctx.table)
+        gg = torch.zeros(1, dtype=torch.float32, device=lidar.device)
+        lidar.cast_backward(ctx.tape, float(gain), grad_I.contiguous().float(), gT, gg)
+        gp = lidar.build_tables_backward(params, gT)
+        return gp, gg.reshape(gain.shape), None, None, None, None, None

@@ -1,0 +1,223 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Small workloads are compared on every beam; the full-size workloads on
+seeded samples of beams the oracle computes one by one, with the GPU run at
+full size in the launch configuration the benchmark uses."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import frame_offsets, gpu_cast, oracle_cast, pick, setup, stratified_sample
+from parity import compare, compare_subray, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REPORT = os.environ.get("LIDAR_PARITY_REPORT")
+
+
+def _report(rep):
+    print(json.dumps(rep))
+    if REPORT:
+        with open(REPORT, "a") as f:
+            f.write(json.dumps(rep) + "\n")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_10295_gb300 import Lidar
+    lid = Lidar(0)
+    yield lid
+    lid.close()
+
+
+def test_beam_dirs_match_oracle_bitwise(L):
+    w = synth.cfg1()
+    L.set_sensor(0, w.sensors[0])
+    got = L.beam_dirs(0)
+    want = oracle.beam_dirs(w.sensors[0].az_rad, w.sensors[0].el_rad)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_tables_match_oracle(L):
+    w = synth.cfg1()
+    T = L.build_tables(torch.tensor(w.params, device=L.device)).cpu().numpy().astype(np.float64)
+    ref = oracle.build_tables(w.params)
+    assert np.allclose(T, ref, rtol=2e-6, atol=2e-7)
+    G = np.random.default_rng(0).normal(size=ref.shape)
+    gp = L.build_tables_backward(torch.tensor(w.params, device=L.device),
+                                 torch.tensor(G, dtype=torch.float32, device=L.device)).cpu().numpy()
+    gref = oracle.build_tables_backward(w.params, G.astype(np.float32).astype(np.float64))
+    assert np.allclose(gp, gref, rtol=1e-5, atol=1e-5 * np.abs(gref).max())
+
+
+def test_cfg0_every_beam(L):
+    w = synth.cfg0()
+    gpu, _ = gpu_cast(L, w)
+    ref = oracle_cast(w)
+    rep = compare(gpu, ref, label="cfg0 all beams")
+    _report(rep)
+    assert rep["returns"] > 5000
+    assert rep["exempt"] <= 0.01 * rep["beams"]
+
+
+@pytest.mark.parametrize("seed", [77, 78])
+def test_small_terrain_every_beam(L, seed):
+    w = synth.small_terrain(seed=seed, n_frames=3, n_az=256)
+    gpu, _ = gpu_cast(L, w)
+    ref = oracle_cast(w)
+    rep = compare(gpu, ref, label=f"small terrain seed {seed}, all beams of 3 frames")
+    _report(rep)
+    assert rep["exempt"] <= 0.02 * rep["beams"]
+
+
+def test_small_terrain_range_exponent(L):
+    w = synth.small_terrain(seed=5, n_frames=1, n_az=128, range_exp=2.0)
+    gpu, _ = gpu_cast(L, w)
+    ref = oracle_cast(w)
+    _report(compare(gpu, ref, label="small terrain, I ~ 1/R^2"))
+
+
+def test_small_terrain_subrays(L):
+    w = synth.small_terrain(seed=9, n_frames=2, n_az=128, n_subrays=7, divergence=2e-3)
+    gpu, _ = gpu_cast(L, w)
+    ref = oracle_cast(w)
+    _report(compare_subray(gpu, ref, label="small terrain, 7 sub-rays"))
+
+
+def test_cfg1_full_frame_sampled(L):
+    w = synth.cfg1()
+    gpu, _ = gpu_cast(L, w)
+    samples = stratified_sample(w, 1536, seed=1)
+    ref = oracle_cast(w, samples)
+    rep = compare(pick(gpu, w, samples), ref, label="cfg1 full frame, 1536 sampled beams")
+    _report(rep)
+    # whole-frame properties that hold at any size
+    v = gpu["valid"] != 0
+    assert v.sum() > 50000
+    assert np.all((gpu["range"][v] >= 0.5) & (gpu["range"][v] <= 200.0))
+    assert np.all(gpu["intensity"][v] > 0)
+    tri = gpu["tri"]
+    hit = tri != 0xFFFFFFFF
+    assert np.all(tri[hit] < w.scene.n_tris)
+    assert np.array_equal(gpu["inst"][hit], w.scene.inst[tri[hit]])
+    assert np.array_equal(gpu["mat"][hit], w.scene.mat[tri[hit]])
+    assert np.all(np.isinf(gpu["t"][~hit]))
+
+
+def test_cfg2_batched_sampled(L):
+    w = synth.cfg2()
+    gpu, _ = gpu_cast(L, w, fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst"))
+    samples = stratified_sample(w, 1024, seed=2)
+    ref = oracle_cast(w, samples)
+    _report(compare(pick(gpu, w, samples), ref, label="cfg2 8 sensors x 64 frames, 1024 sampled beams"))
+
+
+def test_ray_order_and_launch_shapes_bit_identical(L):
+    w = synth.small_terrain(seed=3, n_frames=2, n_az=256)
+    base, scene = gpu_cast(L, w)
+    cfg0 = L.launch_config()
+    try:
+        for cfg in ({"ray_order": 0}, {"block_threads": 64, "tile_rays": 64},
+                    {"block_threads": 256, "tile_rays": 512, "blocks_per_sm": 2}):
+            L.set_launch_config(**cfg)
+            other, _ = gpu_cast(L, w, scene)
+            for k in base:
+                assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), (cfg, k)
+    finally:
+        L.set_launch_config(**cfg0)
+
+
+def test_points_compaction_matches_dense(L):
+    w = synth.small_terrain(seed=4, n_frames=3, n_az=256)
+    scene, _ = setup(L, w)
+    n = L.total_beams(w.frames)
+    beams, pts = L.cast(scene, w.frames, w.seed, dense=True, points_capacity=n)
+    assert L.sync_status() == 0
+    g = to_numpy(beams)
+    cnt = int(pts["count"].item())
+    v = np.flatnonzero(g["valid"])
+    assert cnt == v.size
+    off = frame_offsets(w)
+    fidx = np.searchsorted(off, v, side="right") - 1
+    assert np.array_equal(pts["frame"][:cnt].cpu().numpy(), fidx)
+    assert np.array_equal(pts["beam"][:cnt].cpu().numpy(), v - off[fidx])
+    assert np.array_equal(pts["range"][:cnt].cpu().numpy(), g["range"][v])
+    assert np.array_equal(pts["intensity"][:cnt].cpu().numpy(), g["intensity"][v])
+    assert np.array_equal(pts["instance"][:cnt].cpu().numpy().view(np.uint32), g["inst"][v])
+    dirs = L.beam_dirs(0)
+    xyz = pts["xyz"][:cnt].cpu().numpy()
+    assert np.allclose(xyz, g["range"][v, None] * dirs[v - off[fidx]], rtol=1e-6, atol=1e-6)
+    # capacity overflow: count reports the need, nothing beyond capacity is written
+    cap = cnt // 2
+    pts2 = L.alloc_points(cap + 1)
+    sentinel = torch.full((1,), -7.0, device=L.device)
+    pts2["range"][cap:] = sentinel
+    pts2 = {k: (v_[:cap] if k != "count" else v_) for k, v_ in pts2.items()}
+    L.cast_into(scene, w.frames, w.seed, None, pts2)
+    from paper_2208_10295_gb300 import capi
+    assert L.sync_status() == capi.LIDAR_ECAPACITY
+    assert int(pts2["count"].item()) == cnt
+
+
+def test_empty_and_single_triangle_scenes(L):
+    w = synth.small_terrain(seed=6, n_frames=1, n_az=64)
+    empty = synth.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.uint32), np.zeros(0, np.uint16),
+                        np.zeros(0, np.uint32))
+    we = synth.Workload("empty", empty, w.sensors, w.frames, w.params, w.seed)
+    gpu, _ = gpu_cast(L, we)
+    assert np.all(gpu["tri"] == 0xFFFFFFFF) and not gpu["valid"].any()
+    one = synth.Scene(np.array([[-50, -50, -0.5], [50, -50, -0.5], [0, 80, -0.5]], np.float32) +
+                      w.frames[0]["pose"][[3, 7, 11]],
+                      np.array([[0, 1, 2]], np.uint32), np.array([1], np.uint16), np.array([42], np.uint32))
+    w1 = synth.Workload("one", one, w.sensors, w.frames, w.params, w.seed)
+    gpu, _ = gpu_cast(L, w1)
+    ref = oracle_cast(w1)
+    rep = compare(gpu, ref, label="single triangle")
+    assert rep["hits"] > 100
+
+
+def test_lbvh_invariants(L):
+    w = synth.small_terrain(seed=8, n_cells=48, half=24.0, n_objects=20, n_frames=1, n_az=32)
+    scene, _ = setup(L, w)
+    nodes, leaf_tri = scene.export()
+    n = w.scene.n_tris
+    assert nodes.shape[0] == n - 1
+    assert np.array_equal(np.sort(leaf_tri), np.arange(n))
+    child = nodes[:, 12:14].view(np.int32)
+    seen_leaf = np.zeros(n, int)
+    seen_node = np.zeros(n - 1, int)
+    V = w.scene.verts[w.scene.tris[leaf_tri]]          # leaf-ordered triangles
+    lo_t, hi_t = V.min(1), V.max(1)
+
+    def box_of(c):
+        if c < 0:
+            return lo_t[~c], hi_t[~c]
+        b = nodes[c]
+        lo = np.minimum([b[0], b[2], b[8]], [b[4], b[6], b[10]])
+        hi = np.maximum([b[1], b[3], b[9]], [b[5], b[7], b[11]])
+        return lo, hi
+
+    for i in range(n - 1):
+        b = nodes[i]
+        for side, c in enumerate(child[i]):
+            if c < 0:
+                seen_leaf[~c] += 1
+            else:
+                seen_node[c] += 1
+            lo = np.array([b[0], b[2], b[8]] if side == 0 else [b[4], b[6], b[10]])
+            hi = np.array([b[1], b[3], b[9]] if side == 0 else [b[5], b[7], b[11]])
+            clo, chi = box_of(c)
+            # the parent stores exactly the child's box (exact FP32 min/max)
+            assert np.array_equal(lo, clo) and np.array_equal(hi, chi), (i, side)
+    assert np.all(seen_leaf == 1)
+    assert seen_node[0] == 0 and np.all(seen_node[1:] == 1)
+    assert scene.info()["max_depth"] <= 64
