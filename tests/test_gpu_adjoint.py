@@ -1,0 +1,190 @@
+"""Parity of the adjoint (hits and masks frozen) with the oracle's FP64
+adjoint, and central finite differences of the GPU loss.
+
+Targets are computed by the oracle (hidden material parameters) and passed to
+both sides; beams the oracle flags as ambiguous in either forward pass are
+left out of the mask so both sides sum over the same beams."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import frame_offsets, oracle_cast, stratified_sample
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NORM_RTOL = 1e-5
+
+
+def close_grad(got, ref, label):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = max(np.linalg.norm(ref), 1e-30)
+    rel = np.linalg.norm(got - ref) / scale
+    ent = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30)
+    assert rel <= NORM_RTOL, f"{label}: norm-relative error {rel:.3g}"
+    assert ent <= NORM_RTOL, f"{label}: per-entry error {ent:.3g} of max|g|"
+    return rel
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_10295_gb300 import Lidar
+    lid = Lidar(0)
+    yield lid
+    lid.close()
+
+
+def _gpu_tape(L, w, scene=None):
+    if scene is None:
+        scene = L.build_scene(w.scene.verts, w.scene.tris, w.scene.mat, w.scene.inst)
+    for s, spec in enumerate(w.sensors):
+        L.set_sensor(s, spec)
+    params = torch.tensor(w.params, device=L.device)
+    table = L.build_tables(params)
+    L.set_materials(table)
+    n = L.total_beams(w.frames)
+    tape = L.alloc_beams(n, ("valid", "intensity", "mat", "theta_deg", "rf"))
+    L.cast_into(scene, w.frames, w.seed, tape)
+    assert L.sync_status() == 0
+    return scene, params, table, tape, n
+
+
+def _targets(w, fwd, tgt, n, idx=None):
+    """Oracle targets as FP32 device arrays; mask = target valid, both oracle
+    passes unflagged."""
+    ok = ((fwd.flags & 7) == 0) & ((tgt.flags & 7) == 0) & (tgt.valid != 0)
+    tI = np.zeros(n, np.float32)
+    tv = np.zeros(n, np.uint8)
+    sel = np.arange(n) if idx is None else idx
+    tI[sel] = tgt.intensity.astype(np.float32)
+    tv[sel] = ok.astype(np.uint8)
+    return tI, tv
+
+
+def _gpu_backward_mse(L, tape, table, gain, tI, tv):
+    dev = L.device
+    loss = torch.zeros(1, device=dev)
+    gT = torch.zeros_like(table)
+    gg = torch.zeros(1, device=dev)
+    L.cast_backward_mse(tape, gain, torch.tensor(tI, device=dev), torch.tensor(tv, device=dev), loss, gT, gg)
+    assert L.sync_status() == 0
+    return loss.item(), gT.cpu().numpy(), gg.item()
+
+
+def test_adjoint_small_terrain_every_beam(L):
+    w = synth.small_terrain(seed=31, n_frames=3, n_az=256)
+    scene, params, table, tape, n = _gpu_tape(L, w)
+    fwd = oracle_cast(w)
+    tgt = oracle_cast(w, table=oracle.build_tables(w.hidden_params))
+    tI, tv = _targets(w, fwd, tgt, n)
+    loss, gT, gg = _gpu_backward_mse(L, tape, table, 1.0, tI, tv)
+    # the oracle sums over the same beams: its own tape, the same targets and mask
+    L_ref, gT_ref, gg_ref, N = oracle.cast_backward(fwd.valid, fwd.mat, fwd.theta_deg, fwd.rf,
+                                                    oracle.build_tables(w.params), 1.0, tI.astype(np.float64), tv)
+    assert N > 1000
+    assert loss == pytest.approx(L_ref, rel=NORM_RTOL)
+    close_grad(gT, gT_ref, "dL/dT")
+    assert gg == pytest.approx(gg_ref, rel=NORM_RTOL)
+    gp = L.build_tables_backward(params, torch.tensor(gT, device=L.device)).cpu().numpy()
+    gp_ref = oracle.build_tables_backward(w.params, gT_ref)
+    close_grad(gp, gp_ref, "dL/d(a,s,w)")
+
+
+def test_autograd_path_matches_fused_mse(L):
+    """LidarCast (torch autograd, generic dL/dI) against the fused-MSE kernel."""
+    from paper_2208_10295_gb300 import LidarCast
+    w = synth.small_terrain(seed=32, n_frames=2, n_az=256)
+    scene, params, table, tape, n = _gpu_tape(L, w)
+    fwd = oracle_cast(w)
+    tgt = oracle_cast(w, table=oracle.build_tables(w.hidden_params))
+    tI, tv = _targets(w, fwd, tgt, n)
+    p = params.clone().requires_grad_(True)
+    g = torch.tensor(1.0, device=L.device, requires_grad=True)
+    I, valid = LidarCast.apply(p, g, L, scene, w.frames, w.seed, 0)
+    mask = (valid != 0) & torch.tensor(tv != 0, device=L.device)
+    res = (I - torch.tensor(tI, device=L.device))[mask]
+    loss = (res * res).sum() / mask.sum()
+    loss.backward()
+    L.set_materials(table)
+    l2, gT, gg = _gpu_backward_mse(L, tape, table, 1.0, tI, tv)
+    gp_fused = L.build_tables_backward(params, torch.tensor(gT, device=L.device)).cpu().numpy()
+    assert loss.item() == pytest.approx(l2, rel=1e-5)
+    close_grad(p.grad.cpu().numpy(), gp_fused, "autograd dL/d(a,s,w)")
+    assert g.grad.item() == pytest.approx(gg, rel=1e-5)
+
+
+def test_adjoint_cfg3_sampled(L):
+    """Full 16-frame workload on the GPU; the mask keeps a seeded sample of
+    beams that the oracle computes one by one."""
+    w = synth.cfg3()
+    scene, params, table, tape, n = _gpu_tape(L, w)
+    samples = stratified_sample(w, 1024, seed=3)
+    fwd = oracle_cast(w, samples)
+    tgt = oracle_cast(w, samples, table=oracle.build_tables(w.hidden_params))
+    idx = frame_offsets(w)[samples[0]] + samples[1]
+    tI, tv = _targets(w, fwd, tgt, n, idx)
+    loss, gT, gg = _gpu_backward_mse(L, tape, table, 1.0, tI, tv)
+    L_ref, gT_ref, gg_ref, N = oracle.cast_backward(fwd.valid, fwd.mat, fwd.theta_deg, fwd.rf,
+                                                    oracle.build_tables(w.params), 1.0,
+                                                    tI[idx].astype(np.float64), tv[idx])
+    assert N > 200
+    assert loss == pytest.approx(L_ref, rel=NORM_RTOL)
+    close_grad(gT, gT_ref, "cfg3 dL/dT")
+    assert gg == pytest.approx(gg_ref, rel=NORM_RTOL)
+
+
+def test_cfg3_finite_differences_full_size(L):
+    """All 4.2M beams: the frozen-hit loss is quadratic in T and g, so central
+    differences of the GPU loss match its gradient (rel 1e-3)."""
+    w = synth.cfg3()
+    scene, params, table, tape, n = _gpu_tape(L, w)
+    dev = L.device
+    Th = L.build_tables(torch.tensor(w.hidden_params, device=dev))
+    L.set_materials(Th)
+    tgt = L.alloc_beams(n, ("valid", "intensity", "mat", "theta_deg", "rf"))
+    L.cast_into(scene, w.frames, w.seed, tgt)
+    L.set_materials(table)
+    tI = tgt["intensity"]
+    tv = tgt["valid"]
+    loss0, gT, gg = _gpu_backward_mse(L, tape, table, 1.0, tI.cpu().numpy(), tv.cpu().numpy())
+    assert loss0 > 0
+    rng = np.random.default_rng(0)
+    # entries carrying at least 1% of the largest gradient; the loss is exactly
+    # quadratic in T, so a large step h adds no truncation error and keeps the
+    # FP32 loss difference well above its rounding
+    used = np.argwhere(np.abs(gT) > 1e-2 * np.abs(gT).max())
+    for m, k in used[rng.choice(len(used), 6, replace=False)]:
+        h = 0.5
+        vals = []
+        for sgn in (1, -1):
+            Tp = table.clone()
+            Tp[m, k] += sgn * h
+            L.set_materials(Tp)
+            lval, _, _ = _gpu_backward_mse(L, tape, Tp, 1.0, tI.cpu().numpy(), tv.cpu().numpy())
+            vals.append(lval)
+        L.set_materials(table)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert gT[m, k] == pytest.approx(fd, rel=1e-3, abs=1e-6 * np.abs(gT).max()), (m, k)
+    vals = []
+    for sgn in (1, -1):
+        lval, _, _ = _gpu_backward_mse(L, tape, table, 1.0 + sgn * 0.25, tI.cpu().numpy(), tv.cpu().numpy())
+        vals.append(lval)
+    assert gg == pytest.approx((vals[0] - vals[1]) / 0.5, rel=1e-3)
+
+
+def test_adjoint_deterministic(L):
+    w = synth.small_terrain(seed=33, n_frames=2, n_az=256)
+    scene, params, table, tape, n = _gpu_tape(L, w)
+    rng = np.random.default_rng(1)
+    tI = rng.uniform(0, 0.5, n).astype(np.float32)
+    tv = (rng.uniform(size=n) < 0.7).astype(np.uint8)
+    a = _gpu_backward_mse(L, tape, table, 1.0, tI, tv)
+    b = _gpu_backward_mse(L, tape, table, 1.0, tI, tv)
+    assert a[0] == b[0] and a[2] == b[2]
+    assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
