@@ -243,6 +243,41 @@ lidar_status lidar_cast_backward_mse(lidar_ctx* ctx, int64_t n_beams, const lida
                                      const float* target_I_dev, const uint8_t* target_valid_dev,
                                      float* loss_dev, float* grad_table_dev, float* grad_gain_dev);
 
+/* Allocation-free variant of lidar_cast_backward_mse (no counterpart in the
+ * paper; it exists for callers that must not allocate device memory, such as
+ * code that runs while a CUDA graph is being captured in global capture mode,
+ * sensor loops with hard real-time deadlines that cannot afford cudaMalloc's
+ * implicit synchronisation, or host applications whose memory pool already
+ * holds the device's memory).  It needs no context either: the caller passes
+ * the stream, the tape arrays and the reflectance table directly.
+ *   cuda_stream    cudaStream_t to enqueue on (NULL = legacy default stream),
+ *                  on the device that is current on the calling thread
+ *   valid_dev, mat_dev, theta_deg_dev, rf_dev
+ *                  the tape of lidar_beams, [n_beams] each
+ *   table_dev      [n_materials][91] reflectance table used by the forward pass
+ *   n_materials    1..LIDAR_NOALLOC_MAX_MATERIALS; larger tables are rejected
+ *                  with LIDAR_EINVAL (use lidar_cast_backward_mse)
+ *   gain, target_I_dev, target_valid_dev, loss_dev, grad_table_dev, grad_gain_dev
+ *                  as for lidar_cast_backward_mse (loss overwritten, gradients
+ *                  accumulated)
+ * Scratch lives in a fixed device array inside the library
+ * (LIDAR_NOALLOC_SCRATCH_BYTES, held by every device that loads the library
+ * until the process exits).  The entry point calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Its first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress, once per device, cached), so
+ * make that first call before any stream capture.  All calls share the one
+ * array: the accumulators are cleared on the stream at the start of every call,
+ * and calls whose work overlaps on the GPU (other streams, other threads) race
+ * on it and must be serialised by the caller. */
+#define LIDAR_NOALLOC_MAX_MATERIALS 64
+#define LIDAR_NOALLOC_SCRATCH_BYTES 55296
+lidar_status lidar_cast_backward_mse_noalloc(void* cuda_stream, int64_t n_beams, const uint8_t* valid_dev,
+                                             const uint16_t* mat_dev, const float* theta_deg_dev,
+                                             const float* rf_dev, const float* table_dev, int32_t n_materials,
+                                             float gain, const float* target_I_dev,
+                                             const uint8_t* target_valid_dev, float* loss_dev,
+                                             float* grad_table_dev, float* grad_gain_dev);
+
 /* ----------------------------------------------------------- instrumentation */
 
 /* Work of one cast, counted by an instrumented instantiation of the same

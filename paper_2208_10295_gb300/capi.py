@@ -101,6 +101,9 @@ _PROTOS = [
                                            c_vp, c_vp, c_vp]),
     ("lidar_cast_backward_mse", ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.POINTER(lidar_beams),
                                                ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    ("lidar_cast_backward_mse_noalloc", ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                                       ctypes.c_int32, ctypes.c_float, c_vp, c_vp, c_vp, c_vp,
+                                                       c_vp]),
     ("lidar_count_work", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.POINTER(lidar_work_counts)]),
     ("lidar_get_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
@@ -161,6 +164,7 @@ lidar_set_materials = _fwd("lidar_set_materials")
 lidar_cast = _fwd("lidar_cast")
 lidar_cast_backward = _fwd("lidar_cast_backward")
 lidar_cast_backward_mse = _fwd("lidar_cast_backward_mse")
+lidar_cast_backward_mse_noalloc = _fwd("lidar_cast_backward_mse_noalloc")
 lidar_count_work = _fwd("lidar_count_work")
 lidar_get_launch_config = _fwd("lidar_get_launch_config")
 lidar_set_launch_config = _fwd("lidar_set_launch_config")

@@ -213,6 +213,23 @@ constexpr int kAdjBlocks = 1024;
 
 }  // namespace
 
+// Scratch of the allocation-free backward variant: a file-scope device array
+// sized for kNoAllocMaxMaterials table rows (every device that loads the
+// library holds it until the process exits).
+constexpr int kNoAllocMaxMaterials = LIDAR_NOALLOC_MAX_MATERIALS;
+constexpr size_t kNoAllocScratchBytes =
+    256 + (((size_t)kNoAllocMaxMaterials * LIDAR_TABLE_SIZE + 1) * 8 + 255) / 256 * 256 + kAdjBlocks * sizeof(double);
+static_assert(kNoAllocScratchBytes == LIDAR_NOALLOC_SCRATCH_BYTES, "lidar.h states the scratch size");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+cudaError_t noalloc_scratch(void** ptr, size_t* bytes)
+{
+    // cudaGetSymbolAddress resolves the array on the current device
+    cudaError_t e = cudaGetSymbolAddress(ptr, g_noalloc_scratch);
+    *bytes = kNoAllocScratchBytes;
+    return e;
+}
+
 cudaError_t launch_build_tables(cudaStream_t s, const float* params, int M, float* table)
 {
     const int n = M * LIDAR_TABLE_SIZE;

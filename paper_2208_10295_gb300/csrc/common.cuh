@@ -156,5 +156,7 @@ cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid
                                  float* loss, float* grad_table, float* grad_gain, void* scratch,
                                  size_t scratch_bytes);
 size_t backward_scratch_bytes(int M);
+// address (on the current device) and size of the allocation-free variant's scratch array
+cudaError_t noalloc_scratch(void** ptr, size_t* bytes);
 
 }  // namespace lidar

@@ -592,6 +592,51 @@ lidar_status lidar_cast_backward_mse(lidar_ctx* c, int64_t n, const lidar_beams*
     return backward_common(c, n, tape, gain, nullptr, target_I, target_valid, loss, grad_table, grad_gain);
 }
 
+// Device address of the allocation-free variant's scratch array, looked up once
+// per device (with that device current) and cached.
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[256] = {};
+
+lidar_status lidar_cast_backward_mse_noalloc(void* cuda_stream, int64_t n, const uint8_t* valid, const uint16_t* mat,
+                                             const float* theta_deg, const float* rf, const float* table, int32_t M,
+                                             float gain, const float* target_I, const uint8_t* target_valid,
+                                             float* loss, float* grad_table, float* grad_gain)
+{
+    LIDAR_CHECK_ARG(n >= 0, "lidar_cast_backward_mse_noalloc: negative beam count");
+    LIDAR_CHECK_ARG(table != nullptr && M >= 1, "lidar_cast_backward_mse_noalloc: need a reflectance table");
+    if (M > LIDAR_NOALLOC_MAX_MATERIALS) {
+        set_error("lidar_cast_backward_mse_noalloc: " + std::to_string(M) + " materials exceed the fixed scratch (" +
+                  std::to_string(LIDAR_NOALLOC_MAX_MATERIALS) + " materials max); use lidar_cast_backward_mse");
+        return LIDAR_EINVAL;
+    }
+    LIDAR_CHECK_ARG(n == 0 || (valid && mat && theta_deg && rf && target_I && target_valid),
+                    "lidar_cast_backward_mse_noalloc: tape or target arrays are NULL");
+    int dev = 0;
+    LIDAR_CUDA(cudaGetDevice(&dev));
+    LIDAR_CHECK_ARG(dev >= 0 && dev < 256, "lidar_cast_backward_mse_noalloc: device ordinal out of range");
+    void* scratch = nullptr;
+    size_t bytes = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (g_noalloc_ptr[dev] == nullptr) {
+            void* p = nullptr;
+            cudaError_t e = noalloc_scratch(&p, &bytes);
+            if (e != cudaSuccess || p == nullptr) {
+                set_error(std::string("lidar_cast_backward_mse_noalloc: cudaGetSymbolAddress: ") +
+                          cudaGetErrorString(e));
+                return LIDAR_ECUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    bytes = LIDAR_NOALLOC_SCRATCH_BYTES;
+    TableDev T{table, M};
+    LIDAR_CUDA(launch_cast_backward((cudaStream_t)cuda_stream, n, valid, mat, theta_deg, rf, T, gain, nullptr, target_I,
+                                    target_valid, loss, grad_table, grad_gain, scratch, bytes));
+    return LIDAR_OK;
+}
+
 lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
                               uint64_t seed, lidar_work_counts* out)
 {
