@@ -297,13 +297,32 @@ typedef struct {
 lidar_status lidar_count_work(lidar_ctx* ctx, const lidar_scene* scene, const lidar_frame* frames_host,
                               int32_t n_frames, uint64_t seed, lidar_work_counts* out);
 
+/* --------------------------------------------------------------- scheduling */
+
+/* Ray schedule of a sensor slot.  The cast kernel's warps take groups of 32
+ * consecutive positions of the slot's ray order; by default that order is the
+ * Morton order of the beam directions (coherent warps).  This call measures
+ * the traversal cost of every beam on `frame` (one frame of that slot, cast
+ * with counting enabled), and reorders the 32-beam groups so that the most
+ * expensive groups run first (longest-processing-time-first), which shortens
+ * the tail of a cast where the last warps would otherwise run alone.  The
+ * schedule never changes results, only their timing; use the costs of a nearby
+ * pose (e.g. the previous frame).  Synchronises. */
+lidar_status lidar_schedule_by_cost(lidar_ctx* ctx, const lidar_scene* scene, const lidar_frame* frame,
+                                    uint64_t seed);
+
+/* Restores the Morton order of a slot. */
+lidar_status lidar_reset_schedule(lidar_ctx* ctx, int32_t slot);
+
 /* --------------------------------------------------------------- launch tuning */
 
 typedef struct {
-    int32_t block_threads;   /* threads per block of the cast kernel (multiple of 32, <= 1024) */
+    int32_t block_threads;   /* threads per block of the cast kernel (multiple of 32, <= 256) */
     int32_t blocks_per_sm;   /* persistent blocks per SM */
-    int32_t tile_rays;       /* rays a block takes from the work queue at a time */
+    int32_t tile_rays;       /* rays a warp takes from the work counter at a time (multiple of 32) */
     int32_t ray_order;       /* 0 = beam order, 1 = Morton order of beam directions */
+    int32_t traversal;       /* 0 = each lane tests its triangles as it meets them;
+                                1 = warp-synchronous traversal with postponed triangle tests */
 } lidar_launch_config;
 
 lidar_status lidar_get_launch_config(lidar_ctx* ctx, lidar_launch_config* out);

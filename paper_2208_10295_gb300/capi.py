@@ -70,7 +70,7 @@ class lidar_work_counts(ctypes.Structure):
 
 class lidar_launch_config(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("tile_rays", ctypes.c_int32), ("ray_order", ctypes.c_int32)]
+                ("tile_rays", ctypes.c_int32), ("ray_order", ctypes.c_int32), ("traversal", ctypes.c_int32)]
 
 
 assert ctypes.sizeof(lidar_frame) == 56
@@ -106,6 +106,8 @@ _PROTOS = [
                                                        c_vp]),
     ("lidar_count_work", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.POINTER(lidar_work_counts)]),
+    ("lidar_schedule_by_cost", ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(lidar_frame), ctypes.c_uint64]),
+    ("lidar_reset_schedule", ctypes.c_int, [c_vp, ctypes.c_int32]),
     ("lidar_get_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
     ("lidar_set_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
 ]
@@ -166,5 +168,7 @@ lidar_cast_backward = _fwd("lidar_cast_backward")
 lidar_cast_backward_mse = _fwd("lidar_cast_backward_mse")
 lidar_cast_backward_mse_noalloc = _fwd("lidar_cast_backward_mse_noalloc")
 lidar_count_work = _fwd("lidar_count_work")
+lidar_schedule_by_cost = _fwd("lidar_schedule_by_cost")
+lidar_reset_schedule = _fwd("lidar_reset_schedule")
 lidar_get_launch_config = _fwd("lidar_get_launch_config")
 lidar_set_launch_config = _fwd("lidar_set_launch_config")

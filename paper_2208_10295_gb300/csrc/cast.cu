@@ -84,6 +84,28 @@ __device__ __forceinline__ void shade(const SceneDev& S, const HitRec& h, const 
     out.valid = valid;
 }
 
+// Dense per-beam record of one beam (normal rotated into the sensor frame).
+__device__ __forceinline__ void write_beam(const BeamsOut& out, int64_t o, const BeamResult& b, const float* P,
+                                           int sub)
+{
+    if (out.valid) out.valid[o] = (uint8_t)b.valid;
+    if (out.tri) out.tri[o] = b.tri;
+    if (out.t) out.t[o] = b.t;
+    if (out.range) out.range[o] = b.range;
+    if (out.intensity) out.intensity[o] = b.intensity;
+    if (out.normal) {
+        // n_s = R^T n_w
+        out.normal[3 * o + 0] = P[0] * b.nx + P[4] * b.ny + P[8] * b.nz;
+        out.normal[3 * o + 1] = P[1] * b.nx + P[5] * b.ny + P[9] * b.nz;
+        out.normal[3 * o + 2] = P[2] * b.nx + P[6] * b.ny + P[10] * b.nz;
+    }
+    if (out.mat) out.mat[o] = (uint16_t)b.mat;
+    if (out.inst) out.inst[o] = b.inst;
+    if (out.sub) out.sub[o] = (uint8_t)sub;
+    if (out.theta_deg) out.theta_deg[o] = b.theta_deg;
+    if (out.rf) out.rf[o] = b.rf;
+}
+
 __device__ __forceinline__ int find_frame(const int64_t* __restrict__ prefix, int n_frames, int64_t tile)
 {
     int lo = 0, hi = n_frames - 1;
@@ -94,67 +116,70 @@ __device__ __forceinline__ int find_frame(const int64_t* __restrict__ prefix, in
     return lo;
 }
 
-template <bool kCount>
-__global__ void __launch_bounds__(1024) k_cast(SceneDev S, const SensorDev* __restrict__ sensors,
-                                               const FrameDev* __restrict__ frames, int n_frames,
-                                               const int64_t* __restrict__ tile_prefix, int64_t n_tiles,
-                                               TableDev T, uint64_t seed, BeamsOut out, int* status,
-                                               unsigned long long* work_counter, int tile_rays, WorkCount wc)
+// Persistent kernel, work taken per warp: lane 0 claims a tile of `tile_rays`
+// consecutive ray-order positions of one frame (a multiple of 32) and the warp
+// traces it 32 rays at a time; no block-wide barrier.
+template <bool kCount, int kMinBlocks, bool kWarpSync>
+__global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const SensorDev* __restrict__ sensors,
+                                              const FrameDev* __restrict__ frames, int n_frames,
+                                              const int64_t* __restrict__ tile_prefix, int64_t n_tiles,
+                                              TableDev T, uint64_t seed, BeamsOut out, int* status,
+                                              unsigned long long* work_counter, int tile_rays, WorkCount wc)
 {
-    __shared__ int64_t s_tile;
+    const int lane = threadIdx.x & 31;
+    extern __shared__ int2 sh_stack[];  // [kSharedStack][blockDim.x]
     while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(work_counter, 1ull);
-        __syncthreads();
-        const int64_t tile = s_tile;
+        unsigned long long claimed = 0;
+        if (lane == 0) claimed = atomicAdd(work_counter, 1ull);
+        const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, claimed, 0);
         if (tile >= n_tiles) return;
         const int fi = find_frame(tile_prefix, n_frames, tile);
         const FrameDev& fr = frames[fi];
         const SensorDev& sd = sensors[fr.sensor];
-        for (int j = threadIdx.x; j < tile_rays; j += blockDim.x) {
-            const int64_t pos = (tile - tile_prefix[fi]) * tile_rays + j;
-            if (pos >= sd.n_beams) break;
-            const uint32_t beam = sd.order ? __ldg(&sd.order[pos]) : (uint32_t)pos;
-            const float d0 = __ldg(&sd.dirs[3 * (int64_t)beam]);
-            const float d1 = __ldg(&sd.dirs[3 * (int64_t)beam + 1]);
-            const float d2 = __ldg(&sd.dirs[3 * (int64_t)beam + 2]);
+        const int64_t base = (tile - tile_prefix[fi]) * tile_rays;
+        for (int j0 = 0; j0 < tile_rays; j0 += 32) {
+            const int64_t pos = base + j0 + lane;
+            const bool active = pos < sd.n_beams;
+            if (!__any_sync(0xffffffffu, active)) break;
+            uint32_t beam = 0;
+            float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
+            if (active) {
+                beam = sd.order ? __ldg(&sd.order[pos]) : (uint32_t)pos;
+                d0 = __ldg(&sd.dirs[3 * (int64_t)beam]);
+                d1 = __ldg(&sd.dirs[3 * (int64_t)beam + 1]);
+                d2 = __ldg(&sd.dirs[3 * (int64_t)beam + 2]);
+            }
             const RayW beam_ray = world_ray(fr.pose, d0, d1, d2);
             BeamResult best;
             int best_sub = 0;
             float best_I = -1.0f;
+            unsigned cost = 0;
             for (int k = 0; k < sd.n_sub; ++k) {
                 RayW r = beam_ray;
                 if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
                 const RayPre p = prepare_ray(r);
                 HitRec h;
-                if (!trace_closest<kCount>(S, p, sd.t_max, h, &wc)) raise_status(status, ST_STACK);
-                BeamResult res;
-                shade(S, h, r, sd, T, seed, beam, (uint32_t)fr.frame, (uint32_t)fr.sensor, (uint32_t)k, res);
-                if (k == 0) best = res;
-                if (res.valid && res.intensity > best_I) {
-                    best_I = res.intensity;
-                    best = res;
-                    best_sub = k;
+                bool ok = true;
+                if (kWarpSync) {
+                    ok = trace_closest_warp<kCount>(S, p, sd.t_max, h, active, &wc);
+                } else if (active) {
+                    ok = trace_closest<kCount>(S, p, sd.t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x, &cost);
+                }
+                if (!ok) raise_status(status, ST_STACK);
+                if (active) {
+                    BeamResult res;
+                    shade(S, h, r, sd, T, seed, beam, (uint32_t)fr.frame, (uint32_t)fr.sensor, (uint32_t)k, res);
+                    if (k == 0) best = res;
+                    if (res.valid && res.intensity > best_I) {
+                        best_I = res.intensity;
+                        best = res;
+                        best_sub = k;
+                    }
                 }
             }
-            const int64_t o = fr.beam_offset + beam;
-            if (out.valid) out.valid[o] = (uint8_t)best.valid;
-            if (out.tri) out.tri[o] = best.tri;
-            if (out.t) out.t[o] = best.t;
-            if (out.range) out.range[o] = best.range;
-            if (out.intensity) out.intensity[o] = best.intensity;
-            if (out.normal) {
-                // into the sensor frame: n_s = R^T n_w
-                const float* P = fr.pose;
-                out.normal[3 * o + 0] = P[0] * best.nx + P[4] * best.ny + P[8] * best.nz;
-                out.normal[3 * o + 1] = P[1] * best.nx + P[5] * best.ny + P[9] * best.nz;
-                out.normal[3 * o + 2] = P[2] * best.nx + P[6] * best.ny + P[10] * best.nz;
-            }
-            if (out.mat) out.mat[o] = (uint16_t)best.mat;
-            if (out.inst) out.inst[o] = best.inst;
-            if (out.sub) out.sub[o] = (uint8_t)best_sub;
-            if (out.theta_deg) out.theta_deg[o] = best.theta_deg;
-            if (out.rf) out.rf[o] = best.rf;
+            if (!active) continue;
+            write_beam(out, fr.beam_offset + beam, best, fr.pose, best_sub);
+            if (kCount && wc.beam_cost) wc.beam_cost[fr.beam_offset + beam] = cost;
         }
     }
 }
@@ -162,7 +187,7 @@ __global__ void __launch_bounds__(1024) k_cast(SceneDev S, const SensorDev* __re
 // ------------------------------------------------------------------ compaction
 
 constexpr int kCompactThreads = 256;
-constexpr int kCompactItems = 16;
+constexpr int kCompactItems = 4;
 constexpr int kCompactTile = kCompactThreads * kCompactItems;
 
 __global__ void __launch_bounds__(kCompactThreads) k_count_valid(const uint8_t* __restrict__ valid, int64_t n,
@@ -314,22 +339,38 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                         const FrameDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
                         int64_t n_tiles, TableDev table, uint64_t seed, BeamsOut out, int* status,
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
-                        const WorkCount* count)
+                        int64_t n_beams_total, const WorkCount* count)
 {
     if (n_tiles == 0) return cudaSuccess;
     cudaMemsetAsync(work_counter, 0, sizeof(unsigned long long), s);
+    const int64_t warps = cfg.block_threads / 32;
     int64_t grid = (int64_t)num_sms * cfg.blocks_per_sm;
-    if (grid > n_tiles) grid = n_tiles;
+    if (grid > (n_tiles + warps - 1) / warps) grid = (n_tiles + warps - 1) / warps;
+    // register budget from the requested residency: threads per SM <= 512 ->
+    // up to 128 registers, <= 768 -> 85, more -> 64
+    const int resident = cfg.block_threads * cfg.blocks_per_sm;
+    const int variant = resident <= 512 ? 2 : (resident <= 768 ? 3 : 4);
+    const WorkCount none{nullptr, nullptr, nullptr, nullptr};
+#define LIDAR_LAUNCH_CAST(C, V, W)                                                                               \
+    k_cast<C, V, W><<<(unsigned)grid, cfg.block_threads, smem, s>>>(scene, sensors_dev, frames_dev, n_frames,    \
+                                                                 tile_prefix_dev, n_tiles, table, seed, out,      \
+                                                                 status, work_counter, cfg.tile_rays,             \
+                                                                 C ? *count : none)
+    const bool ws = cfg.traversal == 1;
+    const size_t smem = ws ? 0 : (size_t)kSharedStack * cfg.block_threads * sizeof(int2);
     if (count) {
-        k_cast<true><<<(unsigned)grid, cfg.block_threads, 0, s>>>(scene, sensors_dev, frames_dev, n_frames,
-                                                                  tile_prefix_dev, n_tiles, table, seed, out,
-                                                                  status, work_counter, cfg.tile_rays, *count);
+        // the work counted does not depend on the launch shape
+        LIDAR_LAUNCH_CAST(true, 4, false);
+    } else if (ws) {
+        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, true);
+        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, true);
+        else LIDAR_LAUNCH_CAST(false, 4, true);
     } else {
-        k_cast<false><<<(unsigned)grid, cfg.block_threads, 0, s>>>(scene, sensors_dev, frames_dev, n_frames,
-                                                                   tile_prefix_dev, n_tiles, table, seed, out,
-                                                                   status, work_counter, cfg.tile_rays,
-                                                                   WorkCount{nullptr, nullptr, nullptr});
+        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, false);
+        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, false);
+        else LIDAR_LAUNCH_CAST(false, 4, false);
     }
+#undef LIDAR_LAUNCH_CAST
     return cudaGetLastError();
 }
 
@@ -376,6 +417,56 @@ cudaError_t launch_compact(cudaStream_t s, const SensorDev* sensors_dev, const F
     k_scan_tiles<<<1, 1024, 0, s>>>(counts, tiles, offsets, n_points_dev);
     k_scatter_points<<<(unsigned)tiles, kCompactThreads, 0, s>>>(sensors_dev, frames_dev, n_frames, n, dense,
                                                                  offsets, pts, status);
+    return cudaGetLastError();
+}
+
+namespace {
+constexpr int kScheduleGroup = 32;
+
+__global__ void k_group_cost(const uint32_t* __restrict__ cost, const uint32_t* __restrict__ order, int n,
+                             uint32_t* keys, uint32_t* vals)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_groups = (n + kScheduleGroup - 1) / kScheduleGroup;
+    if (g >= n_groups) return;
+    const int lo = g * kScheduleGroup, hi = min(n, lo + kScheduleGroup);
+    uint32_t mx = 0;
+    for (int j = lo; j < hi; ++j) mx = max(mx, cost[order[j]]);
+    // ascending sort of ~cost runs the most expensive group first (ties keep the
+    // base order); a partial group sorts last so every other group stays whole
+    keys[g] = (hi - lo < kScheduleGroup) ? 0xFFFFFFFFu : ~min(mx, 0xFFFFFFFEu);
+    vals[g] = (uint32_t)g;
+}
+
+__global__ void k_permute_groups(const uint32_t* __restrict__ groups, const uint32_t* __restrict__ base, int n,
+                                 uint32_t* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // output position
+    if (i >= n) return;
+    const int g = (int)groups[i / kScheduleGroup];
+    out[i] = base[g * kScheduleGroup + (i % kScheduleGroup)];
+}
+}  // namespace
+
+size_t cost_schedule_scratch_bytes(int64_t n)
+{
+    const int64_t g = (n + kScheduleGroup - 1) / kScheduleGroup;
+    return ((g * 4 + 255) / 256) * 256 * 2 + radix_sort_scratch_bytes(g);
+}
+
+cudaError_t launch_cost_schedule(cudaStream_t s, const uint32_t* cost, const uint32_t* base_order, int n,
+                                 uint32_t* new_order, void* scratch, size_t scratch_bytes)
+{
+    if (n == 0) return cudaSuccess;
+    if (scratch_bytes < cost_schedule_scratch_bytes(n)) return cudaErrorInvalidValue;
+    const int g = (n + kScheduleGroup - 1) / kScheduleGroup;
+    uint32_t* keys = (uint32_t*)scratch;
+    uint32_t* vals = (uint32_t*)((char*)scratch + ((g * 4 + 255) / 256) * 256);
+    char* rest = (char*)scratch + ((g * 4 + 255) / 256) * 256 * 2;
+    k_group_cost<<<(g + 255) / 256, 256, 0, s>>>(cost, base_order, n, keys, vals);
+    cudaError_t e = radix_sort_pairs_u32(s, keys, vals, g, 32, rest, scratch_bytes - (rest - (char*)scratch));
+    if (e != cudaSuccess) return e;
+    k_permute_groups<<<(n + 255) / 256, 256, 0, s>>>(vals, base_order, n, new_order);
     return cudaGetLastError();
 }
 

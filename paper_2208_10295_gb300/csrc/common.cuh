@@ -105,6 +105,7 @@ struct LaunchCfg {
     int blocks_per_sm;
     int tile_rays;
     int ray_order;
+    int traversal;
 };
 
 // ------------------------------------------------------------------ kernel launchers
@@ -130,12 +131,13 @@ struct WorkCount {
     unsigned long long* totals;   // [0] node visits, [1] triangle tests
     uint32_t* node_bits;          // one bit per internal node touched
     uint32_t* leaf_bits;          // one bit per triangle tested
+    uint32_t* beam_cost;          // optional, dense per beam: node fetches + triangle tests
 };
 cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* sensors_dev,
                         const FrameDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
                         int64_t n_tiles, TableDev table, uint64_t seed, BeamsOut out, int* status,
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
-                        const WorkCount* count = nullptr);
+                        int64_t n_beams_total, const WorkCount* count = nullptr);
 cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_words, unsigned long long* total);
 cudaError_t launch_compact(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev,
                            int n_frames, int64_t n_beams_total, const uint8_t* valid, BeamsOut dense,
@@ -145,6 +147,11 @@ size_t compact_scratch_bytes(int64_t n_beams_total);
 cudaError_t launch_ray_order(cudaStream_t s, const float* dirs, int n_beams, uint32_t* order,
                              void* scratch, size_t scratch_bytes);
 size_t ray_order_scratch_bytes(int64_t n_beams);
+// Reorders 32-ray groups of `base_order` by their largest measured beam cost,
+// most expensive first (cost indexed by beam).
+cudaError_t launch_cost_schedule(cudaStream_t s, const uint32_t* cost, const uint32_t* base_order, int n_beams,
+                                 uint32_t* new_order, void* scratch, size_t scratch_bytes);
+size_t cost_schedule_scratch_bytes(int64_t n_beams);
 
 // adjoint.cu
 cudaError_t launch_build_tables(cudaStream_t s, const float* params, int M, float* table);

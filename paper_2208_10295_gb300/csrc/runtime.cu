@@ -43,7 +43,8 @@ struct SensorSlot {
     bool set = false;
     int64_t n_beams = 0;
     float* dirs_dev = nullptr;
-    uint32_t* order_dev = nullptr;
+    uint32_t* order_dev = nullptr;       // the order the cast kernel follows
+    uint32_t* base_order_dev = nullptr;  // Morton order of the beam directions
     SensorDev dev{};
 };
 
@@ -78,7 +79,7 @@ struct lidar_ctx {
     size_t frames_cap = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
-    LaunchCfg cfg{128, 8, 128, 1};
+    LaunchCfg cfg{128, 8, 32, 1, 0};
     std::set<lidar_scene*> scenes;
 };
 
@@ -215,6 +216,7 @@ void lidar_destroy(lidar_ctx* c)
     for (auto& sl : c->slots) {
         cudaFree(sl.dirs_dev);
         cudaFree(sl.order_dev);
+        cudaFree(sl.base_order_dev);
     }
     cudaFree(c->sensors_dev);
     cudaFree(c->frames_dev);
@@ -357,12 +359,15 @@ lidar_status lidar_set_sensor(lidar_ctx* c, int32_t slot, const lidar_sensor_des
         LIDAR_CUDA(cudaStreamSynchronize(c->stream));
         cudaFree(sl.dirs_dev);
         cudaFree(sl.order_dev);
+        cudaFree(sl.base_order_dev);
         sl = SensorSlot();
     }
     if (dev_alloc((void**)&sl.dirs_dev, n * 3 * sizeof(float)) != cudaSuccess ||
-        dev_alloc((void**)&sl.order_dev, n * sizeof(uint32_t)) != cudaSuccess) {
+        dev_alloc((void**)&sl.order_dev, n * sizeof(uint32_t)) != cudaSuccess ||
+        dev_alloc((void**)&sl.base_order_dev, n * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(sl.dirs_dev);
+        cudaFree(sl.order_dev);
         sl = SensorSlot();
         set_error("lidar_set_sensor: device allocation failed");
         return LIDAR_ENOMEM;
@@ -370,7 +375,9 @@ lidar_status lidar_set_sensor(lidar_ctx* c, int32_t slot, const lidar_sensor_des
     LIDAR_CUDA(cudaMemcpyAsync(sl.dirs_dev, dirs.data(), n * 3 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     lidar_status st = ensure_scratch(c, ray_order_scratch_bytes(n));
     if (st != LIDAR_OK) return st;
-    LIDAR_CUDA(launch_ray_order(c->stream, sl.dirs_dev, (int)n, sl.order_dev, c->scratch, c->scratch_bytes));
+    LIDAR_CUDA(launch_ray_order(c->stream, sl.dirs_dev, (int)n, sl.base_order_dev, c->scratch, c->scratch_bytes));
+    LIDAR_CUDA(cudaMemcpyAsync(sl.order_dev, sl.base_order_dev, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                               c->stream));
     SensorDev& sd = sl.dev;
     sd.dirs = sl.dirs_dev;
     sd.order = sl.order_dev;
@@ -545,7 +552,7 @@ lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_fram
     }
     SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes};
     LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, c->frames_dev, n_frames, c->tile_prefix_dev, n_tiles,
-                           c->table, seed, out, c->status_dev, c->work_counter, c->cfg, c->num_sms));
+                           c->table, seed, out, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total));
     if (points) {
         char* comp = dense_base + dense_bytes;
         LIDAR_CUDA(launch_compact(c->stream, c->sensors_dev, c->frames_dev, n_frames, n_total, out.valid, out,
@@ -637,40 +644,61 @@ lidar_status lidar_cast_backward_mse_noalloc(void* cuda_stream, int64_t n, const
     return LIDAR_OK;
 }
 
-lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
-                              uint64_t seed, lidar_work_counts* out)
+// Instrumented cast: totals h[0..3] (node fetches, triangle tests, distinct
+// nodes, distinct triangles); optionally the per-beam cost (dense layout) in
+// scratch.  `tail_bytes` of scratch after the cost array are left free for the
+// caller (returned through *tail).
+static lidar_status counting_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames,
+                                  int32_t n_frames, uint64_t seed, bool want_cost, size_t tail_bytes,
+                                  unsigned long long h[4], uint32_t** cost, void** tail, int64_t* n_total_out)
 {
-    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr && out != nullptr, "lidar_count_work: NULL argument");
-    LIDAR_CHECK_ARG(scene->ctx == c, "lidar_count_work: scene belongs to another context");
+    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr, "counting cast: NULL argument");
+    LIDAR_CHECK_ARG(scene->ctx == c, "counting cast: scene belongs to another context");
     if (c->table.table == nullptr) {
-        set_error("lidar_count_work: no material table (lidar_set_materials)");
+        set_error("counting cast: no material table (lidar_set_materials)");
         return LIDAR_ESTATE;
     }
-    DeviceGuard g(c->device);
     int64_t n_total = 0, n_tiles = 0;
     lidar_status st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles);
     if (st != LIDAR_OK) return st;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const int64_t node_words = (scene->n_nodes + 31) / 32 + 1, leaf_words = (scene->n_tris + 31) / 32 + 1;
-    const size_t bytes = 64 + (node_words + leaf_words) * 4 + ((n_total + 255) / 256) * 256;
+    const size_t head = al(64 + (node_words + leaf_words) * 4);
+    const size_t bytes = head + al(n_total) + (want_cost ? al(4 * n_total) : 0) + tail_bytes;
     st = ensure_scratch(c, bytes);
     if (st != LIDAR_OK) return st;
     char* p = (char*)c->scratch;
     unsigned long long* totals = (unsigned long long*)p;
     uint32_t* node_bits = (uint32_t*)(p + 64);
     uint32_t* leaf_bits = node_bits + node_words;
-    uint8_t* valid = (uint8_t*)(leaf_bits + leaf_words);
+    uint8_t* valid = (uint8_t*)(p + head);
+    uint32_t* cost_dev = want_cost ? (uint32_t*)(p + head + al(n_total)) : nullptr;
+    if (tail) *tail = p + head + al(n_total) + (want_cost ? al(4 * n_total) : 0);
+    if (cost) *cost = cost_dev;
     LIDAR_CUDA(cudaMemsetAsync(p, 0, 64 + (node_words + leaf_words) * 4, c->stream));
-    WorkCount wc{totals, node_bits, leaf_bits};
+    WorkCount wc{totals, node_bits, leaf_bits, cost_dev};
     BeamsOut dense{};
     dense.valid = valid;
     SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes};
     LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, c->frames_dev, n_frames, c->tile_prefix_dev, n_tiles,
-                           c->table, seed, dense, c->status_dev, c->work_counter, c->cfg, c->num_sms, &wc));
+                           c->table, seed, dense, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total,
+                           &wc));
     LIDAR_CUDA(launch_popcount(c->stream, node_bits, node_words, totals + 2));
     LIDAR_CUDA(launch_popcount(c->stream, leaf_bits, leaf_words, totals + 3));
-    unsigned long long h[4];
-    LIDAR_CUDA(cudaMemcpyAsync(h, totals, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    LIDAR_CUDA(cudaMemcpyAsync(h, totals, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    if (n_total_out) *n_total_out = n_total;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
+                              uint64_t seed, lidar_work_counts* out)
+{
+    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr && out != nullptr, "lidar_count_work: NULL argument");
+    DeviceGuard g(c->device);
+    unsigned long long h[4];
+    lidar_status st = counting_cast(c, scene, frames, n_frames, seed, false, 0, h, nullptr, nullptr, nullptr);
+    if (st != LIDAR_OK) return st;
     uint64_t rays = 0;
     for (int32_t k = 0; k < n_frames; ++k) {
         const SensorSlot& sl = c->slots[frames[k].sensor];
@@ -684,6 +712,46 @@ lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lida
     return LIDAR_OK;
 }
 
+lidar_status lidar_schedule_by_cost(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frame, uint64_t seed)
+{
+    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr && frame != nullptr, "lidar_schedule_by_cost: NULL argument");
+    const int slot = frame->sensor;
+    LIDAR_CHECK_ARG(slot >= 0 && slot < LIDAR_MAX_SENSORS, "lidar_schedule_by_cost: slot out of range");
+    if (!c->slots[slot].set) {
+        set_error("lidar_schedule_by_cost: no sensor in this slot");
+        return LIDAR_ESTATE;
+    }
+    DeviceGuard g(c->device);
+    SensorSlot& sl = c->slots[slot];
+    const int64_t n = sl.n_beams;
+    unsigned long long h[4];
+    uint32_t* cost = nullptr;
+    void* tail = nullptr;
+    lidar_status st = counting_cast(c, scene, frame, 1, seed, true, cost_schedule_scratch_bytes(n), h, &cost,
+                                    &tail, nullptr);
+    if (st != LIDAR_OK) return st;
+    const size_t tail_bytes = c->scratch_bytes - (size_t)((char*)tail - (char*)c->scratch);
+    LIDAR_CUDA(launch_cost_schedule(c->stream, cost, sl.base_order_dev, (int)n, sl.order_dev, tail, tail_bytes));
+    LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    return LIDAR_OK;
+}
+
+lidar_status lidar_reset_schedule(lidar_ctx* c, int32_t slot)
+{
+    LIDAR_CHECK_ARG(c != nullptr, "lidar_reset_schedule: ctx is NULL");
+    LIDAR_CHECK_ARG(slot >= 0 && slot < LIDAR_MAX_SENSORS, "lidar_reset_schedule: slot out of range");
+    if (!c->slots[slot].set) {
+        set_error("lidar_reset_schedule: no sensor in this slot");
+        return LIDAR_ESTATE;
+    }
+    DeviceGuard g(c->device);
+    SensorSlot& sl = c->slots[slot];
+    LIDAR_CUDA(cudaMemcpyAsync(sl.order_dev, sl.base_order_dev, sl.n_beams * sizeof(uint32_t),
+                               cudaMemcpyDeviceToDevice, c->stream));
+    LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    return LIDAR_OK;
+}
+
 lidar_status lidar_get_launch_config(lidar_ctx* c, lidar_launch_config* out)
 {
     LIDAR_CHECK_ARG(c != nullptr && out != nullptr, "lidar_get_launch_config: NULL argument");
@@ -691,22 +759,26 @@ lidar_status lidar_get_launch_config(lidar_ctx* c, lidar_launch_config* out)
     out->blocks_per_sm = c->cfg.blocks_per_sm;
     out->tile_rays = c->cfg.tile_rays;
     out->ray_order = c->cfg.ray_order;
+    out->traversal = c->cfg.traversal;
     return LIDAR_OK;
 }
 
 lidar_status lidar_set_launch_config(lidar_ctx* c, const lidar_launch_config* cfg)
 {
     LIDAR_CHECK_ARG(c != nullptr && cfg != nullptr, "lidar_set_launch_config: NULL argument");
-    LIDAR_CHECK_ARG(cfg->block_threads >= 32 && cfg->block_threads <= 1024 && cfg->block_threads % 32 == 0,
-                    "lidar_set_launch_config: block_threads must be a multiple of 32 in [32, 1024]");
+    LIDAR_CHECK_ARG(cfg->block_threads >= 32 && cfg->block_threads <= 256 && cfg->block_threads % 32 == 0,
+                    "lidar_set_launch_config: block_threads must be a multiple of 32 in [32, 256]");
     LIDAR_CHECK_ARG(cfg->blocks_per_sm >= 1 && cfg->blocks_per_sm <= 64, "lidar_set_launch_config: blocks_per_sm in [1, 64]");
-    LIDAR_CHECK_ARG(cfg->tile_rays >= 1 && cfg->tile_rays <= (1 << 20), "lidar_set_launch_config: tile_rays in [1, 2^20]");
+    LIDAR_CHECK_ARG(cfg->tile_rays >= 32 && cfg->tile_rays <= (1 << 20) && cfg->tile_rays % 32 == 0,
+                    "lidar_set_launch_config: tile_rays must be a multiple of 32 in [32, 2^20]");
     LIDAR_CHECK_ARG(cfg->ray_order == 0 || cfg->ray_order == 1, "lidar_set_launch_config: ray_order is 0 or 1");
+    LIDAR_CHECK_ARG(cfg->traversal == 0 || cfg->traversal == 1, "lidar_set_launch_config: traversal is 0 or 1");
     DeviceGuard g(c->device);
     c->cfg.block_threads = cfg->block_threads;
     c->cfg.blocks_per_sm = cfg->blocks_per_sm;
     c->cfg.tile_rays = cfg->tile_rays;
     c->cfg.ray_order = cfg->ray_order;
+    c->cfg.traversal = cfg->traversal;
     for (int s = 0; s < LIDAR_MAX_SENSORS; ++s)
         if (c->slots[s].set) {
             lidar_status st = upload_sensor_slot(c, s);

@@ -178,9 +178,32 @@ __device__ __forceinline__ void child_boxes(const float4 n0, const float4 n1, co
 // Closest hit in (kTEps, t_max] by BVH traversal with a per-thread stack of
 // deferred far children.  Returns false if the stack would overflow (the
 // build refuses trees deeper than the stack, so this does not happen).
+//
+// The stack's first kSharedStack entries live in shared memory, laid out
+// [depth][thread] (`sh` points at this thread's column, `sh_stride` = threads
+// per block), so lanes at different depths still hit distinct banks; deeper
+// entries go to a per-thread local array.
+constexpr int kSharedStack = 24;
+
+struct SplitStack {
+    int2* sh;
+    int sh_stride;
+    int2 local[kTraversalStack - kSharedStack];
+    __device__ __forceinline__ void put(int i, int2 e)
+    {
+        if (i < kSharedStack) sh[i * sh_stride] = e;
+        else local[i - kSharedStack] = e;
+    }
+    __device__ __forceinline__ int2 get(int i) const
+    {
+        return i < kSharedStack ? sh[i * sh_stride] : local[i - kSharedStack];
+    }
+};
+
 template <bool kCount = false>
 __device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p, float t_max, HitRec& h,
-                                              const WorkCount* wc = nullptr)
+                                              const WorkCount* wc, int2* sh_stack, int sh_stride,
+                                              unsigned* cost = nullptr)
 {
     unsigned long long n_nodes = 0, n_tris = 0;
     h.t = t_max;
@@ -188,7 +211,9 @@ __device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p
     h.idx = 0xFFFFFFFFu;
     h.leaf = -1;
     if (S.n_tris == 0) return true;
-    int2 stack[kTraversalStack];
+    SplitStack stack;
+    stack.sh = sh_stack;
+    stack.sh_stride = sh_stride;
     int sp = 0;
     int node = 0;
     while (true) {
@@ -225,7 +250,7 @@ __device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p
         if (hitL && hitR) {
             const bool lfirst = tL <= tR;
             if (sp >= kTraversalStack) return false;
-            stack[sp++] = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? tR : tL));
+            stack.put(sp++, make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? tR : tL)));
             node = lfirst ? cl : cr;
             continue;
         }
@@ -233,7 +258,7 @@ __device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p
         if (hitR) { node = cr; continue; }
         bool found = false;
         while (sp > 0) {
-            const int2 e = stack[--sp];
+            const int2 e = stack.get(--sp);
             if (__int_as_float(e.y) <= h.cull) {
                 node = e.x;
                 found = true;
@@ -245,8 +270,113 @@ __device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p
     if (kCount) {
         atomicAdd(&wc->totals[0], n_nodes);
         atomicAdd(&wc->totals[1], n_tris);
+        if (cost) *cost += (unsigned)(n_nodes + n_tris);
     }
     return true;
+}
+
+// Warp-synchronous variant of trace_closest (same result).  All 32 lanes of
+// the warp must call it together; lanes with `active` false take part in the
+// warp votes only.  Triangle tests are postponed: a lane that reaches a leaf
+// parks it (at most two, one node's children) and waits while other lanes
+// still descend, so the triangle tests run with most lanes busy instead of
+// one or two lanes per node step (Aila & Laine, "Understanding the Efficiency
+// of Ray Traversal on GPUs", HPG 2009: while-while traversal).
+template <bool kCount = false>
+__device__ __forceinline__ bool trace_closest_warp(const SceneDev& S, const RayPre& p, float t_max, HitRec& h,
+                                                   bool active, const WorkCount* wc = nullptr)
+{
+    unsigned long long n_nodes = 0, n_tris = 0;
+    h.t = t_max;
+    h.cull = t_max * kBestScale;
+    h.idx = 0xFFFFFFFFu;
+    h.leaf = -1;
+    int2 stack[kTraversalStack];
+    int sp = 0;
+    int node = (active && S.n_tris > 0) ? 0 : -1;
+    float node_t = 0.0f;  // entry distance of `node` (culled when it exceeds the best hit)
+    int pend0 = -1, pend1 = -1;
+    bool ok = true;
+    while (__any_sync(0xffffffffu, node >= 0 || pend0 >= 0)) {
+        // descend until this lane holds a leaf or has nothing left
+        while (__any_sync(0xffffffffu, node >= 0 && pend0 < 0)) {
+            if (node >= 0 && pend0 < 0) {
+                if (node_t > h.cull) {
+                    node = -1;
+                } else {
+                    if (kCount) {
+                        ++n_nodes;
+                        atomicOr(&wc->node_bits[node >> 5], 1u << (node & 31));
+                    }
+                    const float4 n0 = __ldg(&S.nodes[4 * (int64_t)node + 0]);
+                    const float4 n1 = __ldg(&S.nodes[4 * (int64_t)node + 1]);
+                    const float4 n2 = __ldg(&S.nodes[4 * (int64_t)node + 2]);
+                    const float4 n3 = __ldg(&S.nodes[4 * (int64_t)node + 3]);
+                    bool hitL, hitR;
+                    float tL, tR;
+                    child_boxes(n0, n1, n2, p, h.cull, hitL, hitR, tL, tR);
+                    const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+                    if (hitL && cl < 0) { pend0 = ~cl; hitL = false; }
+                    if (hitR && cr < 0) {
+                        if (pend0 < 0) pend0 = ~cr; else pend1 = ~cr;
+                        hitR = false;
+                    }
+                    if (hitL && hitR) {
+                        const bool lfirst = tL <= tR;
+                        if (sp >= kTraversalStack) {
+                            ok = false;
+                            node = -1;
+                            sp = 0;
+                        } else {
+                            stack[sp++] = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? tR : tL));
+                            node = lfirst ? cl : cr;
+                            node_t = lfirst ? tL : tR;
+                        }
+                    } else if (hitL) {
+                        node = cl;
+                        node_t = tL;
+                    } else if (hitR) {
+                        node = cr;
+                        node_t = tR;
+                    } else {
+                        node = -1;
+                    }
+                }
+                if (node < 0) {
+                    while (sp > 0) {
+                        const int2 e = stack[--sp];
+                        if (__int_as_float(e.y) <= h.cull) {
+                            node = e.x;
+                            node_t = __int_as_float(e.y);
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+        // intersect the parked triangles
+        if (pend0 >= 0) {
+            if (kCount) {
+                ++n_tris;
+                atomicOr(&wc->leaf_bits[pend0 >> 5], 1u << (pend0 & 31));
+            }
+            intersect_triangle(S.tris, pend0, p, t_max, h);
+            pend0 = -1;
+        }
+        if (pend1 >= 0) {
+            if (kCount) {
+                ++n_tris;
+                atomicOr(&wc->leaf_bits[pend1 >> 5], 1u << (pend1 & 31));
+            }
+            intersect_triangle(S.tris, pend1, p, t_max, h);
+            pend1 = -1;
+        }
+    }
+    if (kCount) {
+        atomicAdd(&wc->totals[0], n_nodes);
+        atomicAdd(&wc->totals[1], n_tris);
+    }
+    return ok;
 }
 
 }  // namespace lidar
