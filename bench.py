@@ -1,12 +1,18 @@
 """Benchmark: LiDAR rays/s on the 128-channel, 2048-azimuth (262,144 beams)
-sensor over the ~1.04M-triangle terrain + objects scene.
+sensor over the 1,036,288-triangle terrain + objects scene.
 
 One step = one pass of the whole per-beam path for one frame: ray generation,
 closest-hit traversal, surface attributes, incidence angle, reflectance lerp,
 Philox range noise, cut-offs, intensity and the ordered compaction of the
 kept returns into a point cloud.  The BVH is built once per scene (timed
 separately, reported as build_ms).  L2 is flushed (256 MiB write) before every
-timed step.
+timed step.  The launch configuration and ray schedule come from the
+autotuner; the cost schedule is measured on a pose 1.1 m away from the timed
+one (as the previous frame of a moving sensor would be).
+
+Also reported (extra keys): the 8-sensor x 64-frame batch replayed as one
+CUDA graph, forward + adjoint of the 16-frame differentiation workload next to
+the plain single-frame forward, and the ~10.7M-triangle city with 7 sub-rays.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -17,7 +23,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -33,6 +38,7 @@ METRIC = "LiDAR rays/sec (128-ch, 1M-tri scene) & roofline %; fwd+bwd vs plain f
 UNIT = "rays/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6800.0
+POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal, material, instance, beam, frame
 
 
 def dist_env():
@@ -43,10 +49,16 @@ def dist_env():
 def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
-            p = json.load(f)
-        return p, "measured"
+            return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": HBM_FALLBACK_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def shard_frames(n_frames_total: int, rank: int, world: int):
+    """Contiguous block of frame indices owned by `rank` (weak scaling: each
+    rank gets the same number of frames)."""
+    per = n_frames_total // world
+    return list(range(rank * per, (rank + 1) * per))
 
 
 class ClockSampler:
@@ -106,12 +118,29 @@ def fp32_peak_tflops(torch, sm_mhz):
     return props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def event_time(torch, stream, fn, flush=None, reps=10, warm=2):
+    ts = []
+    for i in range(reps + warm):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        if i >= warm:
+            ts.append(a.elapsed_time(b))
+    return statistics.mean(ts)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
     import synth
     from paper_2208_10295_gb300 import Lidar
     from paper_2208_10295_gb300.build import build as build_lib
+    from paper_2208_10295_gb300.tune import autotune
 
     torch.cuda.set_device(local_rank)
     if world > 1:
@@ -120,20 +149,21 @@ def run_ours(args, rank, world, local_rank):
     build_lib()
     dev = torch.device("cuda", local_rank)
     w = synth.cfg1()
-    # weak scaling: rank r casts its own frames along the trajectory (no data-path collective)
-    w3 = synth.cfg3(n_frames=max(world, 1))
     frames = w.frames.copy()
     if world > 1:
-        frames = w3.frames[rank:rank + 1].copy()
+        # weak scaling: every rank casts its own frame of the trajectory, no data-path collective
+        w3 = synth.cfg3(n_frames=world)
+        frames = w3.frames[shard_frames(world, rank, world)].copy()
     L = Lidar(local_rank)
     stream = L.stream
     scene = L.build_scene(w.scene.verts, w.scene.tris, w.scene.mat, w.scene.inst)
     L.set_sensor(0, w.sensors[0])
     table = L.build_tables(torch.tensor(w.params, device=dev))
     L.set_materials(table)
-    if args.tune:
-        from paper_2208_10295_gb300.tune import autotune
-        autotune(L, scene, frames, w.seed)
+    near = frames.copy()
+    near[0]["pose"][3] += 1.0
+    near[0]["pose"][7] += 0.5
+    tuned_cfg, tuned_ms = autotune(L, scene, frames, w.seed, schedule_frames=near, use_cache=not args.retune)
     n_beams = L.total_beams(frames)
     build_ms = scene.info()["build_ms"]
     pts = L.alloc_points(n_beams)
@@ -169,8 +199,7 @@ def run_ours(args, rank, world, local_rank):
     st = L.sync_status()
     if st != 0:
         raise RuntimeError(f"device status {st}")
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -179,42 +208,34 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- dominant kernel alone (the cast kernel, dense valid flags out)
     dense = L.alloc_beams(n_beams, ("valid",))
-    k_ms = []
-    for i in range(min(args.steps, 200) + 3):
-        flush.zero_()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        L.cast_into(scene, frames, w.seed, dense)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        if i >= 3:
-            k_ms.append(s0.elapsed_time(s1))
-    kernel_ms = statistics.mean(k_ms)
+    kernel_ms = event_time(torch, stream, lambda: L.cast_into(scene, frames, w.seed, dense), flush,
+                           reps=min(args.steps, 200), warm=3)
 
     # ---- end to end through host buffers: pose in, point cloud out
     host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in pts.items()}
-    e2e_ms = []
-    bo_total = 0
+    e2e_ms, bo_total = [], 0
     n_e2e = min(args.steps, 200)
     for i in range(args.warmup + n_e2e):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        L.cast_into(scene, frames, w.seed, None, pts)   # copies the host frame array in
+        L.cast_into(scene, frames, w.seed, None, pts)   # copies the host frame record in
         host["count"].copy_(pts["count"], non_blocking=True)
         stream.synchronize()
         c = int(host["count"].item())
         for k in ("xyz", "range", "intensity", "normal", "material", "instance", "beam", "frame"):
             host[k][:c].copy_(pts[k][:c], non_blocking=True)
         stream.synchronize()
-        t1 = time.perf_counter()
         if i >= args.warmup:
-            e2e_ms.append((t1 - t0) * 1e3)
-            bo_total += 8 + c * (12 + 4 + 4 + 12 + 2 + 4 + 4 + 4)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            bo_total += 8 + c * POINT_BYTES
     e2e_step_ms = statistics.mean(e2e_ms)
 
     # ---- algorithmic work of one launch (instrumented run of the same kernel)
     counters = L.count_work(scene, frames, w.seed)
+
+    extras = {}
+    if not args.no_extras and world == 1:
+        extras = run_extras(args, torch, L, scene, w, table, flush, stream, step, tuned_cfg)
 
     if rank != 0:
         if world > 1:
@@ -222,12 +243,11 @@ def run_ours(args, rank, world, local_rank):
         return None
     peaks, peaks_src = load_peaks()
     clocks = clk.summary()
-    rays_total = n_beams * args.steps * world
-    value = rays_total / (total_ms / 1e3)
+    value = n_beams * args.steps * world / (total_ms / 1e3)
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
-    uniq_bytes = counters["unique_node_bytes"] + counters["unique_tri_bytes"] + counters["io_bytes"]
     visit_bytes = counters["node_visits"] * 64 + counters["tri_tests"] * 48 + counters["io_bytes"]
-    achieved = uniq_bytes / (kernel_ms / 1e3) / 1e9
+    uniq_bytes = counters["unique_node_bytes"] + counters["unique_tri_bytes"] + counters["io_bytes"]
+    achieved = visit_bytes / (kernel_ms / 1e3) / 1e9
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
     flops = counters["node_visits"] * 2 * 24 + counters["tri_tests"] * 40
     alu_tf = flops / (kernel_ms / 1e3) / 1e12
@@ -235,29 +255,123 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "cfg1: 128-ch x 2048 az (262,144 beams) over 1,036,288-tri terrain+objects "
+        "config": {"workload": "cfg1: 128-ch x 2048 az (262,144 beams) over the 1,036,288-tri terrain+objects "
                                "scene, one frame per step incl. ordered compaction",
                    "beams_per_step_per_gpu": n_beams, "tris": int(w.scene.n_tris),
                    "l2": "flushed (256 MiB write) before every timed step", "build_ms": build_ms,
-                   "points_per_step": n_points, "launch": L.launch_config()},
+                   "points_per_step": n_points, "launch": tuned_cfg},
         "gpu_launches": 4 * args.steps,
         "e2e": {"value": n_beams / (e2e_step_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 56,
                 "d2h_bytes_per_step": bo_total / n_e2e},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
                      "peak_source": f"{peaks_src} hbm_gbs (STREAM-style copy)",
-                     "bytes_per_launch": uniq_bytes, "kernel": "k_cast", "kernel_ms": kernel_ms},
+                     "bytes_per_launch": visit_bytes, "kernel": "k_cast", "kernel_ms": kernel_ms,
+                     "note": "algorithmic bytes = node fetches x 64 B + triangle tests x 48 B + 17 B/ray I/O; "
+                             "L1/L2 serve most of them (compulsory DRAM bytes in compulsory_bytes_per_launch)",
+                     "compulsory_bytes_per_launch": uniq_bytes,
+                     "compulsory_frac": uniq_bytes / (kernel_ms / 1e3) / 1e9 / hbm},
         "work_per_ray": {k: v / n_beams for k, v in counters.items()},
-        "visit_bytes_per_s_GBps": visit_bytes / (kernel_ms / 1e3) / 1e9,
-        "alu": {"achieved_tflops": alu_tf, "peak_tflops": fp32_peak_tflops(torch, sm_mhz),
-                "frac": alu_tf / fp32_peak_tflops(torch, sm_mhz)},
+        "alu": {"flops_per_launch": flops, "achieved_tflops": alu_tf, "peak_tflops": fp32_peak_tflops(torch, sm_mhz),
+                "frac": alu_tf / fp32_peak_tflops(torch, sm_mhz), "peak_source": "152 SMs x 128 FP32 lanes x 2 x "
+                                                                                "median SM clock under load"},
         "clocks": clocks,
     }
+    line.update(extras)
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, args)
     if world > 1:
         torch.distributed.destroy_process_group()
     return line
+
+
+def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tuned_cfg):
+    import synth
+    from paper_2208_10295_gb300.tune import apply as apply_cfg
+    from paper_2208_10295_gb300.tune import autotune
+    out = {}
+    single_ms = event_time(torch, stream, single_step, flush, reps=20, warm=3)
+    # ---- cfg2: 8 sensors x 64 frames as one CUDA graph replay
+    w2 = synth.cfg2()
+    for s, spec in enumerate(w2.sensors):
+        L.set_sensor(s, spec)
+    L.set_materials(table)
+    first = np.concatenate([w2.frames[w2.frames["sensor"] == s][:1] for s in range(len(w2.sensors))])
+    cfg2, _ = autotune(L, scene, w2.frames[: 8 * 4], w2.seed, schedule_frames=first, use_cache=not args.retune)
+    B = L.batch(w2.frames)
+    pts2 = L.alloc_points(B.n_beams)
+    poses = torch.tensor(np.stack([f["pose"] for f in w2.frames]), device=L.device)
+    G = B.graph(scene, w2.seed, points=pts2, poses=poses)
+    g_ms = event_time(torch, stream, G.launch, flush, reps=5, warm=2)
+    out["batched"] = {"workload": "cfg2: 8 sensors (2x16, 2x32, 2x64, 1x128 spinning, 256x128 raster) x 64 frames, "
+                                  "one CUDA-graph replay incl. pose upload and ordered compaction",
+                      "rays_per_launch": B.n_beams, "ms_per_launch": g_ms,
+                      "rays_per_s": B.n_beams / (g_ms / 1e3), "points": int(pts2["count"].item()),
+                      "launch": cfg2}
+    G.free()
+    B.free()
+    del pts2
+    # ---- cfg3: 16 frames forward (dense tape) + fused-MSE adjoint vs plain forward
+    w3 = synth.cfg3()
+    L.set_sensor(0, w3.sensors[0])
+    apply_cfg(L, scene, tuned_cfg, w3.frames[:1], w3.seed)
+    th = L.build_tables(torch.tensor(w3.hidden_params, device=L.device))
+    tp = torch.tensor(w3.params, device=L.device)
+    n3 = L.total_beams(w3.frames)
+    tgt = L.alloc_beams(n3, ("valid", "intensity", "mat", "theta_deg", "rf"))
+    L.set_materials(th)
+    L.cast_into(scene, w3.frames, w3.seed, tgt)
+    tape = L.alloc_beams(n3, ("valid", "intensity", "mat", "theta_deg", "rf"))
+    loss = torch.zeros(1, device=L.device)
+    gT = torch.zeros((tp.shape[0], 91), device=L.device)
+    gg = torch.zeros(1, device=L.device)
+
+    def fwd():
+        T = L.build_tables(tp)
+        L.set_materials(T)
+        L.cast_into(scene, w3.frames, w3.seed, tape)
+        return T
+
+    def fwd_bwd():
+        T = fwd()
+        gT.zero_()
+        gg.zero_()
+        L.cast_backward_mse(tape, 1.0, tgt["intensity"], tgt["valid"], loss, gT, gg)
+        L.build_tables_backward(tp, gT)
+
+    f_ms = event_time(torch, stream, fwd, flush, reps=10, warm=2)
+    fb_ms = event_time(torch, stream, fwd_bwd, flush, reps=10, warm=2)
+    out["differentiation"] = {"workload": "cfg3: 128-ch x 2048 az x 16 frames (4,194,304 beams), forward with tape + "
+                                          "fused MSE adjoint to the 32x91 table, widths and gain",
+                              "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "bwd_ms": fb_ms - f_ms,
+                              "plain_single_frame_fwd_ms": single_ms, "loss": float(loss.item())}
+    L.set_materials(table)
+    L.set_sensor(0, w1.sensors[0])
+    del tgt, tape
+    # ---- cfg4: the ~10.7M-triangle city, 128-ch x 4096 az x 32 frames x 7 sub-rays
+    if not args.no_city:
+        w4 = synth.cfg4()
+        scene4 = L.build_scene(w4.scene.verts, w4.scene.tris, w4.scene.mat, w4.scene.inst)
+        L.set_sensor(0, w4.sensors[0])
+        t4 = L.build_tables(torch.tensor(w4.params, device=L.device))
+        L.set_materials(t4)
+        cfg4, _ = autotune(L, scene4, w4.frames[:4], w4.seed, schedule_frames=w4.frames[:1],
+                           use_cache=not args.retune)
+        B4 = L.batch(w4.frames)
+        pts4 = L.alloc_points(B4.n_beams)
+        c_ms = event_time(torch, stream, lambda: B4.cast_into(scene4, w4.seed, None, pts4), None, reps=3, warm=1)
+        info = scene4.info()
+        out["city"] = {"workload": "cfg4: 10.7M-tri city (4096 m terrain + 20,000 buildings), 128-ch x 4096 az x "
+                                   "32 frames x 7 sub-rays (0.1 mrad), strongest return, ordered compaction",
+                       "tris": int(w4.scene.n_tris), "beams": B4.n_beams, "subrays": B4.n_beams * 7,
+                       "ms": c_ms, "subrays_per_s": B4.n_beams * 7 / (c_ms / 1e3),
+                       "build_ms": info["build_ms"], "bvh_depth": info["max_depth"],
+                       "points": int(pts4["count"].item()), "launch": cfg4}
+        B4.free()
+        scene4.free()
+        L.set_materials(table)
+        L.set_sensor(0, w1.sensors[0])
+    return out
 
 
 def cpu_baseline(w, args, n_beams=None):
@@ -290,14 +404,13 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         vals.append(cpu_baseline(w, args, n_beams=args.ref_beams))
     total = time.perf_counter() - t0
-    nb = args.ref_beams * args.steps
-    value = nb / total
+    value = args.ref_beams * args.steps / total
     cb = vals[-1]
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "cfg1: 128-ch x 2048 az over 1,036,288-tri scene; each step a bounded "
+            "config": {"workload": "cfg1: 128-ch x 2048 az over the 1,036,288-tri scene; each step a bounded "
                                    f"sample of {args.ref_beams} beams"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                              "sample": f"{args.ref_beams} seeded beams per step"},
@@ -313,8 +426,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-beams", type=int, default=2048)
     ap.add_argument("--ref-beams", type=int, default=256)
-    ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched/differentiation/city measurements")
+    ap.add_argument("--no-city", action="store_true", help="skip the 10.7M-triangle city measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()

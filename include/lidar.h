@@ -225,6 +225,41 @@ lidar_status lidar_cast(lidar_ctx* ctx, const lidar_scene* scene, const lidar_fr
                         int32_t n_frames, uint64_t seed, const lidar_beams* beams,
                         const lidar_points* points, int64_t* n_points_dev);
 
+/* -------------------------------------------------------- batches and graphs */
+
+/* A device-resident list of frames for repeated casts (many frames along a
+ * trajectory, several sensors): the frame records are uploaded once, so casts
+ * of a batch make no host copy and can be captured into a CUDA graph.  The
+ * batch keeps the sensor slots' beam counts and the launch configuration's
+ * tile size of the moment it is created; changing either afterwards makes
+ * lidar_cast_batch return LIDAR_ESTATE (create the batch again).  Creating a
+ * batch also sizes the context's scratch for casts of it (dense records and
+ * compaction), so casting it allocates nothing.  Synchronises. */
+typedef struct lidar_batch lidar_batch;
+lidar_status lidar_batch_create(lidar_ctx* ctx, const lidar_frame* frames_host, int32_t n_frames,
+                                lidar_batch** out);
+void lidar_batch_free(lidar_batch* batch);
+
+/* Replaces every frame's pose from device memory poses_dev [n_frames][12]
+ * (row-major 3x4 sensor-to-world), asynchronously on the context stream. */
+lidar_status lidar_batch_set_poses(lidar_ctx* ctx, lidar_batch* batch, const float* poses_dev);
+
+/* lidar_cast over the frames of a batch; same outputs and semantics. */
+lidar_status lidar_cast_batch(lidar_ctx* ctx, const lidar_scene* scene, const lidar_batch* batch, uint64_t seed,
+                              const lidar_beams* beams, const lidar_points* points, int64_t* n_points_dev);
+
+/* Captures [pose update from poses_dev (if not NULL)] + lidar_cast_batch into
+ * a CUDA graph (captured on a private stream) and instantiates it.  Every
+ * lidar_graph_launch replays the whole batch with one launch on the context
+ * stream, reading the poses currently in poses_dev.  All pointers are baked
+ * into the graph and must stay valid while it is used. */
+typedef struct lidar_graph lidar_graph;
+lidar_status lidar_graph_create(lidar_ctx* ctx, const lidar_scene* scene, lidar_batch* batch,
+                                const float* poses_dev, uint64_t seed, const lidar_beams* beams,
+                                const lidar_points* points, int64_t* n_points_dev, lidar_graph** out);
+lidar_status lidar_graph_launch(lidar_graph* graph);
+void lidar_graph_free(lidar_graph* graph);
+
 /* Adjoint of the intensity with the hits and masks of the forward pass held
  * fixed.  For every beam b with tape valid[b] = 1 and grad_I_dev[b] = dL/dI_b:
  *   dL/dT[m][i]   += g rf (1 - f) dL/dI,   dL/dT[m][i+1] += g rf f dL/dI,

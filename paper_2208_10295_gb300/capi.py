@@ -97,6 +97,15 @@ _PROTOS = [
     ("lidar_set_materials", ctypes.c_int, [c_vp, c_vp, ctypes.c_int32]),
     ("lidar_cast", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
                                   ctypes.POINTER(lidar_beams), ctypes.POINTER(lidar_points), c_vp]),
+    ("lidar_batch_create", ctypes.c_int, [c_vp, c_vp, ctypes.c_int32, ctypes.POINTER(c_vp)]),
+    ("lidar_batch_free", None, [c_vp]),
+    ("lidar_batch_set_poses", ctypes.c_int, [c_vp, c_vp, c_vp]),
+    ("lidar_cast_batch", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_uint64, ctypes.POINTER(lidar_beams),
+                                        ctypes.POINTER(lidar_points), c_vp]),
+    ("lidar_graph_create", ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, ctypes.c_uint64, ctypes.POINTER(lidar_beams),
+                                          ctypes.POINTER(lidar_points), c_vp, ctypes.POINTER(c_vp)]),
+    ("lidar_graph_launch", ctypes.c_int, [c_vp]),
+    ("lidar_graph_free", None, [c_vp]),
     ("lidar_cast_backward", ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.POINTER(lidar_beams), ctypes.c_float,
                                            c_vp, c_vp, c_vp]),
     ("lidar_cast_backward_mse", ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.POINTER(lidar_beams),
@@ -164,6 +173,13 @@ lidar_build_tables = _fwd("lidar_build_tables")
 lidar_build_tables_backward = _fwd("lidar_build_tables_backward")
 lidar_set_materials = _fwd("lidar_set_materials")
 lidar_cast = _fwd("lidar_cast")
+lidar_batch_create = _fwd("lidar_batch_create")
+lidar_batch_free = _fwd("lidar_batch_free")
+lidar_batch_set_poses = _fwd("lidar_batch_set_poses")
+lidar_cast_batch = _fwd("lidar_cast_batch")
+lidar_graph_create = _fwd("lidar_graph_create")
+lidar_graph_launch = _fwd("lidar_graph_launch")
+lidar_graph_free = _fwd("lidar_graph_free")
 lidar_cast_backward = _fwd("lidar_cast_backward")
 lidar_cast_backward_mse = _fwd("lidar_cast_backward_mse")
 lidar_cast_backward_mse_noalloc = _fwd("lidar_cast_backward_mse_noalloc")

@@ -351,13 +351,18 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     const int resident = cfg.block_threads * cfg.blocks_per_sm;
     const int variant = resident <= 512 ? 2 : (resident <= 768 ? 3 : 4);
     const WorkCount none{nullptr, nullptr, nullptr, nullptr};
+    // dynamic shared memory: the per-lane traversal keeps its short stack there
+    // (kSharedStack entries per thread); the warp-synchronous one uses none.
+    // It follows the instantiated variant W, not the configuration, because
+    // the counting launch always uses the per-lane traversal.
+    const size_t stack_bytes = (size_t)kSharedStack * cfg.block_threads * sizeof(int2);
 #define LIDAR_LAUNCH_CAST(C, V, W)                                                                               \
-    k_cast<C, V, W><<<(unsigned)grid, cfg.block_threads, smem, s>>>(scene, sensors_dev, frames_dev, n_frames,    \
+    k_cast<C, V, W><<<(unsigned)grid, cfg.block_threads, (W) ? 0 : stack_bytes, s>>>(                           \
+                                                                 scene, sensors_dev, frames_dev, n_frames,        \
                                                                  tile_prefix_dev, n_tiles, table, seed, out,      \
                                                                  status, work_counter, cfg.tile_rays,             \
                                                                  C ? *count : none)
     const bool ws = cfg.traversal == 1;
-    const size_t smem = ws ? 0 : (size_t)kSharedStack * cfg.block_threads * sizeof(int2);
     if (count) {
         // the work counted does not depend on the launch shape
         LIDAR_LAUNCH_CAST(true, 4, false);
@@ -384,6 +389,22 @@ __global__ void k_popcount(const uint32_t* __restrict__ bits, int64_t n_words, u
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(total, c);
 }
 }  // namespace
+
+namespace {
+__global__ void k_set_poses(FrameDev* frames, int n_frames, const float* __restrict__ poses)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_frames * 12) return;
+    frames[i / 12].pose[i % 12] = poses[i];
+}
+}  // namespace
+
+cudaError_t launch_set_poses(cudaStream_t s, FrameDev* frames, int n_frames, const float* poses)
+{
+    if (n_frames <= 0) return cudaSuccess;
+    k_set_poses<<<(n_frames * 12 + 255) / 256, 256, 0, s>>>(frames, n_frames, poses);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_words, unsigned long long* total)
 {

@@ -53,7 +53,7 @@ __device__ __forceinline__ void raise_status(int* status, int code)
 //   v0.xyz, w = original triangle index (bits)
 //   v1.xyz, w = material (bits)
 //   v2.xyz, w = instance (bits)
-constexpr int kTraversalStack = 64;
+constexpr int kTraversalStack = 96;
 
 struct SceneDev {
     const float4* nodes;     // [n_nodes * 4]
@@ -139,6 +139,8 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
                         int64_t n_beams_total, const WorkCount* count = nullptr);
 cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_words, unsigned long long* total);
+// frames[i].pose = poses[12 i .. 12 i + 11]
+cudaError_t launch_set_poses(cudaStream_t s, FrameDev* frames, int n_frames, const float* poses);
 cudaError_t launch_compact(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev,
                            int n_frames, int64_t n_beams_total, const uint8_t* valid, BeamsOut dense,
                            const lidar_points& pts, int64_t* n_points_dev, int* status, void* scratch,

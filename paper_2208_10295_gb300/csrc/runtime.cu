@@ -510,24 +510,24 @@ static lidar_status prepare_frames(lidar_ctx* c, const lidar_frame* frames, int3
     return LIDAR_OK;
 }
 
-lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
-                        uint64_t seed, const lidar_beams* beams, const lidar_points* points, int64_t* n_points_dev)
+// scratch bytes a cast of n_total beams needs (all dense intermediates of the
+// compaction plus its own scratch): used to pre-size scratch for batches
+static size_t cast_scratch_upper_bound(int64_t n_total)
 {
-    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr, "lidar_cast: ctx/scene is NULL");
-    LIDAR_CHECK_ARG(scene->ctx == c, "lidar_cast: scene belongs to another context");
-    if (c->table.table == nullptr) {
-        set_error("lidar_cast: no material table (lidar_set_materials)");
-        return LIDAR_ESTATE;
-    }
-    LIDAR_CHECK_ARG(beams != nullptr || points != nullptr, "lidar_cast: nothing to write (beams and points NULL)");
-    LIDAR_CHECK_ARG(points == nullptr || points->capacity >= 0, "lidar_cast: negative capacity");
-    DeviceGuard g(c->device);
-    int64_t n_total = 0, n_tiles = 0;
-    lidar_status st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles);
-    if (st != LIDAR_OK) return st;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al(n_total) + 2 * al(4 * n_total) + al(12 * n_total) + al(2 * n_total) + al(4 * n_total) +
+           compact_scratch_bytes(n_total);
+}
+
+// Cast over frames already on the device.  `may_alloc` false: fail instead of
+// growing the scratch (stream capture, batches).
+static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const FrameDev* frames_dev,
+                              const int64_t* prefix_dev, int32_t n_frames, int64_t n_total, int64_t n_tiles,
+                              uint64_t seed, const lidar_beams* beams, const lidar_points* points,
+                              int64_t* n_points_dev, bool may_alloc)
+{
     BeamsOut out = to_beams_out(beams);
     // compaction reads the dense records: provide the ones the points need
-    std::vector<void*> tmp;
     char* dense_base = nullptr;
     size_t dense_bytes = 0;
     if (points) {
@@ -538,9 +538,15 @@ lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_fram
         dense_bytes = (need_valid ? al(n_total) : 0) + (need_range ? al(4 * n_total) : 0) +
                       (need_int ? al(4 * n_total) : 0) + (need_norm ? al(12 * n_total) : 0) +
                       (need_mat ? al(2 * n_total) : 0) + (need_inst ? al(4 * n_total) : 0);
-        size_t comp = compact_scratch_bytes(n_total);
-        st = ensure_scratch(c, dense_bytes + comp);
-        if (st != LIDAR_OK) return st;
+        const size_t need = dense_bytes + compact_scratch_bytes(n_total);
+        if (c->scratch_bytes < need) {
+            if (!may_alloc) {
+                set_error("cast: scratch too small for this batch (recreate the batch)");
+                return LIDAR_ESTATE;
+            }
+            lidar_status st = ensure_scratch(c, need);
+            if (st != LIDAR_OK) return st;
+        }
         char* p = (char*)c->scratch;
         dense_base = p;
         if (need_valid) { out.valid = (uint8_t*)p; p += al(n_total); }
@@ -551,15 +557,213 @@ lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_fram
         if (need_inst) { out.inst = (uint32_t*)p; p += al(4 * n_total); }
     }
     SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes};
-    LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, c->frames_dev, n_frames, c->tile_prefix_dev, n_tiles,
-                           c->table, seed, out, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total));
+    LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, frames_dev, n_frames, prefix_dev, n_tiles, c->table, seed,
+                           out, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total));
     if (points) {
         char* comp = dense_base + dense_bytes;
-        LIDAR_CUDA(launch_compact(c->stream, c->sensors_dev, c->frames_dev, n_frames, n_total, out.valid, out,
-                                  *points, n_points_dev, c->status_dev, comp,
-                                  c->scratch_bytes - dense_bytes));
+        LIDAR_CUDA(launch_compact(c->stream, c->sensors_dev, frames_dev, n_frames, n_total, out.valid, out, *points,
+                                  n_points_dev, c->status_dev, comp, c->scratch_bytes - dense_bytes));
     }
     return LIDAR_OK;
+}
+
+static lidar_status cast_checks(lidar_ctx* c, const lidar_scene* scene, const lidar_beams* beams,
+                                const lidar_points* points)
+{
+    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr, "lidar_cast: ctx/scene is NULL");
+    LIDAR_CHECK_ARG(scene->ctx == c, "lidar_cast: scene belongs to another context");
+    if (c->table.table == nullptr) {
+        set_error("lidar_cast: no material table (lidar_set_materials)");
+        return LIDAR_ESTATE;
+    }
+    LIDAR_CHECK_ARG(beams != nullptr || points != nullptr, "lidar_cast: nothing to write (beams and points NULL)");
+    LIDAR_CHECK_ARG(points == nullptr || points->capacity >= 0, "lidar_cast: negative capacity");
+    return LIDAR_OK;
+}
+
+lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
+                        uint64_t seed, const lidar_beams* beams, const lidar_points* points, int64_t* n_points_dev)
+{
+    lidar_status st = cast_checks(c, scene, beams, points);
+    if (st != LIDAR_OK) return st;
+    DeviceGuard g(c->device);
+    int64_t n_total = 0, n_tiles = 0;
+    st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles);
+    if (st != LIDAR_OK) return st;
+    return cast_impl(c, scene, c->frames_dev, c->tile_prefix_dev, n_frames, n_total, n_tiles, seed, beams, points,
+                     n_points_dev, true);
+}
+
+}  // extern "C"
+
+struct lidar_batch {
+    lidar_ctx* ctx = nullptr;
+    FrameDev* frames_dev = nullptr;
+    int64_t* prefix_dev = nullptr;
+    int32_t n_frames = 0;
+    int64_t n_total = 0, n_tiles = 0;
+    int tile_rays = 0;
+    std::vector<int32_t> slot_beams;  // beams of each slot at creation (-1 = unused)
+};
+
+struct lidar_graph {
+    lidar_ctx* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+lidar_status lidar_batch_create(lidar_ctx* c, const lidar_frame* frames, int32_t n_frames, lidar_batch** out)
+{
+    LIDAR_CHECK_ARG(c != nullptr && out != nullptr, "lidar_batch_create: NULL argument");
+    LIDAR_CHECK_ARG(frames != nullptr && n_frames > 0, "lidar_batch_create: need at least one frame");
+    *out = nullptr;
+    DeviceGuard g(c->device);
+    int64_t n_total = 0, n_tiles = 0;
+    lidar_status st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles);
+    if (st != LIDAR_OK) return st;
+    lidar_batch* b = new lidar_batch();
+    b->ctx = c;
+    b->n_frames = n_frames;
+    b->n_total = n_total;
+    b->n_tiles = n_tiles;
+    b->tile_rays = c->cfg.tile_rays;
+    b->slot_beams.assign(LIDAR_MAX_SENSORS, -1);
+    for (int s = 0; s < LIDAR_MAX_SENSORS; ++s)
+        if (c->slots[s].set) b->slot_beams[s] = (int32_t)c->slots[s].n_beams;
+    if (dev_alloc((void**)&b->frames_dev, n_frames * sizeof(FrameDev)) != cudaSuccess ||
+        dev_alloc((void**)&b->prefix_dev, n_frames * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->frames_dev);
+        delete b;
+        set_error("lidar_batch_create: device allocation failed");
+        return LIDAR_ENOMEM;
+    }
+    // the context's staging copies were made by prepare_frames: copy them over
+    cudaMemcpyAsync(b->frames_dev, c->frames_dev, n_frames * sizeof(FrameDev), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(b->prefix_dev, c->tile_prefix_dev, n_frames * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                    c->stream);
+    st = ensure_scratch(c, cast_scratch_upper_bound(n_total));
+    if (st == LIDAR_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        set_error("lidar_batch_create: stream synchronisation failed");
+        st = LIDAR_ECUDA;
+    }
+    if (st != LIDAR_OK) {
+        cudaFree(b->frames_dev);
+        cudaFree(b->prefix_dev);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return LIDAR_OK;
+}
+
+void lidar_batch_free(lidar_batch* b)
+{
+    if (!b) return;
+    DeviceGuard g(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    cudaFree(b->frames_dev);
+    cudaFree(b->prefix_dev);
+    delete b;
+}
+
+lidar_status lidar_batch_set_poses(lidar_ctx* c, lidar_batch* b, const float* poses_dev)
+{
+    LIDAR_CHECK_ARG(c != nullptr && b != nullptr && poses_dev != nullptr, "lidar_batch_set_poses: NULL argument");
+    LIDAR_CHECK_ARG(b->ctx == c, "lidar_batch_set_poses: batch belongs to another context");
+    DeviceGuard g(c->device);
+    LIDAR_CUDA(launch_set_poses(c->stream, b->frames_dev, b->n_frames, poses_dev));
+    return LIDAR_OK;
+}
+
+static lidar_status batch_valid(lidar_ctx* c, const lidar_batch* b)
+{
+    LIDAR_CHECK_ARG(b != nullptr && b->ctx == c, "lidar_cast_batch: batch is NULL or belongs to another context");
+    if (c->cfg.tile_rays != b->tile_rays) {
+        set_error("lidar_cast_batch: launch tile size changed since the batch was created");
+        return LIDAR_ESTATE;
+    }
+    for (int s = 0; s < LIDAR_MAX_SENSORS; ++s) {
+        const int32_t now = c->slots[s].set ? (int32_t)c->slots[s].n_beams : -1;
+        if (b->slot_beams[s] >= 0 && now != b->slot_beams[s]) {
+            set_error("lidar_cast_batch: a sensor slot changed since the batch was created");
+            return LIDAR_ESTATE;
+        }
+    }
+    return LIDAR_OK;
+}
+
+lidar_status lidar_cast_batch(lidar_ctx* c, const lidar_scene* scene, const lidar_batch* b, uint64_t seed,
+                              const lidar_beams* beams, const lidar_points* points, int64_t* n_points_dev)
+{
+    lidar_status st = cast_checks(c, scene, beams, points);
+    if (st != LIDAR_OK) return st;
+    st = batch_valid(c, b);
+    if (st != LIDAR_OK) return st;
+    DeviceGuard g(c->device);
+    return cast_impl(c, scene, b->frames_dev, b->prefix_dev, b->n_frames, b->n_total, b->n_tiles, seed, beams, points,
+                     n_points_dev, false);
+}
+
+lidar_status lidar_graph_create(lidar_ctx* c, const lidar_scene* scene, lidar_batch* b, const float* poses_dev,
+                                uint64_t seed, const lidar_beams* beams, const lidar_points* points,
+                                int64_t* n_points_dev, lidar_graph** out)
+{
+    LIDAR_CHECK_ARG(out != nullptr, "lidar_graph_create: out is NULL");
+    *out = nullptr;
+    lidar_status st = cast_checks(c, scene, beams, points);
+    if (st != LIDAR_OK) return st;
+    st = batch_valid(c, b);
+    if (st != LIDAR_OK) return st;
+    DeviceGuard g(c->device);
+    LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    cudaStream_t cap = nullptr;
+    LIDAR_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = c->stream;
+    c->stream = cap;
+    lidar_graph* gr = new lidar_graph();
+    gr->ctx = c;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        if (poses_dev) e = launch_set_poses(cap, b->frames_dev, b->n_frames, poses_dev);
+        if (e == cudaSuccess)
+            st = cast_impl(c, scene, b->frames_dev, b->prefix_dev, b->n_frames, b->n_total, b->n_tiles, seed, beams,
+                           points, n_points_dev, false);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &gr->graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    c->stream = saved;
+    cudaStreamDestroy(cap);
+    if (e == cudaSuccess && st == LIDAR_OK) e = cudaGraphInstantiate(&gr->exec, gr->graph, 0);
+    if (e != cudaSuccess || st != LIDAR_OK) {
+        if (gr->graph) cudaGraphDestroy(gr->graph);
+        delete gr;
+        if (st != LIDAR_OK) return st;
+        set_error(std::string("lidar_graph_create: ") + cudaGetErrorString(e));
+        return LIDAR_ECUDA;
+    }
+    *out = gr;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_graph_launch(lidar_graph* gr)
+{
+    LIDAR_CHECK_ARG(gr != nullptr, "lidar_graph_launch: graph is NULL");
+    DeviceGuard g(gr->ctx->device);
+    LIDAR_CUDA(cudaGraphLaunch(gr->exec, gr->ctx->stream));
+    return LIDAR_OK;
+}
+
+void lidar_graph_free(lidar_graph* gr)
+{
+    if (!gr) return;
+    DeviceGuard g(gr->ctx->device);
+    cudaStreamSynchronize(gr->ctx->stream);
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    delete gr;
 }
 
 static lidar_status backward_common(lidar_ctx* c, int64_t n, const lidar_beams* tape, float gain,

@@ -200,6 +200,14 @@ class Lidar:
         self.cast_into(scene, frames, seed, beams, points)
         return beams, points
 
+    # ----------------------------------------------------------- batches / graphs
+    def batch(self, frames) -> "Batch":
+        fr = _frames_array(frames)
+        h = ctypes.c_void_p()
+        C.check(C.lidar_batch_create(self.handle, fr.ctypes.data_as(ctypes.c_void_p), len(fr), ctypes.byref(h)),
+                "lidar_batch_create")
+        return Batch(self, h, fr)
+
     def sync_status(self) -> int:
         return C.lidar_sync_status(self.handle)
 
@@ -253,6 +261,66 @@ class Lidar:
         cur.update(kw)
         c = C.lidar_launch_config(**cur)
         C.check(C.lidar_set_launch_config(self.handle, ctypes.byref(c)), "lidar_set_launch_config")
+
+
+class Batch:
+    """Device-resident frames: casts without host copies, CUDA-graph capture."""
+
+    def __init__(self, lidar, handle, frames):
+        self._lidar = lidar
+        self.handle = handle
+        self.frames = frames
+        self.n_beams = lidar.total_beams(frames)
+        self._graphs = []
+
+    def set_poses(self, poses: torch.Tensor):
+        poses = poses.to(self._lidar.device, torch.float32).contiguous()
+        C.check(C.lidar_batch_set_poses(self._lidar.handle, self.handle, _ptr(poses)), "lidar_batch_set_poses")
+
+    def cast_into(self, scene: Scene, seed: int, beams=None, points=None):
+        L = self._lidar
+        bs = L.beams_struct(beams) if beams is not None else None
+        ps = L.points_struct(points) if points is not None else None
+        C.check(C.lidar_cast_batch(L.handle, scene.handle, self.handle, ctypes.c_uint64(seed),
+                                   ctypes.byref(bs) if bs is not None else None,
+                                   ctypes.byref(ps) if ps is not None else None,
+                                   _ptr(points["count"]) if points is not None else None), "lidar_cast_batch")
+
+    def graph(self, scene: Scene, seed: int, beams=None, points=None, poses: torch.Tensor = None) -> "Graph":
+        L = self._lidar
+        bs = L.beams_struct(beams) if beams is not None else None
+        ps = L.points_struct(points) if points is not None else None
+        h = ctypes.c_void_p()
+        C.check(C.lidar_graph_create(L.handle, scene.handle, self.handle, _ptr(poses), ctypes.c_uint64(seed),
+                                     ctypes.byref(bs) if bs is not None else None,
+                                     ctypes.byref(ps) if ps is not None else None,
+                                     _ptr(points["count"]) if points is not None else None, ctypes.byref(h)),
+                "lidar_graph_create")
+        g = Graph(L, h, keep=(beams, points, poses))
+        self._graphs.append(g)
+        return g
+
+    def free(self):
+        for g in self._graphs:
+            g.free()
+        if self.handle is not None and self._lidar.handle is not None:
+            C.lidar_batch_free(self.handle)
+        self.handle = None
+
+
+class Graph:
+    def __init__(self, lidar, handle, keep):
+        self._lidar = lidar
+        self.handle = handle
+        self._keep = keep  # tensors baked into the graph stay alive with it
+
+    def launch(self):
+        C.check(C.lidar_graph_launch(self.handle), "lidar_graph_launch")
+
+    def free(self):
+        if self.handle is not None and self._lidar.handle is not None:
+            C.lidar_graph_free(self.handle)
+        self.handle = None
 
 
 class LidarCast(torch.autograd.Function):

@@ -1,0 +1,116 @@
+"""Autotuner for the cast kernel's launch configuration and ray schedule.
+
+Searches threads per block x resident blocks per SM (which also picks the
+register budget), the traversal variant, the ray order (beam order / Morton
+order of directions) and the schedule (Morton groups / most expensive groups
+first), timing each candidate with CUDA events on the context stream.  Every
+candidate produces bit-identical results (tested), so the choice is purely a
+performance one.  The winner is cached in a JSON file keyed by GPU name, SM
+count and a hash of the workload's shape.
+"""
+from __future__ import annotations
+
+import hashlib
+import itertools
+import json
+import os
+import statistics
+
+import numpy as np
+import torch
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tune_cache.json")
+
+SPACE = {
+    "block_threads": (64, 128, 256),
+    "blocks_per_sm": (2, 4, 8, 12),
+    "traversal": (0, 1),
+    "ray_order": (0, 1),
+    "schedule": ("morton", "cost"),
+}
+
+
+def workload_key(L, scene, frames) -> str:
+    props = torch.cuda.get_device_properties(L.device)
+    fr = np.ascontiguousarray(frames)
+    shape = [int(scene.n_tris)] + [int(L.n_beams[int(s)]) for s in fr["sensor"]]
+    h = hashlib.sha256(json.dumps(shape).encode()).hexdigest()[:16]
+    return f"{props.name}|{props.multi_processor_count}|{h}"
+
+
+def _time_cast(L, scene, frames, seed, out, flush, reps):
+    ts = []
+    stream = L.stream
+    for i in range(reps + 2):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        L.cast_into(scene, frames, seed, out)
+        b.record(stream)
+        b.synchronize()
+        if i >= 2:
+            ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def candidates():
+    for bt, bps, tv, ro, sc in itertools.product(*SPACE.values()):
+        if bt * bps > 2048 or bt * bps < 256:
+            continue
+        if ro == 0 and sc == "cost":
+            continue  # the cost schedule reorders the Morton order
+        yield {"block_threads": bt, "blocks_per_sm": bps, "tile_rays": 32, "traversal": tv, "ray_order": ro,
+               "schedule": sc}
+
+
+def apply(L, scene, cfg, schedule_frames, seed):
+    L.set_launch_config(**{k: v for k, v in cfg.items() if k != "schedule"})
+    slots = sorted({int(s) for s in np.ascontiguousarray(schedule_frames)["sensor"]})
+    for s in slots:
+        L.reset_schedule(s)
+    if cfg.get("schedule") == "cost":
+        fr = np.ascontiguousarray(schedule_frames)
+        for s in slots:
+            first = fr[fr["sensor"] == s][:1]
+            L.schedule_by_cost(scene, first, seed)
+
+
+def autotune(L, scene, frames, seed, schedule_frames=None, cache_path=DEFAULT_CACHE, reps=8, flush_l2=True,
+             use_cache=True, verbose=False):
+    """Picks and applies the fastest configuration for casting `frames`.
+    `schedule_frames` (default `frames`) are the poses whose measured costs
+    order the rays for the cost schedule: pass a nearby pose (the previous
+    frame) to keep the measurement honest.  Returns (config, ms)."""
+    schedule_frames = frames if schedule_frames is None else schedule_frames
+    key = workload_key(L, scene, frames)
+    cache = {}
+    if use_cache and cache_path and os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except Exception:
+            cache = {}
+    if use_cache and key in cache:
+        cfg = cache[key]["config"]
+        apply(L, scene, cfg, schedule_frames, seed)
+        return cfg, cache[key]["ms"]
+    n = L.total_beams(frames)
+    out = L.alloc_beams(n, ("valid",))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=L.device) if flush_l2 else None
+    best = None
+    for cfg in candidates():
+        apply(L, scene, cfg, schedule_frames, seed)
+        ms = _time_cast(L, scene, frames, seed, out, flush, reps)
+        if verbose:
+            print(f"{ms * 1e3:9.1f} us  {cfg}", flush=True)
+        if best is None or ms < best[1]:
+            best = (cfg, ms)
+    apply(L, scene, best[0], schedule_frames, seed)
+    if cache_path:
+        cache[key] = {"config": best[0], "ms": best[1]}
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return best
