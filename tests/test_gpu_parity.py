@@ -266,3 +266,18 @@ def test_batch_and_graph_replay_match_direct_cast(L):
         assert int(pts["count"].item()) == c
         assert torch.equal(ref_pts["range"][:c], pts["range"][:c])
     B.free()
+
+
+def test_cfg4_city_subrays_sampled(L):
+    """The 10.7M-triangle city, 7 sub-rays per beam, all 32 frames cast on the
+    GPU; a seeded sample of beams is recomputed by the oracle (every sub-ray
+    against every triangle)."""
+    w = synth.cfg4()
+    gpu, _ = gpu_cast(L, w, fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst", "sub"))
+    samples = stratified_sample(w, 192, seed=4)
+    ref = oracle_cast(w, samples)
+    rep = compare_subray(pick(gpu, w, samples), ref, label="cfg4 city, 7 sub-rays, 192 sampled beams")
+    _report(rep)
+    # most hit beams have several sub-rays of near-equal intensity on the same
+    # surface: those are checked through the ambiguous-choice path
+    assert rep["hits"] + rep["subray_ambiguous_checked"] > 100
