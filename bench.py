@@ -245,11 +245,12 @@ def run_ours(args, rank, world, local_rank):
     clocks = clk.summary()
     value = n_beams * args.steps * world / (total_ms / 1e3)
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
-    visit_bytes = counters["node_visits"] * 64 + counters["tri_tests"] * 48 + counters["io_bytes"]
+    visit_bytes = counters["node_visits"] * counters["node_bytes"] + counters["tri_tests"] * 48 + counters["io_bytes"]
     uniq_bytes = counters["unique_node_bytes"] + counters["unique_tri_bytes"] + counters["io_bytes"]
     achieved = visit_bytes / (kernel_ms / 1e3) / 1e9
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
-    flops = counters["node_visits"] * 2 * 24 + counters["tri_tests"] * 40
+    # FP32 ops per node fetch: 12 (binary) or 24 (4-wide) slab subtract+multiply pairs; 40 per triangle test
+    flops = counters["node_visits"] * (counters["node_bytes"] // 64) * 2 * 24 + counters["tri_tests"] * 40
     alu_tf = flops / (kernel_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -267,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / hbm, "traffic": None,
                      "peak_source": f"{peaks_src} hbm_gbs (STREAM-style copy)",
                      "bytes_per_launch": visit_bytes, "kernel": "k_cast", "kernel_ms": kernel_ms,
-                     "note": "algorithmic bytes = node fetches x 64 B + triangle tests x 48 B + 17 B/ray I/O; "
+                     "note": "algorithmic bytes = node fetches x node size + triangle tests x 48 B + 17 B/ray I/O; "
                              "L1/L2 serve most of them (compulsory DRAM bytes in compulsory_bytes_per_launch)",
                      "compulsory_bytes_per_launch": uniq_bytes,
                      "compulsory_frac": uniq_bytes / (kernel_ms / 1e3) / 1e9 / hbm},

@@ -80,8 +80,9 @@ lidar_status lidar_sync_status(lidar_ctx* ctx);
 
 /* Builds a linear BVH (Karras 2012: 63-bit Morton codes of triangle centroids,
  * radix sort, hierarchy from key prefixes, bottom-up exact FP32 box refit)
- * over a triangle mesh and copies the triangles, in leaf order, into a
- * library-owned layout.
+ * over a triangle mesh, collapses it into a 4-wide hierarchy over the same
+ * leaves (each 4-wide node opens its largest-area children), and copies the
+ * triangles, in leaf order, into a library-owned layout.
  *   verts_dev        float32 [n_verts][3], metres, world frame
  *   tris_dev         uint32  [n_tris][3], vertex indices (< n_verts)
  *   tri_material_dev uint16  [n_tris], material ID (row of the reflectance table;
@@ -104,6 +105,8 @@ typedef struct {
     int32_t max_depth;     /* longest root-to-leaf path, in internal nodes */
     int64_t device_bytes;  /* bytes held by the scene on the device */
     double build_ms;       /* device time of the last build, CUDA events */
+    int64_t n_nodes4;      /* nodes of the 4-wide hierarchy collapsed from the binary one */
+    int32_t levels4;       /* its height */
 } lidar_scene_info;
 
 lidar_status lidar_get_scene_info(const lidar_scene* scene, lidar_scene_info* out);
@@ -321,7 +324,8 @@ lidar_status lidar_cast_backward_mse_noalloc(void* cuda_stream, int64_t n_beams,
  * algorithmic bytes and flops behind the roofline. */
 typedef struct {
     uint64_t rays;           /* traced rays (beams x sub-rays) */
-    uint64_t node_visits;    /* 64-byte node fetches */
+    uint64_t node_bytes;     /* bytes per node fetch: 64 (binary tree) or 128 (4-wide tree) */
+    uint64_t node_visits;    /* node fetches */
     uint64_t tri_tests;      /* 48-byte triangle fetches + watertight tests */
     uint64_t unique_nodes;   /* distinct nodes fetched */
     uint64_t unique_tris;    /* distinct triangles fetched */
@@ -356,8 +360,9 @@ typedef struct {
     int32_t blocks_per_sm;   /* persistent blocks per SM */
     int32_t tile_rays;       /* rays a warp takes from the work counter at a time (multiple of 32) */
     int32_t ray_order;       /* 0 = beam order, 1 = Morton order of beam directions */
-    int32_t traversal;       /* 0 = each lane tests its triangles as it meets them;
-                                1 = warp-synchronous traversal with postponed triangle tests */
+    int32_t traversal;       /* binary tree: 0 = each lane tests its triangles as it meets them,
+                                1 = warp-synchronous with postponed triangle tests;
+                                2 = 4-wide tree, per lane, children visited near to far */
 } lidar_launch_config;
 
 lidar_status lidar_get_launch_config(lidar_ctx* ctx, lidar_launch_config* out);

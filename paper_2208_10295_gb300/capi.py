@@ -39,7 +39,8 @@ class LidarError(RuntimeError):
 
 class lidar_scene_info(ctypes.Structure):
     _fields_ = [("n_tris", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("max_depth", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double)]
+                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double), ("n_nodes4", ctypes.c_int64),
+                ("levels4", ctypes.c_int32)]
 
 
 class lidar_sensor_desc(ctypes.Structure):
@@ -65,7 +66,8 @@ class lidar_points(ctypes.Structure):
 
 
 class lidar_work_counts(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_uint64) for n in ("rays", "node_visits", "tri_tests", "unique_nodes", "unique_tris")]
+    _fields_ = [(n, ctypes.c_uint64) for n in ("rays", "node_bytes", "node_visits", "tri_tests", "unique_nodes",
+                                               "unique_tris")]
 
 
 class lidar_launch_config(ctypes.Structure):

@@ -316,3 +316,187 @@ cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, cons
 }
 
 }  // namespace lidar
+
+// ---------------------------------------------------------------------------
+// Collapse of the binary hierarchy into a 4-wide one.  Top-down, one frontier
+// of binary nodes per level: each becomes a 4-wide node whose children are
+// found by repeatedly opening the child with the largest surface area until
+// four children or only leaves remain.  Slots of the next level are assigned by
+// an exclusive scan, so the layout is breadth-first and deterministic.
+namespace lidar {
+namespace {
+
+struct Child4 {
+    float lo[3], hi[3];
+    int ref;  // binary node (>= 0) or ~leaf (< 0)
+};
+
+__device__ __forceinline__ void binary_child(const float4* __restrict__ bn, int node, int side, Child4& c)
+{
+    const float4 n0 = bn[4 * (int64_t)node + 0], n1 = bn[4 * (int64_t)node + 1];
+    const float4 n2 = bn[4 * (int64_t)node + 2], n3 = bn[4 * (int64_t)node + 3];
+    if (side == 0) {
+        c.lo[0] = n0.x; c.hi[0] = n0.y; c.lo[1] = n0.z; c.hi[1] = n0.w; c.lo[2] = n2.x; c.hi[2] = n2.y;
+        c.ref = __float_as_int(n3.x);
+    } else {
+        c.lo[0] = n1.x; c.hi[0] = n1.y; c.lo[1] = n1.z; c.hi[1] = n1.w; c.lo[2] = n2.z; c.hi[2] = n2.w;
+        c.ref = __float_as_int(n3.y);
+    }
+}
+
+__device__ __forceinline__ float half_area(const Child4& c)
+{
+    const float dx = c.hi[0] - c.lo[0], dy = c.hi[1] - c.lo[1], dz = c.hi[2] - c.lo[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// children of frontier entry i; returns the number of internal ones
+__device__ int gather4(const float4* __restrict__ bn, int b, Child4 ch[4], int& count)
+{
+    binary_child(bn, b, 0, ch[0]);
+    binary_child(bn, b, 1, ch[1]);
+    count = 2;
+    while (count < 4) {
+        int best = -1;
+        float best_a = -1.0f;
+        for (int k = 0; k < count; ++k)
+            if (ch[k].ref >= 0 && half_area(ch[k]) > best_a) {
+                best_a = half_area(ch[k]);
+                best = k;
+            }
+        if (best < 0) break;
+        const int open = ch[best].ref;
+        binary_child(bn, open, 0, ch[best]);
+        binary_child(bn, open, 1, ch[count]);
+        ++count;
+    }
+    int internal = 0;
+    for (int k = 0; k < count; ++k) internal += ch[k].ref >= 0;
+    return internal;
+}
+
+__global__ void k_collapse_count(const float4* __restrict__ bn, const int* __restrict__ frontier, int n,
+                                 uint32_t* __restrict__ n_internal)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Child4 ch[4];
+    int count;
+    n_internal[i] = (uint32_t)gather4(bn, frontier[i], ch, count);
+}
+
+__global__ void __launch_bounds__(1024) k_collapse_scan(uint32_t* __restrict__ v, int n, uint32_t* total)
+{
+    __shared__ uint32_t s_sum[1024];
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(lo + per, n);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += v[i];
+    s_sum[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t x = (threadIdx.x >= (unsigned)off) ? s_sum[threadIdx.x - off] : 0u;
+        __syncthreads();
+        s_sum[threadIdx.x] += x;
+        __syncthreads();
+    }
+    uint32_t run = threadIdx.x == 0 ? 0u : s_sum[threadIdx.x - 1];
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t c = v[i];
+        v[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == blockDim.x - 1) *total = s_sum[blockDim.x - 1];
+}
+
+// frontier entry i owns 4-wide slot (slot_base + i); its internal children get
+// slots next_base + offset[i] + k and enter the next frontier at offset[i] + k
+__global__ void k_collapse_write(const float4* __restrict__ bn, const int* __restrict__ frontier, int n,
+                                 const uint32_t* __restrict__ offset, int slot_base, int next_base,
+                                 float4* __restrict__ nodes4, int* __restrict__ next_frontier)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Child4 ch[4];
+    int count;
+    gather4(bn, frontier[i], ch, count);
+    float lo[3][4], hi[3][4];
+    int code[4];
+    int k_int = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (k < count) {
+            for (int a = 0; a < 3; ++a) { lo[a][k] = ch[k].lo[a]; hi[a][k] = ch[k].hi[a]; }
+            if (ch[k].ref >= 0) {
+                const int j = (int)offset[i] + k_int++;
+                code[k] = next_base + j;
+                next_frontier[j] = ch[k].ref;
+            } else {
+                code[k] = ch[k].ref;
+            }
+        } else {
+            for (int a = 0; a < 3; ++a) { lo[a][k] = INFINITY; hi[a][k] = -INFINITY; }
+            code[k] = 0;
+        }
+    }
+    float4* out = nodes4 + 8 * (int64_t)(slot_base + i);
+    out[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+    out[1] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+    out[2] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+    out[3] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+    out[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+    out[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+    out[6] = make_float4(__int_as_float(code[0]), __int_as_float(code[1]), __int_as_float(code[2]),
+                         __int_as_float(code[3]));
+    out[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+}  // namespace
+
+size_t collapse_scratch_bytes(int64_t n_binary)
+{
+    const int64_t m = n_binary > 0 ? n_binary : 1;
+    return 2 * ((m * sizeof(int) + 255) / 256) * 256 + ((m * sizeof(uint32_t) + 255) / 256) * 256 + 256;
+}
+
+cudaError_t collapse_bvh4(cudaStream_t s, const float4* binary_nodes, int64_t n_binary, float4* nodes4,
+                          int64_t* n_nodes4, int* levels, void* scratch, size_t scratch_bytes)
+{
+    *n_nodes4 = 0;
+    *levels = 0;
+    if (n_binary == 0) return cudaSuccess;
+    if (scratch_bytes < collapse_scratch_bytes(n_binary)) return cudaErrorInvalidValue;
+    const size_t fb = ((n_binary * sizeof(int) + 255) / 256) * 256;
+    int* fa = (int*)scratch;
+    int* fbuf = (int*)((char*)scratch + fb);
+    uint32_t* counts = (uint32_t*)((char*)scratch + 2 * fb);
+    uint32_t* total = (uint32_t*)((char*)scratch + 2 * fb + ((n_binary * sizeof(uint32_t) + 255) / 256) * 256);
+    const int root = 0;
+    cudaError_t e = cudaMemcpyAsync(fa, &root, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    int n = 1, slot_base = 0;
+    int64_t allocated = 1;
+    int* cur = fa;
+    int* nxt = fbuf;
+    while (n > 0) {
+        const int blocks = (n + 255) / 256;
+        k_collapse_count<<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts);
+        k_collapse_scan<<<1, 1024, 0, s>>>(counts, n, total);
+        k_collapse_write<<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts, slot_base, (int)allocated, nodes4, nxt);
+        uint32_t next_n = 0;
+        e = cudaMemcpyAsync(&next_n, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        slot_base = (int)allocated;
+        allocated += next_n;
+        n = (int)next_n;
+        int* t = cur;
+        cur = nxt;
+        nxt = t;
+        ++*levels;
+    }
+    *n_nodes4 = allocated;
+    return cudaGetLastError();
+}
+
+}  // namespace lidar

@@ -119,7 +119,7 @@ __device__ __forceinline__ int find_frame(const int64_t* __restrict__ prefix, in
 // Persistent kernel, work taken per warp: lane 0 claims a tile of `tile_rays`
 // consecutive ray-order positions of one frame (a multiple of 32) and the warp
 // traces it 32 rays at a time; no block-wide barrier.
-template <bool kCount, int kMinBlocks, bool kWarpSync>
+template <bool kCount, int kMinBlocks, int kTrav>
 __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const SensorDev* __restrict__ sensors,
                                               const FrameDev* __restrict__ frames, int n_frames,
                                               const int64_t* __restrict__ tile_prefix, int64_t n_tiles,
@@ -160,10 +160,15 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                 const RayPre p = prepare_ray(r);
                 HitRec h;
                 bool ok = true;
-                if (kWarpSync) {
+                if (kTrav == 1) {
                     ok = trace_closest_warp<kCount>(S, p, sd.t_max, h, active, &wc);
                 } else if (active) {
-                    ok = trace_closest<kCount>(S, p, sd.t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x, &cost);
+                    if (kTrav == 2)
+                        ok = trace_closest4<kCount>(S, p, sd.t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x,
+                                                    &cost);
+                    else
+                        ok = trace_closest<kCount>(S, p, sd.t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x,
+                                                   &cost);
                 }
                 if (!ok) raise_status(status, ST_STACK);
                 if (active) {
@@ -357,23 +362,27 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     // the counting launch always uses the per-lane traversal.
     const size_t stack_bytes = (size_t)kSharedStack * cfg.block_threads * sizeof(int2);
 #define LIDAR_LAUNCH_CAST(C, V, W)                                                                               \
-    k_cast<C, V, W><<<(unsigned)grid, cfg.block_threads, (W) ? 0 : stack_bytes, s>>>(                           \
+    k_cast<C, V, W><<<(unsigned)grid, cfg.block_threads, (W) == 1 ? 0 : stack_bytes, s>>>(                      \
                                                                  scene, sensors_dev, frames_dev, n_frames,        \
                                                                  tile_prefix_dev, n_tiles, table, seed, out,      \
                                                                  status, work_counter, cfg.tile_rays,             \
                                                                  C ? *count : none)
-    const bool ws = cfg.traversal == 1;
     if (count) {
-        // the work counted does not depend on the launch shape
-        LIDAR_LAUNCH_CAST(true, 4, false);
-    } else if (ws) {
-        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, true);
-        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, true);
-        else LIDAR_LAUNCH_CAST(false, 4, true);
+        // the work counted depends on the tree the traversal walks, not on the launch shape
+        if (cfg.traversal == 2) LIDAR_LAUNCH_CAST(true, 4, 2);
+        else LIDAR_LAUNCH_CAST(true, 4, 0);
+    } else if (cfg.traversal == 1) {
+        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, 1);
+        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, 1);
+        else LIDAR_LAUNCH_CAST(false, 4, 1);
+    } else if (cfg.traversal == 2) {
+        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, 2);
+        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, 2);
+        else LIDAR_LAUNCH_CAST(false, 4, 2);
     } else {
-        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, false);
-        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, false);
-        else LIDAR_LAUNCH_CAST(false, 4, false);
+        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, 0);
+        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, 0);
+        else LIDAR_LAUNCH_CAST(false, 4, 0);
     }
 #undef LIDAR_LAUNCH_CAST
     return cudaGetLastError();

@@ -56,10 +56,12 @@ __device__ __forceinline__ void raise_status(int* status, int code)
 constexpr int kTraversalStack = 96;
 
 struct SceneDev {
-    const float4* nodes;     // [n_nodes * 4]
+    const float4* nodes;     // [n_nodes * 4] binary hierarchy
     const float4* tris;      // [n_tris * 3]
     int64_t n_tris;
     int64_t n_nodes;
+    const float4* nodes4;    // [n_nodes4 * 8] 4-wide hierarchy (same leaves)
+    int64_t n_nodes4;
 };
 
 // ------------------------------------------------------------------ sensors
@@ -117,6 +119,11 @@ cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, cons
                        float4* tris_out, uint32_t* leaf_tri_out, int* status, int* max_depth_dev,
                        void* scratch, size_t scratch_bytes);
 size_t build_scratch_bytes(int64_t n_tris);
+// 4-wide hierarchy from the binary one (breadth-first, deterministic);
+// synchronises once per level.  *levels = height of the 4-wide tree.
+cudaError_t collapse_bvh4(cudaStream_t s, const float4* binary_nodes, int64_t n_binary, float4* nodes4,
+                          int64_t* n_nodes4, int* levels, void* scratch, size_t scratch_bytes);
+size_t collapse_scratch_bytes(int64_t n_binary);
 
 // sort.cu: stable LSD radix sort of (key, value) pairs, keys of `key_bits` bits
 size_t radix_sort_scratch_bytes(int64_t n);

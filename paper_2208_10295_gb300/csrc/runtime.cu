@@ -4,6 +4,7 @@
 // stream.
 #include <math.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -55,10 +56,13 @@ using namespace lidar;
 struct lidar_scene {
     lidar_ctx* ctx = nullptr;
     float4* nodes = nullptr;
+    float4* nodes4 = nullptr;
     float4* tris = nullptr;
     uint32_t* leaf_tri = nullptr;
     int64_t n_tris = 0;
     int64_t n_nodes = 0;
+    int64_t n_nodes4 = 0;
+    int levels4 = 0;
     int max_depth = 0;
     double build_ms = 0.0;
     int64_t bytes = 0;
@@ -200,6 +204,7 @@ void lidar_scene_free(lidar_scene* s)
     DeviceGuard g(s->ctx->device);
     cudaStreamSynchronize(s->ctx->stream);
     cudaFree(s->nodes);
+    cudaFree(s->nodes4);
     cudaFree(s->tris);
     cudaFree(s->leaf_tri);
     s->ctx->scenes.erase(s);
@@ -253,6 +258,7 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
     s->n_nodes = n_tris == 0 ? 0 : (n_tris == 1 ? 1 : n_tris - 1);
     auto fail = [&](lidar_status st) {
         cudaFree(s->nodes);
+        cudaFree(s->nodes4);
         cudaFree(s->tris);
         cudaFree(s->leaf_tri);
         delete s;
@@ -260,39 +266,37 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
     };
     if (n_tris > 0) {
         if (dev_alloc((void**)&s->nodes, (size_t)s->n_nodes * 4 * sizeof(float4)) != cudaSuccess ||
+            dev_alloc((void**)&s->nodes4, (size_t)s->n_nodes * 8 * sizeof(float4)) != cudaSuccess ||
             dev_alloc((void**)&s->tris, (size_t)n_tris * 3 * sizeof(float4)) != cudaSuccess ||
             dev_alloc((void**)&s->leaf_tri, (size_t)n_tris * sizeof(uint32_t)) != cudaSuccess) {
             cudaGetLastError();
             set_error("lidar_scene_build: device allocation failed");
             return fail(LIDAR_ENOMEM);
         }
-        s->bytes = s->n_nodes * 64 + n_tris * 48 + n_tris * 4;
-        lidar_status st = ensure_scratch(c, build_scratch_bytes(n_tris));
+        s->bytes = s->n_nodes * 64 + s->n_nodes * 128 + n_tris * 48 + n_tris * 4;
+        lidar_status st = ensure_scratch(c, std::max(build_scratch_bytes(n_tris), collapse_scratch_bytes(s->n_nodes)));
         if (st != LIDAR_OK) return fail(st);
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
+        struct Events {
+            cudaEvent_t a = nullptr, b = nullptr;
+            Events() { cudaEventCreate(&a); cudaEventCreate(&b); }
+            ~Events() { cudaEventDestroy(a); cudaEventDestroy(b); }
+        } ev;
+        cudaEvent_t e0 = ev.a, e1 = ev.b;
         cudaEventRecord(e0, c->stream);
         cudaError_t e = build_lbvh(c->stream, verts, n_verts, tris, mat, inst, n_tris, s->nodes, s->tris,
                                    s->leaf_tri, c->status_dev, c->aux_dev, c->scratch, c->scratch_bytes);
         cudaEventRecord(e1, c->stream);
         if (e != cudaSuccess) {
             set_error(std::string("lidar_scene_build: ") + cudaGetErrorString(e));
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
             return fail(LIDAR_ECUDA);
         }
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
             set_error("lidar_scene_build: stream synchronisation failed");
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
             return fail(LIDAR_ECUDA);
         }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         s->build_ms = ms;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         int w = 0, h = 0;
         cudaMemcpy(&w, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost);
         cudaMemcpy(&h, c->aux_dev, sizeof(int), cudaMemcpyDeviceToHost);
@@ -302,6 +306,21 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         if (h > kTraversalStack) {
             set_error("lidar_scene_build: BVH height " + std::to_string(h) + " exceeds the traversal stack (" +
                       std::to_string(kTraversalStack) + ")");
+            return fail(LIDAR_ESTACK);
+        }
+        cudaEventRecord(e0, c->stream);
+        cudaError_t e4 = collapse_bvh4(c->stream, s->nodes, s->n_nodes, s->nodes4, &s->n_nodes4, &s->levels4,
+                                       c->scratch, c->scratch_bytes);
+        cudaEventRecord(e1, c->stream);
+        if (e4 != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            set_error(std::string("lidar_scene_build: 4-wide collapse: ") + cudaGetErrorString(e4));
+            return fail(LIDAR_ECUDA);
+        }
+        cudaEventElapsedTime(&ms, e0, e1);
+        s->build_ms += ms;
+        // a 4-wide node pushes at most three children
+        if (3 * s->levels4 > kTraversalStack) {
+            set_error("lidar_scene_build: 4-wide BVH too deep for the traversal stack");
             return fail(LIDAR_ESTACK);
         }
     }
@@ -318,6 +337,8 @@ lidar_status lidar_get_scene_info(const lidar_scene* s, lidar_scene_info* out)
     out->max_depth = s->max_depth;
     out->device_bytes = s->bytes;
     out->build_ms = s->build_ms;
+    out->n_nodes4 = s->n_nodes4;
+    out->levels4 = s->levels4;
     return LIDAR_OK;
 }
 
@@ -556,7 +577,7 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
         if (need_mat) { out.mat = (uint16_t*)p; p += al(2 * n_total); }
         if (need_inst) { out.inst = (uint32_t*)p; p += al(4 * n_total); }
     }
-    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes};
+    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
     LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, frames_dev, n_frames, prefix_dev, n_tiles, c->table, seed,
                            out, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total));
     if (points) {
@@ -883,7 +904,7 @@ static lidar_status counting_cast(lidar_ctx* c, const lidar_scene* scene, const 
     WorkCount wc{totals, node_bits, leaf_bits, cost_dev};
     BeamsOut dense{};
     dense.valid = valid;
-    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes};
+    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
     LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, c->frames_dev, n_frames, c->tile_prefix_dev, n_tiles,
                            c->table, seed, dense, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total,
                            &wc));
@@ -909,6 +930,7 @@ lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lida
         rays += (uint64_t)sl.n_beams * (uint64_t)sl.dev.n_sub;
     }
     out->rays = rays;
+    out->node_bytes = c->cfg.traversal == 2 ? 128 : 64;
     out->node_visits = h[0];
     out->tri_tests = h[1];
     out->unique_nodes = h[2];
@@ -976,7 +998,7 @@ lidar_status lidar_set_launch_config(lidar_ctx* c, const lidar_launch_config* cf
     LIDAR_CHECK_ARG(cfg->tile_rays >= 32 && cfg->tile_rays <= (1 << 20) && cfg->tile_rays % 32 == 0,
                     "lidar_set_launch_config: tile_rays must be a multiple of 32 in [32, 2^20]");
     LIDAR_CHECK_ARG(cfg->ray_order == 0 || cfg->ray_order == 1, "lidar_set_launch_config: ray_order is 0 or 1");
-    LIDAR_CHECK_ARG(cfg->traversal == 0 || cfg->traversal == 1, "lidar_set_launch_config: traversal is 0 or 1");
+    LIDAR_CHECK_ARG(cfg->traversal >= 0 && cfg->traversal <= 2, "lidar_set_launch_config: traversal is 0, 1 or 2");
     DeviceGuard g(c->device);
     c->cfg.block_threads = cfg->block_threads;
     c->cfg.blocks_per_sm = cfg->blocks_per_sm;

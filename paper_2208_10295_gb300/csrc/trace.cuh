@@ -275,6 +275,129 @@ __device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p
     return true;
 }
 
+// Slab test of the four child boxes of a 4-wide node (child boxes as SoA
+// float4 per plane), same rounding and NaN handling as child_boxes.
+__device__ __forceinline__ void slab4(float4 lo, float4 hi, float o, float inv, bool neg, float4& tin, float4& tout)
+{
+    const float4 e = neg ? hi : lo, x = neg ? lo : hi;
+    tin = make_float4(slab_t(e.x, o, inv), slab_t(e.y, o, inv), slab_t(e.z, o, inv), slab_t(e.w, o, inv));
+    tout = make_float4(slab_t(x.x, o, inv), slab_t(x.y, o, inv), slab_t(x.z, o, inv), slab_t(x.w, o, inv));
+}
+
+__device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb)
+{
+    const bool sw = kb < ka;
+    const float tk = sw ? kb : ka;
+    const int tv = sw ? vb : va;
+    kb = sw ? ka : kb;
+    vb = sw ? va : vb;
+    ka = tk;
+    va = tv;
+}
+
+// Closest hit by traversal of the 4-wide hierarchy.  Node (128 bytes, eight
+// 16-byte loads): lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four children as
+// float4s, then the child codes (>= 0 node, < 0 ~leaf; empty slots have an
+// empty box).  Triangle children are tested when met; hit internal children
+// are ordered near to far with a 4-key sorting network, the nearest is visited
+// next and the others pushed far-first.
+template <bool kCount = false>
+__device__ __forceinline__ bool trace_closest4(const SceneDev& S, const RayPre& p, float t_max, HitRec& h,
+                                               const WorkCount* wc, int2* sh_stack, int sh_stride,
+                                               unsigned* cost = nullptr)
+{
+    unsigned long long n_nodes = 0, n_tris = 0;
+    h.t = t_max;
+    h.cull = t_max * kBestScale;
+    h.idx = 0xFFFFFFFFu;
+    h.leaf = -1;
+    if (S.n_tris == 0) return true;
+    SplitStack stack;
+    stack.sh = sh_stack;
+    stack.sh_stride = sh_stride;
+    const bool nx = p.ix < 0.0f, ny = p.iy < 0.0f, nz = p.iz < 0.0f;
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        if (kCount) {
+            ++n_nodes;
+            atomicOr(&wc->node_bits[node >> 5], 1u << (node & 31));
+        }
+        const float4* q = S.nodes4 + 8 * (int64_t)node;
+        float4 tin, tout, ti, to;
+        slab4(__ldg(q + 0), __ldg(q + 1), p.ox, p.ix, nx, tin, tout);
+        slab4(__ldg(q + 2), __ldg(q + 3), p.oy, p.iy, ny, ti, to);
+        tin = make_float4(fmaxf(tin.x, ti.x), fmaxf(tin.y, ti.y), fmaxf(tin.z, ti.z), fmaxf(tin.w, ti.w));
+        tout = make_float4(fminf(tout.x, to.x), fminf(tout.y, to.y), fminf(tout.z, to.z), fminf(tout.w, to.w));
+        slab4(__ldg(q + 4), __ldg(q + 5), p.oz, p.iz, nz, ti, to);
+        const float4 c4 = __ldg(q + 6);
+        float k0 = fmaxf(fmaxf(tin.x, ti.x), kTEps), k1 = fmaxf(fmaxf(tin.y, ti.y), kTEps);
+        float k2 = fmaxf(fmaxf(tin.z, ti.z), kTEps), k3 = fmaxf(fmaxf(tin.w, ti.w), kTEps);
+        const float f0 = fminf(tout.x, to.x) * kFarScale, f1 = fminf(tout.y, to.y) * kFarScale;
+        const float f2 = fminf(tout.z, to.z) * kFarScale, f3 = fminf(tout.w, to.w) * kFarScale;
+        int c0 = __float_as_int(c4.x), c1 = __float_as_int(c4.y), c2 = __float_as_int(c4.z), c3 = __float_as_int(c4.w);
+        bool h0 = k0 <= fminf(f0, h.cull), h1 = k1 <= fminf(f1, h.cull);
+        bool h2 = k2 <= fminf(f2, h.cull), h3 = k3 <= fminf(f3, h.cull);
+        // triangle children first
+#define LIDAR_LEAF4(HIT, C)                                                             \
+        if (HIT && C < 0) {                                                             \
+            if (kCount) {                                                               \
+                ++n_tris;                                                               \
+                atomicOr(&wc->leaf_bits[(~C) >> 5], 1u << ((~C) & 31));                 \
+            }                                                                           \
+            intersect_triangle(S.tris, ~C, p, t_max, h);                                \
+            HIT = false;                                                                \
+        }
+        LIDAR_LEAF4(h0, c0)
+        LIDAR_LEAF4(h1, c1)
+        LIDAR_LEAF4(h2, c2)
+        LIDAR_LEAF4(h3, c3)
+#undef LIDAR_LEAF4
+        // internal children that are still in front of the best hit, near to far
+        k0 = (h0 && k0 <= h.cull) ? k0 : INFINITY;
+        k1 = (h1 && k1 <= h.cull) ? k1 : INFINITY;
+        k2 = (h2 && k2 <= h.cull) ? k2 : INFINITY;
+        k3 = (h3 && k3 <= h.cull) ? k3 : INFINITY;
+        cswap(k0, c0, k1, c1);
+        cswap(k2, c2, k3, c3);
+        cswap(k0, c0, k2, c2);
+        cswap(k1, c1, k3, c3);
+        cswap(k1, c1, k2, c2);
+        if (k0 != INFINITY) {
+            if (k3 != INFINITY) {
+                if (sp >= kTraversalStack) return false;
+                stack.put(sp++, make_int2(c3, __float_as_int(k3)));
+            }
+            if (k2 != INFINITY) {
+                if (sp >= kTraversalStack) return false;
+                stack.put(sp++, make_int2(c2, __float_as_int(k2)));
+            }
+            if (k1 != INFINITY) {
+                if (sp >= kTraversalStack) return false;
+                stack.put(sp++, make_int2(c1, __float_as_int(k1)));
+            }
+            node = c0;
+            continue;
+        }
+        bool found = false;
+        while (sp > 0) {
+            const int2 e = stack.get(--sp);
+            if (__int_as_float(e.y) <= h.cull) {
+                node = e.x;
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+    if (kCount) {
+        atomicAdd(&wc->totals[0], n_nodes);
+        atomicAdd(&wc->totals[1], n_tris);
+        if (cost) *cost += (unsigned)(n_nodes + n_tris);
+    }
+    return true;
+}
+
 // Warp-synchronous variant of trace_closest (same result).  All 32 lanes of
 // the warp must call it together; lanes with `active` false take part in the
 // warp votes only.  Triangle tests are postponed: a lane that reaches a leaf

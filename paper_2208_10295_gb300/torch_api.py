@@ -234,7 +234,7 @@ class Lidar:
         C.check(C.lidar_count_work(self.handle, scene.handle, fr.ctypes.data_as(ctypes.c_void_p), len(fr),
                                    ctypes.c_uint64(seed), ctypes.byref(wc)), "lidar_count_work")
         d = {k: int(getattr(wc, k)) for k, _ in wc._fields_}
-        d["unique_node_bytes"] = d["unique_nodes"] * 64
+        d["unique_node_bytes"] = d["unique_nodes"] * d["node_bytes"]
         d["unique_tri_bytes"] = d["unique_tris"] * 48
         # per ray: beam direction and ray-order index in, one valid byte out
         d["io_bytes"] = d["rays"] * (12 + 4 + 1)

@@ -24,7 +24,7 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
 SPACE = {
     "block_threads": (64, 128, 256),
     "blocks_per_sm": (2, 4, 8, 12),
-    "traversal": (0, 1),
+    "traversal": (0, 1, 2),
     "ray_order": (0, 1),
     "schedule": ("morton", "cost"),
 }

@@ -126,7 +126,7 @@ def test_ray_order_and_launch_shapes_bit_identical(L):
     base, scene = gpu_cast(L, w)
     cfg0 = L.launch_config()
     try:
-        for cfg in ({"ray_order": 0}, {"block_threads": 64, "tile_rays": 64}, {"traversal": 1},
+        for cfg in ({"ray_order": 0}, {"block_threads": 64, "tile_rays": 64}, {"traversal": 1}, {"traversal": 2},
                     {"block_threads": 256, "tile_rays": 512, "blocks_per_sm": 2}):
             L.set_launch_config(**cfg)
             other, _ = gpu_cast(L, w, scene)
