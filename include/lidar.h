@@ -332,9 +332,11 @@ typedef struct {
 } lidar_work_counts;
 
 /* Runs the cast of lidar_cast (dense valid flags only) with counting enabled
- * and returns the totals.  Synchronises. */
+ * and returns the totals.  beam_cost_dev (may be NULL): uint32 per beam in the
+ * dense layout, node fetches + triangle tests of that beam (all sub-rays).
+ * Synchronises. */
 lidar_status lidar_count_work(lidar_ctx* ctx, const lidar_scene* scene, const lidar_frame* frames_host,
-                              int32_t n_frames, uint64_t seed, lidar_work_counts* out);
+                              int32_t n_frames, uint64_t seed, lidar_work_counts* out, uint32_t* beam_cost_dev);
 
 /* --------------------------------------------------------------- scheduling */
 

@@ -119,12 +119,61 @@ __device__ __forceinline__ int find_frame(const int64_t* __restrict__ prefix, in
 // Persistent kernel, work taken per warp: lane 0 claims a tile of `tile_rays`
 // consecutive ray-order positions of one frame (a multiple of 32) and the warp
 // traces it 32 rays at a time; no block-wide barrier.
+// Counts of kept returns per compaction tile of kCompactTileBeams dense
+// indices, gathered by the cast itself (warp-aggregated atomics); the last
+// block to finish turns them into exclusive offsets, so the ordered
+// compaction needs only one more kernel.
+constexpr int kCompactTileBeams = 1024;
+
+struct CompactCounts {
+    unsigned* counts;     // [n_tiles], zeroed before the cast; NULL: not counting
+    unsigned* done;       // finished-block counter, zeroed before the cast
+    int64_t* offsets;     // [n_tiles] exclusive prefix of counts (written by the last block)
+    int64_t* total;       // number of kept returns (may be NULL)
+    int64_t n_tiles;
+};
+
+__device__ __forceinline__ void count_kept_warp(const CompactCounts& cc, bool kept, int64_t dense_index, int lane)
+{
+    const unsigned vm = __ballot_sync(0xffffffffu, kept);
+    if (!kept) return;
+    const unsigned long long t = (unsigned long long)(dense_index / kCompactTileBeams);
+    const unsigned peers = __match_any_sync(vm, t);
+    if (lane == __ffs(peers) - 1) atomicAdd(&cc.counts[t], (unsigned)__popc(peers));
+}
+
+// exclusive scan of cc.counts by one block (runs in the last block only)
+__device__ void scan_counts_block(const CompactCounts& cc)
+{
+    __shared__ long long s_part[256];
+    const int nt = blockDim.x;
+    const int64_t per = (cc.n_tiles + nt - 1) / nt;
+    const int64_t lo = (int64_t)threadIdx.x * per, hi = min(lo + per, cc.n_tiles);
+    long long sum = 0;
+    for (int64_t i = lo; i < hi; ++i) sum += __ldcg(&cc.counts[i]);
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        const long long v = threadIdx.x >= (unsigned)off ? s_part[threadIdx.x - off] : 0;
+        __syncthreads();
+        s_part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    long long run = threadIdx.x == 0 ? 0 : s_part[threadIdx.x - 1];
+    for (int64_t i = lo; i < hi; ++i) {
+        cc.offsets[i] = run;
+        run += __ldcg(&cc.counts[i]);
+    }
+    if (threadIdx.x == nt - 1 && cc.total) *cc.total = s_part[nt - 1];
+}
+
 template <bool kCount, int kMinBlocks, int kTrav>
 __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const SensorDev* __restrict__ sensors,
                                               const FrameDev* __restrict__ frames, int n_frames,
                                               const int64_t* __restrict__ tile_prefix, int64_t n_tiles,
                                               TableDev T, uint64_t seed, BeamsOut out, int* status,
-                                              unsigned long long* work_counter, int tile_rays, WorkCount wc)
+                                              unsigned long long* work_counter, int tile_rays, WorkCount wc,
+                                              CompactCounts cc)
 {
     const int lane = threadIdx.x & 31;
     extern __shared__ int2 sh_stack[];  // [kSharedStack][blockDim.x]
@@ -132,7 +181,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
         unsigned long long claimed = 0;
         if (lane == 0) claimed = atomicAdd(work_counter, 1ull);
         const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, claimed, 0);
-        if (tile >= n_tiles) return;
+        if (tile >= n_tiles) break;
         const int fi = find_frame(tile_prefix, n_frames, tile);
         const FrameDev& fr = frames[fi];
         const SensorDev& sd = sensors[fr.sensor];
@@ -182,9 +231,23 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                     }
                 }
             }
+            if (cc.counts) count_kept_warp(cc, active && best.valid, fr.beam_offset + beam, lane);
             if (!active) continue;
             write_beam(out, fr.beam_offset + beam, best, fr.pose, best_sub);
             if (kCount && wc.beam_cost) wc.beam_cost[fr.beam_offset + beam] = cost;
+        }
+    }
+    if (cc.counts) {
+        __shared__ bool s_last;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(cc.done, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            scan_counts_block(cc);
         }
     }
 }
@@ -194,52 +257,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
 constexpr int kCompactThreads = 256;
 constexpr int kCompactItems = 4;
 constexpr int kCompactTile = kCompactThreads * kCompactItems;
-
-__global__ void __launch_bounds__(kCompactThreads) k_count_valid(const uint8_t* __restrict__ valid, int64_t n,
-                                                                 uint32_t* __restrict__ counts)
-{
-    const int64_t base = (int64_t)blockIdx.x * kCompactTile;
-    uint32_t c = 0;
-    for (int i = threadIdx.x; i < kCompactTile; i += kCompactThreads) {
-        int64_t idx = base + i;
-        if (idx < n) c += valid[idx] ? 1u : 0u;
-    }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    __shared__ uint32_t s[kCompactThreads / 32];
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < kCompactThreads / 32; ++w) t += s[w];
-        counts[blockIdx.x] = t;
-    }
-}
-
-// exclusive scan of the tile counts (one block); writes the total
-__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t* __restrict__ counts, int64_t n,
-                                                     int64_t* __restrict__ offsets, int64_t* total)
-{
-    __shared__ int64_t s_sum[1024];
-    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
-    const int64_t lo = (int64_t)threadIdx.x * per;
-    const int64_t hi = min(lo + per, n);
-    int64_t s = 0;
-    for (int64_t i = lo; i < hi; ++i) s += counts[i];
-    s_sum[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        int64_t v = (threadIdx.x >= (unsigned)off) ? s_sum[threadIdx.x - off] : 0;
-        __syncthreads();
-        s_sum[threadIdx.x] += v;
-        __syncthreads();
-    }
-    int64_t run = (threadIdx.x == 0) ? 0 : s_sum[threadIdx.x - 1];
-    for (int64_t i = lo; i < hi; ++i) {
-        offsets[i] = run;
-        run += counts[i];
-    }
-    if (threadIdx.x == blockDim.x - 1 && total) *total = s_sum[blockDim.x - 1];
-}
+static_assert(kCompactTile == kCompactTileBeams, "the scatter tiles are the cast's counting tiles");
 
 __device__ __forceinline__ int frame_of_index(const FrameDev* __restrict__ frames, int n_frames, int64_t idx)
 {
@@ -344,7 +362,8 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                         const FrameDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
                         int64_t n_tiles, TableDev table, uint64_t seed, BeamsOut out, int* status,
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
-                        int64_t n_beams_total, const WorkCount* count)
+                        int64_t n_beams_total, const WorkCount* count, void* compact_scratch,
+                        int64_t* n_points_dev)
 {
     if (n_tiles == 0) return cudaSuccess;
     cudaMemsetAsync(work_counter, 0, sizeof(unsigned long long), s);
@@ -356,6 +375,16 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     const int resident = cfg.block_threads * cfg.blocks_per_sm;
     const int variant = resident <= 512 ? 2 : (resident <= 768 ? 3 : 4);
     const WorkCount none{nullptr, nullptr, nullptr, nullptr};
+    CompactCounts cc{nullptr, nullptr, nullptr, nullptr, 0};
+    if (compact_scratch) {
+        const int64_t nt = (n_beams_total + kCompactTileBeams - 1) / kCompactTileBeams;
+        cc.n_tiles = nt;
+        cc.offsets = (int64_t*)compact_scratch;
+        cc.counts = (unsigned*)((char*)compact_scratch + ((nt * 8 + 255) / 256) * 256);
+        cc.done = cc.counts + nt;
+        cc.total = n_points_dev;
+        cudaMemsetAsync(cc.counts, 0, (nt + 1) * sizeof(unsigned), s);
+    }
     // dynamic shared memory: the per-lane traversal keeps its short stack there
     // (kSharedStack entries per thread); the warp-synchronous one uses none.
     // It follows the instantiated variant W, not the configuration, because
@@ -366,7 +395,7 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                                                                  scene, sensors_dev, frames_dev, n_frames,        \
                                                                  tile_prefix_dev, n_tiles, table, seed, out,      \
                                                                  status, work_counter, cfg.tile_rays,             \
-                                                                 C ? *count : none)
+                                                                 C ? *count : none, cc)
     if (count) {
         // the work counted depends on the tree the traversal walks, not on the launch shape
         if (cfg.traversal == 2) LIDAR_LAUNCH_CAST(true, 4, 2);
@@ -422,31 +451,19 @@ cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_word
     return cudaGetLastError();
 }
 
-size_t compact_scratch_bytes(int64_t n)
+size_t fused_compact_scratch_bytes(int64_t n)
 {
-    const int64_t tiles = (n + kCompactTile - 1) / kCompactTile;
-    return ((tiles * sizeof(uint32_t) + 255) / 256) * 256 + ((tiles * sizeof(int64_t) + 255) / 256) * 256 + 256;
+    const int64_t nt = (n + kCompactTileBeams - 1) / kCompactTileBeams;
+    return ((nt * 8 + 255) / 256) * 256 + (((nt + 1) * 4 + 255) / 256) * 256;
 }
 
-cudaError_t launch_compact(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev,
-                           int n_frames, int64_t n, const uint8_t* valid, BeamsOut dense,
-                           const lidar_points& pts, int64_t* n_points_dev, int* status, void* scratch,
-                           size_t scratch_bytes)
+cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev, int n_frames,
+                           int64_t n, BeamsOut dense, const lidar_points& pts, void* compact_scratch, int* status)
 {
-    if (scratch_bytes < compact_scratch_bytes(n)) return cudaErrorInvalidValue;
     const int64_t tiles = (n + kCompactTile - 1) / kCompactTile;
-    if (tiles == 0) {
-        if (n_points_dev) cudaMemsetAsync(n_points_dev, 0, sizeof(int64_t), s);
-        return cudaGetLastError();
-    }
-    char* p = (char*)scratch;
-    uint32_t* counts = (uint32_t*)p;
-    p += ((tiles * sizeof(uint32_t) + 255) / 256) * 256;
-    int64_t* offsets = (int64_t*)p;
-    k_count_valid<<<(unsigned)tiles, kCompactThreads, 0, s>>>(valid, n, counts);
-    k_scan_tiles<<<1, 1024, 0, s>>>(counts, tiles, offsets, n_points_dev);
+    if (tiles == 0) return cudaSuccess;
     k_scatter_points<<<(unsigned)tiles, kCompactThreads, 0, s>>>(sensors_dev, frames_dev, n_frames, n, dense,
-                                                                 offsets, pts, status);
+                                                                 (const int64_t*)compact_scratch, pts, status);
     return cudaGetLastError();
 }
 

@@ -144,15 +144,18 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                         const FrameDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
                         int64_t n_tiles, TableDev table, uint64_t seed, BeamsOut out, int* status,
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
-                        int64_t n_beams_total, const WorkCount* count = nullptr);
+                        int64_t n_beams_total, const WorkCount* count = nullptr, void* compact_scratch = nullptr,
+                        int64_t* n_points_dev = nullptr);
+// ordered compaction fused with the cast: the cast counts kept returns per
+// 1024-beam tile and scans them (compact_scratch of fused_compact_scratch_bytes);
+// launch_scatter then writes the points
+size_t fused_compact_scratch_bytes(int64_t n_beams_total);
+cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev, int n_frames,
+                           int64_t n_beams_total, BeamsOut dense, const lidar_points& pts, void* compact_scratch,
+                           int* status);
 cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_words, unsigned long long* total);
 // frames[i].pose = poses[12 i .. 12 i + 11]
 cudaError_t launch_set_poses(cudaStream_t s, FrameDev* frames, int n_frames, const float* poses);
-cudaError_t launch_compact(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev,
-                           int n_frames, int64_t n_beams_total, const uint8_t* valid, BeamsOut dense,
-                           const lidar_points& pts, int64_t* n_points_dev, int* status, void* scratch,
-                           size_t scratch_bytes);
-size_t compact_scratch_bytes(int64_t n_beams_total);
 cudaError_t launch_ray_order(cudaStream_t s, const float* dirs, int n_beams, uint32_t* order,
                              void* scratch, size_t scratch_bytes);
 size_t ray_order_scratch_bytes(int64_t n_beams);

@@ -537,7 +537,7 @@ static size_t cast_scratch_upper_bound(int64_t n_total)
 {
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     return al(n_total) + 2 * al(4 * n_total) + al(12 * n_total) + al(2 * n_total) + al(4 * n_total) +
-           compact_scratch_bytes(n_total);
+           fused_compact_scratch_bytes(n_total);
 }
 
 // Cast over frames already on the device.  `may_alloc` false: fail instead of
@@ -559,7 +559,7 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
         dense_bytes = (need_valid ? al(n_total) : 0) + (need_range ? al(4 * n_total) : 0) +
                       (need_int ? al(4 * n_total) : 0) + (need_norm ? al(12 * n_total) : 0) +
                       (need_mat ? al(2 * n_total) : 0) + (need_inst ? al(4 * n_total) : 0);
-        const size_t need = dense_bytes + compact_scratch_bytes(n_total);
+        const size_t need = dense_bytes + fused_compact_scratch_bytes(n_total);
         if (c->scratch_bytes < need) {
             if (!may_alloc) {
                 set_error("cast: scratch too small for this batch (recreate the batch)");
@@ -578,13 +578,13 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
         if (need_inst) { out.inst = (uint32_t*)p; p += al(4 * n_total); }
     }
     SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
+    char* comp = points ? dense_base + dense_bytes : nullptr;
     LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, frames_dev, n_frames, prefix_dev, n_tiles, c->table, seed,
-                           out, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total));
-    if (points) {
-        char* comp = dense_base + dense_bytes;
-        LIDAR_CUDA(launch_compact(c->stream, c->sensors_dev, frames_dev, n_frames, n_total, out.valid, out, *points,
-                                  n_points_dev, c->status_dev, comp, c->scratch_bytes - dense_bytes));
-    }
+                           out, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total, nullptr, comp,
+                           n_points_dev));
+    if (points)
+        LIDAR_CUDA(launch_scatter(c->stream, c->sensors_dev, frames_dev, n_frames, n_total, out, *points, comp,
+                                  c->status_dev));
     return LIDAR_OK;
 }
 
@@ -917,13 +917,21 @@ static lidar_status counting_cast(lidar_ctx* c, const lidar_scene* scene, const 
 }
 
 lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
-                              uint64_t seed, lidar_work_counts* out)
+                              uint64_t seed, lidar_work_counts* out, uint32_t* beam_cost_dev)
 {
     LIDAR_CHECK_ARG(c != nullptr && scene != nullptr && out != nullptr, "lidar_count_work: NULL argument");
     DeviceGuard g(c->device);
     unsigned long long h[4];
-    lidar_status st = counting_cast(c, scene, frames, n_frames, seed, false, 0, h, nullptr, nullptr, nullptr);
+    uint32_t* cost = nullptr;
+    int64_t n_total = 0;
+    lidar_status st = counting_cast(c, scene, frames, n_frames, seed, beam_cost_dev != nullptr, 0, h, &cost, nullptr,
+                                    &n_total);
     if (st != LIDAR_OK) return st;
+    if (beam_cost_dev) {
+        LIDAR_CUDA(cudaMemcpyAsync(beam_cost_dev, cost, n_total * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    }
     uint64_t rays = 0;
     for (int32_t k = 0; k < n_frames; ++k) {
         const SensorSlot& sl = c->slots[frames[k].sensor];

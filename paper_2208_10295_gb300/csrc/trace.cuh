@@ -179,11 +179,16 @@ __device__ __forceinline__ void child_boxes(const float4 n0, const float4 n1, co
 // deferred far children.  Returns false if the stack would overflow (the
 // build refuses trees deeper than the stack, so this does not happen).
 //
-// The stack's first kSharedStack entries live in shared memory, laid out
+// The stack's first kSharedStack entries can live in shared memory, laid out
 // [depth][thread] (`sh` points at this thread's column, `sh_stride` = threads
 // per block), so lanes at different depths still hit distinct banks; deeper
-// entries go to a per-thread local array.
-constexpr int kSharedStack = 24;
+// entries go to a per-thread local array.  Measured on GB300 the shared part
+// does not pay (it shrinks the L1 the node fetches live in), so the default
+// depth is 0 and the whole stack is local (L1-cached).
+#ifndef LIDAR_SHARED_STACK
+#define LIDAR_SHARED_STACK 0
+#endif
+constexpr int kSharedStack = LIDAR_SHARED_STACK;
 
 struct SplitStack {
     int2* sh;
@@ -277,11 +282,48 @@ __device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p
 
 // Slab test of the four child boxes of a 4-wide node (child boxes as SoA
 // float4 per plane), same rounding and NaN handling as child_boxes.
+// Packed FP32 pairs (sm_100+ f32x2 arithmetic): each lane of the pair is
+// rounded exactly like the scalar __fsub_rn / __fmul_rn, so the slab distances
+// are bit-identical to slab_t, with half the instructions.
+__device__ __forceinline__ unsigned long long pack2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(unsigned long long v, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+__device__ __forceinline__ unsigned long long slab2(unsigned long long planes, unsigned long long o2,
+                                                    unsigned long long inv2)
+{
+    unsigned long long d, t;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(planes), "l"(o2));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(d), "l"(inv2));
+    return t;
+}
+
+// entry/exit planes already chosen by the ray's direction signs
+__device__ __forceinline__ void slab4_planes(float4 e, float4 x, unsigned long long o2, unsigned long long i2,
+                                             float4& tin, float4& tout)
+{
+    unpack2(slab2(pack2(e.x, e.y), o2, i2), tin.x, tin.y);
+    unpack2(slab2(pack2(e.z, e.w), o2, i2), tin.z, tin.w);
+    unpack2(slab2(pack2(x.x, x.y), o2, i2), tout.x, tout.y);
+    unpack2(slab2(pack2(x.z, x.w), o2, i2), tout.z, tout.w);
+}
+
 __device__ __forceinline__ void slab4(float4 lo, float4 hi, float o, float inv, bool neg, float4& tin, float4& tout)
 {
     const float4 e = neg ? hi : lo, x = neg ? lo : hi;
-    tin = make_float4(slab_t(e.x, o, inv), slab_t(e.y, o, inv), slab_t(e.z, o, inv), slab_t(e.w, o, inv));
-    tout = make_float4(slab_t(x.x, o, inv), slab_t(x.y, o, inv), slab_t(x.z, o, inv), slab_t(x.w, o, inv));
+    const unsigned long long o2 = pack2(o, o), i2 = pack2(inv, inv);
+    unpack2(slab2(pack2(e.x, e.y), o2, i2), tin.x, tin.y);
+    unpack2(slab2(pack2(e.z, e.w), o2, i2), tin.z, tin.w);
+    unpack2(slab2(pack2(x.x, x.y), o2, i2), tout.x, tout.y);
+    unpack2(slab2(pack2(x.z, x.w), o2, i2), tout.z, tout.w);
 }
 
 __device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb)
@@ -315,7 +357,11 @@ __device__ __forceinline__ bool trace_closest4(const SceneDev& S, const RayPre& 
     SplitStack stack;
     stack.sh = sh_stack;
     stack.sh_stride = sh_stride;
-    const bool nx = p.ix < 0.0f, ny = p.iy < 0.0f, nz = p.iz < 0.0f;
+    // entry planes per axis: lo for a positive direction, hi for a negative one;
+    // chosen once per ray as load offsets instead of selects per node
+    const int ex = p.ix < 0.0f ? 1 : 0, ey = p.iy < 0.0f ? 3 : 2, ez = p.iz < 0.0f ? 5 : 4;
+    const unsigned long long ox2 = pack2(p.ox, p.ox), oy2 = pack2(p.oy, p.oy), oz2 = pack2(p.oz, p.oz);
+    const unsigned long long ix2 = pack2(p.ix, p.ix), iy2 = pack2(p.iy, p.iy), iz2 = pack2(p.iz, p.iz);
     int sp = 0;
     int node = 0;
     while (true) {
@@ -325,11 +371,11 @@ __device__ __forceinline__ bool trace_closest4(const SceneDev& S, const RayPre& 
         }
         const float4* q = S.nodes4 + 8 * (int64_t)node;
         float4 tin, tout, ti, to;
-        slab4(__ldg(q + 0), __ldg(q + 1), p.ox, p.ix, nx, tin, tout);
-        slab4(__ldg(q + 2), __ldg(q + 3), p.oy, p.iy, ny, ti, to);
+        slab4_planes(__ldg(q + ex), __ldg(q + (1 - ex)), ox2, ix2, tin, tout);
+        slab4_planes(__ldg(q + ey), __ldg(q + (5 - ey)), oy2, iy2, ti, to);
         tin = make_float4(fmaxf(tin.x, ti.x), fmaxf(tin.y, ti.y), fmaxf(tin.z, ti.z), fmaxf(tin.w, ti.w));
         tout = make_float4(fminf(tout.x, to.x), fminf(tout.y, to.y), fminf(tout.z, to.z), fminf(tout.w, to.w));
-        slab4(__ldg(q + 4), __ldg(q + 5), p.oz, p.iz, nz, ti, to);
+        slab4_planes(__ldg(q + ez), __ldg(q + (9 - ez)), oz2, iz2, ti, to);
         const float4 c4 = __ldg(q + 6);
         float k0 = fmaxf(fmaxf(tin.x, ti.x), kTEps), k1 = fmaxf(fmaxf(tin.y, ti.y), kTEps);
         float k2 = fmaxf(fmaxf(tin.z, ti.z), kTEps), k3 = fmaxf(fmaxf(tin.w, ti.w), kTEps);
@@ -338,21 +384,23 @@ __device__ __forceinline__ bool trace_closest4(const SceneDev& S, const RayPre& 
         int c0 = __float_as_int(c4.x), c1 = __float_as_int(c4.y), c2 = __float_as_int(c4.z), c3 = __float_as_int(c4.w);
         bool h0 = k0 <= fminf(f0, h.cull), h1 = k1 <= fminf(f1, h.cull);
         bool h2 = k2 <= fminf(f2, h.cull), h3 = k3 <= fminf(f3, h.cull);
-        // triangle children first
-#define LIDAR_LEAF4(HIT, C)                                                             \
-        if (HIT && C < 0) {                                                             \
-            if (kCount) {                                                               \
-                ++n_tris;                                                               \
-                atomicOr(&wc->leaf_bits[(~C) >> 5], 1u << ((~C) & 31));                 \
-            }                                                                           \
-            intersect_triangle(S.tris, ~C, p, t_max, h);                                \
-            HIT = false;                                                                \
+        // triangle children first, through one call site
+        unsigned leaves = (h0 && c0 < 0 ? 1u : 0u) | (h1 && c1 < 0 ? 2u : 0u) | (h2 && c2 < 0 ? 4u : 0u) |
+                          (h3 && c3 < 0 ? 8u : 0u);
+        h0 = h0 && c0 >= 0;
+        h1 = h1 && c1 >= 0;
+        h2 = h2 && c2 >= 0;
+        h3 = h3 && c3 >= 0;
+        while (leaves) {
+            const int j = __ffs(leaves) - 1;
+            leaves &= leaves - 1;
+            const int leaf = ~(j == 0 ? c0 : (j == 1 ? c1 : (j == 2 ? c2 : c3)));
+            if (kCount) {
+                ++n_tris;
+                atomicOr(&wc->leaf_bits[leaf >> 5], 1u << (leaf & 31));
+            }
+            intersect_triangle(S.tris, leaf, p, t_max, h);
         }
-        LIDAR_LEAF4(h0, c0)
-        LIDAR_LEAF4(h1, c1)
-        LIDAR_LEAF4(h2, c2)
-        LIDAR_LEAF4(h3, c3)
-#undef LIDAR_LEAF4
         // internal children that are still in front of the best hit, near to far
         k0 = (h0 && k0 <= h.cull) ? k0 : INFINITY;
         k1 = (h1 && k1 <= h.cull) ? k1 : INFINITY;

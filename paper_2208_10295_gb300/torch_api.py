@@ -226,13 +226,14 @@ class Lidar:
                                           _ptr(target_valid), _ptr(loss), _ptr(grad_table), _ptr(grad_gain)),
                 "lidar_cast_backward_mse")
 
-    def count_work(self, scene: Scene, frames, seed: int):
+    def count_work(self, scene: Scene, frames, seed: int, beam_cost: torch.Tensor = None):
         """Work of one cast (instrumented kernel): node fetches, triangle tests,
-        distinct nodes/triangles touched, and the bytes they stand for."""
+        distinct nodes/triangles touched, and the bytes they stand for.
+        `beam_cost` (int32 [n_beams], optional) receives each beam's cost."""
         fr = _frames_array(frames)
         wc = C.lidar_work_counts()
         C.check(C.lidar_count_work(self.handle, scene.handle, fr.ctypes.data_as(ctypes.c_void_p), len(fr),
-                                   ctypes.c_uint64(seed), ctypes.byref(wc)), "lidar_count_work")
+                                   ctypes.c_uint64(seed), ctypes.byref(wc), _ptr(beam_cost)), "lidar_count_work")
         d = {k: int(getattr(wc, k)) for k, _ in wc._fields_}
         d["unique_node_bytes"] = d["unique_nodes"] * d["node_bytes"]
         d["unique_tri_bytes"] = d["unique_tris"] * 48
