@@ -346,11 +346,15 @@ lidar_status lidar_count_work(lidar_ctx* ctx, const lidar_scene* scene, const li
  * the traversal cost of every beam on `frame` (one frame of that slot, cast
  * with counting enabled), and reorders the 32-beam groups so that the most
  * expensive groups run first (longest-processing-time-first), which shortens
- * the tail of a cast where the last warps would otherwise run alone.  The
- * schedule never changes results, only their timing; use the costs of a nearby
- * pose (e.g. the previous frame).  Synchronises. */
+ * the tail of a cast where the last warps would otherwise run alone.
+ * mode 0: whole 32-beam groups of the Morton order, by their largest cost;
+ * mode 1: single beams by cost bucket (4 buckets per octave of cost, most
+ *         expensive first, Morton order within a bucket), so that each warp
+ *         gets beams of similar cost (fewer idle lanes).
+ * The schedule never changes results, only their timing; use the costs of a
+ * nearby pose (e.g. the previous frame).  Synchronises. */
 lidar_status lidar_schedule_by_cost(lidar_ctx* ctx, const lidar_scene* scene, const lidar_frame* frame,
-                                    uint64_t seed);
+                                    uint64_t seed, int32_t mode);
 
 /* Restores the Morton order of a slot. */
 lidar_status lidar_reset_schedule(lidar_ctx* ctx, int32_t slot);

@@ -117,7 +117,8 @@ _PROTOS = [
                                                        c_vp]),
     ("lidar_count_work", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.POINTER(lidar_work_counts), c_vp]),
-    ("lidar_schedule_by_cost", ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(lidar_frame), ctypes.c_uint64]),
+    ("lidar_schedule_by_cost", ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(lidar_frame), ctypes.c_uint64,
+                                              ctypes.c_int32]),
     ("lidar_reset_schedule", ctypes.c_int, [c_vp, ctypes.c_int32]),
     ("lidar_get_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
     ("lidar_set_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),

@@ -501,6 +501,38 @@ size_t cost_schedule_scratch_bytes(int64_t n)
     return ((g * 4 + 255) / 256) * 256 * 2 + radix_sort_scratch_bytes(g);
 }
 
+namespace {
+// key of beam at base-order position p: cost bucket (4 per octave, most
+// expensive first) above the base position, so equal buckets keep the
+// base (Morton) order
+__global__ void k_bucket_keys(const uint32_t* __restrict__ cost, const uint32_t* __restrict__ base, int n,
+                              uint64_t* keys, uint32_t* vals)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t b = base[p];
+    const uint32_t bucket = (uint32_t)(4.0f * log2f((float)cost[b] + 1.0f));
+    keys[p] = ((uint64_t)(63u - min(bucket, 63u)) << 32) | (uint64_t)p;
+    vals[p] = b;
+}
+}  // namespace
+
+size_t bucket_schedule_scratch_bytes(int64_t n)
+{
+    return ((n * 8 + 255) / 256) * 256 + radix_sort_scratch_bytes(n);
+}
+
+cudaError_t launch_bucket_schedule(cudaStream_t s, const uint32_t* cost, const uint32_t* base_order, int n,
+                                   uint32_t* new_order, void* scratch, size_t scratch_bytes)
+{
+    if (n == 0) return cudaSuccess;
+    if (scratch_bytes < bucket_schedule_scratch_bytes(n)) return cudaErrorInvalidValue;
+    uint64_t* keys = (uint64_t*)scratch;
+    char* rest = (char*)scratch + ((n * 8 + 255) / 256) * 256;
+    k_bucket_keys<<<(n + 255) / 256, 256, 0, s>>>(cost, base_order, n, keys, new_order);
+    return radix_sort_pairs_u64(s, keys, new_order, n, 38, rest, scratch_bytes - (rest - (char*)scratch));
+}
+
 cudaError_t launch_cost_schedule(cudaStream_t s, const uint32_t* cost, const uint32_t* base_order, int n,
                                  uint32_t* new_order, void* scratch, size_t scratch_bytes)
 {

@@ -164,6 +164,11 @@ size_t ray_order_scratch_bytes(int64_t n_beams);
 cudaError_t launch_cost_schedule(cudaStream_t s, const uint32_t* cost, const uint32_t* base_order, int n_beams,
                                  uint32_t* new_order, void* scratch, size_t scratch_bytes);
 size_t cost_schedule_scratch_bytes(int64_t n_beams);
+// Orders single beams by cost bucket (4 per octave, most expensive first),
+// keeping the base order within a bucket, so each warp gets beams of similar cost.
+cudaError_t launch_bucket_schedule(cudaStream_t s, const uint32_t* cost, const uint32_t* base_order, int n_beams,
+                                   uint32_t* new_order, void* scratch, size_t scratch_bytes);
+size_t bucket_schedule_scratch_bytes(int64_t n_beams);
 
 // adjoint.cu
 cudaError_t launch_build_tables(cudaStream_t s, const float* params, int M, float* table);

@@ -946,8 +946,10 @@ lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lida
     return LIDAR_OK;
 }
 
-lidar_status lidar_schedule_by_cost(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frame, uint64_t seed)
+lidar_status lidar_schedule_by_cost(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frame, uint64_t seed,
+                                    int32_t mode)
 {
+    LIDAR_CHECK_ARG(mode == 0 || mode == 1, "lidar_schedule_by_cost: mode is 0 or 1");
     LIDAR_CHECK_ARG(c != nullptr && scene != nullptr && frame != nullptr, "lidar_schedule_by_cost: NULL argument");
     const int slot = frame->sensor;
     LIDAR_CHECK_ARG(slot >= 0 && slot < LIDAR_MAX_SENSORS, "lidar_schedule_by_cost: slot out of range");
@@ -961,11 +963,15 @@ lidar_status lidar_schedule_by_cost(lidar_ctx* c, const lidar_scene* scene, cons
     unsigned long long h[4];
     uint32_t* cost = nullptr;
     void* tail = nullptr;
-    lidar_status st = counting_cast(c, scene, frame, 1, seed, true, cost_schedule_scratch_bytes(n), h, &cost,
-                                    &tail, nullptr);
+    const size_t need = std::max(cost_schedule_scratch_bytes(n), bucket_schedule_scratch_bytes(n));
+    lidar_status st = counting_cast(c, scene, frame, 1, seed, true, need, h, &cost, &tail, nullptr);
     if (st != LIDAR_OK) return st;
     const size_t tail_bytes = c->scratch_bytes - (size_t)((char*)tail - (char*)c->scratch);
-    LIDAR_CUDA(launch_cost_schedule(c->stream, cost, sl.base_order_dev, (int)n, sl.order_dev, tail, tail_bytes));
+    if (mode == 0)
+        LIDAR_CUDA(launch_cost_schedule(c->stream, cost, sl.base_order_dev, (int)n, sl.order_dev, tail, tail_bytes));
+    else
+        LIDAR_CUDA(launch_bucket_schedule(c->stream, cost, sl.base_order_dev, (int)n, sl.order_dev, tail,
+                                          tail_bytes));
     LIDAR_CUDA(cudaStreamSynchronize(c->stream));
     return LIDAR_OK;
 }

@@ -241,12 +241,13 @@ class Lidar:
         d["io_bytes"] = d["rays"] * (12 + 4 + 1)
         return d
 
-    def schedule_by_cost(self, scene: Scene, frame, seed: int):
-        """Most-expensive-first order of 32-beam groups, from the costs measured
-        on `frame` (one frame record of the slot to reschedule)."""
+    def schedule_by_cost(self, scene: Scene, frame, seed: int, mode: int = 0):
+        """Most-expensive-first ray order from the costs measured on `frame`
+        (one frame record of the slot to reschedule); mode 0 orders 32-beam
+        groups, mode 1 single beams by cost bucket."""
         fr = _frames_array(frame).reshape(-1)[:1]
         C.check(C.lidar_schedule_by_cost(self.handle, scene.handle, fr.ctypes.data_as(ctypes.POINTER(C.lidar_frame)),
-                                         ctypes.c_uint64(seed)), "lidar_schedule_by_cost")
+                                         ctypes.c_uint64(seed), int(mode)), "lidar_schedule_by_cost")
 
     def reset_schedule(self, slot: int):
         C.check(C.lidar_reset_schedule(self.handle, slot), "lidar_reset_schedule")

@@ -26,7 +26,7 @@ SPACE = {
     "blocks_per_sm": (2, 4, 8, 12),
     "traversal": (0, 1, 2),
     "ray_order": (0, 1),
-    "schedule": ("morton", "cost"),
+    "schedule": ("morton", "cost", "bucket"),
 }
 
 
@@ -59,8 +59,8 @@ def candidates():
     for bt, bps, tv, ro, sc in itertools.product(*SPACE.values()):
         if bt * bps > 2048 or bt * bps < 256:
             continue
-        if ro == 0 and sc == "cost":
-            continue  # the cost schedule reorders the Morton order
+        if ro == 0 and sc != "morton":
+            continue  # the cost schedules reorder the Morton order
         yield {"block_threads": bt, "blocks_per_sm": bps, "tile_rays": 32, "traversal": tv, "ray_order": ro,
                "schedule": sc}
 
@@ -70,11 +70,11 @@ def apply(L, scene, cfg, schedule_frames, seed):
     slots = sorted({int(s) for s in np.ascontiguousarray(schedule_frames)["sensor"]})
     for s in slots:
         L.reset_schedule(s)
-    if cfg.get("schedule") == "cost":
+    if cfg.get("schedule") in ("cost", "bucket"):
         fr = np.ascontiguousarray(schedule_frames)
         for s in slots:
             first = fr[fr["sensor"] == s][:1]
-            L.schedule_by_cost(scene, first, seed)
+            L.schedule_by_cost(scene, first, seed, mode=0 if cfg["schedule"] == "cost" else 1)
 
 
 def autotune(L, scene, frames, seed, schedule_frames=None, cache_path=DEFAULT_CACHE, reps=8, flush_l2=True,

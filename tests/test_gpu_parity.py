@@ -134,10 +134,11 @@ def test_ray_order_and_launch_shapes_bit_identical(L):
                 assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), (cfg, k)
         # the cost-ordered schedule changes timing only
         L.set_launch_config(**cfg0)
-        L.schedule_by_cost(scene, w.frames[:1], w.seed)
-        other, _ = gpu_cast(L, w, scene)
-        for k in base:
-            assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), ("cost schedule", k)
+        for mode in (0, 1):
+            L.schedule_by_cost(scene, w.frames[:1], w.seed, mode=mode)
+            other, _ = gpu_cast(L, w, scene)
+            for k in base:
+                assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), ("cost schedule", mode, k)
     finally:
         L.set_launch_config(**cfg0)
         L.reset_schedule(0)
