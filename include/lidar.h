@@ -369,6 +369,8 @@ typedef struct {
     int32_t traversal;       /* binary tree: 0 = each lane tests its triangles as it meets them,
                                 1 = warp-synchronous with postponed triangle tests;
                                 2 = 4-wide tree, per lane, children visited near to far */
+    int32_t fused_scatter;   /* 1: the point-cloud scatter runs inside the cast kernel after a grid-wide
+                                wait (cooperative launch); 0: as a separate kernel */
 } lidar_launch_config;
 
 lidar_status lidar_get_launch_config(lidar_ctx* ctx, lidar_launch_config* out);

@@ -72,7 +72,8 @@ class lidar_work_counts(ctypes.Structure):
 
 class lidar_launch_config(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("tile_rays", ctypes.c_int32), ("ray_order", ctypes.c_int32), ("traversal", ctypes.c_int32)]
+                ("tile_rays", ctypes.c_int32), ("ray_order", ctypes.c_int32), ("traversal", ctypes.c_int32),
+                ("fused_scatter", ctypes.c_int32)]
 
 
 assert ctypes.sizeof(lidar_frame) == 56

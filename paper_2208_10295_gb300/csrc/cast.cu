@@ -6,6 +6,7 @@
 //   intensity -> strongest of the sub-rays
 // writing a dense per-beam record.  A second stage compacts the kept returns
 // in (frame, beam) order.
+
 #include "common.cuh"
 #include "philox.cuh"
 #include "trace.cuh"
@@ -119,12 +120,125 @@ __device__ __forceinline__ int find_frame(const int64_t* __restrict__ prefix, in
 // Persistent kernel, work taken per warp: lane 0 claims a tile of `tile_rays`
 // consecutive ray-order positions of one frame (a multiple of 32) and the warp
 // traces it 32 rays at a time; no block-wide barrier.
+__device__ __forceinline__ int frame_of_index(const FrameDev* __restrict__ frames, int n_frames, int64_t idx)
+{
+    int lo = 0, hi = n_frames - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (frames[mid].beam_offset <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kCompactTileBeams = 1024;
+constexpr int kScatterItems = 4;
+
+// Ordered scatter of one compaction tile of kCompactTileBeams dense beams by
+// the calling block (blockDim a multiple of 32, at most 256).  A chunk is
+// kScatterItems rows of blockDim consecutive beams, row k read by thread t at
+// beam chunk + k * blockDim + t, so the kept beams of one warp row land in
+// consecutive output slots (coalesced stores); ballots rank them in the warp
+// and one table of per-(row, warp) counts in shared memory orders the rows
+// and warps.  `s_warp` holds kScatterItems * 8 words.
+__device__ void scatter_tile(const SensorDev* __restrict__ sensors, const FrameDev* __restrict__ frames,
+                             int n_frames, int64_t n, const BeamsOut& dense, int64_t tile, int64_t tile_offset,
+                             const lidar_points& pts, int* status, uint32_t* s_warp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    const int chunk_beams = blockDim.x * kScatterItems;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int64_t running = tile_offset;
+    for (int chunk = 0; chunk < kCompactTileBeams; chunk += chunk_beams) {
+        const int64_t base = tile * kCompactTileBeams + chunk;
+        // gather every field of the chunk's beams before the scan and the
+        // first store: the point arrays could alias the dense ones as far as
+        // the compiler knows, so loads after a store would wait for it
+        bool v[kScatterItems];
+        float rg[kScatterItems], it[kScatterItems], nx[kScatterItems], ny[kScatterItems], nz[kScatterItems];
+        float dx[kScatterItems], dy[kScatterItems], dz[kScatterItems];
+        uint16_t mt[kScatterItems];
+        uint32_t in[kScatterItems], bm[kScatterItems], fk[kScatterItems];
+#pragma unroll
+        for (int k = 0; k < kScatterItems; ++k) {
+            rg[k] = it[k] = nx[k] = ny[k] = nz[k] = dx[k] = dy[k] = dz[k] = 0.0f;
+            mt[k] = 0;
+            in[k] = bm[k] = fk[k] = 0;
+            v[k] = false;
+            const int row = chunk + k * blockDim.x + threadIdx.x;
+            const int64_t idx = base + k * blockDim.x + threadIdx.x;
+            if (row >= kCompactTileBeams || idx >= n) continue;
+            v[k] = __ldcg(&dense.valid[idx]) != 0;
+            const int fi = frame_of_index(frames, n_frames, idx);
+            const FrameDev& fr = frames[fi];
+            bm[k] = (uint32_t)(idx - fr.beam_offset);
+            fk[k] = (uint32_t)fi;
+            rg[k] = __ldcg(&dense.range[idx]);
+            if (pts.xyz) {
+                const float* dir = sensors[fr.sensor].dirs + 3 * (int64_t)bm[k];
+                dx[k] = __ldg(dir);
+                dy[k] = __ldg(dir + 1);
+                dz[k] = __ldg(dir + 2);
+            }
+            if (pts.intensity) it[k] = __ldcg(&dense.intensity[idx]);
+            if (pts.normal) {
+                nx[k] = __ldcg(&dense.normal[3 * idx + 0]);
+                ny[k] = __ldcg(&dense.normal[3 * idx + 1]);
+                nz[k] = __ldcg(&dense.normal[3 * idx + 2]);
+            }
+            if (pts.material) mt[k] = __ldcg(&dense.mat[idx]);
+            if (pts.instance) in[k] = __ldcg(&dense.inst[idx]);
+        }
+        unsigned mask[kScatterItems];
+#pragma unroll
+        for (int k = 0; k < kScatterItems; ++k) {
+            mask[k] = __ballot_sync(0xffffffffu, v[k]);
+            if (lane == 0) s_warp[k * 8 + warp] = (uint32_t)__popc(mask[k]);
+        }
+        __syncthreads();
+        // slots before row k, warp w: all of rows < k, then warps < w of row k
+        uint32_t before[kScatterItems], total = 0;
+#pragma unroll
+        for (int k = 0; k < kScatterItems; ++k) {
+            for (int w = 0; w < n_warps; ++w) {
+                const uint32_t c = s_warp[k * 8 + w];
+                if (w == warp) before[k] = total;
+                total += c;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kScatterItems; ++k) {
+            if (!v[k]) continue;
+            const int64_t pos = running + before[k] + (uint32_t)__popc(mask[k] & lt_mask);
+            if (pos >= pts.capacity) {
+                raise_status(status, ST_CAPACITY);
+                continue;
+            }
+            if (pts.xyz) {
+                pts.xyz[3 * pos + 0] = rg[k] * dx[k];
+                pts.xyz[3 * pos + 1] = rg[k] * dy[k];
+                pts.xyz[3 * pos + 2] = rg[k] * dz[k];
+            }
+            if (pts.range) pts.range[pos] = rg[k];
+            if (pts.intensity) pts.intensity[pos] = it[k];
+            if (pts.normal) {
+                pts.normal[3 * pos + 0] = nx[k];
+                pts.normal[3 * pos + 1] = ny[k];
+                pts.normal[3 * pos + 2] = nz[k];
+            }
+            if (pts.material) pts.material[pos] = mt[k];
+            if (pts.instance) pts.instance[pos] = in[k];
+            if (pts.beam) pts.beam[pos] = bm[k];
+            if (pts.frame) pts.frame[pos] = fk[k];
+        }
+        running += total;
+        __syncthreads();
+    }
+}
+
 // Counts of kept returns per compaction tile of kCompactTileBeams dense
 // indices, gathered by the cast itself (warp-aggregated atomics); the last
 // block to finish turns them into exclusive offsets, so the ordered
 // compaction needs only one more kernel.
-constexpr int kCompactTileBeams = 1024;
-
 struct CompactCounts {
     unsigned* counts;     // [n_tiles], zeroed before the cast; NULL: not counting
     unsigned* done;       // finished-block counter, zeroed before the cast
@@ -167,13 +281,51 @@ __device__ void scan_counts_block(const CompactCounts& cc)
     if (threadIdx.x == nt - 1 && cc.total) *cc.total = s_part[nt - 1];
 }
 
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier number `k` (1, 2, ...) over a counter zeroed before the
+// launch, for cooperative launches only (all blocks co-resident).  The wait
+// is bounded: after kBarrierTimeoutNs it raises ST_TIMEOUT and returns false
+// in every thread of the block, which then leaves the kernel.
+constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;
+
+__device__ bool grid_barrier(unsigned* counter, unsigned k, int* status)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter, 1u);
+        const unsigned target = k * gridDim.x;
+        const uint64_t t0 = global_ns();
+        int ok = 1;
+        while (*(volatile unsigned*)counter < target) {
+            if (global_ns() - t0 > kBarrierTimeoutNs) {
+                raise_status(status, ST_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 template <bool kCount, int kMinBlocks, int kTrav>
 __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const SensorDev* __restrict__ sensors,
                                               const FrameDev* __restrict__ frames, int n_frames,
                                               const int64_t* __restrict__ tile_prefix, int64_t n_tiles,
                                               TableDev T, uint64_t seed, BeamsOut out, int* status,
                                               unsigned long long* work_counter, int tile_rays, WorkCount wc,
-                                              CompactCounts cc)
+                                              CompactCounts cc, lidar_points pts, int64_t n_beams_total, int fused)
 {
     const int lane = threadIdx.x & 31;
     extern __shared__ int2 sh_stack[];  // [kSharedStack][blockDim.x]
@@ -237,7 +389,17 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
             if (kCount && wc.beam_cost) wc.beam_cost[fr.beam_offset + beam] = cost;
         }
     }
-    if (cc.counts) {
+    if (cc.counts && fused) {
+        // cooperative launch: every block of the grid is resident, so the grid
+        // can wait for the cast, scan the tile counts, then scatter the points
+        if (!grid_barrier(cc.done, 1, status)) return;
+        if (blockIdx.x == 0) scan_counts_block(cc);
+        if (!grid_barrier(cc.done, 2, status)) return;
+        __shared__ uint32_t s_warp[kScatterItems * 8];
+        for (int64_t t = blockIdx.x; t < cc.n_tiles; t += gridDim.x)
+            scatter_tile(sensors, frames, n_frames, n_beams_total, out, t, __ldcg(&cc.offsets[t]), pts, status,
+                         s_warp);
+    } else if (cc.counts) {
         __shared__ bool s_last;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -259,69 +421,13 @@ constexpr int kCompactItems = 4;
 constexpr int kCompactTile = kCompactThreads * kCompactItems;
 static_assert(kCompactTile == kCompactTileBeams, "the scatter tiles are the cast's counting tiles");
 
-__device__ __forceinline__ int frame_of_index(const FrameDev* __restrict__ frames, int n_frames, int64_t idx)
-{
-    int lo = 0, hi = n_frames - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (frames[mid].beam_offset <= idx) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
+// One compaction tile (kCompactTileBeams beams) per block.
 __global__ void __launch_bounds__(kCompactThreads) k_scatter_points(
     const SensorDev* __restrict__ sensors, const FrameDev* __restrict__ frames, int n_frames, int64_t n,
     BeamsOut dense, const int64_t* __restrict__ tile_offsets, lidar_points pts, int* status)
 {
-    __shared__ uint32_t s_warp[kCompactThreads / 32];
-    __shared__ int64_t s_run;
-    const int64_t base = (int64_t)blockIdx.x * kCompactTile;
-    if (threadIdx.x == 0) s_run = tile_offsets[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int it = 0; it < kCompactItems; ++it) {
-        const int64_t idx = base + (int64_t)it * kCompactThreads + threadIdx.x;
-        const bool v = idx < n && dense.valid[idx];
-        const uint32_t bal = __ballot_sync(0xffffffffu, v);
-        if (lane == 0) s_warp[warp] = __popc(bal);
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int w = 0; w < kCompactThreads / 32; ++w) {
-            const uint32_t c = s_warp[w];
-            if (w < warp) before += c;
-            total += c;
-        }
-        const int64_t pos = s_run + before + __popc(bal & ((1u << lane) - 1u));
-        if (v) {
-            if (pos < pts.capacity) {
-                const int fi = frame_of_index(frames, n_frames, idx);
-                const FrameDev& fr = frames[fi];
-                const uint32_t beam = (uint32_t)(idx - fr.beam_offset);
-                const float d = dense.range[idx];
-                if (pts.xyz) {
-                    const float* dir = sensors[fr.sensor].dirs + 3 * (int64_t)beam;
-                    pts.xyz[3 * pos + 0] = d * dir[0];
-                    pts.xyz[3 * pos + 1] = d * dir[1];
-                    pts.xyz[3 * pos + 2] = d * dir[2];
-                }
-                if (pts.range) pts.range[pos] = d;
-                if (pts.intensity) pts.intensity[pos] = dense.intensity[idx];
-                if (pts.normal) {
-                    pts.normal[3 * pos + 0] = dense.normal[3 * idx + 0];
-                    pts.normal[3 * pos + 1] = dense.normal[3 * idx + 1];
-                    pts.normal[3 * pos + 2] = dense.normal[3 * idx + 2];
-                }
-                if (pts.material) pts.material[pos] = dense.mat[idx];
-                if (pts.instance) pts.instance[pos] = dense.inst[idx];
-                if (pts.beam) pts.beam[pos] = beam;
-                if (pts.frame) pts.frame[pos] = (uint32_t)fi;
-            } else {
-                raise_status(status, ST_CAPACITY);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_run += total;
-        __syncthreads();
-    }
+    __shared__ uint32_t s_warp[kScatterItems * 8];
+    scatter_tile(sensors, frames, n_frames, n, dense, blockIdx.x, tile_offsets[blockIdx.x], pts, status, s_warp);
 }
 
 // ------------------------------------------------------------------ ray order
@@ -358,13 +464,60 @@ __global__ void k_dir_keys(const float* __restrict__ dirs, int n, uint32_t* keys
 
 }  // namespace
 
+namespace {
+
+struct CastArgs {
+    SceneDev scene;
+    const SensorDev* sensors;
+    const FrameDev* frames;
+    int n_frames;
+    const int64_t* prefix;
+    int64_t n_tiles;
+    TableDev table;
+    uint64_t seed;
+    BeamsOut out;
+    int* status;
+    unsigned long long* work_counter;
+    int tile_rays;
+    WorkCount wc;
+    CompactCounts cc;
+    lidar_points pts;
+    int64_t n_total;
+    int fused;
+};
+
+template <bool C, int V, int W>
+cudaError_t launch_one(cudaStream_t s, CastArgs a, int64_t grid, int block, size_t smem, int num_sms)
+{
+    auto fn = k_cast<C, V, W>;
+    if (a.fused) {
+        // every block must be resident for the grid-wide waits
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        if (grid > (int64_t)per_sm * num_sms) grid = (int64_t)per_sm * num_sms;
+        void* args[] = {&a.scene, &a.sensors, &a.frames, &a.n_frames, &a.prefix, &a.n_tiles, &a.table, &a.seed,
+                        &a.out, &a.status, &a.work_counter, &a.tile_rays, &a.wc, &a.cc, &a.pts, &a.n_total,
+                        &a.fused};
+        return cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)grid), dim3(block), args, smem, s);
+    }
+    fn<<<(unsigned)grid, block, smem, s>>>(a.scene, a.sensors, a.frames, a.n_frames, a.prefix, a.n_tiles, a.table,
+                                            a.seed, a.out, a.status, a.work_counter, a.tile_rays, a.wc, a.cc, a.pts,
+                                            a.n_total, a.fused);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* sensors_dev,
                         const FrameDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
                         int64_t n_tiles, TableDev table, uint64_t seed, BeamsOut out, int* status,
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
                         int64_t n_beams_total, const WorkCount* count, void* compact_scratch,
-                        int64_t* n_points_dev)
+                        int64_t* n_points_dev, const lidar_points* points, bool* scattered)
 {
+    if (scattered) *scattered = false;
     if (n_tiles == 0) return cudaSuccess;
     cudaMemsetAsync(work_counter, 0, sizeof(unsigned long long), s);
     const int64_t warps = cfg.block_threads / 32;
@@ -374,47 +527,61 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     // up to 128 registers, <= 768 -> 85, more -> 64
     const int resident = cfg.block_threads * cfg.blocks_per_sm;
     const int variant = resident <= 512 ? 2 : (resident <= 768 ? 3 : 4);
-    const WorkCount none{nullptr, nullptr, nullptr, nullptr};
-    CompactCounts cc{nullptr, nullptr, nullptr, nullptr, 0};
+    CastArgs a{};
+    a.scene = scene;
+    a.sensors = sensors_dev;
+    a.frames = frames_dev;
+    a.n_frames = n_frames;
+    a.prefix = tile_prefix_dev;
+    a.n_tiles = n_tiles;
+    a.table = table;
+    a.seed = seed;
+    a.out = out;
+    a.status = status;
+    a.work_counter = work_counter;
+    a.tile_rays = cfg.tile_rays;
+    a.wc = count ? *count : WorkCount{nullptr, nullptr, nullptr, nullptr};
+    a.n_total = n_beams_total;
     if (compact_scratch) {
         const int64_t nt = (n_beams_total + kCompactTileBeams - 1) / kCompactTileBeams;
-        cc.n_tiles = nt;
-        cc.offsets = (int64_t*)compact_scratch;
-        cc.counts = (unsigned*)((char*)compact_scratch + ((nt * 8 + 255) / 256) * 256);
-        cc.done = cc.counts + nt;
-        cc.total = n_points_dev;
-        cudaMemsetAsync(cc.counts, 0, (nt + 1) * sizeof(unsigned), s);
+        a.cc.n_tiles = nt;
+        a.cc.offsets = (int64_t*)compact_scratch;
+        a.cc.counts = (unsigned*)((char*)compact_scratch + ((nt * 8 + 255) / 256) * 256);
+        a.cc.done = a.cc.counts + nt;
+        a.cc.total = n_points_dev;
+        cudaMemsetAsync(a.cc.counts, 0, (nt + 1) * sizeof(unsigned), s);
+        if (points && cfg.fused_scatter) {
+            a.pts = *points;
+            a.fused = 1;
+        }
     }
-    // dynamic shared memory: the per-lane traversal keeps its short stack there
-    // (kSharedStack entries per thread); the warp-synchronous one uses none.
-    // It follows the instantiated variant W, not the configuration, because
-    // the counting launch always uses the per-lane traversal.
+    // dynamic shared memory: the per-lane traversals keep kSharedStack stack
+    // entries per thread there; the warp-synchronous one uses none.  It
+    // follows the instantiated variant W, not the configuration, because the
+    // counting launch always uses a per-lane traversal.
     const size_t stack_bytes = (size_t)kSharedStack * cfg.block_threads * sizeof(int2);
-#define LIDAR_LAUNCH_CAST(C, V, W)                                                                               \
-    k_cast<C, V, W><<<(unsigned)grid, cfg.block_threads, (W) == 1 ? 0 : stack_bytes, s>>>(                      \
-                                                                 scene, sensors_dev, frames_dev, n_frames,        \
-                                                                 tile_prefix_dev, n_tiles, table, seed, out,      \
-                                                                 status, work_counter, cfg.tile_rays,             \
-                                                                 C ? *count : none, cc)
+    const int bt = cfg.block_threads;
+    cudaError_t e;
     if (count) {
         // the work counted depends on the tree the traversal walks, not on the launch shape
-        if (cfg.traversal == 2) LIDAR_LAUNCH_CAST(true, 4, 2);
-        else LIDAR_LAUNCH_CAST(true, 4, 0);
+        a.fused = 0;
+        e = cfg.traversal == 2 ? launch_one<true, 4, 2>(s, a, grid, bt, stack_bytes, num_sms)
+                               : launch_one<true, 4, 0>(s, a, grid, bt, stack_bytes, num_sms);
     } else if (cfg.traversal == 1) {
-        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, 1);
-        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, 1);
-        else LIDAR_LAUNCH_CAST(false, 4, 1);
+        e = variant == 2   ? launch_one<false, 2, 1>(s, a, grid, bt, 0, num_sms)
+            : variant == 3 ? launch_one<false, 3, 1>(s, a, grid, bt, 0, num_sms)
+                           : launch_one<false, 4, 1>(s, a, grid, bt, 0, num_sms);
     } else if (cfg.traversal == 2) {
-        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, 2);
-        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, 2);
-        else LIDAR_LAUNCH_CAST(false, 4, 2);
+        e = variant == 2   ? launch_one<false, 2, 2>(s, a, grid, bt, stack_bytes, num_sms)
+            : variant == 3 ? launch_one<false, 3, 2>(s, a, grid, bt, stack_bytes, num_sms)
+                           : launch_one<false, 4, 2>(s, a, grid, bt, stack_bytes, num_sms);
     } else {
-        if (variant == 2) LIDAR_LAUNCH_CAST(false, 2, 0);
-        else if (variant == 3) LIDAR_LAUNCH_CAST(false, 3, 0);
-        else LIDAR_LAUNCH_CAST(false, 4, 0);
+        e = variant == 2   ? launch_one<false, 2, 0>(s, a, grid, bt, stack_bytes, num_sms)
+            : variant == 3 ? launch_one<false, 3, 0>(s, a, grid, bt, stack_bytes, num_sms)
+                           : launch_one<false, 4, 0>(s, a, grid, bt, stack_bytes, num_sms);
     }
-#undef LIDAR_LAUNCH_CAST
-    return cudaGetLastError();
+    if (e == cudaSuccess && scattered) *scattered = a.fused != 0;
+    return e;
 }
 
 namespace {

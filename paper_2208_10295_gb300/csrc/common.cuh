@@ -108,6 +108,7 @@ struct LaunchCfg {
     int tile_rays;
     int ray_order;
     int traversal;
+    int fused_scatter;   // compaction scatter inside the cast (cooperative launch)
 };
 
 // ------------------------------------------------------------------ kernel launchers
@@ -145,10 +146,13 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                         int64_t n_tiles, TableDev table, uint64_t seed, BeamsOut out, int* status,
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
                         int64_t n_beams_total, const WorkCount* count = nullptr, void* compact_scratch = nullptr,
-                        int64_t* n_points_dev = nullptr);
+                        int64_t* n_points_dev = nullptr, const lidar_points* points = nullptr,
+                        bool* scattered = nullptr);
 // ordered compaction fused with the cast: the cast counts kept returns per
 // 1024-beam tile and scans them (compact_scratch of fused_compact_scratch_bytes);
-// launch_scatter then writes the points
+// with `points` and cfg.fused_scatter it also writes the points after a
+// grid-wide wait (cooperative launch, *scattered = true), otherwise
+// launch_scatter writes them
 size_t fused_compact_scratch_bytes(int64_t n_beams_total);
 cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev, int n_frames,
                            int64_t n_beams_total, BeamsOut dense, const lidar_points& pts, void* compact_scratch,

@@ -83,7 +83,7 @@ struct lidar_ctx {
     size_t frames_cap = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
-    LaunchCfg cfg{128, 8, 32, 1, 0};
+    LaunchCfg cfg{128, 4, 32, 1, 2, 1};
     std::set<lidar_scene*> scenes;
 };
 
@@ -168,6 +168,9 @@ lidar_status lidar_create(int device, void* cuda_stream, lidar_ctx** out)
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    if (!coop) c->cfg.fused_scatter = 0;
     void* p = nullptr;
     cudaError_t e = dev_alloc(&p, 256);
     if (e != cudaSuccess) {
@@ -579,10 +582,11 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
     }
     SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
     char* comp = points ? dense_base + dense_bytes : nullptr;
+    bool scattered = false;
     LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, frames_dev, n_frames, prefix_dev, n_tiles, c->table, seed,
                            out, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total, nullptr, comp,
-                           n_points_dev));
-    if (points)
+                           n_points_dev, points, &scattered));
+    if (points && !scattered)
         LIDAR_CUDA(launch_scatter(c->stream, c->sensors_dev, frames_dev, n_frames, n_total, out, *points, comp,
                                   c->status_dev));
     return LIDAR_OK;
@@ -1000,6 +1004,7 @@ lidar_status lidar_get_launch_config(lidar_ctx* c, lidar_launch_config* out)
     out->tile_rays = c->cfg.tile_rays;
     out->ray_order = c->cfg.ray_order;
     out->traversal = c->cfg.traversal;
+    out->fused_scatter = c->cfg.fused_scatter;
     return LIDAR_OK;
 }
 
@@ -1013,12 +1018,17 @@ lidar_status lidar_set_launch_config(lidar_ctx* c, const lidar_launch_config* cf
                     "lidar_set_launch_config: tile_rays must be a multiple of 32 in [32, 2^20]");
     LIDAR_CHECK_ARG(cfg->ray_order == 0 || cfg->ray_order == 1, "lidar_set_launch_config: ray_order is 0 or 1");
     LIDAR_CHECK_ARG(cfg->traversal >= 0 && cfg->traversal <= 2, "lidar_set_launch_config: traversal is 0, 1 or 2");
+    LIDAR_CHECK_ARG(cfg->fused_scatter == 0 || cfg->fused_scatter == 1,
+                    "lidar_set_launch_config: fused_scatter is 0 or 1");
     DeviceGuard g(c->device);
     c->cfg.block_threads = cfg->block_threads;
     c->cfg.blocks_per_sm = cfg->blocks_per_sm;
     c->cfg.tile_rays = cfg->tile_rays;
     c->cfg.ray_order = cfg->ray_order;
     c->cfg.traversal = cfg->traversal;
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    c->cfg.fused_scatter = (cfg->fused_scatter && coop) ? 1 : 0;
     for (int s = 0; s < LIDAR_MAX_SENSORS; ++s)
         if (c->slots[s].set) {
             lidar_status st = upload_sensor_slot(c, s);

@@ -2,8 +2,10 @@
 
 Searches threads per block x resident blocks per SM (which also picks the
 register budget), the traversal variant, the ray order (beam order / Morton
-order of directions) and the schedule (Morton groups / most expensive groups
-first), timing each candidate with CUDA events on the context stream.  Every
+order of directions), the schedule (Morton groups / most expensive groups
+first / per-beam cost buckets) and, when the point cloud is timed too, whether
+the ordered scatter runs inside the cast (cooperative launch) or as its own
+kernel, timing each candidate with CUDA events on the context stream.  Every
 candidate produces bit-identical results (tested), so the choice is purely a
 performance one.  The winner is cached in a JSON file keyed by GPU name, SM
 count and a hash of the workload's shape.
@@ -27,6 +29,7 @@ SPACE = {
     "traversal": (0, 1, 2),
     "ray_order": (0, 1),
     "schedule": ("morton", "cost", "bucket"),
+    "fused_scatter": (0, 1),
 }
 
 
@@ -38,7 +41,7 @@ def workload_key(L, scene, frames) -> str:
     return f"{props.name}|{props.multi_processor_count}|{h}"
 
 
-def _time_cast(L, scene, frames, seed, out, flush, reps):
+def _time_cast(L, scene, frames, seed, out, pts, flush, reps):
     ts = []
     stream = L.stream
     for i in range(reps + 2):
@@ -47,7 +50,7 @@ def _time_cast(L, scene, frames, seed, out, flush, reps):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        L.cast_into(scene, frames, seed, out)
+        L.cast_into(scene, frames, seed, out, pts)
         b.record(stream)
         b.synchronize()
         if i >= 2:
@@ -55,14 +58,16 @@ def _time_cast(L, scene, frames, seed, out, flush, reps):
     return statistics.median(ts)
 
 
-def candidates():
-    for bt, bps, tv, ro, sc in itertools.product(*SPACE.values()):
+def candidates(points=False):
+    for bt, bps, tv, ro, sc, fs in itertools.product(*SPACE.values()):
         if bt * bps > 2048 or bt * bps < 256:
             continue
         if ro == 0 and sc != "morton":
             continue  # the cost schedules reorder the Morton order
+        if not points and fs == 0:
+            continue  # without a point cloud there is no scatter
         yield {"block_threads": bt, "blocks_per_sm": bps, "tile_rays": 32, "traversal": tv, "ray_order": ro,
-               "schedule": sc}
+               "fused_scatter": fs, "schedule": sc}
 
 
 def apply(L, scene, cfg, schedule_frames, seed):
@@ -78,13 +83,15 @@ def apply(L, scene, cfg, schedule_frames, seed):
 
 
 def autotune(L, scene, frames, seed, schedule_frames=None, cache_path=DEFAULT_CACHE, reps=8, flush_l2=True,
-             use_cache=True, verbose=False):
-    """Picks and applies the fastest configuration for casting `frames`.
-    `schedule_frames` (default `frames`) are the poses whose measured costs
-    order the rays for the cost schedule: pass a nearby pose (the previous
-    frame) to keep the measurement honest.  Returns (config, ms)."""
+             use_cache=True, verbose=False, points=False):
+    """Picks and applies the fastest configuration for casting `frames`
+    (`points`: the cast plus the ordered compaction into a point cloud,
+    otherwise the cast to dense valid flags).  `schedule_frames` (default
+    `frames`) are the poses whose measured costs order the rays for the cost
+    schedules: pass a nearby pose (the previous frame) to keep the
+    measurement honest.  Returns (config, ms)."""
     schedule_frames = frames if schedule_frames is None else schedule_frames
-    key = workload_key(L, scene, frames)
+    key = workload_key(L, scene, frames) + ("|points" if points else "|dense")
     cache = {}
     if use_cache and cache_path and os.path.exists(cache_path):
         try:
@@ -97,12 +104,13 @@ def autotune(L, scene, frames, seed, schedule_frames=None, cache_path=DEFAULT_CA
         apply(L, scene, cfg, schedule_frames, seed)
         return cfg, cache[key]["ms"]
     n = L.total_beams(frames)
-    out = L.alloc_beams(n, ("valid",))
+    out = None if points else L.alloc_beams(n, ("valid",))
+    pts = L.alloc_points(n) if points else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=L.device) if flush_l2 else None
     best = None
-    for cfg in candidates():
+    for cfg in candidates(points):
         apply(L, scene, cfg, schedule_frames, seed)
-        ms = _time_cast(L, scene, frames, seed, out, flush, reps)
+        ms = _time_cast(L, scene, frames, seed, out, pts, flush, reps)
         if verbose:
             print(f"{ms * 1e3:9.1f} us  {cfg}", flush=True)
         if best is None or ms < best[1]:

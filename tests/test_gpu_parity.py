@@ -144,10 +144,22 @@ def test_ray_order_and_launch_shapes_bit_identical(L):
         L.reset_schedule(0)
 
 
-def test_points_compaction_matches_dense(L):
-    w = synth.small_terrain(seed=4, n_frames=3, n_az=256)
+@pytest.mark.parametrize("fused,block_threads", [(0, 128), (1, 64), (1, 256)])
+def test_points_compaction_matches_dense(L, fused, block_threads):
+    # 250 azimuths: frames end inside compaction tiles and the last tile is ragged
+    w = synth.small_terrain(seed=4, n_frames=3, n_az=250)
     scene, _ = setup(L, w)
     n = L.total_beams(w.frames)
+    assert n % 1024 != 0
+    cfg0 = L.launch_config()
+    L.set_launch_config(fused_scatter=fused, block_threads=block_threads)
+    try:
+        _check_points(L, w, scene, n)
+    finally:
+        L.set_launch_config(**cfg0)
+
+
+def _check_points(L, w, scene, n):
     beams, pts = L.cast(scene, w.frames, w.seed, dense=True, points_capacity=n)
     assert L.sync_status() == 0
     g = to_numpy(beams)
