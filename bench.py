@@ -41,6 +41,23 @@ HBM_FALLBACK_GBS = 6800.0
 POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal, material, instance, beam, frame
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the cast kernel as the roofline times it (cfg1 frame, dense valid flags out,
+# L2 flushed before the launch), from one ncu capture, with the digest of the
+# kernel sources the capture ran.  Reported only while the sources still match.
+NCU_TRAFFIC = {"sources": "8848d1800928a1ec", "bytes": 10_275_840}   # profiles/k_cast_cfg1_ncu_full.md
+KERNEL_SOURCES = ("cast.cu", "trace.cuh", "common.cuh", "philox.cuh")
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2208_10295_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -173,6 +190,16 @@ def run_ours(args, rank, world, local_rank):
     def step():
         L.cast_into(scene, frames, w.seed, None, pts)
 
+    if args.kernel_only:
+        # the roofline's kernel alone (profiling runs): cast to dense valid flags
+        dense = L.alloc_beams(n_beams, ("valid",))
+        kernel_ms = event_time(torch, stream, lambda: L.cast_into(scene, frames, w.seed, dense), flush,
+                               reps=args.steps, warm=args.warmup)
+        if L.sync_status() != 0:
+            raise RuntimeError("device status")
+        return {"kernel": "k_cast", "kernel_ms": kernel_ms, "launches": args.warmup + args.steps,
+                "launch": tuned_cfg, "sources": kernel_digest()} if rank == 0 else None
+
     # ---- whole-step timing (cast + compaction), L2 flushed before each step
     for _ in range(args.warmup):
         step()
@@ -251,6 +278,7 @@ def run_ours(args, rank, world, local_rank):
     visit_bytes = counters["node_visits"] * counters["node_bytes"] + counters["tri_tests"] * 48 + counters["io_bytes"]
     uniq_bytes = counters["unique_node_bytes"] + counters["unique_tri_bytes"] + counters["io_bytes"]
     achieved = visit_bytes / (kernel_ms / 1e3) / 1e9
+    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["sources"] == kernel_digest() else None
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
     # FP32 ops per node fetch: 12 (binary) or 24 (4-wide) slab subtract+multiply pairs; 40 per triangle test
     flops = counters["node_visits"] * (counters["node_bytes"] // 64) * 2 * 24 + counters["tri_tests"] * 40
@@ -268,7 +296,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": n_beams / (e2e_step_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 56,
                 "d2h_bytes_per_step": bo_total / n_e2e},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": f"{peaks_src} hbm_gbs (STREAM-style copy)",
                      "bytes_per_launch": visit_bytes, "kernel": "k_cast", "kernel_ms": kernel_ms,
                      "note": "algorithmic bytes = node fetches x node size + triangle tests x 48 B + 17 B/ray I/O; "
@@ -435,6 +463,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched/differentiation/city measurements")
     ap.add_argument("--no-city", action="store_true", help="skip the 10.7M-triangle city measurement")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time only the cast kernel of the roofline (warmup + steps launches) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()
