@@ -57,6 +57,16 @@ class _Out(ctypes.Structure):
                  "R", "rf", "sub", "flags", "sub_valid", "sub_I", "sub_range", "sub_tri", "sub_flags")]
 
 
+class _RasterCfg(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("n_cameras", ctypes.c_int32)]
+
+
+class _RasterOut(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in
+                ("valid", "outside", "cam", "px", "py", "tri", "q_depth", "q_angle", "mat", "inst", "t", "z",
+                 "range", "intensity", "theta_deg", "flags")]
+
+
 def lib():
     global _lib
     with _lock:
@@ -81,6 +91,10 @@ def lib():
                                                vp, vp]
             L.oracle_cast_backward.restype = i64
             L.oracle_max_threads.restype = i32
+            L.oracle_raster.argtypes = [vp, i64, vp, i64, vp, vp, vp, i32, vp, i32, vp, i32, u64,
+                                        ctypes.POINTER(_RasterCfg), vp, vp, i64, ctypes.POINTER(_RasterOut), i32]
+            L.oracle_raster.restype = ctypes.c_int
+            L.oracle_raster_constants.argtypes = [i32, i32, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -164,6 +178,69 @@ class CastResult(dict):
 
     def __getattr__(self, k):
         return self[k]
+
+
+def _inputs(scene, sensors, frames, table, samples):
+    verts = _c(scene.verts, np.float32)
+    tris = _c(scene.tris, np.uint32)
+    mat = _c(scene.mat, np.uint16)
+    inst = _c(scene.inst, np.uint32)
+    table = _c(table, np.float64)
+    keep = []
+    sens = (_Sensor * len(sensors))()
+    for i, s in enumerate(sensors):
+        az = _c(s.az_rad, np.float64)
+        el = _c(s.el_rad, np.float64)
+        keep += [az, el]
+        sens[i] = _Sensor(az.size, az.ctypes.data, el.ctypes.data, s.r_min, s.r_max, s.d_max, s.RL_max,
+                          s.sigma, s.gain, s.range_exp, s.r_ref, s.divergence_rad, s.n_subrays)
+    fr = np.ascontiguousarray(frames)
+    assert fr.dtype.itemsize == 56
+    if samples is None:
+        sf, sb = [], []
+        for k, f in enumerate(fr):
+            nb = sensors[int(f["sensor"])].n_beams
+            sf.append(np.full(nb, k, np.int64))
+            sb.append(np.arange(nb, dtype=np.int64))
+        sf = np.concatenate(sf)
+        sb = np.concatenate(sb)
+    else:
+        sf = _c(samples[0], np.int64)
+        sb = _c(samples[1], np.int64)
+    return verts, tris, mat, inst, table, sens, keep, fr, sf, sb
+
+
+def raster_constants(width, n_cameras):
+    """(f, c, cos[K], sin[K]) of the raster path's cameras, FP32."""
+    f = np.zeros(1, np.float32)
+    c = np.zeros(1, np.float32)
+    ck = np.zeros(n_cameras, np.float32)
+    sk = np.zeros(n_cameras, np.float32)
+    lib().oracle_raster_constants(width, n_cameras, _p(f), _p(c), _p(ck), _p(sk))
+    return float(f[0]), float(c[0]), ck, sk
+
+
+def raster(scene, sensors, frames, table, seed, width, n_cameras, samples=None, n_threads=0):
+    """The raster-and-resample path (K pin-hole cameras of W x W pixels per
+    frame, 24-bit depth and angle, 8-bit material, 24-bit instance, each beam
+    reading its pixel) on (frame entry, beam) samples."""
+    verts, tris, mat, inst, table, sens, keep, fr, sf, sb = _inputs(scene, sensors, frames, table, samples)
+    n = sf.size
+    R = CastResult(
+        valid=np.zeros(n, np.uint8), outside=np.zeros(n, np.uint8), cam=np.zeros(n, np.int32),
+        px=np.zeros(n, np.int32), py=np.zeros(n, np.int32), tri=np.zeros(n, np.uint32),
+        q_depth=np.zeros(n, np.uint32), q_angle=np.zeros(n, np.uint32), mat=np.zeros(n, np.uint16),
+        inst=np.zeros(n, np.uint32), t=np.zeros(n), z=np.zeros(n), range=np.zeros(n), intensity=np.zeros(n),
+        theta_deg=np.zeros(n), flags=np.zeros(n, np.uint32), sample_frame=sf, sample_beam=sb)
+    out = _RasterOut(*[R[name].ctypes.data for name, _ in _RasterOut._fields_])
+    cfg = _RasterCfg(width, n_cameras)
+    rc = lib().oracle_raster(_p(verts), verts.shape[0], _p(tris), tris.shape[0], _p(mat), _p(inst), sens,
+                             len(sensors), fr.ctypes.data_as(ctypes.c_void_p), len(fr), _p(table),
+                             table.shape[0], seed, ctypes.byref(cfg), _p(sf), _p(sb), n, ctypes.byref(out),
+                             n_threads)
+    if rc != 0:
+        raise ValueError("oracle_raster rejected its inputs")
+    return R
 
 
 def cast(scene, sensors, frames, table, seed, samples=None, n_threads=0):

@@ -374,14 +374,11 @@ typedef struct {
     int valid;
 } ray_result;
 
-/* One ray through the whole per-beam model (everything but the sub-ray reduce). */
-static void oracle_one_ray(const oracle_tris* S, const uint16_t* mat, const double* table, int32_t n_mat,
-                           const oracle_sensor* sen, const float* o32, const float* d32, uint64_t seed,
-                           uint64_t beam, uint32_t frame, uint32_t sensor_id, uint32_t sub, ray_result* res)
+/* Closest hit of one ray over every triangle (brute force), with the EDGE,
+ * TIE and (t near T_max) CUTOFF flags.  Returns the triangle or -1. */
+static int64_t oracle_closest(const oracle_tris* S, const double* o, const double* d, double T_max,
+                              double* t_out, uint32_t* flags)
 {
-    double o[3] = {o32[0], o32[1], o32[2]};
-    double d[3] = {d32[0], d32[1], d32[2]};
-    double T_max = (double)fminf(sen->r_max, sen->d_max) + 9.0 * (double)sen->sigma;
     double best_t = INFINITY, second_t = INFINITY;
     int64_t best = -1;
 
@@ -401,7 +398,7 @@ static void oracle_one_ray(const oracle_tris* S, const uint16_t* mat, const doub
         }
     }
 
-    res->flags = 0;
+    uint32_t res_flags = 0;
     double onorm = fmax(fabs(o[0]), fmax(fabs(o[1]), fabs(o[2])));
     /* edge band: any triangle whose crossing is at or before the hit (or before
      * T_max on a miss) and lies within 1e-6 relative of one of its edges */
@@ -412,12 +409,27 @@ static void oracle_one_ray(const oracle_tris* S, const uint16_t* mat, const doub
         if (!(tp > ORACLE_T_EPS * (1.0 - 1e-6) && tp <= limit)) continue;
         double band = 1e-6 * fmax(onorm, fmax(S->vmax[i], fabs(tp)));
         if (fabs(dist) < band) {
-            res->flags |= ORACLE_FLAG_EDGE;
+            res_flags |= ORACLE_FLAG_EDGE;
             break;
         }
     }
-    if (best >= 0 && second_t <= best_t * (1.0 + 1e-6)) res->flags |= ORACLE_FLAG_TIE;
-    if (best >= 0 && fabs(best_t - T_max) <= 1e-5 * T_max) res->flags |= ORACLE_FLAG_CUTOFF;
+    if (best >= 0 && second_t <= best_t * (1.0 + 1e-6)) res_flags |= ORACLE_FLAG_TIE;
+    if (best >= 0 && fabs(best_t - T_max) <= 1e-5 * T_max) res_flags |= ORACLE_FLAG_CUTOFF;
+    *flags = res_flags;
+    *t_out = best_t;
+    return best;
+}
+
+/* One ray through the whole per-beam model (everything but the sub-ray reduce). */
+static void oracle_one_ray(const oracle_tris* S, const uint16_t* mat, const double* table, int32_t n_mat,
+                           const oracle_sensor* sen, const float* o32, const float* d32, uint64_t seed,
+                           uint64_t beam, uint32_t frame, uint32_t sensor_id, uint32_t sub, ray_result* res)
+{
+    double o[3] = {o32[0], o32[1], o32[2]};
+    double d[3] = {d32[0], d32[1], d32[2]};
+    double T_max = (double)fminf(sen->r_max, sen->d_max) + 9.0 * (double)sen->sigma;
+    double best_t;
+    int64_t best = oracle_closest(S, o, d, T_max, &best_t, &res->flags);
     if (best < 0) {
         /* a miss whose nearest crossing is just beyond T_max could flip */
         res->tri = ORACLE_NO_HIT;
@@ -583,6 +595,237 @@ int oracle_cast(const float* verts, int64_t n_verts, const uint32_t* tris, int64
     }
     oracle_tris_free(&S);
     return 0;
+}
+
+/* ------------------------------------------------ raster-and-resample path */
+
+/* The paper's own sampling path (Sec. II-A..II-C): per frame, K pin-hole
+ * cameras at the sensor pose share the sensor's 360-degree horizontal field
+ * (camera k looks along sensor azimuth -pi + (k + 1/2) 2 pi / K, square W x W
+ * image, FOV_c = 2 pi / K); each renders the depth pass, the incidence angle,
+ * the material stencil and the instance colour of the surface seen through
+ * every pixel centre; each beam then reads the pixel its direction projects to
+ * (intrinsics of Eq. 1-2, pixel coordinates of Eq. 3 in the corrected form
+ * n_x = c + f x/z, n_y = c - f y/z with (x, y, z) the beam in camera axes).
+ *
+ *   camera    : the k maximising d . F_k (FP32, ties to the lowest k),
+ *               F_k = (cos, sin, 0) of its azimuth, L_k = (-sin, cos, 0), U = z.
+ *   pixel     : (floor n_x, floor n_y) in FP32, every operation rounded as
+ *               written; the column is clamped to [0, W) (a beam on the border
+ *               of two cameras), a row outside [0, W) leaves the beam without
+ *               a return.
+ *   pixel ray : through the pixel centre, a = (i + 1/2 - c)/f,
+ *               b = (c - (j + 1/2))/f, dir = (F + a L + b U) / sqrt(1 + a^2 + b^2)
+ *               in FP32, then to the world like a beam.
+ *   depth     : z-depth of the closest hit (FP64 brute force), z = t |dir . F|,
+ *               rounded to FP32 and stored as 24-bit fixed point of z / T_max
+ *               (q = rn(z * (2^24 - 1) / T_max), at most 2^24 - 2; 2^24 - 1
+ *               marks no hit) — the "three bytes unsigned precision" of Sec. II-A.
+ *   angle     : incidence angle of the pixel ray on the face (Sec. II-C), FP32,
+ *               24-bit fixed point of theta / 90 degrees; material in the 8-bit
+ *               stencil (mat & 255), instance as a 24-bit colour (inst & 2^24-1).
+ *   beam      : range = z' / (d . F_k) (the pixel's depth read along the beam),
+ *               theta = theta', then noise, Eq. 4 lookup, Eq. 5 and intensity as
+ *               in the ray-cast path (sub-ray 0's noise draw).
+ * The FP32 quantisation codes are computed from the FP64 values rounded to
+ * FP32, with the library's operation order. */
+typedef struct {
+    int32_t width;
+    int32_t n_cameras;
+} oracle_raster_cfg;
+
+typedef struct {
+    uint8_t* valid;
+    uint8_t* outside;      /* beam projects outside every camera image */
+    int32_t* cam;
+    int32_t* px;
+    int32_t* py;
+    uint32_t* tri;         /* triangle seen through the pixel centre */
+    uint32_t* q_depth;
+    uint32_t* q_angle;
+    uint16_t* mat;         /* 8-bit stencil */
+    uint32_t* inst;        /* 24-bit colour */
+    double* t;             /* pixel ray distance to the hit */
+    double* z;             /* z-depth before quantisation */
+    double* range;
+    double* intensity;
+    double* theta_deg;     /* decoded */
+    uint32_t* flags;
+} oracle_raster_out;
+
+/* camera constants as FP32, from the definitions in FP64 */
+static void oracle_raster_consts(const oracle_raster_cfg* cfg, float* f, float* c, float* ck, float* sk)
+{
+    double fov = 2.0 * M_PI / (double)cfg->n_cameras;
+    *f = (float)((double)cfg->width / (2.0 * tan(0.5 * fov)));
+    *c = (float)(0.5 * (double)cfg->width);
+    for (int k = 0; k < cfg->n_cameras; ++k) {
+        double az = -M_PI + ((double)k + 0.5) * fov;
+        ck[k] = (float)cos(az);
+        sk[k] = (float)sin(az);
+    }
+}
+
+int oracle_raster(const float* verts, int64_t n_verts, const uint32_t* tris, int64_t n_tris,
+                  const uint16_t* mat, const uint32_t* inst, const oracle_sensor* sensors, int32_t n_sensors,
+                  const oracle_frame* frames, int32_t n_frames, const double* table, int32_t n_mat,
+                  uint64_t seed, const oracle_raster_cfg* cfg, const int64_t* sample_frame,
+                  const int64_t* sample_beam, int64_t n_samples, oracle_raster_out* out, int32_t n_threads)
+{
+    if (cfg->width < 1 || cfg->n_cameras < 3 || cfg->n_cameras > 64) return -1;
+    for (int64_t i = 0; i < 3 * n_tris; ++i)
+        if ((int64_t)tris[i] >= n_verts) return -1;
+    for (int64_t s = 0; s < n_samples; ++s) {
+        if (sample_frame[s] < 0 || sample_frame[s] >= n_frames) return -1;
+        const oracle_frame* fr = frames + sample_frame[s];
+        if (fr->sensor < 0 || fr->sensor >= n_sensors) return -1;
+        if (sample_beam[s] < 0 || sample_beam[s] >= sensors[fr->sensor].n_beams) return -1;
+    }
+    float f, c, ck[64], sk[64];
+    oracle_raster_consts(cfg, &f, &c, ck, sk);
+    const int W = cfg->width, K = cfg->n_cameras;
+    oracle_tris S;
+    oracle_tris_init(&S, verts, tris, n_tris);
+
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t s = 0; s < n_samples; ++s) {
+        const oracle_frame* fr = frames + sample_frame[s];
+        const oracle_sensor* sen = sensors + fr->sensor;
+        const int64_t b = sample_beam[s];
+        float ds[3];
+        oracle_beam_dirs(1, sen->az + b, sen->el + b, ds);
+        out->valid[s] = 0;
+        out->outside[s] = 1;
+        out->cam[s] = -1;
+        out->px[s] = out->py[s] = -1;
+        out->tri[s] = ORACLE_NO_HIT;
+        out->q_depth[s] = 0xFFFFFFu;
+        out->q_angle[s] = 0;
+        out->mat[s] = 0;
+        out->inst[s] = 0;
+        out->t[s] = out->z[s] = out->range[s] = INFINITY;
+        out->intensity[s] = 0.0;
+        out->theta_deg[s] = 0.0;
+        out->flags[s] = 0;
+
+        /* camera: largest d . F_k */
+        int k = 0;
+        float zk = 0.0f;
+        for (int j = 0; j < K; ++j) {
+            float p0 = ds[0] * ck[j];
+            float p1 = ds[1] * sk[j];
+            float zj = p0 + p1;
+            if (j == 0 || zj > zk) { zk = zj; k = j; }
+        }
+        out->cam[s] = k;
+        if (!(zk > 0.0f)) continue;
+        /* projection (corrected Eq. 3) */
+        float xa = ds[0] * (-sk[k]);
+        float xb = ds[1] * ck[k];
+        float x = xa + xb;
+        float y = ds[2];
+        float rx = x / zk, ry = y / zk;
+        float fx = f * rx, fy = f * ry;
+        float nx = c + fx;
+        float ny = c - fy;
+        float fnx = floorf(nx), fny = floorf(ny);
+        /* the chosen camera is within half its field of the beam, so a column
+         * outside the image is a boundary beam (n_x = 0 or W): clamp it; rows
+         * outside the image are beams above or below the camera's field */
+        if (!(fnx == fnx) || !(fny >= 0.0f && fny < (float)W)) continue;
+        if (fnx < 0.0f) fnx = 0.0f;
+        if (fnx > (float)(W - 1)) fnx = (float)(W - 1);
+        const int ix = (int)fnx, iy = (int)fny;
+        out->outside[s] = 0;
+        out->px[s] = ix;
+        out->py[s] = iy;
+        /* pixel-centre ray */
+        float cxp = (float)ix + 0.5f, cyp = (float)iy + 0.5f;
+        float an = cxp - c, bn = c - cyp;
+        float a = an / f, bb = bn / f;
+        float a2 = a * a, b2 = bb * bb;
+        float s2 = 1.0f + a2;
+        s2 = s2 + b2;
+        float inv = 1.0f / sqrtf(s2);
+        float as = a * sk[k], ac = a * ck[k];
+        float dpx = ck[k] - as, dpy = sk[k] + ac;
+        float dps[3] = {dpx * inv, dpy * inv, bb * inv};
+        float o32[3], dw[3];
+        oracle_world_ray(fr->pose, dps, o32, dw);
+        double o[3] = {o32[0], o32[1], o32[2]};
+        double d[3] = {dw[0], dw[1], dw[2]};
+        const double T_max = (double)fminf(sen->r_max, sen->d_max) + 9.0 * (double)sen->sigma;
+        double t;
+        uint32_t flags;
+        int64_t best = oracle_closest(&S, o, d, T_max, &t, &flags);
+        out->flags[s] = flags;
+        if (best < 0) continue;
+        out->tri[s] = (uint32_t)best;
+        out->t[s] = t;
+        /* depth pass: z-depth, 24-bit */
+        const float Tm = fminf(sen->r_max, sen->d_max) + 9.0f * sen->sigma;
+        double zd = t * (double)inv;
+        out->z[s] = zd;
+        float z32 = (float)zd;
+        float qs = 16777215.0f / Tm;
+        float qz = z32 * qs;
+        uint32_t q = (uint32_t)rintf(qz);
+        if (q > 16777214u) q = 16777214u;
+        out->q_depth[s] = q;
+        /* incidence angle on the face, 24-bit */
+        const double* e1 = S.e1 + 3 * best;
+        const double* e2 = S.e2 + 3 * best;
+        double n[3], cr[3];
+        cross3(e1, e2, n);
+        double nl = sqrt(dot3(n, n));
+        n[0] /= nl; n[1] /= nl; n[2] /= nl;
+        cross3(d, n, cr);
+        double theta = atan2(sqrt(dot3(cr, cr)), fabs(dot3(d, n))) * 180.0 / M_PI;
+        float th32 = (float)theta;
+        float qa_s = 16777215.0f / 90.0f;
+        float qa_f = th32 * qa_s;
+        uint32_t qa = (uint32_t)rintf(qa_f);
+        if (qa > 16777215u) qa = 16777215u;
+        out->q_angle[s] = qa;
+        const uint32_t m8 = (uint32_t)mat[best] & 0xFFu;
+        out->mat[s] = (uint16_t)m8;
+        out->inst[s] = inst[best] & 0xFFFFFFu;
+        /* resample: the pixel's depth read along the beam */
+        double zq = (double)q * ((double)Tm / 16777215.0);
+        double th = (double)qa * (90.0 / 16777215.0);
+        double d_beam = zq / (double)zk;
+        double zn = oracle_normal(seed, (uint64_t)b, (uint32_t)fr->frame, (uint32_t)fr->sensor, 0);
+        double dist = d_beam + (double)sen->sigma * zn;
+        int mrow = (int)m8 < n_mat ? (int)m8 : n_mat - 1;
+        int ii;
+        double ff;
+        double R = oracle_lerp_row(table + (int64_t)mrow * ORACLE_NTAB, th, &ii, &ff);
+        double r_min = sen->r_min, r_max = sen->r_max, d_max = sen->d_max, RL = sen->RL_max;
+        double RLd = RL * dist / d_max;
+        int valid = (dist >= r_min) && (dist <= r_max) && (dist <= d_max) && (RLd <= R);
+        /* margins: quantisation codes may differ by a few steps between FP32 paths */
+        double tol = 1e-5 * fabs(dist) + 4.0 * (double)Tm / 16777215.0;
+        if (fabs(dist - r_min) <= tol || fabs(dist - r_max) <= tol || fabs(dist - d_max) <= tol ||
+            fabs(RLd - R) <= 1e-5 * fmax(fabs(R), fabs(RLd)) + RL * tol / d_max)
+            out->flags[s] |= ORACLE_FLAG_CUTOFF;
+        double rf = (sen->range_exp == 0.0f) ? 1.0 : pow((double)sen->r_ref / dist, (double)sen->range_exp);
+        out->range[s] = dist;
+        out->intensity[s] = (double)sen->gain * R * rf;
+        out->theta_deg[s] = th;
+        out->valid[s] = (uint8_t)valid;
+    }
+    oracle_tris_free(&S);
+    return 0;
+}
+
+/* Camera constants of the raster path (for the tests' pins). */
+void oracle_raster_constants(int32_t width, int32_t n_cameras, float* f, float* c, float* ck, float* sk)
+{
+    oracle_raster_cfg cfg = {width, n_cameras};
+    oracle_raster_consts(&cfg, f, c, ck, sk);
 }
 
 /* --------------------------------------------------------------- adjoint */
