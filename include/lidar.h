@@ -359,6 +359,46 @@ lidar_status lidar_schedule_by_cost(lidar_ctx* ctx, const lidar_scene* scene, co
 /* Restores the Morton order of a slot. */
 lidar_status lidar_reset_schedule(lidar_ctx* ctx, int32_t slot);
 
+/* ------------------------------------------------- raster-and-resample path */
+
+/* The paper's own sampling (Sec. II-A..II-C), as compute rasterisation: per
+ * frame, n_cameras pin-hole cameras at the sensor pose share the 360-degree
+ * horizontal field (camera k looks along sensor azimuth
+ * -pi + (k + 1/2) 2 pi / n_cameras; square width x width image; Eq. 1-2:
+ * f = width / (2 tan(pi / n_cameras)), c = width / 2).  Each camera renders,
+ * through every pixel centre, the depth pass as z-depth in three bytes
+ * (q = rn(z (2^24 - 1) / T_max), 2^24 - 1 = no hit), the incidence angle in
+ * three bytes (theta / 90 degrees), the material stencil in one byte
+ * (material & 255) and the instance colour in three bytes (instance & 2^24-1).
+ * A beam reads the pixel its direction d projects to (Eq. 3, corrected:
+ * camera = largest d . F_k, n_x = c + f x/z, n_y = c - f y/z with (x, y, z)
+ * = d in camera axes, pixel = floor; a column outside the image is clamped —
+ * a beam on the border of two cameras — and a row outside it leaves the beam
+ * without a return), takes range = depth / (d . F_k) and the decoded angle
+ * and stencil, and goes through the noise, Eq. 4 lookup, Eq. 5 and intensity
+ * of lidar_cast (the draw of sub-ray 0; sensors' sub-rays are not used). */
+typedef struct {
+    int32_t width;       /* pixels per side of each camera image, 1..16384 */
+    int32_t n_cameras;   /* cameras around the vertical axis, 3..64 (FOV_c = 360 / n_cameras degrees) */
+} lidar_raster_config;
+
+/* Dense per-beam outputs like lidar_cast (beams required; points are not
+ * produced): tri = the triangle seen through the beam's pixel centre, t = the
+ * range before noise, normal = 0 (the G-buffer has no normal), mat = the
+ * 8-bit stencil, inst = the 24-bit colour, sub = 0.  Frames are rendered one
+ * after another in the context's scratch (about 16 + 4 bytes per pixel per
+ * camera plus 3 bytes per triangle and camera).  Asynchronous. */
+lidar_status lidar_raster_cast(lidar_ctx* ctx, const lidar_scene* scene, const lidar_frame* frames_host,
+                               int32_t n_frames, uint64_t seed, const lidar_raster_config* cfg,
+                               const lidar_beams* beams);
+
+/* The G-buffer of one frame, [n_cameras][width][width] uint32 each (any may be
+ * NULL): depth code, angle code | stencil << 24, colour, and the original index
+ * of the triangle seen (LIDAR_NO_HIT on a miss).  Asynchronous. */
+lidar_status lidar_raster_gbuffer(lidar_ctx* ctx, const lidar_scene* scene, const lidar_frame* frame_host,
+                                  const lidar_raster_config* cfg, uint32_t* depth_dev, uint32_t* angle_mat_dev,
+                                  uint32_t* inst_dev, uint32_t* tri_dev);
+
 /* --------------------------------------------------------------- launch tuning */
 
 typedef struct {

@@ -76,6 +76,10 @@ class lidar_launch_config(ctypes.Structure):
                 ("fused_scatter", ctypes.c_int32)]
 
 
+class lidar_raster_config(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("n_cameras", ctypes.c_int32)]
+
+
 assert ctypes.sizeof(lidar_frame) == 56
 
 _lock = threading.Lock()
@@ -121,6 +125,10 @@ _PROTOS = [
     ("lidar_schedule_by_cost", ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(lidar_frame), ctypes.c_uint64,
                                               ctypes.c_int32]),
     ("lidar_reset_schedule", ctypes.c_int, [c_vp, ctypes.c_int32]),
+    ("lidar_raster_cast", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
+                                         ctypes.POINTER(lidar_raster_config), ctypes.POINTER(lidar_beams)]),
+    ("lidar_raster_gbuffer", ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(lidar_frame),
+                                            ctypes.POINTER(lidar_raster_config), c_vp, c_vp, c_vp, c_vp]),
     ("lidar_get_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
     ("lidar_set_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
 ]
@@ -188,6 +196,8 @@ lidar_cast_backward = _fwd("lidar_cast_backward")
 lidar_cast_backward_mse = _fwd("lidar_cast_backward_mse")
 lidar_cast_backward_mse_noalloc = _fwd("lidar_cast_backward_mse_noalloc")
 lidar_count_work = _fwd("lidar_count_work")
+lidar_raster_cast = _fwd("lidar_raster_cast")
+lidar_raster_gbuffer = _fwd("lidar_raster_gbuffer")
 lidar_schedule_by_cost = _fwd("lidar_schedule_by_cost")
 lidar_reset_schedule = _fwd("lidar_reset_schedule")
 lidar_get_launch_config = _fwd("lidar_get_launch_config")

@@ -187,4 +187,45 @@ size_t backward_scratch_bytes(int M);
 // address (on the current device) and size of the allocation-free variant's scratch array
 cudaError_t noalloc_scratch(void** ptr, size_t* bytes);
 
+// ------------------------------------------------------------ raster path
+
+constexpr int kMaxCameras = 64;
+
+// K pin-hole cameras of W x W pixels around the sensor's vertical axis
+// (Eq. 1-2): focal length f = W / (2 tan(pi / K)), principal point c = W / 2,
+// camera k looking along sensor azimuth -pi + (k + 1/2) 2 pi / K.
+struct RasterCams {
+    int W, K;
+    float f, c;
+    float ck[kMaxCameras], sk[kMaxCameras];   // cos, sin of each camera's azimuth
+};
+
+// One frame: pose, search range, and each camera's L, U, F axes in the world
+struct RasterFrame {
+    float pose[12];
+    float t_max;
+    float axes[9 * kMaxCameras];
+};
+
+// G-buffer of K images (SoA, [K][W][W]): depth code (24 bits, 2^24 - 1 = no
+// hit), angle code (24 bits) | material stencil << 24, instance colour
+// (24 bits), and (optional) the triangle's original index
+struct GBuffer {
+    uint32_t* depth;
+    uint32_t* angle_mat;
+    uint32_t* inst;
+    uint32_t* tri;
+};
+
+size_t raster_big_capacity(int n_cameras, int64_t n_tris);
+size_t raster_scratch_bytes(int width, int n_cameras, int64_t n_tris, bool with_tri);
+cudaError_t launch_invert_leaf_order(cudaStream_t s, const uint32_t* leaf_tri, int64_t n, uint32_t* orig_to_leaf);
+// rasterises one frame's K images into scratch (raster_scratch_bytes); *G
+// receives the G-buffer's location inside it (with_tri: also the triangles)
+cudaError_t launch_rasterise(cudaStream_t s, const SceneDev& S, const RasterCams& C, const RasterFrame& F,
+                             const uint32_t* orig_to_leaf, void* scratch, bool with_tri, GBuffer* G, int num_sms);
+cudaError_t launch_resample(cudaStream_t s, const RasterCams& C, const RasterFrame& F, const SensorDev* sensors_dev,
+                            int sensor, int n_beams, int frame_id, int64_t beam_offset, TableDev T, uint64_t seed,
+                            const GBuffer& G, BeamsOut out);
+
 }  // namespace lidar

@@ -59,6 +59,7 @@ struct lidar_scene {
     float4* nodes4 = nullptr;
     float4* tris = nullptr;
     uint32_t* leaf_tri = nullptr;
+    uint32_t* orig_to_leaf = nullptr;  // inverse of leaf_tri, made on the first raster cast
     int64_t n_tris = 0;
     int64_t n_nodes = 0;
     int64_t n_nodes4 = 0;
@@ -210,6 +211,7 @@ void lidar_scene_free(lidar_scene* s)
     cudaFree(s->nodes4);
     cudaFree(s->tris);
     cudaFree(s->leaf_tri);
+    cudaFree(s->orig_to_leaf);
     s->ctx->scenes.erase(s);
     delete s;
 }
@@ -617,6 +619,133 @@ lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_fram
     if (st != LIDAR_OK) return st;
     return cast_impl(c, scene, c->frames_dev, c->tile_prefix_dev, n_frames, n_total, n_tiles, seed, beams, points,
                      n_points_dev, true);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ raster path
+
+static lidar_status raster_setup(lidar_ctx* c, const lidar_scene* scene, const lidar_raster_config* cfg,
+                                 bool with_tri, RasterCams& C)
+{
+    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr && cfg != nullptr, "raster: NULL argument");
+    LIDAR_CHECK_ARG(scene->ctx == c, "raster: scene belongs to another context");
+    LIDAR_CHECK_ARG(cfg->width >= 1 && cfg->width <= 16384, "raster: width must be in [1, 16384]");
+    LIDAR_CHECK_ARG(cfg->n_cameras >= 3 && cfg->n_cameras <= kMaxCameras, "raster: n_cameras must be in [3, 64]");
+    LIDAR_CHECK_ARG(scene->n_tris < ((int64_t)1 << 26), "raster: at most 2^26 triangles");
+    C.W = cfg->width;
+    C.K = cfg->n_cameras;
+    const double fov = 2.0 * M_PI / (double)C.K;
+    C.f = (float)((double)C.W / (2.0 * tan(0.5 * fov)));
+    C.c = (float)(0.5 * (double)C.W);
+    for (int k = 0; k < kMaxCameras; ++k) {
+        const double az = -M_PI + ((double)k + 0.5) * fov;
+        C.ck[k] = k < C.K ? (float)cos(az) : 0.0f;
+        C.sk[k] = k < C.K ? (float)sin(az) : 0.0f;
+    }
+    lidar_scene* sc = const_cast<lidar_scene*>(scene);
+    if (!sc->orig_to_leaf && sc->n_tris > 0) {
+        if (dev_alloc((void**)&sc->orig_to_leaf, (size_t)sc->n_tris * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            sc->orig_to_leaf = nullptr;
+            set_error("raster: device allocation failed");
+            return LIDAR_ENOMEM;
+        }
+        LIDAR_CUDA(launch_invert_leaf_order(c->stream, sc->leaf_tri, sc->n_tris, sc->orig_to_leaf));
+    }
+    return ensure_scratch(c, raster_scratch_bytes(C.W, C.K, scene->n_tris, with_tri));
+}
+
+static RasterFrame raster_frame(const RasterCams& C, const lidar_frame& fr, float t_max)
+{
+    RasterFrame F;
+    memcpy(F.pose, fr.pose, sizeof(F.pose));
+    F.t_max = t_max;
+    for (int k = 0; k < kMaxCameras; ++k) {
+        // sensor-frame axes L = (-s, c, 0), U = (0, 0, 1), F = (c, s, 0), rotated by the pose
+        const double ax[3][3] = {{-(double)C.sk[k], (double)C.ck[k], 0.0}, {0.0, 0.0, 1.0},
+                                 {(double)C.ck[k], (double)C.sk[k], 0.0}};
+        for (int a = 0; a < 3; ++a)
+            for (int r = 0; r < 3; ++r)
+                F.axes[9 * k + 3 * a + r] =
+                    (float)((double)fr.pose[4 * r] * ax[a][0] + (double)fr.pose[4 * r + 1] * ax[a][1] +
+                            (double)fr.pose[4 * r + 2] * ax[a][2]);
+    }
+    return F;
+}
+
+static SceneDev scene_dev(const lidar_scene* scene)
+{
+    return SceneDev{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
+}
+
+extern "C" {
+
+lidar_status lidar_raster_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
+                               uint64_t seed, const lidar_raster_config* cfg, const lidar_beams* beams)
+{
+    LIDAR_CHECK_ARG(beams != nullptr, "lidar_raster_cast: beams is NULL");
+    LIDAR_CHECK_ARG(frames != nullptr && n_frames > 0, "lidar_raster_cast: need at least one frame");
+    lidar_status st = cast_checks(c, scene, beams, nullptr);
+    if (st != LIDAR_OK) return st;
+    for (int32_t k = 0; k < n_frames; ++k) {
+        const int s = frames[k].sensor;
+        LIDAR_CHECK_ARG(s >= 0 && s < LIDAR_MAX_SENSORS, "lidar_raster_cast: sensor slot out of range");
+        if (!c->slots[s].set) {
+            set_error("lidar_raster_cast: frame " + std::to_string(k) + " names an empty sensor slot");
+            return LIDAR_ESTATE;
+        }
+        for (int j = 0; j < 12; ++j)
+            LIDAR_CHECK_ARG(isfinite(frames[k].pose[j]), "lidar_raster_cast: non-finite pose");
+    }
+    DeviceGuard g(c->device);
+    RasterCams C;
+    const BeamsOut out = to_beams_out(beams);
+    st = raster_setup(c, scene, cfg, out.tri != nullptr, C);
+    if (st != LIDAR_OK) return st;
+    const SceneDev S = scene_dev(scene);
+    int64_t offset = 0;
+    for (int32_t k = 0; k < n_frames; ++k) {
+        const SensorSlot& sl = c->slots[frames[k].sensor];
+        const RasterFrame F = raster_frame(C, frames[k], sl.dev.t_max);
+        GBuffer G{};
+        LIDAR_CUDA(launch_rasterise(c->stream, S, C, F, scene->orig_to_leaf, c->scratch, out.tri != nullptr, &G,
+                                    c->num_sms));
+        LIDAR_CUDA(launch_resample(c->stream, C, F, c->sensors_dev, frames[k].sensor, (int)sl.n_beams, frames[k].frame,
+                                   offset, c->table, seed, G, out));
+        offset += sl.n_beams;
+    }
+    return LIDAR_OK;
+}
+
+lidar_status lidar_raster_gbuffer(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frame,
+                                  const lidar_raster_config* cfg, uint32_t* depth_dev, uint32_t* angle_mat_dev,
+                                  uint32_t* inst_dev, uint32_t* tri_dev)
+{
+    LIDAR_CHECK_ARG(c != nullptr && frame != nullptr, "lidar_raster_gbuffer: NULL argument");
+    const int s = frame->sensor;
+    LIDAR_CHECK_ARG(s >= 0 && s < LIDAR_MAX_SENSORS, "lidar_raster_gbuffer: sensor slot out of range");
+    if (!c->slots[s].set) {
+        set_error("lidar_raster_gbuffer: the frame names an empty sensor slot");
+        return LIDAR_ESTATE;
+    }
+    for (int j = 0; j < 12; ++j)
+        LIDAR_CHECK_ARG(isfinite(frame->pose[j]), "lidar_raster_gbuffer: non-finite pose");
+    DeviceGuard g(c->device);
+    RasterCams C;
+    lidar_status st = raster_setup(c, scene, cfg, tri_dev != nullptr, C);
+    if (st != LIDAR_OK) return st;
+    const RasterFrame F = raster_frame(C, *frame, c->slots[s].dev.t_max);
+    GBuffer G{};
+    LIDAR_CUDA(launch_rasterise(c->stream, scene_dev(scene), C, F, scene->orig_to_leaf, c->scratch, tri_dev != nullptr,
+                                &G, c->num_sms));
+    const size_t bytes = (size_t)C.K * C.W * C.W * sizeof(uint32_t);
+    if (depth_dev) LIDAR_CUDA(cudaMemcpyAsync(depth_dev, G.depth, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (angle_mat_dev)
+        LIDAR_CUDA(cudaMemcpyAsync(angle_mat_dev, G.angle_mat, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (inst_dev) LIDAR_CUDA(cudaMemcpyAsync(inst_dev, G.inst, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (tri_dev) LIDAR_CUDA(cudaMemcpyAsync(tri_dev, G.tri, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return LIDAR_OK;
 }
 
 }  // extern "C"

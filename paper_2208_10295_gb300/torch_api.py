@@ -252,6 +252,30 @@ class Lidar:
     def reset_schedule(self, slot: int):
         C.check(C.lidar_reset_schedule(self.handle, slot), "lidar_reset_schedule")
 
+    # ----------------------------------------------------------- raster path
+    def raster_cast_into(self, scene: Scene, frames, seed: int, beams, width: int = 1024, n_cameras: int = 6):
+        """The paper's raster-and-resample sampling (K pin-hole cameras of
+        W x W pixels per frame, quantised G-buffer, each beam reading its pixel)
+        into dense beam buffers."""
+        fr = _frames_array(frames)
+        cfg = C.lidar_raster_config(width, n_cameras)
+        C.check(C.lidar_raster_cast(self.handle, scene.handle, fr.ctypes.data_as(ctypes.c_void_p), len(fr),
+                                    ctypes.c_uint64(seed), ctypes.byref(cfg), ctypes.byref(self.beams_struct(beams))),
+                "lidar_raster_cast")
+
+    def raster_gbuffer(self, scene: Scene, frame, width: int = 1024, n_cameras: int = 6):
+        """One frame's G-buffer: dict of [K, W, W] int32 tensors depth (24-bit
+        code), angle_mat (24-bit angle code | stencil << 24), inst, tri."""
+        fr = _frames_array(frame).reshape(-1)[:1]
+        shape = (n_cameras, width, width)
+        g = {k: torch.empty(shape, dtype=torch.int32, device=self.device)
+             for k in ("depth", "angle_mat", "inst", "tri")}
+        cfg = C.lidar_raster_config(width, n_cameras)
+        C.check(C.lidar_raster_gbuffer(self.handle, scene.handle, fr.ctypes.data_as(ctypes.POINTER(C.lidar_frame)),
+                                       ctypes.byref(cfg), *[_ptr(g[k]) for k in ("depth", "angle_mat", "inst", "tri")]),
+                "lidar_raster_gbuffer")
+        return g
+
     # ----------------------------------------------------------- tuning
     def launch_config(self):
         c = C.lidar_launch_config()
