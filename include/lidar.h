@@ -136,6 +136,8 @@ typedef struct {
     float r_ref;
     float divergence_rad;      /* full beam divergence; sampled by n_subrays rays, strongest return kept */
     int32_t n_subrays;         /* 1..LIDAR_MAX_SUBRAYS */
+    float sigma_k;             /* range-scaled noise: the standard deviation at true range t is
+                                  sigma + sigma_k t, in [0, 0.1); 0 = the paper's constant factor */
 } lidar_sensor_desc;
 
 /* Installs a sensor in slot [0, LIDAR_MAX_SENSORS).  Copies the beam

@@ -48,7 +48,7 @@ class _Sensor(ctypes.Structure):
                 ("r_min", ctypes.c_float), ("r_max", ctypes.c_float), ("d_max", ctypes.c_float),
                 ("RL_max", ctypes.c_float), ("sigma", ctypes.c_float), ("gain", ctypes.c_float),
                 ("range_exp", ctypes.c_float), ("r_ref", ctypes.c_float), ("divergence", ctypes.c_float),
-                ("n_sub", ctypes.c_int32)]
+                ("n_sub", ctypes.c_int32), ("sigma_k", ctypes.c_float)]
 
 
 class _Out(ctypes.Structure):
@@ -65,6 +65,11 @@ class _RasterOut(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in
                 ("valid", "outside", "cam", "px", "py", "tri", "q_depth", "q_angle", "mat", "inst", "t", "z",
                  "range", "intensity", "theta_deg", "flags")]
+
+
+class _Echoes(ctypes.Structure):
+    _fields_ = [("n_echoes", ctypes.c_int32), ("mode", ctypes.c_int32), ("separation", ctypes.c_float)] + \
+               [(n, ctypes.c_void_p) for n in ("count", "range", "intensity", "tri", "sub")]
 
 
 def lib():
@@ -95,6 +100,13 @@ def lib():
                                         ctypes.POINTER(_RasterCfg), vp, vp, i64, ctypes.POINTER(_RasterOut), i32]
             L.oracle_raster.restype = ctypes.c_int
             L.oracle_raster_constants.argtypes = [i32, i32, vp, vp, vp, vp]
+            L.oracle_sweep_fraction.argtypes = [ctypes.c_double]
+            L.oracle_sweep_fraction.restype = ctypes.c_float
+            L.oracle_sweep_quaternions.argtypes = [vp, vp, vp, vp]
+            L.oracle_sweep_pose.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp]
+            L.oracle_cast_sweep.argtypes = [vp, i64, vp, i64, vp, vp, vp, i32, vp, i32, vp, i32, u64, vp, vp, i64,
+                                            i32, ctypes.POINTER(_Out), ctypes.POINTER(_Echoes), i32]
+            L.oracle_cast_sweep.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -193,7 +205,8 @@ def _inputs(scene, sensors, frames, table, samples):
         el = _c(s.el_rad, np.float64)
         keep += [az, el]
         sens[i] = _Sensor(az.size, az.ctypes.data, el.ctypes.data, s.r_min, s.r_max, s.d_max, s.RL_max,
-                          s.sigma, s.gain, s.range_exp, s.r_ref, s.divergence_rad, s.n_subrays)
+                          s.sigma, s.gain, s.range_exp, s.r_ref, s.divergence_rad, s.n_subrays,
+                          getattr(s, "sigma_k", 0.0))
     fr = np.ascontiguousarray(frames)
     assert fr.dtype.itemsize == 56
     if samples is None:
@@ -243,6 +256,72 @@ def raster(scene, sensors, frames, table, seed, width, n_cameras, samples=None, 
     return R
 
 
+def sweep_fraction(az):
+    return float(lib().oracle_sweep_fraction(float(az)))
+
+
+def sweep_quaternions(pose0, pose1):
+    p0 = _c(pose0, np.float32).reshape(12)
+    p1 = _c(pose1, np.float32).reshape(12)
+    q0 = np.zeros(4, np.float32)
+    q1 = np.zeros(4, np.float32)
+    lib().oracle_sweep_quaternions(_p(p0), _p(p1), _p(q0), _p(q1))
+    return q0, q1
+
+
+def sweep_pose(pose0, pose1, s):
+    """Pose (row-major 3x4, FP32) at fraction s of a sweep from pose0 to pose1."""
+    p0 = _c(pose0, np.float32).reshape(12)
+    p1 = _c(pose1, np.float32).reshape(12)
+    q0, q1 = sweep_quaternions(p0, p1)
+    P = np.zeros(12, np.float32)
+    lib().oracle_sweep_pose(_p(q0), _p(q1), _p(p0), _p(p1), float(s), _p(P))
+    return P
+
+
+def cast_sweep(scene, sensors, frames, table, seed, samples=None, echoes=None, n_threads=0):
+    """Rolling-shutter cast: `frames` has SWEEP_FRAME_DTYPE (pose0 at the
+    sweep's start, pose1 at its end); each beam sees the pose at its firing
+    fraction.  `echoes` = (n_echoes, mode, separation) adds the multi-echo
+    outputs echo_count, echo_range, echo_intensity, echo_tri, echo_sub."""
+    fr = np.ascontiguousarray(frames)
+    assert fr.dtype.itemsize == 104
+    if samples is None:
+        sf, sb = [], []
+        for k, f in enumerate(fr):
+            nb = sensors[int(f["sensor"])].n_beams
+            sf.append(np.full(nb, k, np.int64))
+            sb.append(np.arange(nb, dtype=np.int64))
+        samples = (np.concatenate(sf), np.concatenate(sb))
+    verts, tris, mat, inst, table, sens, keep, _, sf, sb = _inputs(scene, sensors, np.zeros(0, dtype=[
+        ("sensor", np.int32), ("frame", np.int32), ("pose", np.float32, (12,))]), table, samples)
+    n = sf.size
+    nsub = max(int(s.n_subrays) for s in sensors)
+    R = CastResult(
+        valid=np.zeros(n, np.uint8), tri=np.zeros(n, np.uint32), t=np.zeros(n), range=np.zeros(n),
+        intensity=np.zeros(n), normal=np.zeros((n, 3)), xyz=np.zeros((n, 3)), mat=np.zeros(n, np.uint16),
+        inst=np.zeros(n, np.uint32), theta_deg=np.zeros(n), R=np.zeros(n), rf=np.zeros(n),
+        sub=np.zeros(n, np.int32), flags=np.zeros(n, np.uint32),
+        sub_valid=np.zeros((n, nsub), np.uint8), sub_I=np.zeros((n, nsub)), sub_range=np.zeros((n, nsub)),
+        sub_tri=np.zeros((n, nsub), np.uint32), sub_flags=np.zeros((n, nsub), np.uint32),
+        sample_frame=sf, sample_beam=sb)
+    out = _Out(*[R[name].ctypes.data for name, _ in _Out._fields_])
+    ep = None
+    if echoes is not None:
+        ne, mode, sep = echoes
+        R.update(echo_count=np.zeros(n, np.uint8), echo_range=np.zeros((n, ne)), echo_intensity=np.zeros((n, ne)),
+                 echo_tri=np.zeros((n, ne), np.uint32), echo_sub=np.zeros((n, ne), np.int32))
+        ep = _Echoes(ne, mode, sep, R["echo_count"].ctypes.data, R["echo_range"].ctypes.data,
+                     R["echo_intensity"].ctypes.data, R["echo_tri"].ctypes.data, R["echo_sub"].ctypes.data)
+    rc = lib().oracle_cast_sweep(_p(verts), verts.shape[0], _p(tris), tris.shape[0], _p(mat), _p(inst), sens,
+                                 len(sensors), fr.ctypes.data_as(ctypes.c_void_p), len(fr), _p(table),
+                                 table.shape[0], seed, _p(sf), _p(sb), n, nsub, ctypes.byref(out),
+                                 ctypes.byref(ep) if ep is not None else None, n_threads)
+    if rc != 0:
+        raise ValueError("oracle_cast_sweep rejected its inputs")
+    return R
+
+
 def cast(scene, sensors, frames, table, seed, samples=None, n_threads=0):
     """Run the oracle on (frame entry, beam) samples (default: every beam of
     every frame).  `scene` has verts/tris/mat/inst; `sensors` are objects with
@@ -260,7 +339,8 @@ def cast(scene, sensors, frames, table, seed, samples=None, n_threads=0):
         el = _c(s.el_rad, np.float64)
         keep += [az, el]
         sens[i] = _Sensor(az.size, az.ctypes.data, el.ctypes.data, s.r_min, s.r_max, s.d_max, s.RL_max,
-                          s.sigma, s.gain, s.range_exp, s.r_ref, s.divergence_rad, s.n_subrays)
+                          s.sigma, s.gain, s.range_exp, s.r_ref, s.divergence_rad, s.n_subrays,
+                          getattr(s, "sigma_k", 0.0))
     fr = np.ascontiguousarray(frames)
     assert fr.dtype.itemsize == 56
     if samples is None:

@@ -17,7 +17,8 @@
  *               theta = atan2(|d x n|, |d . n|).
  *   reflectance (Eq. 4, generalised to a 91-entry table per material that is
  *               interpolated linearly over incidence angle, Sec. III).
- *   noise (Sec. II-A): d = t + sigma * z, z standard normal drawn by
+ *   noise (Sec. II-A): d = t + (sigma + sigma_k t) z (sigma_k = 0: the paper's
+ *               constant noise factor), z standard normal drawn by
  *               Box-Muller from Philox4x64-10 (Salmon et al., SC'11).
  *   capability model (Sec. II-D, Eq. 5): detected iff R_L(d) = RL_max/d_max*d
  *               <= R, with d <= d_max, and d inside [r_min, r_max].
@@ -55,6 +56,7 @@ typedef struct {
     const double* el;
     float r_min, r_max, d_max, RL_max, sigma, gain, range_exp, r_ref, divergence;
     int32_t n_sub;
+    float sigma_k;   /* noise standard deviation sigma + sigma_k * t at true range t */
 } oracle_sensor;
 
 typedef struct {
@@ -427,7 +429,8 @@ static void oracle_one_ray(const oracle_tris* S, const uint16_t* mat, const doub
 {
     double o[3] = {o32[0], o32[1], o32[2]};
     double d[3] = {d32[0], d32[1], d32[2]};
-    double T_max = (double)fminf(sen->r_max, sen->d_max) + 9.0 * (double)sen->sigma;
+    double T_max = ((double)fminf(sen->r_max, sen->d_max) + 9.0 * (double)sen->sigma) /
+                   (1.0 - 9.0 * (double)sen->sigma_k);
     double best_t;
     int64_t best = oracle_closest(S, o, d, T_max, &best_t, &res->flags);
     if (best < 0) {
@@ -467,7 +470,7 @@ static void oracle_one_ray(const oracle_tris* S, const uint16_t* mat, const doub
 
     /* range noise */
     double z = oracle_normal(seed, beam, frame, sensor_id, sub);
-    double dist = best_t + (double)sen->sigma * z;
+    double dist = best_t + ((double)sen->sigma + (double)sen->sigma_k * best_t) * z;
 
     /* cut-offs */
     double r_min = sen->r_min, r_max = sen->r_max, d_max = sen->d_max, RL = sen->RL_max;
@@ -587,6 +590,293 @@ int oracle_cast(const float* verts, int64_t n_verts, const uint32_t* tris, int64
                                          (double)fr->pose[4 + c] * best_res.n_world[1] +
                                          (double)fr->pose[8 + c] * best_res.n_world[2];
             for (int c = 0; c < 3; ++c) out->xyz[3 * s + c] = best_res.range * (double)ds[c];
+        } else {
+            out->mat[s] = 0;
+            out->inst[s] = 0;
+            for (int c = 0; c < 3; ++c) { out->normal[3 * s + c] = 0.0; out->xyz[3 * s + c] = 0.0; }
+        }
+    }
+    oracle_tris_free(&S);
+    return 0;
+}
+
+/* ---------------------------------------- rolling shutter and multi-echo */
+
+/* Rolling shutter (Sec. II-A: the camera is turned with the sensor's spin
+ * over each time step): beam b fires at the fraction s_b of the sweep, its
+ * azimuth over 2 pi taken in [0, 1) (the sweep starts at azimuth 0 and turns
+ * towards +y), and sees the pose interpolated between the sweep's start and
+ * end poses: translation (1 - s) t0 + s t1, rotation the normalised linear
+ * blend (1 - s) q0 + s q1 of the two poses' unit quaternions (taken on the
+ * same hemisphere); both blends are exact at s = 0 and s = 1.
+ * The quaternions are found from the rotation matrices in FP64 and rounded
+ * once; the blend, its normalisation, the matrix of the blended quaternion and
+ * the translation are FP32 with every operation rounded as written.
+ *
+ * Multi-echo (Sec. IV, future work): from the returns of a beam's sub-rays,
+ *   mode 0: the n strongest, strongest first (ties to the lower sub-ray),
+ *           skipping a return closer than `separation` in range to one kept;
+ *   mode 1: the first (smallest range) and the last (largest range) return,
+ *           the last only if it lies at least `separation` beyond the first
+ *           (ties to the lower sub-ray). */
+#define ORACLE_FLAG_ECHO 32u /* echo choice within tolerance of a tie or of the separation */
+
+typedef struct {
+    int32_t sensor;
+    int32_t frame;
+    float pose0[12];
+    float pose1[12];
+} oracle_sweep_frame;
+
+typedef struct {
+    int32_t n_echoes;
+    int32_t mode;
+    float separation;
+    uint8_t* count;
+    double* range;      /* [n][n_echoes] */
+    double* intensity;
+    uint32_t* tri;
+    int32_t* sub;
+} oracle_echoes;
+
+/* firing fraction of a beam of azimuth az */
+float oracle_sweep_fraction(double az)
+{
+    double s = fmod(az, 2.0 * M_PI) / (2.0 * M_PI);
+    if (s < 0.0) s += 1.0;
+    if (s >= 1.0) s = 0.0;
+    return (float)s;
+}
+
+/* unit quaternion (w, x, y, z) of the rotation part of a row-major 3x4 pose,
+ * by the largest of the four diagonal combinations (Shepperd 1978), FP64 */
+static void pose_quaternion(const float* P, double* q)
+{
+    const double m00 = P[0], m01 = P[1], m02 = P[2], m10 = P[4], m11 = P[5], m12 = P[6];
+    const double m20 = P[8], m21 = P[9], m22 = P[10];
+    const double tr = m00 + m11 + m22;
+    if (tr >= m00 && tr >= m11 && tr >= m22) {
+        const double r = sqrt(1.0 + tr), h = 0.5 / r;
+        q[0] = 0.5 * r; q[1] = (m21 - m12) * h; q[2] = (m02 - m20) * h; q[3] = (m10 - m01) * h;
+    } else if (m00 >= m11 && m00 >= m22) {
+        const double r = sqrt(1.0 + m00 - m11 - m22), h = 0.5 / r;
+        q[0] = (m21 - m12) * h; q[1] = 0.5 * r; q[2] = (m01 + m10) * h; q[3] = (m02 + m20) * h;
+    } else if (m11 >= m22) {
+        const double r = sqrt(1.0 + m11 - m00 - m22), h = 0.5 / r;
+        q[0] = (m02 - m20) * h; q[1] = (m01 + m10) * h; q[2] = 0.5 * r; q[3] = (m12 + m21) * h;
+    } else {
+        const double r = sqrt(1.0 + m22 - m00 - m11), h = 0.5 / r;
+        q[0] = (m10 - m01) * h; q[1] = (m02 + m20) * h; q[2] = (m12 + m21) * h; q[3] = 0.5 * r;
+    }
+    const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) q[i] /= n;
+}
+
+/* the sweep's two quaternions, same hemisphere, rounded to FP32 */
+void oracle_sweep_quaternions(const float* pose0, const float* pose1, float* q0f, float* q1f)
+{
+    double q0[4], q1[4];
+    pose_quaternion(pose0, q0);
+    pose_quaternion(pose1, q1);
+    const double dq = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2] + q0[3] * q1[3];
+    for (int i = 0; i < 4; ++i) {
+        q0f[i] = (float)q0[i];
+        q1f[i] = (float)(dq < 0.0 ? -q1[i] : q1[i]);
+    }
+}
+
+/* pose at fraction s of the sweep, FP32, every operation rounded as written */
+void oracle_sweep_pose(const float* q0, const float* q1, const float* pose0, const float* pose1, float s,
+                       float* P)
+{
+    const float ms = 1.0f - s;
+    float q[4];
+    for (int i = 0; i < 4; ++i) {
+        float a = ms * q0[i];
+        q[i] = fmaf(s, q1[i], a);
+    }
+    float n2 = q[0] * q[0];
+    float t1 = q[1] * q[1];
+    float t2 = q[2] * q[2];
+    float t3 = q[3] * q[3];
+    n2 = n2 + t1;
+    n2 = n2 + t2;
+    n2 = n2 + t3;
+    float inv = 1.0f / sqrtf(n2);
+    const float w = q[0] * inv, x = q[1] * inv, y = q[2] * inv, z = q[3] * inv;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    const float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
+    float a;
+    a = yy + zz; P[0] = 1.0f - 2.0f * a;
+    a = xy - wz; P[1] = 2.0f * a;
+    a = xz + wy; P[2] = 2.0f * a;
+    a = xy + wz; P[4] = 2.0f * a;
+    a = xx + zz; P[5] = 1.0f - 2.0f * a;
+    a = yz - wx; P[6] = 2.0f * a;
+    a = xz - wy; P[8] = 2.0f * a;
+    a = yz + wx; P[9] = 2.0f * a;
+    a = xx + yy; P[10] = 1.0f - 2.0f * a;
+    for (int r = 0; r < 3; ++r) {
+        float a = ms * pose0[4 * r + 3];
+        P[4 * r + 3] = fmaf(s, pose1[4 * r + 3], a);
+    }
+}
+
+/* echo choice from the kept sub-ray returns of one beam */
+static int oracle_pick_echoes(int n_sub, const ray_result* rr, int mode, int n_echoes, double sep, int* pick,
+                              uint32_t* flags)
+{
+    int n = 0;
+    uint32_t f = 0;
+    int idx[64], m = 0;
+    for (int k = 0; k < n_sub; ++k)
+        if (rr[k].valid) idx[m++] = k;
+    for (int a = 0; a < m; ++a)
+        for (int b = a + 1; b < m; ++b) {
+            const ray_result *ra = rr + idx[a], *rb = rr + idx[b];
+            const double dI = fabs(ra->I - rb->I), dR = fabs(ra->range - rb->range);
+            if (mode == 0 && dI <= 1e-4 * fmax(ra->I, rb->I) + 1e-7) f |= ORACLE_FLAG_ECHO;
+            if (mode == 1 && dR <= 1e-5 * fmax(ra->range, rb->range)) f |= ORACLE_FLAG_ECHO;
+            if (fabs(dR - sep) <= 1e-5 * fmax(ra->range, rb->range) + 1e-6) f |= ORACLE_FLAG_ECHO;
+        }
+    for (int k = 0; k < n_sub; ++k)
+        if (rr[k].flags & (ORACLE_FLAG_EDGE | ORACLE_FLAG_TIE | ORACLE_FLAG_CUTOFF)) f |= ORACLE_FLAG_ECHO;
+    if (mode == 0) {
+        int used[64] = {0};
+        while (n < n_echoes) {
+            int best = -1;
+            for (int a = 0; a < m; ++a) {
+                if (used[a]) continue;
+                if (best < 0 || rr[idx[a]].I > rr[idx[best]].I) best = a;
+            }
+            if (best < 0) break;
+            used[best] = 1;
+            int ok = 1;
+            for (int j = 0; j < n; ++j)
+                if (fabs(rr[idx[best]].range - rr[pick[j]].range) < sep) ok = 0;
+            if (ok) pick[n++] = idx[best];
+        }
+    } else if (m > 0) {
+        int first = idx[0], last = idx[0];
+        for (int a = 1; a < m; ++a) {
+            if (rr[idx[a]].range < rr[first].range) first = idx[a];
+            if (rr[idx[a]].range > rr[last].range) last = idx[a];
+        }
+        pick[n++] = first;
+        if (n_echoes > 1 && rr[last].range - rr[first].range >= sep) pick[n++] = last;
+    }
+    *flags |= f;
+    return n;
+}
+
+int oracle_cast_sweep(const float* verts, int64_t n_verts, const uint32_t* tris, int64_t n_tris,
+                      const uint16_t* mat, const uint32_t* inst, const oracle_sensor* sensors, int32_t n_sensors,
+                      const oracle_sweep_frame* frames, int32_t n_frames, const double* table, int32_t n_mat,
+                      uint64_t seed, const int64_t* sample_frame, const int64_t* sample_beam, int64_t n_samples,
+                      int32_t n_sub_max, oracle_out* out, oracle_echoes* echo, int32_t n_threads)
+{
+    if (echo && (echo->n_echoes < 1 || echo->n_echoes > 4 || echo->mode < 0 || echo->mode > 1)) return -1;
+    for (int64_t i = 0; i < 3 * n_tris; ++i)
+        if ((int64_t)tris[i] >= n_verts) return -1;
+    for (int64_t s = 0; s < n_samples; ++s) {
+        if (sample_frame[s] < 0 || sample_frame[s] >= n_frames) return -1;
+        const oracle_sweep_frame* fr = frames + sample_frame[s];
+        if (fr->sensor < 0 || fr->sensor >= n_sensors) return -1;
+        if (sample_beam[s] < 0 || sample_beam[s] >= sensors[fr->sensor].n_beams) return -1;
+        if (sensors[fr->sensor].n_sub > n_sub_max || sensors[fr->sensor].n_sub < 1 ||
+            sensors[fr->sensor].n_sub > 64) return -1;
+    }
+    oracle_tris S;
+    oracle_tris_init(&S, verts, tris, n_tris);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t s = 0; s < n_samples; ++s) {
+        const oracle_sweep_frame* fr = frames + sample_frame[s];
+        const oracle_sensor* sen = sensors + fr->sensor;
+        const int64_t b = sample_beam[s];
+        float q0[4], q1[4], P[12];
+        oracle_sweep_quaternions(fr->pose0, fr->pose1, q0, q1);
+        oracle_sweep_pose(q0, q1, fr->pose0, fr->pose1, oracle_sweep_fraction(sen->az[b]), P);
+        float ds[3], o32[3], dw[3];
+        oracle_beam_dirs(1, sen->az + b, sen->el + b, ds);
+        oracle_world_ray(P, ds, o32, dw);
+        float alpha[64], beta[64];
+        oracle_subray_offsets(sen->divergence, sen->n_sub, alpha, beta);
+        ray_result rr[64];
+        int chosen = 0;
+        double best_I = -1.0, second_I = -1.0;
+        uint32_t any_flags = 0;
+        for (int k = 0; k < sen->n_sub; ++k) {
+            float dk[3];
+            oracle_subray_dir(dw, alpha[k], beta[k], k, dk);
+            oracle_one_ray(&S, mat, table, n_mat, sen, o32, dk, seed, (uint64_t)b, (uint32_t)fr->frame,
+                           (uint32_t)fr->sensor, (uint32_t)k, rr + k);
+            any_flags |= rr[k].flags;
+            if (rr[k].valid) {
+                if (rr[k].I > best_I) {
+                    second_I = best_I;
+                    best_I = rr[k].I;
+                    chosen = k;
+                } else if (rr[k].I > second_I) {
+                    second_I = rr[k].I;
+                }
+            }
+        }
+        const ray_result* best = rr + chosen;
+        uint32_t flags = best->flags;
+        if (sen->n_sub > 1) {
+            double tolI = 1e-4 * fabs(best_I) + 1e-7 * (double)sen->gain;
+            if ((second_I >= 0.0 && best_I - second_I <= tolI) ||
+                (any_flags & (ORACLE_FLAG_EDGE | ORACLE_FLAG_TIE | ORACLE_FLAG_CUTOFF)))
+                flags |= ORACLE_FLAG_SUBTIE;
+        }
+        if (echo) {
+            int pick[4];
+            const int ne = oracle_pick_echoes(sen->n_sub, rr, echo->mode, echo->n_echoes, (double)echo->separation,
+                                              pick, &flags);
+            echo->count[s] = (uint8_t)ne;
+            for (int j = 0; j < echo->n_echoes; ++j) {
+                const int64_t e = s * echo->n_echoes + j;
+                if (j < ne) {
+                    echo->range[e] = rr[pick[j]].range;
+                    echo->intensity[e] = rr[pick[j]].I;
+                    echo->tri[e] = rr[pick[j]].tri;
+                    echo->sub[e] = pick[j];
+                } else {
+                    echo->range[e] = 0.0;
+                    echo->intensity[e] = 0.0;
+                    echo->tri[e] = ORACLE_NO_HIT;
+                    echo->sub[e] = -1;
+                }
+            }
+        }
+        out->valid[s] = (uint8_t)best->valid;
+        out->tri[s] = best->tri;
+        out->t[s] = best->t;
+        out->range[s] = best->range;
+        out->intensity[s] = best->I;
+        out->theta_deg[s] = best->theta_deg;
+        out->R[s] = best->R;
+        out->rf[s] = best->rf;
+        out->sub[s] = chosen;
+        out->flags[s] = flags;
+        if (out->sub_valid)
+            for (int k = 0; k < sen->n_sub; ++k) {
+                out->sub_valid[s * n_sub_max + k] = (uint8_t)rr[k].valid;
+                out->sub_I[s * n_sub_max + k] = rr[k].I;
+                out->sub_range[s * n_sub_max + k] = rr[k].range;
+                out->sub_tri[s * n_sub_max + k] = rr[k].tri;
+                out->sub_flags[s * n_sub_max + k] = rr[k].flags;
+            }
+        if (best->tri != ORACLE_NO_HIT) {
+            out->mat[s] = mat[best->tri];
+            out->inst[s] = inst[best->tri];
+            for (int c = 0; c < 3; ++c)
+                out->normal[3 * s + c] = (double)P[0 + c] * best->n_world[0] + (double)P[4 + c] * best->n_world[1] +
+                                         (double)P[8 + c] * best->n_world[2];
+            for (int c = 0; c < 3; ++c) out->xyz[3 * s + c] = best->range * (double)ds[c];
         } else {
             out->mat[s] = 0;
             out->inst[s] = 0;
@@ -757,7 +1047,8 @@ int oracle_raster(const float* verts, int64_t n_verts, const uint32_t* tris, int
         oracle_world_ray(fr->pose, dps, o32, dw);
         double o[3] = {o32[0], o32[1], o32[2]};
         double d[3] = {dw[0], dw[1], dw[2]};
-        const double T_max = (double)fminf(sen->r_max, sen->d_max) + 9.0 * (double)sen->sigma;
+        const double T_max = ((double)fminf(sen->r_max, sen->d_max) + 9.0 * (double)sen->sigma) /
+                             (1.0 - 9.0 * (double)sen->sigma_k);
         double t;
         uint32_t flags;
         int64_t best = oracle_closest(&S, o, d, T_max, &t, &flags);
@@ -766,7 +1057,7 @@ int oracle_raster(const float* verts, int64_t n_verts, const uint32_t* tris, int
         out->tri[s] = (uint32_t)best;
         out->t[s] = t;
         /* depth pass: z-depth, 24-bit */
-        const float Tm = fminf(sen->r_max, sen->d_max) + 9.0f * sen->sigma;
+        const float Tm = (fminf(sen->r_max, sen->d_max) + 9.0f * sen->sigma) / (1.0f - 9.0f * sen->sigma_k);
         double zd = t * (double)inv;
         out->z[s] = zd;
         float z32 = (float)zd;
@@ -798,7 +1089,7 @@ int oracle_raster(const float* verts, int64_t n_verts, const uint32_t* tris, int
         double th = (double)qa * (90.0 / 16777215.0);
         double d_beam = zq / (double)zk;
         double zn = oracle_normal(seed, (uint64_t)b, (uint32_t)fr->frame, (uint32_t)fr->sensor, 0);
-        double dist = d_beam + (double)sen->sigma * zn;
+        double dist = d_beam + ((double)sen->sigma + (double)sen->sigma_k * d_beam) * zn;
         int mrow = (int)m8 < n_mat ? (int)m8 : n_mat - 1;
         int ii;
         double ff;

@@ -48,7 +48,7 @@ class lidar_sensor_desc(ctypes.Structure):
                 ("r_min", ctypes.c_float), ("r_max", ctypes.c_float), ("d_max", ctypes.c_float),
                 ("RL_max", ctypes.c_float), ("sigma", ctypes.c_float), ("gain", ctypes.c_float),
                 ("range_exp", ctypes.c_float), ("r_ref", ctypes.c_float), ("divergence_rad", ctypes.c_float),
-                ("n_subrays", ctypes.c_int32)]
+                ("n_subrays", ctypes.c_int32), ("sigma_k", ctypes.c_float)]
 
 
 class lidar_frame(ctypes.Structure):

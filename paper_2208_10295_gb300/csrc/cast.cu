@@ -68,7 +68,7 @@ __device__ __forceinline__ void shade(const SceneDev& S, const HitRec& h, const 
     const float R = R0 * (1.0f - f) + R1 * f;
     // range with Gaussian noise (Sec. II-A)
     const float z = range_noise_normal(seed, beam, frame, sensor, sub);
-    const float d = h.t + sd.sigma * z;
+    const float d = h.t + __fmaf_rn(sd.sigma_k, h.t, sd.sigma) * z;
     // capability model (Eq. 5) and range limits
     const float RLd = __fdiv_rn(__fmul_rn(sd.RL_max, d), sd.d_max);
     const int valid = (d >= sd.r_min) && (d <= sd.r_max) && (d <= sd.d_max) && (RLd <= R);

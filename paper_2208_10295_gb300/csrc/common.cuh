@@ -72,7 +72,8 @@ struct SensorDev {
     int32_t n_beams;
     int32_t n_sub;
     float r_min, r_max, d_max, RL_max, sigma, gain, range_exp, r_ref;
-    float t_max;              // search range end: min(r_max, d_max) + 9 sigma
+    float sigma_k;            // range-scaled noise: std = sigma + sigma_k t
+    float t_max;              // search range end: (min(r_max, d_max) + 9 sigma) / (1 - 9 sigma_k)
     float alpha[LIDAR_MAX_SUBRAYS], beta[LIDAR_MAX_SUBRAYS];
 };
 

@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256) k_resample(RasterCams C, RasterFrame F, c
     const float* row = T.table + (int64_t)mrow * LIDAR_TABLE_SIZE;
     const float R = __ldg(&row[i]) * (1.0f - f) + __ldg(&row[i + 1]) * f;
     const float zn = range_noise_normal(seed, (uint32_t)b, (uint32_t)frame_id, (uint32_t)sensor, 0u);
-    const float d = d_beam + sd.sigma * zn;
+    const float d = d_beam + __fmaf_rn(sd.sigma_k, d_beam, sd.sigma) * zn;
     const float RLd = __fdiv_rn(__fmul_rn(sd.RL_max, d), sd.d_max);
     const int valid = (d >= sd.r_min) && (d <= sd.r_max) && (d <= sd.d_max) && (RLd <= R);
     const float rf = (sd.range_exp == 0.0f) ? 1.0f : powf(sd.r_ref / d, sd.range_exp);

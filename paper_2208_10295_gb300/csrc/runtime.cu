@@ -369,6 +369,7 @@ lidar_status lidar_set_sensor(lidar_ctx* c, int32_t slot, const lidar_sensor_des
     LIDAR_CHECK_ARG(d->r_min >= 0.0f && d->r_max > d->r_min, "lidar_set_sensor: need 0 <= r_min < r_max");
     LIDAR_CHECK_ARG(d->d_max > 0.0f && d->RL_max >= 0.0f, "lidar_set_sensor: need d_max > 0, RL_max >= 0");
     LIDAR_CHECK_ARG(d->sigma >= 0.0f && isfinite(d->sigma), "lidar_set_sensor: sigma must be finite, >= 0");
+    LIDAR_CHECK_ARG(d->sigma_k >= 0.0f && d->sigma_k < 0.1f, "lidar_set_sensor: sigma_k must be in [0, 0.1)");
     LIDAR_CHECK_ARG(d->divergence_rad >= 0.0f && d->divergence_rad < 0.1f, "lidar_set_sensor: divergence out of range");
     DeviceGuard g(c->device);
     const int64_t n = d->n_beams;
@@ -411,7 +412,9 @@ lidar_status lidar_set_sensor(lidar_ctx* c, int32_t slot, const lidar_sensor_des
     sd.n_sub = d->n_subrays;
     sd.r_min = d->r_min; sd.r_max = d->r_max; sd.d_max = d->d_max; sd.RL_max = d->RL_max;
     sd.sigma = d->sigma; sd.gain = d->gain; sd.range_exp = d->range_exp; sd.r_ref = d->r_ref;
-    sd.t_max = fminf(d->r_max, d->d_max) + 9.0f * d->sigma;
+    sd.sigma_k = d->sigma_k;
+    // |z| <= 8.6 for the 53-bit uniforms: t (1 - 9 sigma_k) - 9 sigma > d_lim for any t beyond this
+    sd.t_max = (fminf(d->r_max, d->d_max) + 9.0f * d->sigma) / (1.0f - 9.0f * d->sigma_k);
     // sub-ray offsets: ray 0 is the beam, rays 1..n-1 on the cone of half-angle divergence/2
     const double rad = tan(0.5 * (double)d->divergence_rad);
     for (int k = 0; k < LIDAR_MAX_SUBRAYS; ++k) {

@@ -103,7 +103,7 @@ class Lidar:
         el = np.ascontiguousarray(spec.el_rad, dtype=np.float64)
         d = C.lidar_sensor_desc(az.size, az.ctypes.data, el.ctypes.data, spec.r_min, spec.r_max, spec.d_max,
                                 spec.RL_max, spec.sigma, spec.gain, spec.range_exp, spec.r_ref,
-                                spec.divergence_rad, spec.n_subrays)
+                                spec.divergence_rad, spec.n_subrays, getattr(spec, "sigma_k", 0.0))
         C.check(C.lidar_set_sensor(self.handle, slot, ctypes.byref(d)), "lidar_set_sensor")
         self.n_beams[slot] = az.size
         self.gains[slot] = float(np.float32(spec.gain))

@@ -28,6 +28,7 @@ class SensorSpec:
     r_ref: float = 1.0
     divergence_rad: float = 0.0  # full beam divergence; 0 = single ray per beam
     n_subrays: int = 1
+    sigma_k: float = 0.0        # range-scaled noise: std = sigma + sigma_k * t
 
     @property
     def n_beams(self) -> int:

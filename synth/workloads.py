@@ -60,6 +60,22 @@ def pose_rows(R: np.ndarray, t: np.ndarray) -> np.ndarray:
     return P.reshape(12).astype(np.float32)
 
 
+# a sweep: the pose at its start and at its end (rolling shutter)
+SWEEP_FRAME_DTYPE = np.dtype([("sensor", np.int32), ("frame", np.int32), ("pose0", np.float32, (12,)),
+                              ("pose1", np.float32, (12,))], align=False)
+
+
+def make_sweep_frames(entries):
+    """entries: (sensor, frame, pose0 rows [12], pose1 rows [12])."""
+    fr = np.zeros(len(entries), dtype=SWEEP_FRAME_DTYPE)
+    for i, (s, f, p0, p1) in enumerate(entries):
+        fr[i]["sensor"] = s
+        fr[i]["frame"] = f
+        fr[i]["pose0"] = np.asarray(p0, np.float32).reshape(12)
+        fr[i]["pose1"] = np.asarray(p1, np.float32).reshape(12)
+    return fr
+
+
 def make_frames(entries):
     fr = np.zeros(len(entries), dtype=FRAME_DTYPE)
     for k, (s, f, pose) in enumerate(entries):

@@ -305,3 +305,41 @@ def test_cfg0_flag_rates(oracle_lib):
     r = oracle_lib.cast(w.scene, w.sensors, w.frames, T, w.seed)
     assert r.valid.sum() > 5000
     assert ((r.flags & 7) != 0).mean() < 0.01
+
+
+def test_range_scaled_noise_closed_form(oracle_lib):
+    """Range-scaled noise (the noise factor of Sec. II-A growing with range):
+    d = t + (sigma + sigma_k t) z, with z the Box-Muller draw of the beam's
+    Philox4x64-10 block (counter (beam, frame | sensor << 32, sub-ray, 0), key
+    (seed, 0)) computed here from numpy's Philox."""
+    from test_oracle_pieces import _numpy_philox_block
+    h, seed = 1.8, 77
+    phis = np.array([1.0, 3.0, 8.0, 20.0, 45.0, 80.0])
+    sig, sk = 0.02, 0.004
+    scene = quads_scene([ground_quad()])
+    s = sensor(np.linspace(0, 6, phis.size), -np.radians(phis), r_min=0.01, r_max=500.0, d_max=500.0,
+               RL_max=1e-6, sigma=sig, sigma_k=sk)
+    r = oracle_lib.cast(scene, [s], identity_frame((0.0, 0.0, h), frame=5), const_table(0.5), seed=seed)
+    t = r.t
+    assert np.allclose(t, h / np.sin(np.radians(phis)), rtol=1e-6)
+    z = []
+    for b in range(phis.size):
+        x = _numpy_philox_block([b, 5 | (0 << 32), 0, 0], [seed, 0])
+        u0 = ((int(x[0]) >> 11) + 0.5) * 2.0 ** -53
+        u1 = ((int(x[1]) >> 11) + 0.5) * 2.0 ** -53
+        z.append(math.sqrt(-2.0 * math.log(u0)) * math.cos(2.0 * math.pi * u1))
+    z = np.array(z)
+    s32, k32 = float(np.float32(sig)), float(np.float32(sk))
+    assert np.allclose(r.range, t + (s32 + k32 * t) * z, rtol=1e-12, atol=1e-12)
+
+
+def test_range_scaled_noise_search_range(oracle_lib):
+    """With sigma_k > 0 the search range is (d_lim + 9 sigma) / (1 - 9 sigma_k):
+    a wall just inside it is hit, one just beyond it is a miss."""
+    sig, sk, dlim = 0.05, 0.02, 100.0
+    T = (float(np.float32(dlim)) + 9.0 * float(np.float32(sig))) / (1.0 - 9.0 * float(np.float32(sk)))
+    for x, hit in ((T * (1 - 1e-4), True), (T * (1 + 1e-4), False)):
+        scene = quads_scene([wall_x(x, half=10.0)])
+        s = sensor(np.zeros(1), np.zeros(1), r_min=0.5, r_max=dlim, d_max=dlim, RL_max=1e-6, sigma=sig, sigma_k=sk)
+        r = oracle_lib.cast(scene, [s], identity_frame(), const_table(0.5), seed=1)
+        assert (r.tri[0] != oracle_lib.NO_HIT) == hit
