@@ -46,7 +46,7 @@ POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal,
 # L2 flushed before the launch), from one ncu capture, with the digest of the
 # kernel sources the capture ran.  Reported only while the sources still match.
 NCU_TRAFFIC = {"sources": "8848d1800928a1ec", "bytes": 10_275_840}   # profiles/k_cast_cfg1_ncu_full.md
-KERNEL_SOURCES = ("cast.cu", "trace.cuh", "common.cuh", "philox.cuh")
+KERNEL_SOURCES = ("cast.cu", "shade.cuh", "trace.cuh", "common.cuh", "philox.cuh")
 
 
 def kernel_digest():

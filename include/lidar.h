@@ -361,6 +361,52 @@ lidar_status lidar_schedule_by_cost(lidar_ctx* ctx, const lidar_scene* scene, co
 /* Restores the Morton order of a slot. */
 lidar_status lidar_reset_schedule(lidar_ctx* ctx, int32_t slot);
 
+/* --------------------------------------------- rolling shutter, multi-echo */
+
+/* One sweep of a spinning sensor: the sensor-to-world pose at its start and
+ * at its end (row-major 3x4 each).  Beam b fires at the fraction s_b of the
+ * sweep — its azimuth over 2 pi, in [0, 1): the sweep starts at azimuth 0 and
+ * turns towards +y — and sees the blended pose (Sec. II-A turns the render
+ * camera with the sensor's spin over each time step): translation
+ * (1 - s) t0 + s t1, rotation of the normalised blend (1 - s) q0 + s q1 of the
+ * poses' unit quaternions (found in FP64, rounded once, same hemisphere),
+ * both in FP32 with every operation rounded as written. */
+typedef struct {
+    int32_t sensor;
+    int32_t frame;
+    float pose0[12];
+    float pose1[12];
+} lidar_sweep_frame;
+
+/* Multiple returns per beam (Sec. IV: multiple echoes are future work), from
+ * the returns of the beam's sub-rays (LIDAR_MAX_SUBRAYS at most):
+ *   mode 0: the n_echoes strongest, strongest first (ties to the lower
+ *           sub-ray), skipping a return closer than `separation` metres in
+ *           range to one already kept;
+ *   mode 1: the first (smallest range) and, if n_echoes >= 2 and it lies at
+ *           least `separation` beyond it, the last (largest range) return.
+ * Per beam (dense layout): count, and [n][n_echoes] range, intensity, tri
+ * (original index), sub (sub-ray index); slots past count hold 0,
+ * LIDAR_NO_HIT and 255.  count is required, the arrays optional. */
+typedef struct {
+    int32_t n_echoes;      /* 1..4 */
+    int32_t mode;          /* 0 strongest, 1 first and last */
+    float separation;      /* metres, >= 0 */
+    uint8_t* count;
+    float* range;
+    float* intensity;
+    uint32_t* tri;
+    uint8_t* sub;
+} lidar_echoes;
+
+/* Casts every beam of every sweep (dense outputs as lidar_cast: the strongest
+ * return in `beams`, normals rotated by the beam's own pose; no point cloud)
+ * and, if `echoes` is given, the multi-echo outputs.  One thread per beam with
+ * the 4-wide traversal; the sub-rays, noise draws and model are those of
+ * lidar_cast.  Asynchronous. */
+lidar_status lidar_cast_sweep(lidar_ctx* ctx, const lidar_scene* scene, const lidar_sweep_frame* frames_host,
+                              int32_t n_frames, uint64_t seed, const lidar_beams* beams, const lidar_echoes* echoes);
+
 /* ------------------------------------------------- raster-and-resample path */
 
 /* The paper's own sampling (Sec. II-A..II-C), as compute rasterisation: per

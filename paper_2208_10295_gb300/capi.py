@@ -76,11 +76,22 @@ class lidar_launch_config(ctypes.Structure):
                 ("fused_scatter", ctypes.c_int32)]
 
 
+class lidar_sweep_frame(ctypes.Structure):
+    _fields_ = [("sensor", ctypes.c_int32), ("frame", ctypes.c_int32), ("pose0", ctypes.c_float * 12),
+                ("pose1", ctypes.c_float * 12)]
+
+
+class lidar_echoes(ctypes.Structure):
+    _fields_ = [("n_echoes", ctypes.c_int32), ("mode", ctypes.c_int32), ("separation", ctypes.c_float)] + \
+               [(n, c_vp) for n in ("count", "range", "intensity", "tri", "sub")]
+
+
 class lidar_raster_config(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("n_cameras", ctypes.c_int32)]
 
 
 assert ctypes.sizeof(lidar_frame) == 56
+assert ctypes.sizeof(lidar_sweep_frame) == 104
 
 _lock = threading.Lock()
 _lib = None
@@ -125,6 +136,8 @@ _PROTOS = [
     ("lidar_schedule_by_cost", ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(lidar_frame), ctypes.c_uint64,
                                               ctypes.c_int32]),
     ("lidar_reset_schedule", ctypes.c_int, [c_vp, ctypes.c_int32]),
+    ("lidar_cast_sweep", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.POINTER(lidar_beams), ctypes.POINTER(lidar_echoes)]),
     ("lidar_raster_cast", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
                                          ctypes.POINTER(lidar_raster_config), ctypes.POINTER(lidar_beams)]),
     ("lidar_raster_gbuffer", ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(lidar_frame),
@@ -197,6 +210,7 @@ lidar_cast_backward_mse = _fwd("lidar_cast_backward_mse")
 lidar_cast_backward_mse_noalloc = _fwd("lidar_cast_backward_mse_noalloc")
 lidar_count_work = _fwd("lidar_count_work")
 lidar_raster_cast = _fwd("lidar_raster_cast")
+lidar_cast_sweep = _fwd("lidar_cast_sweep")
 lidar_raster_gbuffer = _fwd("lidar_raster_gbuffer")
 lidar_schedule_by_cost = _fwd("lidar_schedule_by_cost")
 lidar_reset_schedule = _fwd("lidar_reset_schedule")

@@ -68,6 +68,7 @@ struct SceneDev {
 
 struct SensorDev {
     const float* dirs;        // [n_beams][3], sensor frame
+    const float* sweep;       // [n_beams] firing fraction of each beam in a sweep (azimuth / 2 pi in [0, 1))
     const uint32_t* order;    // ray order permutation [n_beams] (beam processed at position j)
     int32_t n_beams;
     int32_t n_sub;
@@ -187,6 +188,31 @@ cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid
 size_t backward_scratch_bytes(int M);
 // address (on the current device) and size of the allocation-free variant's scratch array
 cudaError_t noalloc_scratch(void** ptr, size_t* bytes);
+
+// --------------------------------------------- rolling shutter, multi-echo
+
+// One sweep: unit quaternions (w, x, y, z) and translations of the poses at
+// its start and end (same hemisphere), the frame's ids and dense offset
+struct SweepDev {
+    float q0[4], q1[4], t0[3], t1[3];
+    int32_t sensor, frame;
+    int64_t beam_offset;
+};
+
+struct EchoOut {
+    int n_echoes;     // 1..4 (0: no echo output)
+    int mode;         // 0: strongest, 1: first and last
+    float separation;
+    uint8_t* count;
+    float* range;     // [n][n_echoes]
+    float* intensity;
+    uint32_t* tri;
+    uint8_t* sub;
+};
+
+cudaError_t launch_cast_sweep(cudaStream_t s, const SceneDev& S, const SensorDev* sensors_dev,
+                              const SweepDev* frames_dev, int n_frames, int64_t n_total, TableDev T, uint64_t seed,
+                              BeamsOut out, EchoOut echo, int* status);
 
 // ------------------------------------------------------------ raster path
 

@@ -46,6 +46,7 @@ struct SensorSlot {
     float* dirs_dev = nullptr;
     uint32_t* order_dev = nullptr;       // the order the cast kernel follows
     uint32_t* base_order_dev = nullptr;  // Morton order of the beam directions
+    float* sweep_dev = nullptr;          // firing fraction of each beam in a sweep
     SensorDev dev{};
 };
 
@@ -82,6 +83,8 @@ struct lidar_ctx {
     FrameDev* frames_dev = nullptr;
     int64_t* tile_prefix_dev = nullptr;
     size_t frames_cap = 0;
+    SweepDev* sweeps_dev = nullptr;
+    size_t sweeps_cap = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
     LaunchCfg cfg{128, 4, 32, 1, 2, 1};
@@ -227,8 +230,10 @@ void lidar_destroy(lidar_ctx* c)
         cudaFree(sl.dirs_dev);
         cudaFree(sl.order_dev);
         cudaFree(sl.base_order_dev);
+        cudaFree(sl.sweep_dev);
     }
     cudaFree(c->sensors_dev);
+    cudaFree(c->sweeps_dev);
     cudaFree(c->frames_dev);
     cudaFree(c->tile_prefix_dev);
     cudaFree(c->scratch);
@@ -387,19 +392,32 @@ lidar_status lidar_set_sensor(lidar_ctx* c, int32_t slot, const lidar_sensor_des
         cudaFree(sl.dirs_dev);
         cudaFree(sl.order_dev);
         cudaFree(sl.base_order_dev);
+        cudaFree(sl.sweep_dev);
         sl = SensorSlot();
     }
     if (dev_alloc((void**)&sl.dirs_dev, n * 3 * sizeof(float)) != cudaSuccess ||
         dev_alloc((void**)&sl.order_dev, n * sizeof(uint32_t)) != cudaSuccess ||
-        dev_alloc((void**)&sl.base_order_dev, n * sizeof(uint32_t)) != cudaSuccess) {
+        dev_alloc((void**)&sl.base_order_dev, n * sizeof(uint32_t)) != cudaSuccess ||
+        dev_alloc((void**)&sl.sweep_dev, n * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(sl.dirs_dev);
         cudaFree(sl.order_dev);
+        cudaFree(sl.base_order_dev);
         sl = SensorSlot();
         set_error("lidar_set_sensor: device allocation failed");
         return LIDAR_ENOMEM;
     }
     LIDAR_CUDA(cudaMemcpyAsync(sl.dirs_dev, dirs.data(), n * 3 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    // firing fraction in a sweep: azimuth over 2 pi in [0, 1) (the sweep starts at azimuth 0, towards +y)
+    std::vector<float> frac((size_t)n);
+    for (int64_t b = 0; b < n; ++b) {
+        double s = fmod(d->az_rad[b], 2.0 * M_PI) / (2.0 * M_PI);
+        if (s < 0.0) s += 1.0;
+        if (s >= 1.0) s = 0.0;
+        frac[(size_t)b] = (float)s;
+    }
+    LIDAR_CUDA(cudaMemcpyAsync(sl.sweep_dev, frac.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    LIDAR_CUDA(cudaStreamSynchronize(c->stream));
     lidar_status st = ensure_scratch(c, ray_order_scratch_bytes(n));
     if (st != LIDAR_OK) return st;
     LIDAR_CUDA(launch_ray_order(c->stream, sl.dirs_dev, (int)n, sl.base_order_dev, c->scratch, c->scratch_bytes));
@@ -407,6 +425,7 @@ lidar_status lidar_set_sensor(lidar_ctx* c, int32_t slot, const lidar_sensor_des
                                c->stream));
     SensorDev& sd = sl.dev;
     sd.dirs = sl.dirs_dev;
+    sd.sweep = sl.sweep_dev;
     sd.order = sl.order_dev;
     sd.n_beams = (int32_t)n;
     sd.n_sub = d->n_subrays;
@@ -718,6 +737,103 @@ lidar_status lidar_raster_cast(lidar_ctx* c, const lidar_scene* scene, const lid
                                    offset, c->table, seed, G, out));
         offset += sl.n_beams;
     }
+    return LIDAR_OK;
+}
+
+// Unit quaternion (w, x, y, z) of a pose's rotation part, FP64: Shepperd's
+// method (the largest of trace and diagonal entries picks the stable formula).
+static void rotation_quaternion(const float* P, double q[4])
+{
+    const double r00 = P[0], r01 = P[1], r02 = P[2], r10 = P[4], r11 = P[5], r12 = P[6];
+    const double r20 = P[8], r21 = P[9], r22 = P[10];
+    const double tr = r00 + r11 + r22;
+    if (tr >= r00 && tr >= r11 && tr >= r22) {
+        const double r = sqrt(1.0 + tr), h = 0.5 / r;
+        q[0] = 0.5 * r; q[1] = (r21 - r12) * h; q[2] = (r02 - r20) * h; q[3] = (r10 - r01) * h;
+    } else if (r00 >= r11 && r00 >= r22) {
+        const double r = sqrt(1.0 + r00 - r11 - r22), h = 0.5 / r;
+        q[0] = (r21 - r12) * h; q[1] = 0.5 * r; q[2] = (r01 + r10) * h; q[3] = (r02 + r20) * h;
+    } else if (r11 >= r22) {
+        const double r = sqrt(1.0 + r11 - r00 - r22), h = 0.5 / r;
+        q[0] = (r02 - r20) * h; q[1] = (r01 + r10) * h; q[2] = 0.5 * r; q[3] = (r12 + r21) * h;
+    } else {
+        const double r = sqrt(1.0 + r22 - r00 - r11), h = 0.5 / r;
+        q[0] = (r10 - r01) * h; q[1] = (r02 + r20) * h; q[2] = (r12 + r21) * h; q[3] = 0.5 * r;
+    }
+    const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) q[i] /= n;
+}
+
+lidar_status lidar_cast_sweep(lidar_ctx* c, const lidar_scene* scene, const lidar_sweep_frame* frames,
+                              int32_t n_frames, uint64_t seed, const lidar_beams* beams, const lidar_echoes* echoes)
+{
+    LIDAR_CHECK_ARG(c != nullptr && scene != nullptr, "lidar_cast_sweep: ctx/scene is NULL");
+    LIDAR_CHECK_ARG(scene->ctx == c, "lidar_cast_sweep: scene belongs to another context");
+    LIDAR_CHECK_ARG(frames != nullptr && n_frames > 0, "lidar_cast_sweep: need at least one frame");
+    LIDAR_CHECK_ARG(beams != nullptr || echoes != nullptr, "lidar_cast_sweep: nothing to write");
+    if (c->table.table == nullptr) {
+        set_error("lidar_cast_sweep: no material table (lidar_set_materials)");
+        return LIDAR_ESTATE;
+    }
+    EchoOut echo{0, 0, 0.0f, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (echoes) {
+        LIDAR_CHECK_ARG(echoes->n_echoes >= 1 && echoes->n_echoes <= 4, "lidar_cast_sweep: n_echoes in [1, 4]");
+        LIDAR_CHECK_ARG(echoes->mode == 0 || echoes->mode == 1, "lidar_cast_sweep: echo mode is 0 or 1");
+        LIDAR_CHECK_ARG(isfinite(echoes->separation) && echoes->separation >= 0.0f,
+                        "lidar_cast_sweep: separation must be finite, >= 0");
+        LIDAR_CHECK_ARG(echoes->count != nullptr, "lidar_cast_sweep: echoes->count is NULL");
+        echo = EchoOut{echoes->n_echoes, echoes->mode, echoes->separation, echoes->count, echoes->range,
+                       echoes->intensity, echoes->tri, echoes->sub};
+    }
+    std::vector<SweepDev> fd((size_t)n_frames);
+    int64_t off = 0;
+    for (int32_t k = 0; k < n_frames; ++k) {
+        const int s = frames[k].sensor;
+        LIDAR_CHECK_ARG(s >= 0 && s < LIDAR_MAX_SENSORS, "lidar_cast_sweep: sensor slot out of range");
+        if (!c->slots[s].set) {
+            set_error("lidar_cast_sweep: frame " + std::to_string(k) + " names an empty sensor slot");
+            return LIDAR_ESTATE;
+        }
+        for (int j = 0; j < 12; ++j)
+            LIDAR_CHECK_ARG(isfinite(frames[k].pose0[j]) && isfinite(frames[k].pose1[j]),
+                            "lidar_cast_sweep: non-finite pose");
+        double q0[4], q1[4];
+        rotation_quaternion(frames[k].pose0, q0);
+        rotation_quaternion(frames[k].pose1, q1);
+        const double dq = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2] + q0[3] * q1[3];
+        SweepDev& f = fd[(size_t)k];
+        for (int i = 0; i < 4; ++i) {
+            f.q0[i] = (float)q0[i];
+            f.q1[i] = (float)(dq < 0.0 ? -q1[i] : q1[i]);
+        }
+        for (int r = 0; r < 3; ++r) {
+            f.t0[r] = frames[k].pose0[4 * r + 3];
+            f.t1[r] = frames[k].pose1[4 * r + 3];
+        }
+        f.sensor = s;
+        f.frame = frames[k].frame;
+        f.beam_offset = off;
+        off += c->slots[s].n_beams;
+    }
+    DeviceGuard g(c->device);
+    if ((size_t)n_frames > c->sweeps_cap) {
+        LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+        cudaFree(c->sweeps_dev);
+        c->sweeps_dev = nullptr;
+        c->sweeps_cap = 0;
+        if (dev_alloc((void**)&c->sweeps_dev, (size_t)n_frames * sizeof(SweepDev)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("lidar_cast_sweep: device allocation failed");
+            return LIDAR_ENOMEM;
+        }
+        c->sweeps_cap = n_frames;
+    }
+    // pageable source: the copy is staged before the call returns
+    LIDAR_CUDA(cudaMemcpyAsync(c->sweeps_dev, fd.data(), (size_t)n_frames * sizeof(SweepDev), cudaMemcpyHostToDevice,
+                               c->stream));
+    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
+    LIDAR_CUDA(launch_cast_sweep(c->stream, S, c->sensors_dev, c->sweeps_dev, n_frames, off, c->table, seed,
+                                 to_beams_out(beams), echo, c->status_dev));
     return LIDAR_OK;
 }
 

@@ -1,0 +1,145 @@
+// Rolling shutter and multi-echo returns.  A sweep carries the sensor pose at
+// its start and at its end; beam b fires at the fraction s_b of the sweep (its
+// azimuth over 2 pi) and sees the pose blended between the two (translation
+// (1 - s) t0 + s t1; rotation of the normalised blend (1 - s) q0 + s q1 of the
+// unit quaternions) — the camera turned with the sensor's spin over the time
+// step of Sec. II-A, here per beam.  From the returns of a beam's sub-rays it
+// also reports several echoes (Sec. IV: multiple returns are future work):
+// mode 0 the n strongest apart by at least `separation` in range, mode 1 the
+// first and the last.  One thread per beam, 4-wide traversal.
+#include "common.cuh"
+#include "philox.cuh"
+#include "trace.cuh"
+#include "shade.cuh"
+
+namespace lidar {
+namespace {
+
+// pose at fraction s of a sweep, FP32, every operation rounded as written
+__device__ __forceinline__ void sweep_pose(const SweepDev& f, float s, float* P)
+{
+    const float ms = __fsub_rn(1.0f, s);
+    float q[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = __fmaf_rn(s, f.q1[i], __fmul_rn(ms, f.q0[i]));
+    float n2 = __fmul_rn(q[0], q[0]);
+    n2 = __fadd_rn(n2, __fmul_rn(q[1], q[1]));
+    n2 = __fadd_rn(n2, __fmul_rn(q[2], q[2]));
+    n2 = __fadd_rn(n2, __fmul_rn(q[3], q[3]));
+    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(n2));
+    const float w = __fmul_rn(q[0], inv), x = __fmul_rn(q[1], inv), y = __fmul_rn(q[2], inv),
+                z = __fmul_rn(q[3], inv);
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    const float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+    const float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+    P[0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+    P[1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+    P[2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+    P[4] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+    P[5] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+    P[6] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+    P[8] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+    P[9] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+    P[10] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+#pragma unroll
+    for (int r = 0; r < 3; ++r) P[4 * r + 3] = __fmaf_rn(s, f.t1[r], __fmul_rn(ms, f.t0[r]));
+}
+
+__global__ void __launch_bounds__(128) k_cast_sweep(SceneDev S, const SensorDev* __restrict__ sensors,
+                                                    const SweepDev* __restrict__ frames, int n_frames,
+                                                    int64_t n_total, TableDev T, uint64_t seed, BeamsOut out,
+                                                    EchoOut echo, int* status)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n_total) return;
+    int lo = 0, hi = n_frames - 1;  // last frame starting at or before g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (frames[mid].beam_offset <= g) lo = mid; else hi = mid - 1;
+    }
+    const SweepDev f = frames[lo];
+    const SensorDev& sd = sensors[f.sensor];
+    const uint32_t beam = (uint32_t)(g - f.beam_offset);
+    float P[12];
+    sweep_pose(f, __ldg(&sd.sweep[beam]), P);
+    const RayW beam_ray = world_ray(P, __ldg(&sd.dirs[3 * (int64_t)beam]), __ldg(&sd.dirs[3 * (int64_t)beam + 1]),
+                                    __ldg(&sd.dirs[3 * (int64_t)beam + 2]));
+    float sub_range[LIDAR_MAX_SUBRAYS], sub_I[LIDAR_MAX_SUBRAYS];
+    uint32_t sub_tri[LIDAR_MAX_SUBRAYS];
+    bool sub_ok[LIDAR_MAX_SUBRAYS];
+    BeamResult best;
+    int best_sub = 0;
+    float best_I = -1.0f;
+    for (int k = 0; k < sd.n_sub; ++k) {
+        RayW r = beam_ray;
+        if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
+        const RayPre p = prepare_ray(r);
+        HitRec h;
+        if (!trace_closest4<false>(S, p, sd.t_max, h, nullptr, nullptr, 0)) raise_status(status, ST_STACK);
+        BeamResult res;
+        shade(S, h, r, sd, T, seed, beam, (uint32_t)f.frame, (uint32_t)f.sensor, (uint32_t)k, res);
+        sub_range[k] = res.range;
+        sub_I[k] = res.intensity;
+        sub_tri[k] = res.tri;
+        sub_ok[k] = res.valid != 0;
+        if (k == 0) best = res;
+        if (res.valid && res.intensity > best_I) {
+            best_I = res.intensity;
+            best = res;
+            best_sub = k;
+        }
+    }
+    write_beam(out, g, best, P, best_sub);
+    if (echo.n_echoes <= 0) return;
+    int pick[4];
+    int n = 0;
+    if (echo.mode == 0) {
+        bool used[LIDAR_MAX_SUBRAYS];
+        for (int k = 0; k < sd.n_sub; ++k) used[k] = false;
+        while (n < echo.n_echoes) {
+            int b = -1;
+            for (int k = 0; k < sd.n_sub; ++k)
+                if (sub_ok[k] && !used[k] && (b < 0 || sub_I[k] > sub_I[b])) b = k;
+            if (b < 0) break;
+            used[b] = true;
+            bool apart = true;
+            for (int j = 0; j < n; ++j)
+                if (fabsf(sub_range[b] - sub_range[pick[j]]) < echo.separation) apart = false;
+            if (apart) pick[n++] = b;
+        }
+    } else {
+        int first = -1, last = -1;
+        for (int k = 0; k < sd.n_sub; ++k) {
+            if (!sub_ok[k]) continue;
+            if (first < 0 || sub_range[k] < sub_range[first]) first = k;
+            if (last < 0 || sub_range[k] > sub_range[last]) last = k;
+        }
+        if (first >= 0) {
+            pick[n++] = first;
+            if (echo.n_echoes > 1 && sub_range[last] - sub_range[first] >= echo.separation) pick[n++] = last;
+        }
+    }
+    echo.count[g] = (uint8_t)n;
+    for (int j = 0; j < echo.n_echoes; ++j) {
+        const int64_t e = g * echo.n_echoes + j;
+        const bool have = j < n;
+        if (echo.range) echo.range[e] = have ? sub_range[pick[j]] : 0.0f;
+        if (echo.intensity) echo.intensity[e] = have ? sub_I[pick[j]] : 0.0f;
+        if (echo.tri) echo.tri[e] = have ? sub_tri[pick[j]] : LIDAR_NO_HIT;
+        if (echo.sub) echo.sub[e] = have ? (uint8_t)pick[j] : (uint8_t)0xFF;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_cast_sweep(cudaStream_t s, const SceneDev& S, const SensorDev* sensors_dev,
+                              const SweepDev* frames_dev, int n_frames, int64_t n_total, TableDev T, uint64_t seed,
+                              BeamsOut out, EchoOut echo, int* status)
+{
+    if (n_total == 0) return cudaSuccess;
+    k_cast_sweep<<<(unsigned)((n_total + 127) / 128), 128, 0, s>>>(S, sensors_dev, frames_dev, n_frames, n_total, T,
+                                                                   seed, out, echo, status);
+    return cudaGetLastError();
+}
+
+}  // namespace lidar

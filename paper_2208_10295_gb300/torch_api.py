@@ -140,7 +140,8 @@ class Lidar:
 
     # ----------------------------------------------------------- cast
     def total_beams(self, frames) -> int:
-        fr = _frames_array(frames)
+        """Beams of all frames (frame records or sweep records)."""
+        fr = np.atleast_1d(np.asarray(frames))
         return int(sum(self.n_beams[int(s)] for s in fr["sensor"]))
 
     def alloc_beams(self, n: int, fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst",
@@ -251,6 +252,29 @@ class Lidar:
 
     def reset_schedule(self, slot: int):
         C.check(C.lidar_reset_schedule(self.handle, slot), "lidar_reset_schedule")
+
+    # ----------------------------------------------------------- sweeps and echoes
+    def alloc_echoes(self, n: int, n_echoes: int):
+        return {"count": torch.empty(n, dtype=torch.uint8, device=self.device),
+                "range": torch.empty((n, n_echoes), dtype=torch.float32, device=self.device),
+                "intensity": torch.empty((n, n_echoes), dtype=torch.float32, device=self.device),
+                "tri": torch.empty((n, n_echoes), dtype=torch.int32, device=self.device),
+                "sub": torch.empty((n, n_echoes), dtype=torch.uint8, device=self.device)}
+
+    def cast_sweep_into(self, scene: Scene, sweeps, seed: int, beams=None, echoes=None, mode: int = 0,
+                        separation: float = 1.0):
+        """Rolling-shutter cast of sweeps (records with sensor, frame, pose0,
+        pose1), with optional multi-echo outputs (alloc_echoes)."""
+        fr = np.ascontiguousarray(sweeps)
+        assert fr.dtype.itemsize == 104
+        bs = self.beams_struct(beams) if beams is not None else None
+        es = None
+        if echoes is not None:
+            es = C.lidar_echoes(int(echoes["range"].shape[1]), mode, separation,
+                                *[_ptr(echoes[k]) for k in ("count", "range", "intensity", "tri", "sub")])
+        C.check(C.lidar_cast_sweep(self.handle, scene.handle, fr.ctypes.data_as(ctypes.c_void_p), len(fr),
+                                   ctypes.c_uint64(seed), ctypes.byref(bs) if bs is not None else None,
+                                   ctypes.byref(es) if es is not None else None), "lidar_cast_sweep")
 
     # ----------------------------------------------------------- raster path
     def raster_cast_into(self, scene: Scene, frames, seed: int, beams, width: int = 1024, n_cameras: int = 6):
