@@ -345,6 +345,11 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
     B.free()
     del pts2
     # ---- the paper's own raster-and-resample sampling on the same cfg1 frame, against the ray cast
+    L.set_sensor(0, w1.sensors[0])
+    near1 = w1.frames.copy()
+    near1[0]["pose"][3] += 1.0
+    near1[0]["pose"][7] += 0.5
+    apply_cfg(L, scene, tuned_cfg, near1, w1.seed)
     fr1 = w1.frames
     nb1 = L.total_beams(fr1)
     rf = ("valid", "tri", "t")
@@ -370,6 +375,22 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
                                  "depth/angle G-buffer), compared beam by beam with the ray cast of the same frame",
                      "ray_cast_ms_per_frame": cast_ms, "by_width": rows}
     del ref, ras
+    # ---- rolling-shutter sweeps along the cfg3 trajectory vs the frame cast of the same poses
+    w3s = synth.cfg3()
+    L.set_sensor(0, w3s.sensors[0])
+    sw = synth.make_sweep_frames([(0, int(a["frame"]), a["pose"], b["pose"])
+                                  for a, b in zip(w3s.frames[:-1], w3s.frames[1:])])
+    nsw = L.total_beams(sw)
+    sbuf = L.alloc_beams(nsw, ("valid", "range", "intensity"))
+    sw_ms = event_time(torch, stream, lambda: L.cast_sweep_into(scene, sw, w3s.seed, sbuf), flush, reps=5, warm=2)
+    fr_ms = event_time(torch, stream, lambda: L.cast_into(scene, w3s.frames[:-1], w3s.seed, sbuf), flush, reps=5,
+                       warm=2)
+    out["rolling_shutter"] = {"workload": "15 sweeps of the 128-ch sensor along the 16-frame trajectory over the "
+                                          "1.04M-tri scene, each beam at its own interpolated pose",
+                              "beams": nsw, "sweep_ms": sw_ms, "rays_per_s": nsw / (sw_ms / 1e3),
+                              "frame_cast_same_poses_ms": fr_ms}
+    del sbuf
+    L.set_sensor(0, w1.sensors[0])
     # ---- cfg3: 16 frames forward (dense tape) + fused-MSE adjoint vs plain forward
     w3 = synth.cfg3()
     L.set_sensor(0, w3.sensors[0])
@@ -427,6 +448,18 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
                        "build_ms": info["build_ms"], "bvh_depth": info["max_depth"],
                        "points": int(pts4["count"].item()), "launch": cfg4}
         B4.free()
+        # multi-echo (first and last of the 7 sub-ray returns, 0.5 m apart) over sweeps of the same trajectory
+        sw4 = synth.make_sweep_frames([(0, int(a["frame"]), a["pose"], b["pose"])
+                                       for a, b in zip(w4.frames[:-1], w4.frames[1:])])
+        n4 = L.total_beams(sw4)
+        e4 = L.alloc_echoes(n4, 2)
+        e_ms = event_time(torch, stream, lambda: L.cast_sweep_into(scene4, sw4, w4.seed, None, e4, mode=1,
+                                                                   separation=0.5), None, reps=3, warm=1)
+        cnt = e4["count"].cpu().numpy()
+        out["city"]["echoes"] = {"workload": "31 sweeps x 524,288 beams x 7 sub-rays, first and last return "
+                                             ">= 0.5 m apart", "ms": e_ms, "subrays_per_s": n4 * 7 / (e_ms / 1e3),
+                                 "beams_with_return": int((cnt > 0).sum()), "beams_with_two": int((cnt > 1).sum())}
+        del e4
         scene4.free()
         L.set_materials(table)
         L.set_sensor(0, w1.sensors[0])
