@@ -86,6 +86,10 @@ class lidar_echoes(ctypes.Structure):
                [(n, c_vp) for n in ("count", "range", "intensity", "tri", "sub")]
 
 
+class lidar_build_options(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("ploc_radius", ctypes.c_int32)]
+
+
 class lidar_raster_config(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("n_cameras", ctypes.c_int32)]
 
@@ -142,6 +146,8 @@ _PROTOS = [
                                          ctypes.POINTER(lidar_raster_config), ctypes.POINTER(lidar_beams)]),
     ("lidar_raster_gbuffer", ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(lidar_frame),
                                             ctypes.POINTER(lidar_raster_config), c_vp, c_vp, c_vp, c_vp]),
+    ("lidar_set_build_options", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_build_options)]),
+    ("lidar_get_build_options", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_build_options)]),
     ("lidar_get_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
     ("lidar_set_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
 ]
@@ -211,6 +217,8 @@ lidar_cast_backward_mse_noalloc = _fwd("lidar_cast_backward_mse_noalloc")
 lidar_count_work = _fwd("lidar_count_work")
 lidar_raster_cast = _fwd("lidar_raster_cast")
 lidar_cast_sweep = _fwd("lidar_cast_sweep")
+lidar_set_build_options = _fwd("lidar_set_build_options")
+lidar_get_build_options = _fwd("lidar_get_build_options")
 lidar_raster_gbuffer = _fwd("lidar_raster_gbuffer")
 lidar_schedule_by_cost = _fwd("lidar_schedule_by_cost")
 lidar_reset_schedule = _fwd("lidar_reset_schedule")

@@ -11,6 +11,8 @@
 //      height; the first stops.  The root height bounds the traversal stack.
 #include "common.cuh"
 
+#include <utility>
+
 namespace lidar {
 namespace {
 
@@ -275,10 +277,13 @@ size_t build_scratch_bytes(int64_t n)
            align256((size_t)n * 2 * sizeof(float4)) + align256(64) + radix_sort_scratch_bytes(n);
 }
 
+cudaError_t build_ploc(cudaStream_t s, const float4* tris_sorted, int64_t n, float4* nodes_out, int* max_height_dev,
+                       int radius, void* scratch, size_t scratch_bytes, unsigned long long* host_total);
+
 cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, const uint32_t* tris,
                        const uint16_t* mat, const uint32_t* inst, int64_t n, float4* nodes_out,
                        float4* tris_out, uint32_t* leaf_tri_out, int* status, int* max_height_dev,
-                       void* scratch, size_t scratch_bytes)
+                       void* scratch, size_t scratch_bytes, int method, int radius)
 {
     if (n == 0) return cudaSuccess;
     if (scratch_bytes < build_scratch_bytes(n)) return cudaErrorInvalidValue;
@@ -307,11 +312,238 @@ cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, cons
         k_single<<<1, 1, 0, s>>>(tris_out, nodes_out, max_height_dev);
         return cudaGetLastError();
     }
+    if (method == 1) {
+        // clustering over the Morton-ordered leaves; the sort's buffers are free again
+        unsigned long long total = 0;
+        return build_ploc(s, tris_out, n, nodes_out, max_height_dev, radius, scratch, scratch_bytes, &total);
+    }
     const int iblocks = (int)((n - 1 + kBuildThreads - 1) / kBuildThreads);
     k_karras<<<iblocks, kBuildThreads, 0, s>>>(keys, n, nodes_out, parent_node, parent_leaf);
     cudaMemsetAsync(visits, 0, n * sizeof(int), s);
     k_refit<<<blocks, kBuildThreads, 0, s>>>(tris_out, n, nodes_out, node_boxes, heights, parent_node, parent_leaf,
                                              visits, max_height_dev);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// PLOC: Parallel Locally-Ordered Clustering (Meister and Bittner, "Parallel
+// Locally-Ordered Clustering for Bounding Volume Hierarchy Construction",
+// IEEE TVCG 2018), an alternative to the Karras hierarchy over the same
+// Morton-ordered leaves.  Clusters start as the leaves; each iteration every
+// cluster finds its nearest neighbour within `radius` positions of the
+// cluster array (distance: surface area of the union box; ties to the lower
+// position), mutual nearest pairs merge into a new node at the lower position,
+// and the array is compacted in order.  Node ids count down from n - 2, so the
+// last merge is the root at 0.  Boxes are exact FP32 min/max unions.
+namespace {
+
+struct PlocClusters {
+    int* ref;        // ~leaf or node id
+    float4* box;     // [2 per cluster] lo, hi
+    int* height;
+};
+
+__device__ __forceinline__ float union_half_area(float4 alo, float4 ahi, float4 blo, float4 bhi)
+{
+    const float dx = fmaxf(ahi.x, bhi.x) - fminf(alo.x, blo.x);
+    const float dy = fmaxf(ahi.y, bhi.y) - fminf(alo.y, blo.y);
+    const float dz = fmaxf(ahi.z, bhi.z) - fminf(alo.z, blo.z);
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_ploc_init(const float4* __restrict__ tris, int64_t n,
+                                                             PlocClusters C)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Box b = leaf_box(tris, (int)i);
+    C.ref[i] = ~(int)i;
+    C.box[2 * i] = make_float4(b.lo[0], b.lo[1], b.lo[2], 0.0f);
+    C.box[2 * i + 1] = make_float4(b.hi[0], b.hi[1], b.hi[2], 0.0f);
+    C.height[i] = 0;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_ploc_nearest(PlocClusters C, int n, int radius, int* nn)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 alo = C.box[2 * (int64_t)i], ahi = C.box[2 * (int64_t)i + 1];
+    int best = -1;
+    float best_d = INFINITY;
+    const int lo = max(i - radius, 0), hi = min(i + radius, n - 1);
+    for (int j = lo; j <= hi; ++j) {
+        if (j == i) continue;
+        const float d = union_half_area(alo, ahi, C.box[2 * (int64_t)j], C.box[2 * (int64_t)j + 1]);
+        if (d < best_d) {  // ascending j: ties keep the lower position
+            best_d = d;
+            best = j;
+        }
+    }
+    nn[i] = best;
+}
+
+// flags: high word 1 if i creates a node, low word 1 if i's cluster survives
+__global__ void __launch_bounds__(kBuildThreads) k_ploc_flags(const int* __restrict__ nn, int n, int force_pairs,
+                                                              unsigned long long* flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int j = nn[i];
+    bool merge_low, merged_away;
+    if (force_pairs) {
+        // no mutual pair anywhere (not expected): merge positions 2k, 2k+1
+        merge_low = (i % 2 == 0) && i + 1 < n;
+        merged_away = (i % 2 == 1);
+    } else {
+        const bool mutual = j >= 0 && nn[j] == i;
+        merge_low = mutual && i < j;
+        merged_away = mutual && j < i;
+    }
+    flags[i] = ((unsigned long long)(merge_low ? 1u : 0u) << 32) | (merged_away ? 0ull : 1ull);
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_ploc_merge(PlocClusters C, PlocClusters D, const int* __restrict__ nn,
+                                                              int n, int force_pairs,
+                                                              const unsigned long long* __restrict__ flags,
+                                                              const unsigned long long* __restrict__ prefix,
+                                                              int64_t id_base, float4* nodes, int* max_height)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long f = flags[i];
+    if ((f & 0xFFFFFFFFull) == 0) return;  // merged into a lower position
+    const int out = (int)(prefix[i] & 0xFFFFFFFFull);
+    if ((f >> 32) == 0) {
+        D.ref[out] = C.ref[i];
+        D.box[2 * (int64_t)out] = C.box[2 * (int64_t)i];
+        D.box[2 * (int64_t)out + 1] = C.box[2 * (int64_t)i + 1];
+        D.height[out] = C.height[i];
+        return;
+    }
+    const int j = force_pairs ? i + 1 : nn[i];
+    const int64_t id = id_base - (int64_t)(prefix[i] >> 32);
+    const float4 llo = C.box[2 * (int64_t)i], lhi = C.box[2 * (int64_t)i + 1];
+    const float4 rlo = C.box[2 * (int64_t)j], rhi = C.box[2 * (int64_t)j + 1];
+    nodes[4 * id + 0] = make_float4(llo.x, lhi.x, llo.y, lhi.y);
+    nodes[4 * id + 1] = make_float4(rlo.x, rhi.x, rlo.y, rhi.y);
+    nodes[4 * id + 2] = make_float4(llo.z, lhi.z, rlo.z, rhi.z);
+    nodes[4 * id + 3] = make_float4(__int_as_float(C.ref[i]), __int_as_float(C.ref[j]), 0.0f, 0.0f);
+    const int h = 1 + max(C.height[i], C.height[j]);
+    D.ref[out] = (int)id;
+    D.box[2 * (int64_t)out] = make_float4(fminf(llo.x, rlo.x), fminf(llo.y, rlo.y), fminf(llo.z, rlo.z), 0.0f);
+    D.box[2 * (int64_t)out + 1] = make_float4(fmaxf(lhi.x, rhi.x), fmaxf(lhi.y, rhi.y), fmaxf(lhi.z, rhi.z), 0.0f);
+    D.height[out] = h;
+    if (id == 0) *max_height = h;
+}
+
+// exclusive scan of uint64 flags: per-block scans, one block over the block
+// sums, then the block offsets added
+constexpr int kScanItems = 1024;
+
+__global__ void __launch_bounds__(kScanItems) k_scan_local(const unsigned long long* __restrict__ in, int n,
+                                                          unsigned long long* out, unsigned long long* sums)
+{
+    __shared__ unsigned long long s[kScanItems];
+    const int i = blockIdx.x * kScanItems + threadIdx.x;
+    const unsigned long long v = i < n ? in[i] : 0ull;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kScanItems; o <<= 1) {
+        const unsigned long long a = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        s[threadIdx.x] += a;
+        __syncthreads();
+    }
+    if (i < n) out[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == kScanItems - 1) sums[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kScanItems) k_scan_sums(unsigned long long* sums, int m)
+{
+    __shared__ unsigned long long s[kScanItems];
+    unsigned long long carry = 0;
+    for (int base = 0; base < m; base += kScanItems) {
+        const int i = base + threadIdx.x;
+        const unsigned long long v = i < m ? sums[i] : 0ull;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < kScanItems; o <<= 1) {
+            const unsigned long long a = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0ull;
+            __syncthreads();
+            s[threadIdx.x] += a;
+            __syncthreads();
+        }
+        if (i < m) sums[i] = carry + s[threadIdx.x] - v;
+        const unsigned long long total = s[kScanItems - 1];
+        __syncthreads();
+        carry += total;
+    }
+    if (threadIdx.x == 0) sums[m] = carry;
+}
+
+__global__ void __launch_bounds__(kScanItems) k_scan_add(unsigned long long* out, int n,
+                                                        const unsigned long long* __restrict__ sums)
+{
+    const int i = blockIdx.x * kScanItems + threadIdx.x;
+    if (i < n) out[i] += sums[blockIdx.x];
+}
+
+}  // namespace
+
+size_t ploc_scratch_bytes(int64_t n)
+{
+    const size_t m = (size_t)(n + kScanItems - 1) / kScanItems + 1;
+    return 2 * (align256(n * sizeof(int)) + align256((size_t)n * 2 * sizeof(float4)) + align256(n * sizeof(int))) +
+           align256(n * sizeof(int)) + 2 * align256(n * sizeof(unsigned long long)) + align256(m * 8) + 256;
+}
+
+cudaError_t build_ploc(cudaStream_t s, const float4* tris_sorted, int64_t n, float4* nodes_out, int* max_height_dev,
+                       int radius, void* scratch, size_t scratch_bytes, unsigned long long* host_total)
+{
+    if (n < 2) return cudaErrorInvalidValue;
+    if (scratch_bytes < ploc_scratch_bytes(n)) return cudaErrorInvalidValue;
+    char* p = (char*)scratch;
+    PlocClusters A, B;
+    A.ref = (int*)p; p += align256(n * sizeof(int));
+    A.box = (float4*)p; p += align256((size_t)n * 2 * sizeof(float4));
+    A.height = (int*)p; p += align256(n * sizeof(int));
+    B.ref = (int*)p; p += align256(n * sizeof(int));
+    B.box = (float4*)p; p += align256((size_t)n * 2 * sizeof(float4));
+    B.height = (int*)p; p += align256(n * sizeof(int));
+    int* nn = (int*)p; p += align256(n * sizeof(int));
+    unsigned long long* flags = (unsigned long long*)p; p += align256(n * sizeof(unsigned long long));
+    unsigned long long* prefix = (unsigned long long*)p; p += align256(n * sizeof(unsigned long long));
+    unsigned long long* sums = (unsigned long long*)p;
+    const int blocks0 = (int)((n + kBuildThreads - 1) / kBuildThreads);
+    k_ploc_init<<<blocks0, kBuildThreads, 0, s>>>(tris_sorted, n, A);
+    int nc = (int)n;
+    int64_t created = 0;
+    for (int iter = 0; nc > 1; ++iter) {
+        if (iter > 4 * n) return cudaErrorUnknown;
+        const int blocks = (nc + kBuildThreads - 1) / kBuildThreads;
+        const int sblocks = (nc + kScanItems - 1) / kScanItems;
+        int force = 0;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            k_ploc_nearest<<<blocks, kBuildThreads, 0, s>>>(A, nc, radius, nn);
+            k_ploc_flags<<<blocks, kBuildThreads, 0, s>>>(nn, nc, force, flags);
+            k_scan_local<<<sblocks, kScanItems, 0, s>>>(flags, nc, prefix, sums);
+            k_scan_sums<<<1, kScanItems, 0, s>>>(sums, sblocks);
+            k_scan_add<<<sblocks, kScanItems, 0, s>>>(prefix, nc, sums);
+            cudaError_t e = cudaMemcpyAsync(host_total, sums + sblocks, sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return e;
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return e;
+            if ((*host_total >> 32) > 0) break;
+            force = 1;  // no mutual pair: merge neighbours pairwise
+        }
+        const unsigned long long total = *host_total;
+        k_ploc_merge<<<blocks, kBuildThreads, 0, s>>>(A, B, nn, nc, force, flags, prefix, (n - 2) - created,
+                                                      nodes_out, max_height_dev);
+        created += (int64_t)(total >> 32);
+        nc = (int)(total & 0xFFFFFFFFull);
+        std::swap(A, B);
+    }
     return cudaGetLastError();
 }
 

@@ -8,6 +8,10 @@
 // in (frame, beam) order.
 
 #include "common.cuh"
+
+#include <map>
+#include <mutex>
+#include <utility>
 #include "philox.cuh"
 #include "trace.cuh"
 #include "shade.cuh"
@@ -399,10 +403,23 @@ cudaError_t launch_one(cudaStream_t s, CastArgs a, int64_t grid, int block, size
 {
     auto fn = k_cast<C, V, W>;
     if (a.fused) {
-        // every block must be resident for the grid-wide waits
+        // every block must be resident for the grid-wide waits; the occupancy
+        // of this instantiation depends only on the block size and the shared
+        // memory, so it is asked once per pair
+        static std::mutex m;
+        static std::map<std::pair<int, size_t>, int> cache;
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
-        if (e != cudaSuccess) return e;
+        {
+            std::lock_guard<std::mutex> lock(m);
+            auto it = cache.find({block, smem});
+            if (it != cache.end()) {
+                per_sm = it->second;
+            } else {
+                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
+                if (e != cudaSuccess) return e;
+                cache[{block, smem}] = per_sm;
+            }
+        }
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         if (grid > (int64_t)per_sm * num_sms) grid = (int64_t)per_sm * num_sms;
         void* args[] = {&a.scene, &a.sensors, &a.frames, &a.n_frames, &a.prefix, &a.n_tiles, &a.table, &a.seed,

@@ -120,7 +120,9 @@ struct BuildScratch;
 cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, const uint32_t* tris,
                        const uint16_t* mat, const uint32_t* inst, int64_t n_tris, float4* nodes_out,
                        float4* tris_out, uint32_t* leaf_tri_out, int* status, int* max_depth_dev,
-                       void* scratch, size_t scratch_bytes);
+                       void* scratch, size_t scratch_bytes, int method = 0, int ploc_radius = 16);
+// scratch of the clustering build (method 1), on top of nothing: it reuses build_lbvh's scratch
+size_t ploc_scratch_bytes(int64_t n_tris);
 size_t build_scratch_bytes(int64_t n_tris);
 // 4-wide hierarchy from the binary one (breadth-first, deterministic);
 // synchronises once per level.  *levels = height of the 4-wide tree.

@@ -80,14 +80,19 @@ struct lidar_ctx {
     SensorSlot slots[LIDAR_MAX_SENSORS];
     SensorDev* sensors_dev = nullptr;
     TableDev table{nullptr, 0};
-    FrameDev* frames_dev = nullptr;
+    FrameDev* frames_dev = nullptr;      // frame table and tile prefix, one device block
     int64_t* tile_prefix_dev = nullptr;
     size_t frames_cap = 0;
+    char* stage_host[2] = {nullptr, nullptr};  // pinned staging of that block, used alternately
+    cudaEvent_t stage_done[2] = {nullptr, nullptr};
+    int stage_next = 0;
     SweepDev* sweeps_dev = nullptr;
     size_t sweeps_cap = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
     LaunchCfg cfg{128, 4, 32, 1, 2, 1};
+    int build_method = 1;     // 0 Karras LBVH, 1 PLOC clustering (fewer node fetches per ray)
+    int ploc_radius = 16;
     std::set<lidar_scene*> scenes;
 };
 
@@ -194,6 +199,7 @@ lidar_status lidar_create(int device, void* cuda_stream, lidar_ctx** out)
     }
     cudaMemsetAsync(p, 0, 256, c->stream);
     cudaMemsetAsync(c->sensors_dev, 0, sizeof(SensorDev) * LIDAR_MAX_SENSORS, c->stream);
+    for (int i = 0; i < 2; ++i) cudaEventCreateWithFlags(&c->stage_done[i], cudaEventDisableTiming);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         cudaFree(p);
         cudaFree(c->sensors_dev);
@@ -235,7 +241,10 @@ void lidar_destroy(lidar_ctx* c)
     cudaFree(c->sensors_dev);
     cudaFree(c->sweeps_dev);
     cudaFree(c->frames_dev);
-    cudaFree(c->tile_prefix_dev);
+    for (int i = 0; i < 2; ++i) {
+        cudaFreeHost(c->stage_host[i]);
+        if (c->stage_done[i]) cudaEventDestroy(c->stage_done[i]);
+    }
     cudaFree(c->scratch);
     cudaFree(c->status_dev);
     delete c;
@@ -284,7 +293,8 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
             return fail(LIDAR_ENOMEM);
         }
         s->bytes = s->n_nodes * 64 + s->n_nodes * 128 + n_tris * 48 + n_tris * 4;
-        lidar_status st = ensure_scratch(c, std::max(build_scratch_bytes(n_tris), collapse_scratch_bytes(s->n_nodes)));
+        lidar_status st = ensure_scratch(c, std::max({build_scratch_bytes(n_tris), collapse_scratch_bytes(s->n_nodes),
+                                                      c->build_method == 1 ? ploc_scratch_bytes(n_tris) : (size_t)0}));
         if (st != LIDAR_OK) return fail(st);
         struct Events {
             cudaEvent_t a = nullptr, b = nullptr;
@@ -294,7 +304,8 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         cudaEvent_t e0 = ev.a, e1 = ev.b;
         cudaEventRecord(e0, c->stream);
         cudaError_t e = build_lbvh(c->stream, verts, n_verts, tris, mat, inst, n_tris, s->nodes, s->tris,
-                                   s->leaf_tri, c->status_dev, c->aux_dev, c->scratch, c->scratch_bytes);
+                                   s->leaf_tri, c->status_dev, c->aux_dev, c->scratch, c->scratch_bytes,
+                                   n_tris >= 2 ? c->build_method : 0, c->ploc_radius);
         cudaEventRecord(e1, c->stream);
         if (e != cudaSuccess) {
             set_error(std::string("lidar_scene_build: ") + cudaGetErrorString(e));
@@ -533,26 +544,43 @@ static lidar_status prepare_frames(lidar_ctx* c, const lidar_frame* frames, int3
         off += c->slots[s].n_beams;
         tiles += (c->slots[s].n_beams + tr - 1) / tr;
     }
+    // frame table and tile prefix travel as one block: frames, then the prefix at a 256-byte boundary
+    const size_t prefix_at = ((size_t)n_frames * sizeof(FrameDev) + 255) / 256 * 256;
+    const size_t block = prefix_at + (size_t)n_frames * sizeof(int64_t);
     if ((size_t)n_frames > c->frames_cap) {
         LIDAR_CUDA(cudaStreamSynchronize(c->stream));
         cudaFree(c->frames_dev);
-        cudaFree(c->tile_prefix_dev);
+        for (int i = 0; i < 2; ++i) {
+            cudaFreeHost(c->stage_host[i]);
+            c->stage_host[i] = nullptr;
+        }
         c->frames_dev = nullptr;
         c->tile_prefix_dev = nullptr;
         c->frames_cap = 0;
-        if (dev_alloc((void**)&c->frames_dev, n_frames * sizeof(FrameDev)) != cudaSuccess ||
-            dev_alloc((void**)&c->tile_prefix_dev, n_frames * sizeof(int64_t)) != cudaSuccess) {
+        if (dev_alloc((void**)&c->frames_dev, block) != cudaSuccess) {
             cudaGetLastError();
             set_error("lidar_cast: device allocation failed");
             return LIDAR_ENOMEM;
         }
+        for (int i = 0; i < 2; ++i)
+            if (cudaHostAlloc((void**)&c->stage_host[i], block, cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("lidar_cast: pinned host allocation failed");
+                return LIDAR_ENOMEM;
+            }
+        c->tile_prefix_dev = (int64_t*)((char*)c->frames_dev + prefix_at);
         c->frames_cap = n_frames;
     }
-    // pageable source: the copy is staged before the call returns
-    LIDAR_CUDA(cudaMemcpyAsync(c->frames_dev, fd.data(), n_frames * sizeof(FrameDev), cudaMemcpyHostToDevice,
-                               c->stream));
-    LIDAR_CUDA(cudaMemcpyAsync(c->tile_prefix_dev, prefix.data(), n_frames * sizeof(int64_t),
-                               cudaMemcpyHostToDevice, c->stream));
+    // the block's device layout depends on n_frames: keep the prefix pointer in step
+    c->tile_prefix_dev = (int64_t*)((char*)c->frames_dev + prefix_at);
+    // pinned staging used alternately: wait until the copy made from this buffer two calls ago is done
+    const int slot = c->stage_next;
+    c->stage_next ^= 1;
+    LIDAR_CUDA(cudaEventSynchronize(c->stage_done[slot]));
+    memcpy(c->stage_host[slot], fd.data(), (size_t)n_frames * sizeof(FrameDev));
+    memcpy(c->stage_host[slot] + prefix_at, prefix.data(), (size_t)n_frames * sizeof(int64_t));
+    LIDAR_CUDA(cudaMemcpyAsync(c->frames_dev, c->stage_host[slot], block, cudaMemcpyHostToDevice, c->stream));
+    LIDAR_CUDA(cudaEventRecord(c->stage_done[slot], c->stream));
     *n_beams_total = off;
     *n_tiles = tiles;
     return LIDAR_OK;
@@ -1241,6 +1269,24 @@ lidar_status lidar_reset_schedule(lidar_ctx* c, int32_t slot)
     LIDAR_CUDA(cudaMemcpyAsync(sl.order_dev, sl.base_order_dev, sl.n_beams * sizeof(uint32_t),
                                cudaMemcpyDeviceToDevice, c->stream));
     LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+    return LIDAR_OK;
+}
+
+lidar_status lidar_set_build_options(lidar_ctx* c, const lidar_build_options* o)
+{
+    LIDAR_CHECK_ARG(c != nullptr && o != nullptr, "lidar_set_build_options: NULL argument");
+    LIDAR_CHECK_ARG(o->method == 0 || o->method == 1, "lidar_set_build_options: method is 0 or 1");
+    LIDAR_CHECK_ARG(o->ploc_radius >= 1 && o->ploc_radius <= 64, "lidar_set_build_options: ploc_radius in [1, 64]");
+    c->build_method = o->method;
+    c->ploc_radius = o->ploc_radius;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_get_build_options(lidar_ctx* c, lidar_build_options* o)
+{
+    LIDAR_CHECK_ARG(c != nullptr && o != nullptr, "lidar_get_build_options: NULL argument");
+    o->method = c->build_method;
+    o->ploc_radius = c->ploc_radius;
     return LIDAR_OK;
 }
 

@@ -300,6 +300,17 @@ class Lidar:
                 "lidar_raster_gbuffer")
         return g
 
+    # ----------------------------------------------------------- build options
+    def set_build_options(self, method: int = 1, ploc_radius: int = 16):
+        """Hierarchy of scenes built afterwards: 0 Karras LBVH, 1 PLOC (default)."""
+        o = C.lidar_build_options(method, ploc_radius)
+        C.check(C.lidar_set_build_options(self.handle, ctypes.byref(o)), "lidar_set_build_options")
+
+    def build_options(self):
+        o = C.lidar_build_options()
+        C.check(C.lidar_get_build_options(self.handle, ctypes.byref(o)), "lidar_get_build_options")
+        return {"method": o.method, "ploc_radius": o.ploc_radius}
+
     # ----------------------------------------------------------- tuning
     def launch_config(self):
         c = C.lidar_launch_config()

@@ -205,9 +205,17 @@ def test_empty_and_single_triangle_scenes(L):
     assert rep["hits"] > 100
 
 
-def test_lbvh_invariants(L):
+@pytest.mark.parametrize("method", [0, 1])
+def test_lbvh_invariants(L, method):
+    """Both hierarchies (Karras LBVH, PLOC clustering): every leaf once, every
+    node but the root once, parent boxes equal to their children's boxes, depth
+    within the traversal stack."""
     w = synth.small_terrain(seed=8, n_cells=48, half=24.0, n_objects=20, n_frames=1, n_az=32)
-    scene, _ = setup(L, w)
+    L.set_build_options(method=method)
+    try:
+        scene, _ = setup(L, w)
+    finally:
+        L.set_build_options(method=1)
     nodes, leaf_tri = scene.export()
     n = w.scene.n_tris
     assert nodes.shape[0] == n - 1
@@ -241,6 +249,42 @@ def test_lbvh_invariants(L):
     assert np.all(seen_leaf == 1)
     assert seen_node[0] == 0 and np.all(seen_node[1:] == 1)
     assert scene.info()["max_depth"] <= 96
+
+
+@pytest.mark.parametrize("radius", [1, 16])
+def test_ploc_tree_casts_bit_identical(L, radius):
+    """The closest hit does not depend on the hierarchy: a PLOC tree gives every
+    dense field bit for bit as the LBVH tree does (cfg0 and a small terrain
+    with sub-rays), and its casts match the oracle."""
+    for w in (synth.cfg0(), synth.small_terrain(seed=9, n_frames=2, n_az=128, n_subrays=7, divergence=2e-3)):
+        L.set_build_options(method=0)
+        try:
+            base, _ = gpu_cast(L, w)
+        finally:
+            L.set_build_options(method=1)
+        L.set_build_options(method=1, ploc_radius=radius)
+        try:
+            other, _ = gpu_cast(L, w)
+        finally:
+            L.set_build_options(method=1, ploc_radius=16)
+        for k in base:
+            assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), (w.name, radius, k)
+
+
+def test_ploc_cfg1_full_frame_bit_identical(L):
+    w = synth.cfg1()
+    fields = ("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst", "theta_deg")
+    L.set_build_options(method=0)
+    try:
+        base, s0 = gpu_cast(L, w, fields=fields)
+    finally:
+        L.set_build_options(method=1)
+    v0 = L.count_work(s0, w.frames, w.seed)["node_visits"]
+    other, s1 = gpu_cast(L, w, fields=fields)
+    v1 = L.count_work(s1, w.frames, w.seed)["node_visits"]
+    for k in fields:
+        assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), k
+    _report({"label": "cfg1 PLOC vs LBVH node fetches per ray", "lbvh": v0 / 262144, "ploc": v1 / 262144})
 
 
 def test_batch_and_graph_replay_match_direct_cast(L):
