@@ -814,7 +814,9 @@ lidar_status lidar_cast_sweep(lidar_ctx* c, const lidar_scene* scene, const lida
                        echoes->intensity, echoes->tri, echoes->sub};
     }
     std::vector<SweepDev> fd((size_t)n_frames);
-    int64_t off = 0;
+    std::vector<int64_t> prefix((size_t)n_frames);
+    const int tr = c->cfg.tile_rays;
+    int64_t off = 0, tiles = 0;
     for (int32_t k = 0; k < n_frames; ++k) {
         const int s = frames[k].sensor;
         LIDAR_CHECK_ARG(s >= 0 && s < LIDAR_MAX_SENSORS, "lidar_cast_sweep: sensor slot out of range");
@@ -841,15 +843,19 @@ lidar_status lidar_cast_sweep(lidar_ctx* c, const lidar_scene* scene, const lida
         f.sensor = s;
         f.frame = frames[k].frame;
         f.beam_offset = off;
+        prefix[(size_t)k] = tiles;
         off += c->slots[s].n_beams;
+        tiles += (c->slots[s].n_beams + tr - 1) / tr;
     }
     DeviceGuard g(c->device);
+    // sweep records, then the tile prefix at a 256-byte boundary, in one block
+    const size_t prefix_at = ((size_t)n_frames * sizeof(SweepDev) + 255) / 256 * 256;
     if ((size_t)n_frames > c->sweeps_cap) {
         LIDAR_CUDA(cudaStreamSynchronize(c->stream));
         cudaFree(c->sweeps_dev);
         c->sweeps_dev = nullptr;
         c->sweeps_cap = 0;
-        if (dev_alloc((void**)&c->sweeps_dev, (size_t)n_frames * sizeof(SweepDev)) != cudaSuccess) {
+        if (dev_alloc((void**)&c->sweeps_dev, prefix_at + (size_t)n_frames * sizeof(int64_t)) != cudaSuccess) {
             cudaGetLastError();
             set_error("lidar_cast_sweep: device allocation failed");
             return LIDAR_ENOMEM;
@@ -859,7 +865,17 @@ lidar_status lidar_cast_sweep(lidar_ctx* c, const lidar_scene* scene, const lida
     // pageable source: the copy is staged before the call returns
     LIDAR_CUDA(cudaMemcpyAsync(c->sweeps_dev, fd.data(), (size_t)n_frames * sizeof(SweepDev), cudaMemcpyHostToDevice,
                                c->stream));
+    int64_t* prefix_dev = (int64_t*)((char*)c->sweeps_dev + prefix_at);
+    LIDAR_CUDA(cudaMemcpyAsync(prefix_dev, prefix.data(), (size_t)n_frames * sizeof(int64_t), cudaMemcpyHostToDevice,
+                               c->stream));
     SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
+    if (echoes == nullptr) {
+        // dense records only: the persistent tiles follow the slots' ray orders
+        LIDAR_CUDA(launch_sweep_tiles(c->stream, S, c->sensors_dev, c->sweeps_dev, n_frames, prefix_dev, tiles,
+                                      c->table, seed, to_beams_out(beams), c->status_dev, c->work_counter, c->cfg,
+                                      c->num_sms));
+        return LIDAR_OK;
+    }
     LIDAR_CUDA(launch_cast_sweep(c->stream, S, c->sensors_dev, c->sweeps_dev, n_frames, off, c->table, seed,
                                  to_beams_out(beams), echo, c->status_dev));
     return LIDAR_OK;

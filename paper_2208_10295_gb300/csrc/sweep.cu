@@ -6,7 +6,8 @@
 // step of Sec. II-A, here per beam.  From the returns of a beam's sub-rays it
 // also reports several echoes (Sec. IV: multiple returns are future work):
 // mode 0 the n strongest apart by at least `separation` in range, mode 1 the
-// first and the last.  One thread per beam, 4-wide traversal.
+// first and the last.  With echoes one thread per beam; without, the
+// persistent tiles of the frame cast.  4-wide traversal.
 #include "common.cuh"
 #include "philox.cuh"
 #include "trace.cuh"
@@ -130,7 +131,91 @@ __global__ void __launch_bounds__(128) k_cast_sweep(SceneDev S, const SensorDev*
     }
 }
 
+// Persistent variant (no echoes): warps take tiles of `tile_rays` positions of
+// a sweep's ray order from the work counter, as the frame cast does, so the
+// sensor's schedule applies; dense records only.
+template <int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) k_sweep_tiles(SceneDev S, const SensorDev* __restrict__ sensors,
+                                                                 const SweepDev* __restrict__ frames, int n_frames,
+                                                                 const int64_t* __restrict__ tile_prefix,
+                                                                 int64_t n_tiles, int tile_rays, TableDev T,
+                                                                 uint64_t seed, BeamsOut out, int* status,
+                                                                 unsigned long long* work_counter)
+{
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long claimed = 0;
+        if (lane == 0) claimed = atomicAdd(work_counter, 1ull);
+        const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, claimed, 0);
+        if (tile >= n_tiles) break;
+        int lo = 0, hi = n_frames - 1;  // last sweep whose first tile is at or before `tile`
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+        }
+        const SweepDev f = frames[lo];
+        const SensorDev& sd = sensors[f.sensor];
+        const int64_t base = (tile - tile_prefix[lo]) * tile_rays;
+        for (int j0 = 0; j0 < tile_rays; j0 += 32) {
+            const int64_t pos = base + j0 + lane;
+            const bool active = pos < sd.n_beams;
+            if (!__any_sync(0xffffffffu, active)) break;
+            if (!active) continue;
+            const uint32_t beam = sd.order ? __ldg(&sd.order[pos]) : (uint32_t)pos;
+            float P[12];
+            sweep_pose(f, __ldg(&sd.sweep[beam]), P);
+            const RayW beam_ray = world_ray(P, __ldg(&sd.dirs[3 * (int64_t)beam]),
+                                            __ldg(&sd.dirs[3 * (int64_t)beam + 1]),
+                                            __ldg(&sd.dirs[3 * (int64_t)beam + 2]));
+            BeamResult best;
+            int best_sub = 0;
+            float best_I = -1.0f;
+            for (int k = 0; k < sd.n_sub; ++k) {
+                RayW r = beam_ray;
+                if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
+                const RayPre p = prepare_ray(r);
+                HitRec h;
+                if (!trace_closest4<false>(S, p, sd.t_max, h, nullptr, nullptr, 0)) raise_status(status, ST_STACK);
+                BeamResult res;
+                shade(S, h, r, sd, T, seed, beam, (uint32_t)f.frame, (uint32_t)f.sensor, (uint32_t)k, res);
+                if (k == 0) best = res;
+                if (res.valid && res.intensity > best_I) {
+                    best_I = res.intensity;
+                    best = res;
+                    best_sub = k;
+                }
+            }
+            write_beam(out, f.beam_offset + beam, best, P, best_sub);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_sweep_tiles(cudaStream_t s, const SceneDev& S, const SensorDev* sensors_dev,
+                               const SweepDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
+                               int64_t n_tiles, TableDev T, uint64_t seed, BeamsOut out, int* status,
+                               unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms)
+{
+    if (n_tiles == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int64_t warps = cfg.block_threads / 32;
+    int64_t grid = (int64_t)num_sms * cfg.blocks_per_sm;
+    if (grid > (n_tiles + warps - 1) / warps) grid = (n_tiles + warps - 1) / warps;
+    const int resident = cfg.block_threads * cfg.blocks_per_sm;
+    const int bt = cfg.block_threads;
+    if (resident <= 512)
+        k_sweep_tiles<2><<<(unsigned)grid, bt, 0, s>>>(S, sensors_dev, frames_dev, n_frames, tile_prefix_dev, n_tiles,
+                                                       cfg.tile_rays, T, seed, out, status, work_counter);
+    else if (resident <= 768)
+        k_sweep_tiles<3><<<(unsigned)grid, bt, 0, s>>>(S, sensors_dev, frames_dev, n_frames, tile_prefix_dev, n_tiles,
+                                                       cfg.tile_rays, T, seed, out, status, work_counter);
+    else
+        k_sweep_tiles<4><<<(unsigned)grid, bt, 0, s>>>(S, sensors_dev, frames_dev, n_frames, tile_prefix_dev, n_tiles,
+                                                       cfg.tile_rays, T, seed, out, status, work_counter);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_cast_sweep(cudaStream_t s, const SceneDev& S, const SensorDev* sensors_dev,
                               const SweepDev* frames_dev, int n_frames, int64_t n_total, TableDev T, uint64_t seed,

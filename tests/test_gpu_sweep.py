@@ -139,3 +139,27 @@ def test_sweep_rejects_bad_echo_arguments(L):
         with pytest.raises(capi.LidarError) as e:
             L.cast_sweep_into(scene, sw, w.seed, None, echoes, mode=mode, separation=sep)
         assert e.value.status == capi.LIDAR_EINVAL
+
+
+@pytest.mark.parametrize("cfg", [{}, {"ray_order": 0}, {"block_threads": 128, "blocks_per_sm": 4}])
+def test_sweep_persistent_path_equals_per_beam_path(L, cfg):
+    """Without echoes the sweep cast runs the persistent, scheduled tiles; its
+    dense records are bit for bit those of the one-thread-per-beam path."""
+    w = synth.small_terrain(seed=12, n_frames=3, n_az=128, n_subrays=7, divergence=2e-3)
+    sw = sweeps_of(w)
+    scene, _ = setup(L, w)
+    n = L.total_beams(sw)
+    cfg0 = L.launch_config()
+    try:
+        L.set_launch_config(**cfg)
+        L.schedule_by_cost(scene, w.frames[:1], w.seed, mode=1)
+        a = L.alloc_beams(n)
+        L.cast_sweep_into(scene, sw, w.seed, a)
+        b = L.alloc_beams(n)
+        L.cast_sweep_into(scene, sw, w.seed, b, L.alloc_echoes(n, 2), mode=1, separation=0.5)
+        assert L.sync_status() == 0
+    finally:
+        L.set_launch_config(**cfg0)
+        L.reset_schedule(0)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
