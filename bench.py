@@ -241,24 +241,51 @@ def run_ours(args, rank, world, local_rank):
     kernel_ms = event_time(torch, stream, lambda: L.cast_into(scene, frames, w.seed, dense), flush,
                            reps=min(args.steps, 200), warm=3)
 
-    # ---- end to end through host buffers: pose in, point cloud out
-    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in pts.items()}
-    e2e_ms, bo_total = [], 0
-    n_e2e = min(args.steps, 200)
-    for i in range(args.warmup + n_e2e):
+    # ---- end to end through host buffers: pose in, point cloud out.  Steps are
+    # pipelined: step i's cast (its frame record copied in from pinned memory by
+    # the call) runs while step i-1's point cloud is copied out on a copy stream
+    # into pinned host buffers; two device point buffers alternate.
+    fields = ("xyz", "range", "intensity", "normal", "material", "instance", "beam", "frame")
+    pbuf = [pts, L.alloc_points(n_beams)]
+    host = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in pts.items()} for _ in range(2)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    cast_done = [torch.cuda.Event() for _ in range(2)]
+    copy_done = [torch.cuda.Event() for _ in range(2)]
+    count_ready = torch.cuda.Event()
+    n_e2e = min(args.steps, 1000)
+
+    def drain(i):
+        """Copies step i's point cloud to the host (count first, then its points)."""
+        b = i % 2
+        copy_stream.wait_event(cast_done[b])
+        with torch.cuda.stream(copy_stream):
+            host[b]["count"].copy_(pbuf[b]["count"], non_blocking=True)
+            count_ready.record(copy_stream)
+            count_ready.synchronize()
+            c = int(host[b]["count"][0])
+            for k in fields:
+                host[b][k][:c].copy_(pbuf[b][k][:c], non_blocking=True)
+            copy_done[b].record(copy_stream)
+        return c
+
+    bo_total = 0
+    for rep in range(2):   # first pass warms up, second is timed
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        L.cast_into(scene, frames, w.seed, None, pts)   # copies the host frame record in
-        host["count"].copy_(pts["count"], non_blocking=True)
-        stream.synchronize()
-        c = int(host["count"].item())
-        for k in ("xyz", "range", "intensity", "normal", "material", "instance", "beam", "frame"):
-            host[k][:c].copy_(pts[k][:c], non_blocking=True)
-        stream.synchronize()
-        if i >= args.warmup:
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-            bo_total += 8 + c * POINT_BYTES
-    e2e_step_ms = statistics.mean(e2e_ms)
+        total_pts = 0
+        for i in range(n_e2e + 1):
+            if i < n_e2e:
+                b = i % 2
+                stream.wait_event(copy_done[b])          # buffer b's previous copy-out is done
+                L.cast_into(scene, frames, w.seed, None, pbuf[b])
+                cast_done[b].record(stream)
+            if i >= 1:
+                total_pts += drain(i - 1)
+        copy_stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        bo_total = n_e2e * 8 + total_pts * POINT_BYTES
+    e2e_step_ms = e2e_s / n_e2e * 1e3
+    del pbuf[1]
 
     # ---- algorithmic work of one launch (instrumented run of the same kernel)
     counters = L.count_work(scene, frames, w.seed)
@@ -294,7 +321,9 @@ def run_ours(args, rank, world, local_rank):
                    "points_per_step": n_points, "launch": tuned_cfg},
         "gpu_launches": launches_per_step * args.steps,
         "e2e": {"value": n_beams / (e2e_step_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 56,
-                "d2h_bytes_per_step": bo_total / n_e2e},
+                "d2h_bytes_per_step": bo_total / n_e2e, "steps": n_e2e,
+                "how": "host wall clock over pipelined steps: frame record in from pinned memory, count and "
+                       "points out to pinned memory on a copy stream overlapping the next step's cast"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": f"{peaks_src} hbm_gbs (STREAM-style copy)",
