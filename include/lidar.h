@@ -107,6 +107,9 @@ typedef struct {
     double build_ms;       /* device time of the last build, CUDA events */
     int64_t n_nodes4;      /* nodes of the 4-wide hierarchy collapsed from the binary one */
     int32_t levels4;       /* its height */
+    int64_t n_nodes8;      /* nodes of the 8-wide hierarchy (same collapse), 0 when not kept because
+                              its traversal could need a deeper stack than the kernel's 96 entries */
+    int32_t levels8;       /* its height */
 } lidar_scene_info;
 
 lidar_status lidar_get_scene_info(const lidar_scene* scene, lidar_scene_info* out);
@@ -133,6 +136,15 @@ lidar_status lidar_get_build_options(lidar_ctx* ctx, lidar_build_options* option
  * nodes [n_nodes][16] float32 bit patterns in the device layout, and the
  * leaf-order -> original triangle index map [n_tris].  Synchronises. */
 lidar_status lidar_scene_export(const lidar_scene* scene, float* nodes_host, uint32_t* leaf_tri_host);
+
+/* Exports a wide hierarchy for validation: width 4 -> [n_nodes4][32] floats,
+ * width 8 -> [n_nodes8][64] floats (host buffer), the device layout: for axis
+ * a and group g of four children (G = width / 4 groups), lower planes at float4
+ * (2a)G + g, upper planes at (2a + 1)G + g, child codes (int32 bit patterns:
+ * >= 0 wide node, < 0 ~leaf position, empty slots an empty box and code 0) at
+ * 6G + g.  LIDAR_EINVAL for another width or an 8-wide tree the scene does
+ * not have.  Synchronises. */
+lidar_status lidar_scene_export_wide(const lidar_scene* scene, int32_t width, float* nodes_host);
 
 /* ----------------------------------------------------------------- sensors */
 
@@ -344,7 +356,7 @@ lidar_status lidar_cast_backward_mse_noalloc(void* cuda_stream, int64_t n_beams,
  * algorithmic bytes and flops behind the roofline. */
 typedef struct {
     uint64_t rays;           /* traced rays (beams x sub-rays) */
-    uint64_t node_bytes;     /* bytes per node fetch: 64 (binary tree) or 128 (4-wide tree) */
+    uint64_t node_bytes;     /* bytes per node fetch: 64 (binary tree), 128 (4-wide) or 256 (8-wide) */
     uint64_t node_visits;    /* node fetches */
     uint64_t tri_tests;      /* 48-byte triangle fetches + watertight tests */
     uint64_t unique_nodes;   /* distinct nodes fetched */
@@ -474,7 +486,9 @@ typedef struct {
     int32_t ray_order;       /* 0 = beam order, 1 = Morton order of beam directions */
     int32_t traversal;       /* binary tree: 0 = each lane tests its triangles as it meets them,
                                 1 = warp-synchronous with postponed triangle tests;
-                                2 = 4-wide tree, per lane, children visited near to far */
+                                2 = 4-wide tree, per lane, children visited near to far;
+                                3 = 8-wide tree, per lane, children visited near to far (a cast on a
+                                    scene without an 8-wide tree returns LIDAR_EINVAL) */
     int32_t fused_scatter;   /* 1: the point-cloud scatter runs inside the cast kernel after a grid-wide
                                 wait (cooperative launch); 0: as a separate kernel */
 } lidar_launch_config;

@@ -40,7 +40,7 @@ class LidarError(RuntimeError):
 class lidar_scene_info(ctypes.Structure):
     _fields_ = [("n_tris", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("max_depth", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double), ("n_nodes4", ctypes.c_int64),
-                ("levels4", ctypes.c_int32)]
+                ("levels4", ctypes.c_int32), ("n_nodes8", ctypes.c_int64), ("levels8", ctypes.c_int32)]
 
 
 class lidar_sensor_desc(ctypes.Structure):
@@ -111,6 +111,7 @@ _PROTOS = [
     ("lidar_scene_free", None, [c_vp]),
     ("lidar_get_scene_info", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_scene_info)]),
     ("lidar_scene_export", ctypes.c_int, [c_vp, c_vp, c_vp]),
+    ("lidar_scene_export_wide", ctypes.c_int, [c_vp, ctypes.c_int32, c_vp]),
     ("lidar_set_sensor", ctypes.c_int, [c_vp, ctypes.c_int32, ctypes.POINTER(lidar_sensor_desc)]),
     ("lidar_set_sensor_gain", ctypes.c_int, [c_vp, ctypes.c_int32, ctypes.c_float]),
     ("lidar_get_beam_dirs", ctypes.c_int, [c_vp, ctypes.c_int32, c_vp]),
@@ -197,6 +198,7 @@ lidar_scene_build = _fwd("lidar_scene_build")
 lidar_scene_free = _fwd("lidar_scene_free")
 lidar_get_scene_info = _fwd("lidar_get_scene_info")
 lidar_scene_export = _fwd("lidar_scene_export")
+lidar_scene_export_wide = _fwd("lidar_scene_export_wide")
 lidar_set_sensor = _fwd("lidar_set_sensor")
 lidar_set_sensor_gain = _fwd("lidar_set_sensor_gain")
 lidar_get_beam_dirs = _fwd("lidar_get_beam_dirs")

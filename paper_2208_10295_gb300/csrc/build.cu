@@ -550,20 +550,36 @@ cudaError_t build_ploc(cudaStream_t s, const float4* tris_sorted, int64_t n, flo
 }  // namespace lidar
 
 // ---------------------------------------------------------------------------
-// Collapse of the binary hierarchy into a 4-wide one.  Top-down, one frontier
-// of binary nodes per level: each becomes a 4-wide node whose children are
-// found by repeatedly opening the child with the largest surface area until
-// four children or only leaves remain.  Slots of the next level are assigned by
-// an exclusive scan, so the layout is breadth-first and deterministic.
+// Collapse of the binary hierarchy into a W-wide one (W = 4 or 8).  Top-down,
+// one frontier of binary nodes per level: each becomes a wide node whose
+// children are found by repeatedly opening the child with the largest surface
+// area until W children or only leaves remain.  Slots of the next level are
+// assigned by an exclusive scan, so the layout is breadth-first and
+// deterministic.
+//
+// Wide node of G = W/4 groups of four children, 8G float4s: for axis a the
+// lower planes of group g at (2a)G + g, the upper planes at (2a + 1)G + g, the
+// child codes of group g at 6G + g (>= 0: wide node, < 0: ~leaf; empty slots
+// have an empty box and code 0), then G float4s of metadata (128 bytes for
+// W = 4, 256 for W = 8).  A node keeps its internal children in the first
+// slots, in the order of their (consecutive) node ids, and its first metadata
+// float4 holds the first internal child's id and the mask of leaf slots, so a
+// traversal finds an internal child as first + slot.
+//
+// Alongside each frontier entry travels the number of stack entries its
+// ancestors can leave behind: a traversal that descends into one hit internal
+// child pushes at most the node's other internal children, so the deepest
+// stack the tree can need is max over nodes of (ancestors' pushes + the
+// node's internal children - 1).
 namespace lidar {
 namespace {
 
-struct Child4 {
+struct ChildBox {
     float lo[3], hi[3];
     int ref;  // binary node (>= 0) or ~leaf (< 0)
 };
 
-__device__ __forceinline__ void binary_child(const float4* __restrict__ bn, int node, int side, Child4& c)
+__device__ __forceinline__ void binary_child(const float4* __restrict__ bn, int node, int side, ChildBox& c)
 {
     const float4 n0 = bn[4 * (int64_t)node + 0], n1 = bn[4 * (int64_t)node + 1];
     const float4 n2 = bn[4 * (int64_t)node + 2], n3 = bn[4 * (int64_t)node + 3];
@@ -576,19 +592,20 @@ __device__ __forceinline__ void binary_child(const float4* __restrict__ bn, int 
     }
 }
 
-__device__ __forceinline__ float half_area(const Child4& c)
+__device__ __forceinline__ float half_area(const ChildBox& c)
 {
     const float dx = c.hi[0] - c.lo[0], dy = c.hi[1] - c.lo[1], dz = c.hi[2] - c.lo[2];
     return dx * dy + dy * dz + dz * dx;
 }
 
-// children of frontier entry i; returns the number of internal ones
-__device__ int gather4(const float4* __restrict__ bn, int b, Child4 ch[4], int& count)
+// children of binary node b; returns the number of internal ones
+template <int W>
+__device__ int gather_children(const float4* __restrict__ bn, int b, ChildBox ch[W], int& count)
 {
     binary_child(bn, b, 0, ch[0]);
     binary_child(bn, b, 1, ch[1]);
     count = 2;
-    while (count < 4) {
+    while (count < W) {
         int best = -1;
         float best_a = -1.0f;
         for (int k = 0; k < count; ++k)
@@ -607,14 +624,15 @@ __device__ int gather4(const float4* __restrict__ bn, int b, Child4 ch[4], int& 
     return internal;
 }
 
+template <int W>
 __global__ void k_collapse_count(const float4* __restrict__ bn, const int* __restrict__ frontier, int n,
                                  uint32_t* __restrict__ n_internal)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    Child4 ch[4];
+    ChildBox ch[W];
     int count;
-    n_internal[i] = (uint32_t)gather4(bn, frontier[i], ch, count);
+    n_internal[i] = (uint32_t)gather_children<W>(bn, frontier[i], ch, count);
 }
 
 __global__ void __launch_bounds__(1024) k_collapse_scan(uint32_t* __restrict__ v, int n, uint32_t* total)
@@ -641,45 +659,68 @@ __global__ void __launch_bounds__(1024) k_collapse_scan(uint32_t* __restrict__ v
     if (threadIdx.x == blockDim.x - 1) *total = s_sum[blockDim.x - 1];
 }
 
-// frontier entry i owns 4-wide slot (slot_base + i); its internal children get
-// slots next_base + offset[i] + k and enter the next frontier at offset[i] + k
-__global__ void k_collapse_write(const float4* __restrict__ bn, const int* __restrict__ frontier, int n,
-                                 const uint32_t* __restrict__ offset, int slot_base, int next_base,
-                                 float4* __restrict__ nodes4, int* __restrict__ next_frontier)
+// frontier entry i owns wide slot (slot_base + i); its internal children get
+// slots next_base + offset[i] + k and enter the next frontier at offset[i] + k.
+// With nodes == nullptr only the next frontier and the stack bound are made.
+template <int W>
+__global__ void k_collapse_write(const float4* __restrict__ bn, const int* __restrict__ frontier,
+                                 const int* __restrict__ pushes_in, int n, const uint32_t* __restrict__ offset,
+                                 int slot_base, int next_base, float4* __restrict__ nodes,
+                                 int* __restrict__ next_frontier, int* __restrict__ pushes_out, int* stack_need)
 {
+    constexpr int G = W / 4;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    Child4 ch[4];
+    ChildBox ch[W];
     int count;
-    gather4(bn, frontier[i], ch, count);
-    float lo[3][4], hi[3][4];
-    int code[4];
+    const int internal = gather_children<W>(bn, frontier[i], ch, count);
+    const int below = pushes_in[i] + (internal > 0 ? internal - 1 : 0);
+    atomicMax(stack_need, below);
+    {
+        // internal children first, keeping their order (a stable partition)
+        ChildBox tmp[W];
+        int m = 0;
+        for (int k = 0; k < count; ++k)
+            if (ch[k].ref >= 0) tmp[m++] = ch[k];
+        for (int k = 0; k < count; ++k)
+            if (ch[k].ref < 0) tmp[m++] = ch[k];
+        for (int k = 0; k < count; ++k) ch[k] = tmp[k];
+    }
+    float lo[3][W], hi[3][W];
+    int code[W];
     int k_int = 0;
-    for (int k = 0; k < 4; ++k) {
+    unsigned leaf_mask = 0;
+    for (int k = 0; k < W; ++k) {
         if (k < count) {
             for (int a = 0; a < 3; ++a) { lo[a][k] = ch[k].lo[a]; hi[a][k] = ch[k].hi[a]; }
             if (ch[k].ref >= 0) {
                 const int j = (int)offset[i] + k_int++;
                 code[k] = next_base + j;
                 next_frontier[j] = ch[k].ref;
+                pushes_out[j] = below;
             } else {
                 code[k] = ch[k].ref;
+                leaf_mask |= 1u << k;
             }
         } else {
             for (int a = 0; a < 3; ++a) { lo[a][k] = INFINITY; hi[a][k] = -INFINITY; }
             code[k] = 0;
         }
     }
-    float4* out = nodes4 + 8 * (int64_t)(slot_base + i);
-    out[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
-    out[1] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
-    out[2] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
-    out[3] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
-    out[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
-    out[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
-    out[6] = make_float4(__int_as_float(code[0]), __int_as_float(code[1]), __int_as_float(code[2]),
-                         __int_as_float(code[3]));
-    out[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (!nodes) return;
+    float4* out = nodes + 8 * G * (int64_t)(slot_base + i);
+    for (int g = 0; g < G; ++g) {
+        const int c = 4 * g;
+        for (int a = 0; a < 3; ++a) {
+            out[(2 * a) * G + g] = make_float4(lo[a][c], lo[a][c + 1], lo[a][c + 2], lo[a][c + 3]);
+            out[(2 * a + 1) * G + g] = make_float4(hi[a][c], hi[a][c + 1], hi[a][c + 2], hi[a][c + 3]);
+        }
+        out[6 * G + g] = make_float4(__int_as_float(code[c]), __int_as_float(code[c + 1]),
+                                     __int_as_float(code[c + 2]), __int_as_float(code[c + 3]));
+        out[7 * G + g] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    out[7 * G] = make_float4(__int_as_float(internal > 0 ? next_base + (int)offset[i] : 0),
+                             __int_as_float((int)leaf_mask), 0.0f, 0.0f);
 }
 
 }  // namespace
@@ -687,33 +728,51 @@ __global__ void k_collapse_write(const float4* __restrict__ bn, const int* __res
 size_t collapse_scratch_bytes(int64_t n_binary)
 {
     const int64_t m = n_binary > 0 ? n_binary : 1;
-    return 2 * ((m * sizeof(int) + 255) / 256) * 256 + ((m * sizeof(uint32_t) + 255) / 256) * 256 + 256;
+    const size_t arr = ((m * sizeof(int) + 255) / 256) * 256;
+    return 5 * arr + 256;
 }
 
-cudaError_t collapse_bvh4(cudaStream_t s, const float4* binary_nodes, int64_t n_binary, float4* nodes4,
-                          int64_t* n_nodes4, int* levels, void* scratch, size_t scratch_bytes)
+cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, int64_t n_binary, float4* nodes,
+                         int64_t* n_wide, int* levels, int* stack_need, void* scratch, size_t scratch_bytes)
 {
-    *n_nodes4 = 0;
+    *n_wide = 0;
     *levels = 0;
+    *stack_need = 0;
+    if (width != 4 && width != 8) return cudaErrorInvalidValue;
     if (n_binary == 0) return cudaSuccess;
     if (scratch_bytes < collapse_scratch_bytes(n_binary)) return cudaErrorInvalidValue;
-    const size_t fb = ((n_binary * sizeof(int) + 255) / 256) * 256;
+    const size_t arr = ((n_binary * sizeof(int) + 255) / 256) * 256;
     int* fa = (int*)scratch;
-    int* fbuf = (int*)((char*)scratch + fb);
-    uint32_t* counts = (uint32_t*)((char*)scratch + 2 * fb);
-    uint32_t* total = (uint32_t*)((char*)scratch + 2 * fb + ((n_binary * sizeof(uint32_t) + 255) / 256) * 256);
-    const int root = 0;
-    cudaError_t e = cudaMemcpyAsync(fa, &root, sizeof(int), cudaMemcpyHostToDevice, s);
+    int* fbuf = (int*)((char*)scratch + arr);
+    int* pa = (int*)((char*)scratch + 2 * arr);
+    int* pb = (int*)((char*)scratch + 3 * arr);
+    uint32_t* counts = (uint32_t*)((char*)scratch + 4 * arr);
+    uint32_t* total = (uint32_t*)((char*)scratch + 5 * arr);
+    int* need = (int*)(total + 1);
+    const int init[2] = {0, 0};  // root, no pushes above it
+    cudaError_t e = cudaMemcpyAsync(fa, &init[0], sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pa, &init[1], sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(need, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     int n = 1, slot_base = 0;
     int64_t allocated = 1;
     int* cur = fa;
     int* nxt = fbuf;
+    int* pcur = pa;
+    int* pnxt = pb;
     while (n > 0) {
         const int blocks = (n + 255) / 256;
-        k_collapse_count<<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts);
-        k_collapse_scan<<<1, 1024, 0, s>>>(counts, n, total);
-        k_collapse_write<<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts, slot_base, (int)allocated, nodes4, nxt);
+        if (width == 4) {
+            k_collapse_count<4><<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts);
+            k_collapse_scan<<<1, 1024, 0, s>>>(counts, n, total);
+            k_collapse_write<4><<<blocks, 256, 0, s>>>(binary_nodes, cur, pcur, n, counts, slot_base,
+                                                      (int)allocated, nodes, nxt, pnxt, need);
+        } else {
+            k_collapse_count<8><<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts);
+            k_collapse_scan<<<1, 1024, 0, s>>>(counts, n, total);
+            k_collapse_write<8><<<blocks, 256, 0, s>>>(binary_nodes, cur, pcur, n, counts, slot_base,
+                                                      (int)allocated, nodes, nxt, pnxt, need);
+        }
         uint32_t next_n = 0;
         e = cudaMemcpyAsync(&next_n, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return e;
@@ -722,12 +781,14 @@ cudaError_t collapse_bvh4(cudaStream_t s, const float4* binary_nodes, int64_t n_
         slot_base = (int)allocated;
         allocated += next_n;
         n = (int)next_n;
-        int* t = cur;
-        cur = nxt;
-        nxt = t;
+        std::swap(cur, nxt);
+        std::swap(pcur, pnxt);
         ++*levels;
     }
-    *n_nodes4 = allocated;
+    e = cudaMemcpyAsync(stack_need, need, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *n_wide = allocated;
     return cudaGetLastError();
 }
 

@@ -276,7 +276,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                 if (kTrav == 1) {
                     ok = trace_closest_warp<kCount>(S, p, sd.t_max, h, active, &wc);
                 } else if (active) {
-                    if (kTrav == 2)
+                    if (kTrav == 3)
+                        ok = trace_closest8<kCount>(S, p, sd.t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x,
+                                                    &cost);
+                    else if (kTrav == 2)
                         ok = trace_closest4<kCount>(S, p, sd.t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x,
                                                     &cost);
                     else
@@ -490,8 +493,9 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     if (count) {
         // the work counted depends on the tree the traversal walks, not on the launch shape
         a.fused = 0;
-        e = cfg.traversal == 2 ? launch_one<true, 4, 2>(s, a, grid, bt, stack_bytes, num_sms)
-                               : launch_one<true, 4, 0>(s, a, grid, bt, stack_bytes, num_sms);
+        e = cfg.traversal == 3   ? launch_one<true, 4, 3>(s, a, grid, bt, stack_bytes, num_sms)
+            : cfg.traversal == 2 ? launch_one<true, 4, 2>(s, a, grid, bt, stack_bytes, num_sms)
+                                 : launch_one<true, 4, 0>(s, a, grid, bt, stack_bytes, num_sms);
     } else if (cfg.traversal == 1) {
         e = variant == 2   ? launch_one<false, 2, 1>(s, a, grid, bt, 0, num_sms)
             : variant == 3 ? launch_one<false, 3, 1>(s, a, grid, bt, 0, num_sms)
@@ -500,6 +504,10 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
         e = variant == 2   ? launch_one<false, 2, 2>(s, a, grid, bt, stack_bytes, num_sms)
             : variant == 3 ? launch_one<false, 3, 2>(s, a, grid, bt, stack_bytes, num_sms)
                            : launch_one<false, 4, 2>(s, a, grid, bt, stack_bytes, num_sms);
+    } else if (cfg.traversal == 3) {
+        e = variant == 2   ? launch_one<false, 2, 3>(s, a, grid, bt, stack_bytes, num_sms)
+            : variant == 3 ? launch_one<false, 3, 3>(s, a, grid, bt, stack_bytes, num_sms)
+                           : launch_one<false, 4, 3>(s, a, grid, bt, stack_bytes, num_sms);
     } else {
         e = variant == 2   ? launch_one<false, 2, 0>(s, a, grid, bt, stack_bytes, num_sms)
             : variant == 3 ? launch_one<false, 3, 0>(s, a, grid, bt, stack_bytes, num_sms)

@@ -62,6 +62,8 @@ struct SceneDev {
     int64_t n_nodes;
     const float4* nodes4;    // [n_nodes4 * 8] 4-wide hierarchy (same leaves)
     int64_t n_nodes4;
+    const float4* nodes8;    // [n_nodes8 * 16] 8-wide hierarchy (same leaves), NULL if not built
+    int64_t n_nodes8;
 };
 
 // ------------------------------------------------------------------ sensors
@@ -124,10 +126,12 @@ cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, cons
 // scratch of the clustering build (method 1), on top of nothing: it reuses build_lbvh's scratch
 size_t ploc_scratch_bytes(int64_t n_tris);
 size_t build_scratch_bytes(int64_t n_tris);
-// 4-wide hierarchy from the binary one (breadth-first, deterministic);
-// synchronises once per level.  *levels = height of the 4-wide tree.
-cudaError_t collapse_bvh4(cudaStream_t s, const float4* binary_nodes, int64_t n_binary, float4* nodes4,
-                          int64_t* n_nodes4, int* levels, void* scratch, size_t scratch_bytes);
+// W-wide hierarchy (width 4 or 8) from the binary one (breadth-first,
+// deterministic); synchronises once per level.  `nodes` may be NULL to count
+// only.  *n_wide = wide nodes, *levels = height of the wide tree, *stack_need =
+// deepest traversal stack the tree can require.
+cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, int64_t n_binary, float4* nodes,
+                         int64_t* n_wide, int* levels, int* stack_need, void* scratch, size_t scratch_bytes);
 size_t collapse_scratch_bytes(int64_t n_binary);
 
 // sort.cu: stable LSD radix sort of (key, value) pairs, keys of `key_bits` bits

@@ -65,10 +65,19 @@ struct lidar_scene {
     int64_t n_nodes = 0;
     int64_t n_nodes4 = 0;
     int levels4 = 0;
+    float4* nodes8 = nullptr;  // NULL when the 8-wide tree could need a deeper stack than the traversal has
+    int64_t n_nodes8 = 0;
+    int levels8 = 0;
     int max_depth = 0;
     double build_ms = 0.0;
     int64_t bytes = 0;
 };
+
+static SceneDev scene_dev(const lidar_scene* scene)
+{
+    return SceneDev{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes,
+                    scene->nodes4, scene->n_nodes4, scene->nodes8, scene->n_nodes8};
+}
 
 struct lidar_ctx {
     int device = 0;
@@ -218,6 +227,7 @@ void lidar_scene_free(lidar_scene* s)
     cudaStreamSynchronize(s->ctx->stream);
     cudaFree(s->nodes);
     cudaFree(s->nodes4);
+    cudaFree(s->nodes8);
     cudaFree(s->tris);
     cudaFree(s->leaf_tri);
     cudaFree(s->orig_to_leaf);
@@ -278,6 +288,7 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
     auto fail = [&](lidar_status st) {
         cudaFree(s->nodes);
         cudaFree(s->nodes4);
+        cudaFree(s->nodes8);
         cudaFree(s->tris);
         cudaFree(s->leaf_tri);
         delete s;
@@ -330,18 +341,37 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
             return fail(LIDAR_ESTACK);
         }
         cudaEventRecord(e0, c->stream);
-        cudaError_t e4 = collapse_bvh4(c->stream, s->nodes, s->n_nodes, s->nodes4, &s->n_nodes4, &s->levels4,
-                                       c->scratch, c->scratch_bytes);
+        int need4 = 0;
+        cudaError_t e4 = collapse_bvh(c->stream, 4, s->nodes, s->n_nodes, s->nodes4, &s->n_nodes4, &s->levels4,
+                                      &need4, c->scratch, c->scratch_bytes);
+        // the 8-wide tree: count its nodes and the stack it could need, then
+        // write it into an exact allocation; a tree that could need more than
+        // the traversal stack is not kept (the 4-wide and binary ones serve)
+        int64_t n8 = 0;
+        int levels8 = 0, need8 = 0;
+        if (e4 == cudaSuccess)
+            e4 = collapse_bvh(c->stream, 8, s->nodes, s->n_nodes, nullptr, &n8, &levels8, &need8, c->scratch,
+                              c->scratch_bytes);
+        if (e4 == cudaSuccess && need8 <= kTraversalStack && n8 > 0) {
+            if (dev_alloc((void**)&s->nodes8, (size_t)n8 * 16 * sizeof(float4)) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("lidar_scene_build: device allocation failed (8-wide tree)");
+                return fail(LIDAR_ENOMEM);
+            }
+            e4 = collapse_bvh(c->stream, 8, s->nodes, s->n_nodes, s->nodes8, &s->n_nodes8, &s->levels8, &need8,
+                              c->scratch, c->scratch_bytes);
+            s->bytes += s->n_nodes8 * 256;
+        }
         cudaEventRecord(e1, c->stream);
         if (e4 != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
-            set_error(std::string("lidar_scene_build: 4-wide collapse: ") + cudaGetErrorString(e4));
+            set_error(std::string("lidar_scene_build: wide collapse: ") + cudaGetErrorString(e4));
             return fail(LIDAR_ECUDA);
         }
         cudaEventElapsedTime(&ms, e0, e1);
         s->build_ms += ms;
-        // a 4-wide node pushes at most three children
-        if (3 * s->levels4 > kTraversalStack) {
-            set_error("lidar_scene_build: 4-wide BVH too deep for the traversal stack");
+        if (need4 > kTraversalStack) {
+            set_error("lidar_scene_build: 4-wide BVH could need " + std::to_string(need4) +
+                      " stack entries, more than the traversal stack (" + std::to_string(kTraversalStack) + ")");
             return fail(LIDAR_ESTACK);
         }
     }
@@ -360,6 +390,8 @@ lidar_status lidar_get_scene_info(const lidar_scene* s, lidar_scene_info* out)
     out->build_ms = s->build_ms;
     out->n_nodes4 = s->n_nodes4;
     out->levels4 = s->levels4;
+    out->n_nodes8 = s->n_nodes8;
+    out->levels8 = s->levels8;
     return LIDAR_OK;
 }
 
@@ -372,6 +404,21 @@ lidar_status lidar_scene_export(const lidar_scene* s, float* nodes_host, uint32_
         LIDAR_CUDA(cudaMemcpy(nodes_host, s->nodes, (size_t)s->n_nodes * 64, cudaMemcpyDeviceToHost));
     if (leaf_tri_host && s->n_tris)
         LIDAR_CUDA(cudaMemcpy(leaf_tri_host, s->leaf_tri, (size_t)s->n_tris * 4, cudaMemcpyDeviceToHost));
+    return LIDAR_OK;
+}
+
+lidar_status lidar_scene_export_wide(const lidar_scene* s, int32_t width, float* nodes_host)
+{
+    LIDAR_CHECK_ARG(s != nullptr && nodes_host != nullptr, "lidar_scene_export_wide: NULL argument");
+    LIDAR_CHECK_ARG(width == 4 || width == 8, "lidar_scene_export_wide: width is 4 or 8");
+    LIDAR_CHECK_ARG(width == 4 || s->nodes8 != nullptr || s->n_tris == 0,
+                    "lidar_scene_export_wide: the scene has no 8-wide tree");
+    DeviceGuard g(s->ctx->device);
+    LIDAR_CUDA(cudaStreamSynchronize(s->ctx->stream));
+    const int64_t n = width == 4 ? s->n_nodes4 : s->n_nodes8;
+    if (n)
+        LIDAR_CUDA(cudaMemcpy(nodes_host, width == 4 ? s->nodes4 : s->nodes8, (size_t)n * 32 * width,
+                              cudaMemcpyDeviceToHost));
     return LIDAR_OK;
 }
 
@@ -595,6 +642,17 @@ static size_t cast_scratch_upper_bound(int64_t n_total)
            fused_compact_scratch_bytes(n_total);
 }
 
+// The 8-wide traversal needs the scene's 8-wide tree (not kept for trees that
+// could need a deeper stack than the traversal has).
+static lidar_status traversal_available(const lidar_ctx* c, const lidar_scene* scene, const char* who)
+{
+    if (c->cfg.traversal == 3 && scene->n_tris > 0 && scene->nodes8 == nullptr) {
+        set_error(std::string(who) + ": traversal 3 needs the scene's 8-wide tree, which this scene does not have");
+        return LIDAR_EINVAL;
+    }
+    return LIDAR_OK;
+}
+
 // Cast over frames already on the device.  `may_alloc` false: fail instead of
 // growing the scratch (stream capture, batches).
 static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const FrameDev* frames_dev,
@@ -602,6 +660,8 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
                               uint64_t seed, const lidar_beams* beams, const lidar_points* points,
                               int64_t* n_points_dev, bool may_alloc)
 {
+    lidar_status tst = traversal_available(c, scene, "cast");
+    if (tst != LIDAR_OK) return tst;
     BeamsOut out = to_beams_out(beams);
     // compaction reads the dense records: provide the ones the points need
     char* dense_base = nullptr;
@@ -632,7 +692,7 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
         if (need_mat) { out.mat = (uint16_t*)p; p += al(2 * n_total); }
         if (need_inst) { out.inst = (uint32_t*)p; p += al(4 * n_total); }
     }
-    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
+    SceneDev S = scene_dev(scene);
     char* comp = points ? dense_base + dense_bytes : nullptr;
     bool scattered = false;
     LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, frames_dev, n_frames, prefix_dev, n_tiles, c->table, seed,
@@ -724,10 +784,6 @@ static RasterFrame raster_frame(const RasterCams& C, const lidar_frame& fr, floa
     return F;
 }
 
-static SceneDev scene_dev(const lidar_scene* scene)
-{
-    return SceneDev{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
-}
 
 extern "C" {
 
@@ -868,7 +924,7 @@ lidar_status lidar_cast_sweep(lidar_ctx* c, const lidar_scene* scene, const lida
     int64_t* prefix_dev = (int64_t*)((char*)c->sweeps_dev + prefix_at);
     LIDAR_CUDA(cudaMemcpyAsync(prefix_dev, prefix.data(), (size_t)n_frames * sizeof(int64_t), cudaMemcpyHostToDevice,
                                c->stream));
-    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
+    SceneDev S = scene_dev(scene);
     if (echoes == nullptr) {
         // dense records only: the persistent tiles follow the slots' ray orders
         LIDAR_CUDA(launch_sweep_tiles(c->stream, S, c->sensors_dev, c->sweeps_dev, n_frames, prefix_dev, tiles,
@@ -1179,8 +1235,10 @@ static lidar_status counting_cast(lidar_ctx* c, const lidar_scene* scene, const 
         set_error("counting cast: no material table (lidar_set_materials)");
         return LIDAR_ESTATE;
     }
+    lidar_status st = traversal_available(c, scene, "counting cast");
+    if (st != LIDAR_OK) return st;
     int64_t n_total = 0, n_tiles = 0;
-    lidar_status st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles);
+    st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles);
     if (st != LIDAR_OK) return st;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const int64_t node_words = (scene->n_nodes + 31) / 32 + 1, leaf_words = (scene->n_tris + 31) / 32 + 1;
@@ -1200,7 +1258,7 @@ static lidar_status counting_cast(lidar_ctx* c, const lidar_scene* scene, const 
     WorkCount wc{totals, node_bits, leaf_bits, cost_dev};
     BeamsOut dense{};
     dense.valid = valid;
-    SceneDev S{scene->nodes, scene->tris, scene->n_tris, scene->n_nodes, scene->nodes4, scene->n_nodes4};
+    SceneDev S = scene_dev(scene);
     LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, c->frames_dev, n_frames, c->tile_prefix_dev, n_tiles,
                            c->table, seed, dense, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total,
                            &wc));
@@ -1234,7 +1292,7 @@ lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lida
         rays += (uint64_t)sl.n_beams * (uint64_t)sl.dev.n_sub;
     }
     out->rays = rays;
-    out->node_bytes = c->cfg.traversal == 2 ? 128 : 64;
+    out->node_bytes = c->cfg.traversal == 3 ? 256 : (c->cfg.traversal == 2 ? 128 : 64);
     out->node_visits = h[0];
     out->tri_tests = h[1];
     out->unique_nodes = h[2];
@@ -1327,7 +1385,7 @@ lidar_status lidar_set_launch_config(lidar_ctx* c, const lidar_launch_config* cf
     LIDAR_CHECK_ARG(cfg->tile_rays >= 32 && cfg->tile_rays <= (1 << 20) && cfg->tile_rays % 32 == 0,
                     "lidar_set_launch_config: tile_rays must be a multiple of 32 in [32, 2^20]");
     LIDAR_CHECK_ARG(cfg->ray_order == 0 || cfg->ray_order == 1, "lidar_set_launch_config: ray_order is 0 or 1");
-    LIDAR_CHECK_ARG(cfg->traversal >= 0 && cfg->traversal <= 2, "lidar_set_launch_config: traversal is 0, 1 or 2");
+    LIDAR_CHECK_ARG(cfg->traversal >= 0 && cfg->traversal <= 3, "lidar_set_launch_config: traversal is 0, 1, 2 or 3");
     LIDAR_CHECK_ARG(cfg->fused_scatter == 0 || cfg->fused_scatter == 1,
                     "lidar_set_launch_config: fused_scatter is 0 or 1");
     DeviceGuard g(c->device);

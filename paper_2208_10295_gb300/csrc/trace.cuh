@@ -316,33 +316,52 @@ __device__ __forceinline__ void slab4_planes(float4 e, float4 x, unsigned long l
     unpack2(slab2(pack2(x.z, x.w), o2, i2), tout.z, tout.w);
 }
 
-__device__ __forceinline__ void slab4(float4 lo, float4 hi, float o, float inv, bool neg, float4& tin, float4& tout)
+// Near and far slab distances of four child boxes (entry and exit planes per
+// axis already chosen by the direction signs): near = max(axis entries,
+// t_eps), far = min(axis exits) * kFarScale, each slab distance rounded as
+// slab_t rounds it.
+__device__ __forceinline__ void near_far4(float4 xe, float4 xx, float4 ye, float4 yx, float4 ze, float4 zx,
+                                          unsigned long long ox2, unsigned long long oy2, unsigned long long oz2,
+                                          unsigned long long ix2, unsigned long long iy2, unsigned long long iz2,
+                                          float4& kn, float4& kf)
 {
-    const float4 e = neg ? hi : lo, x = neg ? lo : hi;
-    const unsigned long long o2 = pack2(o, o), i2 = pack2(inv, inv);
-    unpack2(slab2(pack2(e.x, e.y), o2, i2), tin.x, tin.y);
-    unpack2(slab2(pack2(e.z, e.w), o2, i2), tin.z, tin.w);
-    unpack2(slab2(pack2(x.x, x.y), o2, i2), tout.x, tout.y);
-    unpack2(slab2(pack2(x.z, x.w), o2, i2), tout.z, tout.w);
+    float4 tin, tout, ti, to;
+    slab4_planes(xe, xx, ox2, ix2, tin, tout);
+    slab4_planes(ye, yx, oy2, iy2, ti, to);
+    tin = make_float4(fmaxf(tin.x, ti.x), fmaxf(tin.y, ti.y), fmaxf(tin.z, ti.z), fmaxf(tin.w, ti.w));
+    tout = make_float4(fminf(tout.x, to.x), fminf(tout.y, to.y), fminf(tout.z, to.z), fminf(tout.w, to.w));
+    slab4_planes(ze, zx, oz2, iz2, ti, to);
+    kn = make_float4(fmaxf(fmaxf(tin.x, ti.x), kTEps), fmaxf(fmaxf(tin.y, ti.y), kTEps),
+                     fmaxf(fmaxf(tin.z, ti.z), kTEps), fmaxf(fmaxf(tin.w, ti.w), kTEps));
+    kf = make_float4(fminf(tout.x, to.x) * kFarScale, fminf(tout.y, to.y) * kFarScale,
+                     fminf(tout.z, to.z) * kFarScale, fminf(tout.w, to.w) * kFarScale);
 }
 
-__device__ __forceinline__ void cswap(float& ka, int& va, float& kb, int& vb)
+// child code of slot j (0..7) of an 8-wide node
+__device__ __forceinline__ int code8(const int4& a, const int4& b, unsigned j)
 {
-    const bool sw = kb < ka;
-    const float tk = sw ? kb : ka;
-    const int tv = sw ? vb : va;
-    kb = sw ? ka : kb;
-    vb = sw ? va : vb;
-    ka = tk;
-    va = tv;
+    const int4 v = (j & 4u) ? b : a;
+    const int lo = (j & 1u) ? v.y : v.x, hi = (j & 1u) ? v.w : v.z;
+    return (j & 2u) ? hi : lo;
+}
+
+__device__ __forceinline__ void sort2u(unsigned& a, unsigned& b)
+{
+    const unsigned lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
 }
 
 // Closest hit by traversal of the 4-wide hierarchy.  Node (128 bytes, eight
 // 16-byte loads): lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four children as
-// float4s, then the child codes (>= 0 node, < 0 ~leaf; empty slots have an
-// empty box).  Triangle children are tested when met; hit internal children
-// are ordered near to far with a 4-key sorting network, the nearest is visited
-// next and the others pushed far-first.
+// float4s, the child codes (>= 0 node, < 0 ~leaf; empty slots have an empty
+// box), then the id of the first internal child and the mask of leaf slots.
+// Internal children fill the first slots with consecutive ids (slot j holds
+// node first + j).  Triangle children are tested when met.  Of the hit
+// internal children a single one is visited directly; several are ordered near
+// to far by a 4-key sorting network over 32-bit keys (the entry distance's
+// bits with the low bits replaced by the slot, as in trace_closest8); the
+// nearest is visited next and the others pushed far-first.
 template <bool kCount = false>
 __device__ __forceinline__ bool trace_closest4(const SceneDev& S, const RayPre& p, float t_max, HitRec& h,
                                                const WorkCount* wc, int2* sh_stack, int sh_stride,
@@ -362,6 +381,7 @@ __device__ __forceinline__ bool trace_closest4(const SceneDev& S, const RayPre& 
     const int ex = p.ix < 0.0f ? 1 : 0, ey = p.iy < 0.0f ? 3 : 2, ez = p.iz < 0.0f ? 5 : 4;
     const unsigned long long ox2 = pack2(p.ox, p.ox), oy2 = pack2(p.oy, p.oy), oz2 = pack2(p.oz, p.oz);
     const unsigned long long ix2 = pack2(p.ix, p.ix), iy2 = pack2(p.iy, p.iy), iz2 = pack2(p.iz, p.iz);
+    constexpr unsigned kNone = 0xFFFFFFFFu;
     int sp = 0;
     int node = 0;
     while (true) {
@@ -370,61 +390,185 @@ __device__ __forceinline__ bool trace_closest4(const SceneDev& S, const RayPre& 
             atomicOr(&wc->node_bits[node >> 5], 1u << (node & 31));
         }
         const float4* q = S.nodes4 + 8 * (int64_t)node;
-        float4 tin, tout, ti, to;
-        slab4_planes(__ldg(q + ex), __ldg(q + (1 - ex)), ox2, ix2, tin, tout);
-        slab4_planes(__ldg(q + ey), __ldg(q + (5 - ey)), oy2, iy2, ti, to);
-        tin = make_float4(fmaxf(tin.x, ti.x), fmaxf(tin.y, ti.y), fmaxf(tin.z, ti.z), fmaxf(tin.w, ti.w));
-        tout = make_float4(fminf(tout.x, to.x), fminf(tout.y, to.y), fminf(tout.z, to.z), fminf(tout.w, to.w));
-        slab4_planes(__ldg(q + ez), __ldg(q + (9 - ez)), oz2, iz2, ti, to);
-        const float4 c4 = __ldg(q + 6);
-        float k0 = fmaxf(fmaxf(tin.x, ti.x), kTEps), k1 = fmaxf(fmaxf(tin.y, ti.y), kTEps);
-        float k2 = fmaxf(fmaxf(tin.z, ti.z), kTEps), k3 = fmaxf(fmaxf(tin.w, ti.w), kTEps);
-        const float f0 = fminf(tout.x, to.x) * kFarScale, f1 = fminf(tout.y, to.y) * kFarScale;
-        const float f2 = fminf(tout.z, to.z) * kFarScale, f3 = fminf(tout.w, to.w) * kFarScale;
-        int c0 = __float_as_int(c4.x), c1 = __float_as_int(c4.y), c2 = __float_as_int(c4.z), c3 = __float_as_int(c4.w);
-        bool h0 = k0 <= fminf(f0, h.cull), h1 = k1 <= fminf(f1, h.cull);
-        bool h2 = k2 <= fminf(f2, h.cull), h3 = k3 <= fminf(f3, h.cull);
-        // triangle children first, through one call site
-        unsigned leaves = (h0 && c0 < 0 ? 1u : 0u) | (h1 && c1 < 0 ? 2u : 0u) | (h2 && c2 < 0 ? 4u : 0u) |
-                          (h3 && c3 < 0 ? 8u : 0u);
-        h0 = h0 && c0 >= 0;
-        h1 = h1 && c1 >= 0;
-        h2 = h2 && c2 >= 0;
-        h3 = h3 && c3 >= 0;
-        while (leaves) {
-            const int j = __ffs(leaves) - 1;
-            leaves &= leaves - 1;
-            const int leaf = ~(j == 0 ? c0 : (j == 1 ? c1 : (j == 2 ? c2 : c3)));
-            if (kCount) {
-                ++n_tris;
-                atomicOr(&wc->leaf_bits[leaf >> 5], 1u << (leaf & 31));
+        const int2 meta = __ldg(reinterpret_cast<const int2*>(q + 7));
+        float4 kn, kf;
+        near_far4(__ldg(q + ex), __ldg(q + (1 - ex)), __ldg(q + ey), __ldg(q + (5 - ey)), __ldg(q + ez),
+                  __ldg(q + (9 - ez)), ox2, oy2, oz2, ix2, iy2, iz2, kn, kf);
+        const unsigned hit = (kn.x <= fminf(kf.x, h.cull) ? 1u : 0u) | (kn.y <= fminf(kf.y, h.cull) ? 2u : 0u) |
+                             (kn.z <= fminf(kf.z, h.cull) ? 4u : 0u) | (kn.w <= fminf(kf.w, h.cull) ? 8u : 0u);
+        const unsigned leafm = (unsigned)meta.y;
+        unsigned vm = hit & ~leafm;  // hit internal children
+        unsigned leaves = hit & leafm;
+        if (leaves) {
+            // triangle children first, through one call site
+            const float cull0 = h.cull;
+            const int4 c = __ldg(reinterpret_cast<const int4*>(q + 6));
+            while (leaves) {
+                const unsigned j = (unsigned)(__ffs(leaves) - 1);
+                leaves &= leaves - 1;
+                const int leaf = ~((j & 2u) ? ((j & 1u) ? c.w : c.z) : ((j & 1u) ? c.y : c.x));
+                if (kCount) {
+                    ++n_tris;
+                    atomicOr(&wc->leaf_bits[leaf >> 5], 1u << (leaf & 31));
+                }
+                intersect_triangle(S.tris, leaf, p, t_max, h);
             }
-            intersect_triangle(S.tris, leaf, p, t_max, h);
+            if (h.cull < cull0) {
+                // a closer hit: keep only the internal children still in front of it
+                const float cl = h.cull;
+                vm &= (kn.x <= cl ? 1u : 0u) | (kn.y <= cl ? 2u : 0u) | (kn.z <= cl ? 4u : 0u) |
+                      (kn.w <= cl ? 8u : 0u);
+            }
         }
-        // internal children that are still in front of the best hit, near to far
-        k0 = (h0 && k0 <= h.cull) ? k0 : INFINITY;
-        k1 = (h1 && k1 <= h.cull) ? k1 : INFINITY;
-        k2 = (h2 && k2 <= h.cull) ? k2 : INFINITY;
-        k3 = (h3 && k3 <= h.cull) ? k3 : INFINITY;
-        cswap(k0, c0, k1, c1);
-        cswap(k2, c2, k3, c3);
-        cswap(k0, c0, k2, c2);
-        cswap(k1, c1, k3, c3);
-        cswap(k1, c1, k2, c2);
-        if (k0 != INFINITY) {
-            if (k3 != INFINITY) {
-                if (sp >= kTraversalStack) return false;
-                stack.put(sp++, make_int2(c3, __float_as_int(k3)));
+        if (vm) {
+            const int first = meta.x;
+            if ((vm & (vm - 1u)) == 0u) {
+                node = first + (__ffs(vm) - 1);
+                continue;
             }
-            if (k2 != INFINITY) {
+            auto key = [vm](float k, unsigned j) -> unsigned {
+                return ((vm >> j) & 1u) ? ((__float_as_uint(k) & ~7u) | j) : kNone;
+            };
+            unsigned s0 = key(kn.x, 0u), s1 = key(kn.y, 1u), s2 = key(kn.z, 2u), s3 = key(kn.w, 3u);
+            sort2u(s0, s1); sort2u(s2, s3); sort2u(s0, s2); sort2u(s1, s3); sort2u(s1, s2);
+            if (s3 != kNone) {
                 if (sp >= kTraversalStack) return false;
-                stack.put(sp++, make_int2(c2, __float_as_int(k2)));
+                stack.put(sp++, make_int2(first + (int)(s3 & 7u), (int)(s3 & ~7u)));
             }
-            if (k1 != INFINITY) {
+            if (s2 != kNone) {
                 if (sp >= kTraversalStack) return false;
-                stack.put(sp++, make_int2(c1, __float_as_int(k1)));
+                stack.put(sp++, make_int2(first + (int)(s2 & 7u), (int)(s2 & ~7u)));
             }
-            node = c0;
+            if (sp >= kTraversalStack) return false;
+            stack.put(sp++, make_int2(first + (int)(s1 & 7u), (int)(s1 & ~7u)));
+            node = first + (int)(s0 & 7u);
+            continue;
+        }
+        bool found = false;
+        while (sp > 0) {
+            const int2 e = stack.get(--sp);
+            if (__int_as_float(e.y) <= h.cull) {
+                node = e.x;
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+    if (kCount) {
+        atomicAdd(&wc->totals[0], n_nodes);
+        atomicAdd(&wc->totals[1], n_tris);
+        if (cost) *cost += (unsigned)(n_nodes + n_tris);
+    }
+    return true;
+}
+
+// Closest hit by traversal of the 8-wide hierarchy.  Node (256 bytes): per
+// axis the lower planes of children 0-3 and 4-7, then their upper planes, as
+// float4s (x at 0-3, y at 4-7, z at 8-11), the eight child codes (12-13), then
+// the id of the first internal child and the mask of leaf slots (14).  Internal
+// children fill the first slots with consecutive ids, so slot j holds node
+// first + j.  Triangle children are tested when met.  Of the hit internal
+// children a single one is visited directly; several are ordered near to far
+// by a sorting network (4 keys when they all sit in slots 0-3, else Batcher's
+// 8-key odd-even merge network) over 32-bit keys: the entry distance's bits with
+// the three lowest replaced by the slot.  Entry distances are positive, so their
+// bit patterns order like the values; clearing low bits only lowers a key, so
+// the stacked keys still prune conservatively.  The nearest child is visited
+// next, the others are pushed far-first.
+template <bool kCount = false>
+__device__ __forceinline__ bool trace_closest8(const SceneDev& S, const RayPre& p, float t_max, HitRec& h,
+                                               const WorkCount* wc, int2* sh_stack, int sh_stride,
+                                               unsigned* cost = nullptr)
+{
+    unsigned long long n_nodes = 0, n_tris = 0;
+    h.t = t_max;
+    h.cull = t_max * kBestScale;
+    h.idx = 0xFFFFFFFFu;
+    h.leaf = -1;
+    if (S.n_tris == 0) return true;
+    SplitStack stack;
+    stack.sh = sh_stack;
+    stack.sh_stride = sh_stride;
+    // entry planes per axis (lower ones for a positive direction), as load offsets
+    const int ex = p.ix < 0.0f ? 2 : 0, ey = p.iy < 0.0f ? 6 : 4, ez = p.iz < 0.0f ? 10 : 8;
+    const unsigned long long ox2 = pack2(p.ox, p.ox), oy2 = pack2(p.oy, p.oy), oz2 = pack2(p.oz, p.oz);
+    const unsigned long long ix2 = pack2(p.ix, p.ix), iy2 = pack2(p.iy, p.iy), iz2 = pack2(p.iz, p.iz);
+    constexpr unsigned kNone = 0xFFFFFFFFu;
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        if (kCount) {
+            ++n_nodes;
+            atomicOr(&wc->node_bits[node >> 5], 1u << (node & 31));
+        }
+        const float4* q = S.nodes8 + 16 * (int64_t)node;
+        const int2 meta = __ldg(reinterpret_cast<const int2*>(q + 14));
+        float4 ka, fa, kb, fb;
+        near_far4(__ldg(q + ex), __ldg(q + (2 - ex)), __ldg(q + ey), __ldg(q + (10 - ey)), __ldg(q + ez),
+                  __ldg(q + (18 - ez)), ox2, oy2, oz2, ix2, iy2, iz2, ka, fa);
+        near_far4(__ldg(q + ex + 1), __ldg(q + (3 - ex)), __ldg(q + ey + 1), __ldg(q + (11 - ey)),
+                  __ldg(q + ez + 1), __ldg(q + (19 - ez)), ox2, oy2, oz2, ix2, iy2, iz2, kb, fb);
+        const unsigned hit = (ka.x <= fminf(fa.x, h.cull) ? 1u : 0u) | (ka.y <= fminf(fa.y, h.cull) ? 2u : 0u) |
+                             (ka.z <= fminf(fa.z, h.cull) ? 4u : 0u) | (ka.w <= fminf(fa.w, h.cull) ? 8u : 0u) |
+                             (kb.x <= fminf(fb.x, h.cull) ? 16u : 0u) | (kb.y <= fminf(fb.y, h.cull) ? 32u : 0u) |
+                             (kb.z <= fminf(fb.z, h.cull) ? 64u : 0u) | (kb.w <= fminf(fb.w, h.cull) ? 128u : 0u);
+        const unsigned leafm = (unsigned)meta.y;
+        unsigned vm = hit & ~leafm;  // hit internal children
+        unsigned leaves = hit & leafm;
+        if (leaves) {
+            const float cull0 = h.cull;
+            const int4 ca = __ldg(reinterpret_cast<const int4*>(q + 12));
+            const int4 cb = __ldg(reinterpret_cast<const int4*>(q + 13));
+            while (leaves) {
+                const unsigned j = (unsigned)(__ffs(leaves) - 1);
+                leaves &= leaves - 1;
+                const int leaf = ~code8(ca, cb, j);
+                if (kCount) {
+                    ++n_tris;
+                    atomicOr(&wc->leaf_bits[leaf >> 5], 1u << (leaf & 31));
+                }
+                intersect_triangle(S.tris, leaf, p, t_max, h);
+            }
+            if (h.cull < cull0) {
+                // a closer hit: keep only the internal children still in front of it
+                const float c = h.cull;
+                vm &= (ka.x <= c ? 1u : 0u) | (ka.y <= c ? 2u : 0u) | (ka.z <= c ? 4u : 0u) |
+                      (ka.w <= c ? 8u : 0u) | (kb.x <= c ? 16u : 0u) | (kb.y <= c ? 32u : 0u) |
+                      (kb.z <= c ? 64u : 0u) | (kb.w <= c ? 128u : 0u);
+            }
+        }
+        if (vm) {
+            const int first = meta.x;
+            if ((vm & (vm - 1u)) == 0u) {
+                node = first + (__ffs(vm) - 1);
+                continue;
+            }
+            auto key = [vm](float k, unsigned j) -> unsigned {
+                return ((vm >> j) & 1u) ? ((__float_as_uint(k) & ~7u) | j) : kNone;
+            };
+            auto push = [&](unsigned s) -> bool {
+                if (s == kNone) return true;
+                if (sp >= kTraversalStack) return false;
+                stack.put(sp++, make_int2(first + (int)(s & 7u), (int)(s & ~7u)));
+                return true;
+            };
+            unsigned s0 = key(ka.x, 0u), s1 = key(ka.y, 1u), s2 = key(ka.z, 2u), s3 = key(ka.w, 3u);
+            if ((vm & 0xF0u) == 0u) {
+                sort2u(s0, s1); sort2u(s2, s3); sort2u(s0, s2); sort2u(s1, s3); sort2u(s1, s2);
+                if (!push(s3) || !push(s2) || !push(s1)) return false;
+            } else {
+                unsigned s4 = key(kb.x, 4u), s5 = key(kb.y, 5u), s6 = key(kb.z, 6u), s7 = key(kb.w, 7u);
+                sort2u(s0, s1); sort2u(s2, s3); sort2u(s4, s5); sort2u(s6, s7);
+                sort2u(s0, s2); sort2u(s1, s3); sort2u(s4, s6); sort2u(s5, s7);
+                sort2u(s1, s2); sort2u(s5, s6);
+                sort2u(s0, s4); sort2u(s1, s5); sort2u(s2, s6); sort2u(s3, s7);
+                sort2u(s2, s4); sort2u(s3, s5);
+                sort2u(s1, s2); sort2u(s3, s4); sort2u(s5, s6);
+                if (!push(s7) || !push(s6) || !push(s5) || !push(s4) || !push(s3) || !push(s2) || !push(s1))
+                    return false;
+            }
+            node = first + (int)(s0 & 7u);
             continue;
         }
         bool found = false;

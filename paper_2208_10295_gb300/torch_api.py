@@ -53,6 +53,14 @@ class Scene:
                                      leaf.ctypes.data_as(ctypes.c_void_p)), "lidar_scene_export")
         return nodes[:info["n_nodes"]], leaf[:self.n_tris]
 
+    def export_wide(self, width):
+        """The 4- or 8-wide tree as float32 [n][8 * width] (device layout)."""
+        n = self.info()["n_nodes4" if width == 4 else "n_nodes8"]
+        nodes = np.zeros((max(n, 1), 8 * width), np.float32)
+        C.check(C.lidar_scene_export_wide(self.handle, width, nodes.ctypes.data_as(ctypes.c_void_p)),
+                "lidar_scene_export_wide")
+        return nodes[:n]
+
     def free(self):
         if self.handle is not None and self._lidar.handle is not None:
             C.lidar_scene_free(self.handle)

@@ -26,7 +26,7 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
 SPACE = {
     "block_threads": (64, 128, 256),
     "blocks_per_sm": (2, 4, 8, 12),
-    "traversal": (0, 1, 2),
+    "traversal": (0, 1, 2, 3),
     "ray_order": (0, 1),
     "schedule": ("morton", "cost", "bucket"),
     "fused_scatter": (0, 1),
@@ -58,10 +58,12 @@ def _time_cast(L, scene, frames, seed, out, pts, flush, reps):
     return statistics.median(ts)
 
 
-def candidates(points=False):
+def candidates(points=False, wide8=True):
     for bt, bps, tv, ro, sc, fs in itertools.product(*SPACE.values()):
         if bt * bps > 2048 or bt * bps < 256:
             continue
+        if tv == 3 and not wide8:
+            continue  # the scene kept no 8-wide tree
         if ro == 0 and sc != "morton":
             continue  # the cost schedules reorder the Morton order
         if not points and fs == 0:
@@ -108,7 +110,7 @@ def autotune(L, scene, frames, seed, schedule_frames=None, cache_path=DEFAULT_CA
     pts = L.alloc_points(n) if points else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=L.device) if flush_l2 else None
     best = None
-    for cfg in candidates(points):
+    for cfg in candidates(points, wide8=scene.info()["n_nodes8"] > 0 or scene.n_tris == 0):
         apply(L, scene, cfg, schedule_frames, seed)
         ms = _time_cast(L, scene, frames, seed, out, pts, flush, reps)
         if verbose:

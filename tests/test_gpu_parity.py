@@ -127,6 +127,7 @@ def test_ray_order_and_launch_shapes_bit_identical(L):
     cfg0 = L.launch_config()
     try:
         for cfg in ({"ray_order": 0}, {"block_threads": 64, "tile_rays": 64}, {"traversal": 1}, {"traversal": 2},
+                    {"traversal": 3}, {"traversal": 3, "block_threads": 128, "blocks_per_sm": 4},
                     {"block_threads": 256, "tile_rays": 512, "blocks_per_sm": 2}):
             L.set_launch_config(**cfg)
             other, _ = gpu_cast(L, w, scene)
@@ -285,6 +286,96 @@ def test_ploc_cfg1_full_frame_bit_identical(L):
     for k in fields:
         assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), k
     _report({"label": "cfg1 PLOC vs LBVH node fetches per ray", "lbvh": v0 / 262144, "ploc": v1 / 262144})
+
+
+def _wide_tree_invariants(nodes, width, n_tris, lo_t, hi_t):
+    """Every leaf once, every wide node but the root once (breadth-first: a
+    child's slot is above its parent's), each child box equal to the union of
+    the boxes below it (exact FP32 min/max), empty slots empty, internal
+    children first with consecutive ids and the metadata that says so."""
+    G = width // 4
+    n = nodes.shape[0]
+    f4 = nodes.reshape(n, 8 * G, 4)
+    lo = np.stack([f4[:, (2 * a) * G:(2 * a) * G + G].reshape(n, width) for a in range(3)], -1)
+    hi = np.stack([f4[:, (2 * a + 1) * G:(2 * a + 1) * G + G].reshape(n, width) for a in range(3)], -1)
+    code = f4[:, 6 * G:7 * G].reshape(n, width).view(np.int32)
+    # metadata: first internal child's id, mask of leaf slots; internal
+    # children fill the first slots with consecutive ids
+    meta = f4[:, 7 * G].view(np.int32)
+    assert np.all(meta[:, 2:] == 0) and np.all(f4[:, 7 * G + 1:] == 0)
+    for i in range(n):
+        internal = code[i] > 0
+        m = int(internal.sum())
+        assert np.all(internal[:m]) and not internal[m:].any(), i
+        assert np.array_equal(code[i, :m], meta[i, 0] + np.arange(m)), i
+        leaf_bits = sum(1 << j for j in range(width) if code[i, j] < 0)
+        assert meta[i, 1] == leaf_bits, i
+    seen_leaf = np.zeros(n_tris, int)
+    seen_node = np.zeros(n, int)
+    box_lo = np.full((n, 3), np.inf, np.float32)
+    box_hi = np.full((n, 3), -np.inf, np.float32)
+    for i in range(n - 1, -1, -1):
+        for j in range(width):
+            c = int(code[i, j])
+            empty = np.all(lo[i, j] == np.inf) and np.all(hi[i, j] == -np.inf)
+            if empty:
+                assert c == 0
+                continue
+            if c < 0:
+                seen_leaf[~c] += 1
+                want_lo, want_hi = lo_t[~c], hi_t[~c]
+            else:
+                assert i < c < n
+                seen_node[c] += 1
+                want_lo, want_hi = box_lo[c], box_hi[c]
+            assert np.array_equal(lo[i, j], want_lo) and np.array_equal(hi[i, j], want_hi), (i, j)
+            box_lo[i] = np.minimum(box_lo[i], lo[i, j])
+            box_hi[i] = np.maximum(box_hi[i], hi[i, j])
+    assert np.all(seen_leaf == 1)
+    assert seen_node[0] == 0 and np.all(seen_node[1:] == 1)
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_wide_tree_invariants(L, method):
+    """The 4- and 8-wide trees collapsed from either binary hierarchy hold every
+    leaf once with exact boxes; the 8-wide tree is shallower."""
+    w = synth.small_terrain(seed=8, n_cells=48, half=24.0, n_objects=20, n_frames=1, n_az=32)
+    L.set_build_options(method=method)
+    try:
+        scene, _ = setup(L, w)
+    finally:
+        L.set_build_options(method=1)
+    _, leaf_tri = scene.export()
+    V = w.scene.verts[w.scene.tris[leaf_tri]]
+    lo_t, hi_t = V.min(1).astype(np.float32), V.max(1).astype(np.float32)
+    info = scene.info()
+    assert info["n_nodes8"] > 0 and info["levels8"] < info["levels4"]
+    for width in (4, 8):
+        _wide_tree_invariants(scene.export_wide(width), width, w.scene.n_tris, lo_t, hi_t)
+
+
+def test_wide8_cfg1_full_frame_bit_identical(L):
+    """The 8-wide traversal returns every dense field of the full cfg1 frame bit
+    for bit as the 4-wide one, with fewer node fetches."""
+    w = synth.cfg1()
+    fields = ("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst", "theta_deg")
+    cfg0 = L.launch_config()
+    try:
+        L.set_launch_config(traversal=2)
+        base, scene = gpu_cast(L, w, fields=fields)
+        c4 = L.count_work(scene, w.frames, w.seed)
+        L.set_launch_config(traversal=3)
+        other, _ = gpu_cast(L, w, scene, fields=fields)
+        c8 = L.count_work(scene, w.frames, w.seed)
+    finally:
+        L.set_launch_config(**cfg0)
+    for k in fields:
+        assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), k
+    assert c8["node_bytes"] == 256 and c4["node_bytes"] == 128
+    assert c8["node_visits"] < c4["node_visits"]
+    _report({"label": "cfg1 node fetches per ray, 4-wide vs 8-wide", "wide4": c4["node_visits"] / 262144,
+             "wide8": c8["node_visits"] / 262144, "tri_tests4": c4["tri_tests"] / 262144,
+             "tri_tests8": c8["tri_tests"] / 262144})
 
 
 def test_batch_and_graph_replay_match_direct_cast(L):
