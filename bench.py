@@ -45,7 +45,7 @@ POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal,
 # the cast kernel as the roofline times it (cfg1 frame, dense valid flags out,
 # L2 flushed before the launch), from one ncu capture, with the digest of the
 # kernel sources the capture ran.  Reported only while the sources still match.
-NCU_TRAFFIC = {"sources": "4b5cb9a345099f64", "bytes": 10_295_808}   # profiles/k_cast_cfg1_ncu_full.md
+NCU_TRAFFIC = {"sources": "26df06cd0e1fef9c", "bytes": 10_468_864}   # profiles/k_cast_cfg1_ncu_full.md
 KERNEL_SOURCES = ("cast.cu", "shade.cuh", "trace.cuh", "common.cuh", "philox.cuh")
 
 
@@ -332,7 +332,7 @@ def run_ours(args, rank, world, local_rank):
                              "L1/L2 serve most of them (compulsory DRAM bytes in compulsory_bytes_per_launch)",
                      "compulsory_bytes_per_launch": uniq_bytes,
                      "compulsory_frac": uniq_bytes / (kernel_ms / 1e3) / 1e9 / hbm},
-        "work_per_ray": {k: v / n_beams for k, v in counters.items()},
+        "work_per_ray": {k: (v if k == "node_bytes" else v / n_beams) for k, v in counters.items()},
         "alu": {"flops_per_launch": flops, "achieved_tflops": alu_tf, "peak_tflops": fp32_peak_tflops(torch, sm_mhz),
                 "frac": alu_tf / fp32_peak_tflops(torch, sm_mhz), "peak_source": "152 SMs x 128 FP32 lanes x 2 x "
                                                                                 "median SM clock under load"},
@@ -545,8 +545,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-beams", type=int, default=2048)
-    ap.add_argument("--ref-beams", type=int, default=256)
+    ap.add_argument("--cpu-beams", type=int, default=16384,
+                    help="beams of the oracle's timed sample (about 13 s on 16 cores)")
+    ap.add_argument("--ref-beams", type=int, default=None,
+                    help="beams per reference-arm step (default: about 90 s of oracle work over all steps)")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched/differentiation/city measurements")
@@ -555,6 +557,9 @@ def main():
                     help="time only the cast kernel of the roofline (warmup + steps launches) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.ref_beams is None:
+        # the oracle does ~1,250 beams/s of this frame on 16 cores: bound the whole reference run
+        args.ref_beams = int(min(4096, max(16, 90 * 1250 // max(args.steps, 1))))
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         line = run_reference(args, rank, world)
