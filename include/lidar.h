@@ -431,9 +431,9 @@ typedef struct {
 
 /* Casts every beam of every sweep (dense outputs as lidar_cast: the strongest
  * return in `beams`, normals rotated by the beam's own pose; no point cloud)
- * and, if `echoes` is given, the multi-echo outputs.  One thread per beam with
- * the 4-wide traversal; the sub-rays, noise draws and model are those of
- * lidar_cast.  Asynchronous. */
+ * and, if `echoes` is given, the multi-echo outputs.  Persistent warp tiles
+ * over each slot's ray order and cost schedule with the 4-wide traversal; the
+ * sub-rays, noise draws and model are those of lidar_cast.  Asynchronous. */
 lidar_status lidar_cast_sweep(lidar_ctx* ctx, const lidar_scene* scene, const lidar_sweep_frame* frames_host,
                               int32_t n_frames, uint64_t seed, const lidar_beams* beams, const lidar_echoes* echoes);
 

@@ -217,13 +217,11 @@ struct EchoOut {
 };
 
 // persistent sweep cast (dense records, no echoes), tiles as in launch_cast
+// echo.n_echoes == 0: dense records only
 cudaError_t launch_sweep_tiles(cudaStream_t s, const SceneDev& S, const SensorDev* sensors_dev,
                                const SweepDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
-                               int64_t n_tiles, TableDev T, uint64_t seed, BeamsOut out, int* status,
+                               int64_t n_tiles, TableDev T, uint64_t seed, BeamsOut out, EchoOut echo, int* status,
                                unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms);
-cudaError_t launch_cast_sweep(cudaStream_t s, const SceneDev& S, const SensorDev* sensors_dev,
-                              const SweepDev* frames_dev, int n_frames, int64_t n_total, TableDev T, uint64_t seed,
-                              BeamsOut out, EchoOut echo, int* status);
 
 // ------------------------------------------------------------ raster path
 

@@ -924,16 +924,10 @@ lidar_status lidar_cast_sweep(lidar_ctx* c, const lidar_scene* scene, const lida
     int64_t* prefix_dev = (int64_t*)((char*)c->sweeps_dev + prefix_at);
     LIDAR_CUDA(cudaMemcpyAsync(prefix_dev, prefix.data(), (size_t)n_frames * sizeof(int64_t), cudaMemcpyHostToDevice,
                                c->stream));
-    SceneDev S = scene_dev(scene);
-    if (echoes == nullptr) {
-        // dense records only: the persistent tiles follow the slots' ray orders
-        LIDAR_CUDA(launch_sweep_tiles(c->stream, S, c->sensors_dev, c->sweeps_dev, n_frames, prefix_dev, tiles,
-                                      c->table, seed, to_beams_out(beams), c->status_dev, c->work_counter, c->cfg,
-                                      c->num_sms));
-        return LIDAR_OK;
-    }
-    LIDAR_CUDA(launch_cast_sweep(c->stream, S, c->sensors_dev, c->sweeps_dev, n_frames, off, c->table, seed,
-                                 to_beams_out(beams), echo, c->status_dev));
+    // persistent tiles that follow the slots' ray orders and schedules
+    LIDAR_CUDA(launch_sweep_tiles(c->stream, scene_dev(scene), c->sensors_dev, c->sweeps_dev, n_frames, prefix_dev,
+                                  tiles, c->table, seed, to_beams_out(beams), echo, c->status_dev, c->work_counter,
+                                  c->cfg, c->num_sms));
     return LIDAR_OK;
 }
 

@@ -6,8 +6,8 @@
 // step of Sec. II-A, here per beam.  From the returns of a beam's sub-rays it
 // also reports several echoes (Sec. IV: multiple returns are future work):
 // mode 0 the n strongest apart by at least `separation` in range, mode 1 the
-// first and the last.  With echoes one thread per beam; without, the
-// persistent tiles of the frame cast.  4-wide traversal.
+// first and the last.  Persistent warp tiles like the frame cast's, 4-wide
+// traversal.
 #include "common.cuh"
 #include "philox.cuh"
 #include "trace.cuh"
@@ -46,60 +46,21 @@ __device__ __forceinline__ void sweep_pose(const SweepDev& f, float s, float* P)
     for (int r = 0; r < 3; ++r) P[4 * r + 3] = __fmaf_rn(s, f.t1[r], __fmul_rn(ms, f.t0[r]));
 }
 
-__global__ void __launch_bounds__(128) k_cast_sweep(SceneDev S, const SensorDev* __restrict__ sensors,
-                                                    const SweepDev* __restrict__ frames, int n_frames,
-                                                    int64_t n_total, TableDev T, uint64_t seed, BeamsOut out,
-                                                    EchoOut echo, int* status)
+// The echoes of one beam from its sub-rays' returns (sub_ok: kept), written at
+// dense position g.
+__device__ __forceinline__ void write_echoes(const EchoOut& echo, int64_t g, int n_sub, const float* sub_range,
+                                             const float* sub_I, const uint32_t* sub_tri, const bool* sub_ok)
 {
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= n_total) return;
-    int lo = 0, hi = n_frames - 1;  // last frame starting at or before g
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (frames[mid].beam_offset <= g) lo = mid; else hi = mid - 1;
-    }
-    const SweepDev f = frames[lo];
-    const SensorDev& sd = sensors[f.sensor];
-    const uint32_t beam = (uint32_t)(g - f.beam_offset);
-    float P[12];
-    sweep_pose(f, __ldg(&sd.sweep[beam]), P);
-    const RayW beam_ray = world_ray(P, __ldg(&sd.dirs[3 * (int64_t)beam]), __ldg(&sd.dirs[3 * (int64_t)beam + 1]),
-                                    __ldg(&sd.dirs[3 * (int64_t)beam + 2]));
-    float sub_range[LIDAR_MAX_SUBRAYS], sub_I[LIDAR_MAX_SUBRAYS];
-    uint32_t sub_tri[LIDAR_MAX_SUBRAYS];
-    bool sub_ok[LIDAR_MAX_SUBRAYS];
-    BeamResult best;
-    int best_sub = 0;
-    float best_I = -1.0f;
-    for (int k = 0; k < sd.n_sub; ++k) {
-        RayW r = beam_ray;
-        if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
-        const RayPre p = prepare_ray(r);
-        HitRec h;
-        if (!trace_closest4<false>(S, p, sd.t_max, h, nullptr, nullptr, 0)) raise_status(status, ST_STACK);
-        BeamResult res;
-        shade(S, h, r, sd, T, seed, beam, (uint32_t)f.frame, (uint32_t)f.sensor, (uint32_t)k, res);
-        sub_range[k] = res.range;
-        sub_I[k] = res.intensity;
-        sub_tri[k] = res.tri;
-        sub_ok[k] = res.valid != 0;
-        if (k == 0) best = res;
-        if (res.valid && res.intensity > best_I) {
-            best_I = res.intensity;
-            best = res;
-            best_sub = k;
-        }
-    }
-    write_beam(out, g, best, P, best_sub);
-    if (echo.n_echoes <= 0) return;
     int pick[4];
     int n = 0;
     if (echo.mode == 0) {
+        // strongest first (ties to the lower sub-ray), skipping returns within
+        // `separation` in range of one already kept
         bool used[LIDAR_MAX_SUBRAYS];
-        for (int k = 0; k < sd.n_sub; ++k) used[k] = false;
+        for (int k = 0; k < n_sub; ++k) used[k] = false;
         while (n < echo.n_echoes) {
             int b = -1;
-            for (int k = 0; k < sd.n_sub; ++k)
+            for (int k = 0; k < n_sub; ++k)
                 if (sub_ok[k] && !used[k] && (b < 0 || sub_I[k] > sub_I[b])) b = k;
             if (b < 0) break;
             used[b] = true;
@@ -109,8 +70,9 @@ __global__ void __launch_bounds__(128) k_cast_sweep(SceneDev S, const SensorDev*
             if (apart) pick[n++] = b;
         }
     } else {
+        // first and last (ties to the lower sub-ray)
         int first = -1, last = -1;
-        for (int k = 0; k < sd.n_sub; ++k) {
+        for (int k = 0; k < n_sub; ++k) {
             if (!sub_ok[k]) continue;
             if (first < 0 || sub_range[k] < sub_range[first]) first = k;
             if (last < 0 || sub_range[k] > sub_range[last]) last = k;
@@ -131,16 +93,17 @@ __global__ void __launch_bounds__(128) k_cast_sweep(SceneDev S, const SensorDev*
     }
 }
 
-// Persistent variant (no echoes): warps take tiles of `tile_rays` positions of
-// a sweep's ray order from the work counter, as the frame cast does, so the
-// sensor's schedule applies; dense records only.
-template <int kMinBlocks>
+// Persistent sweep cast: warps take tiles of `tile_rays` positions of a
+// sweep's ray order from the work counter, as the frame cast does, so the
+// sensor's ray order and cost schedule apply.  Dense records (the strongest
+// return) and, with kEcho, the echoes of each beam's sub-rays.
+template <int kMinBlocks, bool kEcho>
 __global__ void __launch_bounds__(256, kMinBlocks) k_sweep_tiles(SceneDev S, const SensorDev* __restrict__ sensors,
                                                                  const SweepDev* __restrict__ frames, int n_frames,
                                                                  const int64_t* __restrict__ tile_prefix,
                                                                  int64_t n_tiles, int tile_rays, TableDev T,
-                                                                 uint64_t seed, BeamsOut out, int* status,
-                                                                 unsigned long long* work_counter)
+                                                                 uint64_t seed, BeamsOut out, EchoOut echo,
+                                                                 int* status, unsigned long long* work_counter)
 {
     const int lane = threadIdx.x & 31;
     while (true) {
@@ -167,6 +130,9 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_sweep_tiles(SceneDev S, con
             const RayW beam_ray = world_ray(P, __ldg(&sd.dirs[3 * (int64_t)beam]),
                                             __ldg(&sd.dirs[3 * (int64_t)beam + 1]),
                                             __ldg(&sd.dirs[3 * (int64_t)beam + 2]));
+            float sub_range[kEcho ? LIDAR_MAX_SUBRAYS : 1], sub_I[kEcho ? LIDAR_MAX_SUBRAYS : 1];
+            uint32_t sub_tri[kEcho ? LIDAR_MAX_SUBRAYS : 1];
+            bool sub_ok[kEcho ? LIDAR_MAX_SUBRAYS : 1];
             BeamResult best;
             int best_sub = 0;
             float best_I = -1.0f;
@@ -178,6 +144,12 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_sweep_tiles(SceneDev S, con
                 if (!trace_closest4<false>(S, p, sd.t_max, h, nullptr, nullptr, 0)) raise_status(status, ST_STACK);
                 BeamResult res;
                 shade(S, h, r, sd, T, seed, beam, (uint32_t)f.frame, (uint32_t)f.sensor, (uint32_t)k, res);
+                if (kEcho) {
+                    sub_range[k] = res.range;
+                    sub_I[k] = res.intensity;
+                    sub_tri[k] = res.tri;
+                    sub_ok[k] = res.valid != 0;
+                }
                 if (k == 0) best = res;
                 if (res.valid && res.intensity > best_I) {
                     best_I = res.intensity;
@@ -185,7 +157,9 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_sweep_tiles(SceneDev S, con
                     best_sub = k;
                 }
             }
-            write_beam(out, f.beam_offset + beam, best, P, best_sub);
+            const int64_t g = f.beam_offset + beam;
+            write_beam(out, g, best, P, best_sub);
+            if (kEcho) write_echoes(echo, g, sd.n_sub, sub_range, sub_I, sub_tri, sub_ok);
         }
     }
 }
@@ -194,7 +168,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_sweep_tiles(SceneDev S, con
 
 cudaError_t launch_sweep_tiles(cudaStream_t s, const SceneDev& S, const SensorDev* sensors_dev,
                                const SweepDev* frames_dev, int n_frames, const int64_t* tile_prefix_dev,
-                               int64_t n_tiles, TableDev T, uint64_t seed, BeamsOut out, int* status,
+                               int64_t n_tiles, TableDev T, uint64_t seed, BeamsOut out, EchoOut echo, int* status,
                                unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms)
 {
     if (n_tiles == 0) return cudaSuccess;
@@ -205,25 +179,19 @@ cudaError_t launch_sweep_tiles(cudaStream_t s, const SceneDev& S, const SensorDe
     if (grid > (n_tiles + warps - 1) / warps) grid = (n_tiles + warps - 1) / warps;
     const int resident = cfg.block_threads * cfg.blocks_per_sm;
     const int bt = cfg.block_threads;
-    if (resident <= 512)
-        k_sweep_tiles<2><<<(unsigned)grid, bt, 0, s>>>(S, sensors_dev, frames_dev, n_frames, tile_prefix_dev, n_tiles,
-                                                       cfg.tile_rays, T, seed, out, status, work_counter);
-    else if (resident <= 768)
-        k_sweep_tiles<3><<<(unsigned)grid, bt, 0, s>>>(S, sensors_dev, frames_dev, n_frames, tile_prefix_dev, n_tiles,
-                                                       cfg.tile_rays, T, seed, out, status, work_counter);
-    else
-        k_sweep_tiles<4><<<(unsigned)grid, bt, 0, s>>>(S, sensors_dev, frames_dev, n_frames, tile_prefix_dev, n_tiles,
-                                                       cfg.tile_rays, T, seed, out, status, work_counter);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cast_sweep(cudaStream_t s, const SceneDev& S, const SensorDev* sensors_dev,
-                              const SweepDev* frames_dev, int n_frames, int64_t n_total, TableDev T, uint64_t seed,
-                              BeamsOut out, EchoOut echo, int* status)
-{
-    if (n_total == 0) return cudaSuccess;
-    k_cast_sweep<<<(unsigned)((n_total + 127) / 128), 128, 0, s>>>(S, sensors_dev, frames_dev, n_frames, n_total, T,
-                                                                   seed, out, echo, status);
+    const dim3 gd((unsigned)grid);
+#define LIDAR_SWEEP_LAUNCH(MB, EC)                                                                              \
+    k_sweep_tiles<MB, EC><<<gd, bt, 0, s>>>(S, sensors_dev, frames_dev, n_frames, tile_prefix_dev, n_tiles,     \
+                                            cfg.tile_rays, T, seed, out, echo, status, work_counter)
+    const bool ec = echo.n_echoes > 0;
+    if (resident <= 512) {
+        if (ec) LIDAR_SWEEP_LAUNCH(2, true); else LIDAR_SWEEP_LAUNCH(2, false);
+    } else if (resident <= 768) {
+        if (ec) LIDAR_SWEEP_LAUNCH(3, true); else LIDAR_SWEEP_LAUNCH(3, false);
+    } else {
+        if (ec) LIDAR_SWEEP_LAUNCH(4, true); else LIDAR_SWEEP_LAUNCH(4, false);
+    }
+#undef LIDAR_SWEEP_LAUNCH
     return cudaGetLastError();
 }
 

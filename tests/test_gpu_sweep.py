@@ -141,25 +141,39 @@ def test_sweep_rejects_bad_echo_arguments(L):
         assert e.value.status == capi.LIDAR_EINVAL
 
 
-@pytest.mark.parametrize("cfg", [{}, {"ray_order": 0}, {"block_threads": 128, "blocks_per_sm": 4}])
-def test_sweep_persistent_path_equals_per_beam_path(L, cfg):
-    """Without echoes the sweep cast runs the persistent, scheduled tiles; its
-    dense records are bit for bit those of the one-thread-per-beam path."""
+def test_sweep_records_independent_of_echoes_shape_and_schedule(L):
+    """The sweep cast runs on persistent, scheduled warp tiles with or without
+    echoes: its dense records are bit for bit the same with echoes requested or
+    not, at three launch shapes, in beam or Morton order, with the cost
+    schedule, and its echoes are the same at every shape."""
     w = synth.small_terrain(seed=12, n_frames=3, n_az=128, n_subrays=7, divergence=2e-3)
     sw = sweeps_of(w)
     scene, _ = setup(L, w)
     n = L.total_beams(sw)
     cfg0 = L.launch_config()
+    base = L.alloc_beams(n)
+    base_e = L.alloc_echoes(n, 2)
+    L.cast_sweep_into(scene, sw, w.seed, base, base_e, mode=1, separation=0.5)
+    assert L.sync_status() == 0
     try:
-        L.set_launch_config(**cfg)
-        L.schedule_by_cost(scene, w.frames[:1], w.seed, mode=1)
-        a = L.alloc_beams(n)
-        L.cast_sweep_into(scene, sw, w.seed, a)
-        b = L.alloc_beams(n)
-        L.cast_sweep_into(scene, sw, w.seed, b, L.alloc_echoes(n, 2), mode=1, separation=0.5)
-        assert L.sync_status() == 0
+        for cfg in ({}, {"ray_order": 0}, {"block_threads": 128, "blocks_per_sm": 4},
+                    {"block_threads": 64, "blocks_per_sm": 12}):
+            L.set_launch_config(**cfg)
+            for sched in (None, 1):
+                if sched is not None:
+                    L.schedule_by_cost(scene, w.frames[:1], w.seed, mode=sched)
+                a = L.alloc_beams(n)
+                L.cast_sweep_into(scene, sw, w.seed, a)
+                b = L.alloc_beams(n)
+                e = L.alloc_echoes(n, 2)
+                L.cast_sweep_into(scene, sw, w.seed, b, e, mode=1, separation=0.5)
+                assert L.sync_status() == 0
+                for k in base:
+                    assert torch.equal(a[k], base[k]), (cfg, sched, k)
+                    assert torch.equal(b[k], base[k]), (cfg, sched, k)
+                for k in base_e:
+                    assert torch.equal(e[k], base_e[k]), (cfg, sched, k)
+                L.reset_schedule(0)
     finally:
         L.set_launch_config(**cfg0)
         L.reset_schedule(0)
-    for k in a:
-        assert torch.equal(a[k], b[k]), k
