@@ -190,6 +190,17 @@ def run_ours(args, rank, world, local_rank):
     def step():
         L.cast_into(scene, frames, w.seed, None, pts)
 
+    if args.adjoint_only:
+        # the cfg3 fused-MSE backward alone (profiling runs)
+        d3 = cfg3_adjoint(torch, L, scene, tuned_cfg)
+        d3["fwd"]()
+        bwd_ms = event_time(torch, stream, d3["bwd"], flush, reps=args.steps, warm=args.warmup)
+        if L.sync_status() != 0:
+            raise RuntimeError("device status")
+        return {"kernel": "k_adj_absmax + k_adj_accumulate + k_adj_finalize", "bwd_ms": bwd_ms,
+                "beams": d3["n"], "launches": args.warmup + args.steps,
+                "loss": float(d3["loss"].item())} if rank == 0 else None
+
     if args.kernel_only:
         # the roofline's kernel alone (profiling runs): cast to dense valid flags
         dense = L.alloc_beams(n_beams, ("valid",))
@@ -346,6 +357,48 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+TAPE_BYTES_PER_BEAM = 16  # valid 1 + mat 2 + theta 4 + rf 4 (tape) + intensity 4 + valid 1 (targets)
+
+
+def cfg3_adjoint(torch, L, scene, tuned_cfg):
+    """cfg3 (16 frames of the 128-ch sensor): targets from the hidden table, the
+    tape of a forward at the model's table, and closures for the forward, the
+    fused-MSE backward alone and both."""
+    import synth
+    from paper_2208_10295_gb300.tune import apply as apply_cfg
+    w3 = synth.cfg3()
+    L.set_sensor(0, w3.sensors[0])
+    apply_cfg(L, scene, tuned_cfg, w3.frames[:1], w3.seed)
+    th = L.build_tables(torch.tensor(w3.hidden_params, device=L.device))
+    tp = torch.tensor(w3.params, device=L.device)
+    n3 = L.total_beams(w3.frames)
+    tgt = L.alloc_beams(n3, ("valid", "intensity", "mat", "theta_deg", "rf"))
+    L.set_materials(th)
+    L.cast_into(scene, w3.frames, w3.seed, tgt)
+    tape = L.alloc_beams(n3, ("valid", "intensity", "mat", "theta_deg", "rf"))
+    loss = torch.zeros(1, device=L.device)
+    gT = torch.zeros((tp.shape[0], 91), device=L.device)
+    gg = torch.zeros(1, device=L.device)
+
+    def fwd():
+        T = L.build_tables(tp)
+        L.set_materials(T)
+        L.cast_into(scene, w3.frames, w3.seed, tape)
+        return T
+
+    def bwd():
+        gT.zero_()
+        gg.zero_()
+        L.cast_backward_mse(tape, 1.0, tgt["intensity"], tgt["valid"], loss, gT, gg)
+        L.build_tables_backward(tp, gT)
+
+    def fwd_bwd():
+        fwd()
+        bwd()
+
+    return {"n": n3, "fwd": fwd, "bwd": bwd, "fwd_bwd": fwd_bwd, "loss": loss, "tape": tape, "targets": tgt}
+
+
 def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tuned_cfg):
     import synth
     from paper_2208_10295_gb300.tune import apply as apply_cfg
@@ -421,42 +474,28 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
     del sbuf
     L.set_sensor(0, w1.sensors[0])
     # ---- cfg3: 16 frames forward (dense tape) + fused-MSE adjoint vs plain forward
-    w3 = synth.cfg3()
-    L.set_sensor(0, w3.sensors[0])
-    apply_cfg(L, scene, tuned_cfg, w3.frames[:1], w3.seed)
-    th = L.build_tables(torch.tensor(w3.hidden_params, device=L.device))
-    tp = torch.tensor(w3.params, device=L.device)
-    n3 = L.total_beams(w3.frames)
-    tgt = L.alloc_beams(n3, ("valid", "intensity", "mat", "theta_deg", "rf"))
-    L.set_materials(th)
-    L.cast_into(scene, w3.frames, w3.seed, tgt)
-    tape = L.alloc_beams(n3, ("valid", "intensity", "mat", "theta_deg", "rf"))
-    loss = torch.zeros(1, device=L.device)
-    gT = torch.zeros((tp.shape[0], 91), device=L.device)
-    gg = torch.zeros(1, device=L.device)
-
-    def fwd():
-        T = L.build_tables(tp)
-        L.set_materials(T)
-        L.cast_into(scene, w3.frames, w3.seed, tape)
-        return T
-
-    def fwd_bwd():
-        T = fwd()
-        gT.zero_()
-        gg.zero_()
-        L.cast_backward_mse(tape, 1.0, tgt["intensity"], tgt["valid"], loss, gT, gg)
-        L.build_tables_backward(tp, gT)
-
-    f_ms = event_time(torch, stream, fwd, flush, reps=10, warm=2)
-    fb_ms = event_time(torch, stream, fwd_bwd, flush, reps=10, warm=2)
+    d3 = cfg3_adjoint(torch, L, scene, tuned_cfg)
+    f_ms = event_time(torch, stream, d3["fwd"], flush, reps=10, warm=2)
+    fb_ms = event_time(torch, stream, d3["fwd_bwd"], flush, reps=10, warm=2)
+    b_ms = event_time(torch, stream, d3["bwd"], flush, reps=20, warm=3)
+    # the backward's two passes each read the tape and the targets
+    b_bytes = 2 * TAPE_BYTES_PER_BEAM * d3["n"]
+    hbm = float(load_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS))
     out["differentiation"] = {"workload": "cfg3: 128-ch x 2048 az x 16 frames (4,194,304 beams), forward with tape + "
                                           "fused MSE adjoint to the 32x91 table, widths and gain",
                               "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "bwd_ms": fb_ms - f_ms,
-                              "plain_single_frame_fwd_ms": single_ms, "loss": float(loss.item())}
+                              "bwd_alone_ms": b_ms, "plain_single_frame_fwd_ms": single_ms,
+                              "loss": float(d3["loss"].item()),
+                              "bwd_roofline": {"bound": "hbm", "achieved": b_bytes / (b_ms / 1e3) / 1e9,
+                                               "peak": hbm, "unit": "GB/s",
+                                               "frac": b_bytes / (b_ms / 1e3) / 1e9 / hbm,
+                                               "bytes_per_launch": b_bytes,
+                                               "note": "tape + targets (16 B/beam) read by both passes (the "
+                                                       "scale pass, then the fixed-point accumulation); L2 "
+                                                       "flushed before each backward"}}
     L.set_materials(table)
     L.set_sensor(0, w1.sensors[0])
-    del tgt, tape
+    del d3
     # ---- cfg4: the ~10.7M-triangle city, 128-ch x 4096 az x 32 frames x 7 sub-rays
     if not args.no_city:
         w4 = synth.cfg4()
@@ -553,6 +592,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched/differentiation/city measurements")
     ap.add_argument("--no-city", action="store_true", help="skip the 10.7M-triangle city measurement")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the cfg3 fused-MSE backward (warmup + steps calls) and exit")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the cast kernel of the roofline (warmup + steps launches) and exit")
     args = ap.parse_args()
