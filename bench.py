@@ -190,6 +190,34 @@ def run_ours(args, rank, world, local_rank):
     def step():
         L.cast_into(scene, frames, w.seed, None, pts)
 
+    if args.raster_only:
+        # the raster-and-resample path alone on the cfg1 frame (profiling runs): 6 cameras, W = 1024
+        ras = L.alloc_beams(n_beams, ("valid", "tri", "t"))
+        r_ms = event_time(torch, stream, lambda: L.raster_cast_into(scene, frames, w.seed, ras, width=1024,
+                                                                    n_cameras=6), flush,
+                          reps=args.steps, warm=args.warmup)
+        if L.sync_status() != 0:
+            raise RuntimeError("device status")
+        return {"kernel": "k_raster_tris + k_big_scan + k_raster_big + k_gbuffer + k_resample", "ms": r_ms,
+                "width": 1024, "n_cameras": 6, "calls": args.warmup + args.steps} if rank == 0 else None
+
+    if args.city_only:
+        # one frame of the city (7 sub-rays per beam) cast to dense valid flags (profiling runs)
+        w4 = synth.cfg4()
+        scene4 = L.build_scene(w4.scene.verts, w4.scene.tris, w4.scene.mat, w4.scene.inst)
+        L.set_sensor(0, w4.sensors[0])
+        L.set_materials(L.build_tables(torch.tensor(w4.params, device=dev)))
+        cfg4, _ = autotune(L, scene4, w4.frames[:4], w4.seed, schedule_frames=w4.frames[:1],
+                           use_cache=not args.retune, points=True)
+        fr4 = w4.frames[1:2]
+        d4 = L.alloc_beams(L.total_beams(fr4), ("valid",))
+        c_ms = event_time(torch, stream, lambda: L.cast_into(scene4, fr4, w4.seed, d4), flush,
+                          reps=args.steps, warm=args.warmup)
+        if L.sync_status() != 0:
+            raise RuntimeError("device status")
+        return {"kernel": "k_cast", "kernel_ms": c_ms, "launches": args.warmup + args.steps, "launch": cfg4,
+                "subrays": L.total_beams(fr4) * 7} if rank == 0 else None
+
     if args.adjoint_only:
         # the cfg3 fused-MSE backward alone (profiling runs)
         d3 = cfg3_adjoint(torch, L, scene, tuned_cfg)
@@ -509,12 +537,25 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
         pts4 = L.alloc_points(B4.n_beams)
         c_ms = event_time(torch, stream, lambda: B4.cast_into(scene4, w4.seed, None, pts4), None, reps=3, warm=1)
         info = scene4.info()
+        # traversal work of four frames (instrumented kernel), scaled to the 32-frame launch
+        cw = L.count_work(scene4, w4.frames[:4], w4.seed)
+        sub_bytes = (cw["node_visits"] * cw["node_bytes"] + cw["tri_tests"] * 48) / cw["rays"]
+        city_bytes = sub_bytes * B4.n_beams * 7
+        hbm = float(load_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS))
         out["city"] = {"workload": "cfg4: 10.7M-tri city (4096 m terrain + 20,000 buildings), 128-ch x 4096 az x "
                                    "32 frames x 7 sub-rays (0.1 mrad), strongest return, ordered compaction",
                        "tris": int(w4.scene.n_tris), "beams": B4.n_beams, "subrays": B4.n_beams * 7,
                        "ms": c_ms, "subrays_per_s": B4.n_beams * 7 / (c_ms / 1e3),
                        "build_ms": info["build_ms"], "bvh_depth": info["max_depth"],
-                       "points": int(pts4["count"].item()), "launch": cfg4}
+                       "points": int(pts4["count"].item()), "launch": cfg4,
+                       "work_per_subray": {"node_visits": cw["node_visits"] / cw["rays"],
+                                           "tri_tests": cw["tri_tests"] / cw["rays"],
+                                           "node_bytes": cw["node_bytes"],
+                                           "unique_bytes_4_frames": cw["unique_node_bytes"] + cw["unique_tri_bytes"]},
+                       "roofline": {"bound": "hbm", "achieved": city_bytes / (c_ms / 1e3) / 1e9, "peak": hbm,
+                                    "unit": "GB/s", "frac": city_bytes / (c_ms / 1e3) / 1e9 / hbm,
+                                    "note": "algorithmic node and triangle bytes of the traversal (as the "
+                                            "headline roofline), per sub-ray from four frames"}}
         B4.free()
         # multi-echo (first and last of the 7 sub-ray returns, 0.5 m apart) over sweeps of the same trajectory
         sw4 = synth.make_sweep_frames([(0, int(a["frame"]), a["pose"], b["pose"])
@@ -592,6 +633,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched/differentiation/city measurements")
     ap.add_argument("--no-city", action="store_true", help="skip the 10.7M-triangle city measurement")
+    ap.add_argument("--raster-only", action="store_true",
+                    help="time only the raster-and-resample path on the cfg1 frame (warmup + steps calls) and exit")
+    ap.add_argument("--city-only", action="store_true",
+                    help="time only the cast of one city frame with 7 sub-rays (warmup + steps launches) and exit")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="time only the cfg3 fused-MSE backward (warmup + steps calls) and exit")
     ap.add_argument("--kernel-only", action="store_true",

@@ -121,9 +121,15 @@ __device__ __forceinline__ void triangle_box(const RasterCams& C, const RasterFr
     y1 = (int)floorf(fminf(hy, W - 1.0f));
 }
 
+// Boxes above kSmallBox pixels go to a list in row bands of at most
+// kChunkPixels pixels (a box wider than that: one row per entry), so that one
+// warp can take any entry: the pixel work of a large triangle is spread over
+// many warps without a scan or a search.
+constexpr int kChunkPixels = 256;
+
 __global__ void __launch_bounds__(256) k_raster_tris(SceneDev S, RasterCams C, RasterFrame F,
-                                                     unsigned long long* keys, BigBox* big, unsigned* n_big,
-                                                     unsigned big_cap)
+                                                     unsigned long long* keys, BigBox* big,
+                                                     unsigned long long* n_big, unsigned big_cap)
 {
     const int64_t n = (int64_t)C.K * S.n_tris;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n; w += (int64_t)gridDim.x * blockDim.x) {
@@ -136,68 +142,44 @@ __global__ void __launch_bounds__(256) k_raster_tris(SceneDev S, RasterCams C, R
         triangle_box(C, F, k, a, b, c, x0, x1, y0, y1);
         if (x1 < x0 || y1 < y0) continue;
         const int nx = x1 - x0 + 1, ny = y1 - y0 + 1;
+        int y_here = y0;  // rows from here on are tested by this thread
         if (nx * ny > kSmallBox) {
-            const unsigned slot = atomicAdd(n_big, 1u);
-            if (slot < big_cap) {
-                big[slot].cam_leaf = ((uint32_t)k << 26) | (uint32_t)leaf;
-                big[slot].x0 = (uint16_t)x0;
-                big[slot].y0 = (uint16_t)y0;
-                big[slot].nx = (uint16_t)nx;
-                big[slot].ny = (uint16_t)ny;
-                continue;
+            const int rows = max(1, kChunkPixels / nx);
+            const int n_chunks = (ny + rows - 1) / rows;
+            // a 64-bit counter cannot wrap; every slot below the capacity is
+            // written by the box that took it, the bands past it are tested here
+            const unsigned long long slot = atomicAdd(n_big, (unsigned long long)n_chunks);
+            const int fit = slot >= big_cap ? 0 : (int)min((unsigned long long)n_chunks, big_cap - slot);
+            for (int q = 0; q < fit; ++q) {
+                const int r0 = q * rows;
+                BigBox& e = big[slot + q];
+                e.cam_leaf = ((uint32_t)k << 26) | (uint32_t)leaf;
+                e.x0 = (uint16_t)x0;
+                e.y0 = (uint16_t)(y0 + r0);
+                e.nx = (uint16_t)nx;
+                e.ny = (uint16_t)min(rows, ny - r0);
             }
-            // list full: test the box here
+            y_here = y0 + min(ny, fit * rows);
         }
-        for (int iy = y0; iy <= y1; ++iy)
+        for (int iy = y_here; iy <= y1; ++iy)
             for (int ix = x0; ix <= x1; ++ix) raster_pixel(S, C, F, k, leaf, ix, iy, keys);
     }
 }
 
-// exclusive prefix of the listed boxes' pixel counts (one block)
-__global__ void __launch_bounds__(1024) k_big_scan(const BigBox* big, const unsigned* n_big, unsigned big_cap,
-                                                   unsigned long long* offsets)
-{
-    __shared__ unsigned long long s_part[1024];
-    const unsigned n = min(*n_big, big_cap);
-    const unsigned per = (n + blockDim.x - 1) / blockDim.x;
-    const unsigned lo = threadIdx.x * per, hi = min(lo + per, n);
-    unsigned long long sum = 0;
-    for (unsigned i = lo; i < hi; ++i) sum += (unsigned long long)big[i].nx * big[i].ny;
-    s_part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        const unsigned long long v = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0ull;
-        __syncthreads();
-        s_part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    unsigned long long run = s_part[threadIdx.x] - sum;
-    for (unsigned i = lo; i < hi; ++i) {
-        offsets[i] = run;
-        run += (unsigned long long)big[i].nx * big[i].ny;
-    }
-    if (threadIdx.x == blockDim.x - 1) offsets[n] = s_part[threadIdx.x];
-}
-
-// the listed boxes' pixels, spread evenly: work item w -> box by binary search
+// the listed row bands, one warp per band
 __global__ void __launch_bounds__(256) k_raster_big(SceneDev S, RasterCams C, RasterFrame F, const BigBox* big,
-                                                    const unsigned* n_big, unsigned big_cap,
-                                                    const unsigned long long* offsets, unsigned long long* keys)
+                                                    const unsigned long long* n_big, unsigned big_cap,
+                                                    unsigned long long* keys)
 {
-    const unsigned n = min(*n_big, big_cap);
-    if (n == 0) return;
-    const unsigned long long total = offsets[n];
-    for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < total;
-         w += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned lo = 0, hi = n - 1;  // last box with offset <= w
-        while (lo < hi) {
-            const unsigned mid = (lo + hi + 1) >> 1;
-            if (offsets[mid] <= w) lo = mid; else hi = mid - 1;
-        }
-        const BigBox bx = big[lo];
-        const unsigned local = (unsigned)(w - offsets[lo]);
-        const int ix = bx.x0 + (int)(local % bx.nx), iy = bx.y0 + (int)(local / bx.nx);
-        raster_pixel(S, C, F, (int)(bx.cam_leaf >> 26), (int)(bx.cam_leaf & ((1u << 26) - 1)), ix, iy, keys);
+    const unsigned n = (unsigned)min(*n_big, (unsigned long long)big_cap);
+    const int lane = threadIdx.x & 31;
+    const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
+    for (unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < n; e += n_warps) {
+        const BigBox bx = big[e];
+        const int k = (int)(bx.cam_leaf >> 26), leaf = (int)(bx.cam_leaf & ((1u << 26) - 1));
+        const int nxy = (int)bx.nx * bx.ny;
+        for (int q = lane; q < nxy; q += 32)
+            raster_pixel(S, C, F, k, leaf, bx.x0 + q % bx.nx, bx.y0 + q / bx.nx, keys);
     }
 }
 
@@ -350,13 +332,12 @@ size_t raster_scratch_bytes(int width, int n_cameras, int64_t n_tris, bool with_
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t px = (size_t)n_cameras * width * width;
     const size_t cap = raster_big_capacity(n_cameras, n_tris);
-    return al(px * 8) + 3 * al(px * 4) + (with_tri ? al(px * 4) : 0) + al(cap * sizeof(BigBox)) +
-           al((cap + 1) * 8) + 256;
+    return al(px * 8) + 3 * al(px * 4) + (with_tri ? al(px * 4) : 0) + al(cap * sizeof(BigBox)) + 256;
 }
 
 size_t raster_big_capacity(int n_cameras, int64_t n_tris)
 {
-    return (size_t)(((int64_t)n_cameras * n_tris) / 8 + 4096);
+    return (size_t)(((int64_t)n_cameras * n_tris) / 4 + 65536);
 }
 
 cudaError_t launch_invert_leaf_order(cudaStream_t s, const uint32_t* leaf_tri, int64_t n, uint32_t* orig_to_leaf)
@@ -382,18 +363,16 @@ cudaError_t launch_rasterise(cudaStream_t s, const SceneDev& S, const RasterCams
     G.tri = with_tri ? (uint32_t*)p : nullptr;
     if (with_tri) p += al(px * 4);
     BigBox* big = (BigBox*)p; p += al((size_t)cap * sizeof(BigBox));
-    unsigned long long* offsets = (unsigned long long*)p; p += al(((size_t)cap + 1) * 8);
-    unsigned* n_big = (unsigned*)p;
+    unsigned long long* n_big = (unsigned long long*)p;
     cudaError_t e = cudaMemsetAsync(keys, 0xFF, px * 8, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(n_big, 0, sizeof(unsigned), s);
+    e = cudaMemsetAsync(n_big, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if (S.n_tris > 0) {
         const int64_t work = (int64_t)C.K * S.n_tris;
         const int64_t blocks = std::min<int64_t>((work + 255) / 256, (int64_t)num_sms * 16);
         k_raster_tris<<<(unsigned)blocks, 256, 0, s>>>(S, C, F, keys, big, n_big, cap);
-        k_big_scan<<<1, 1024, 0, s>>>(big, n_big, cap, offsets);
-        k_raster_big<<<(unsigned)num_sms * 16, 256, 0, s>>>(S, C, F, big, n_big, cap, offsets, keys);
+        k_raster_big<<<(unsigned)num_sms * 16, 256, 0, s>>>(S, C, F, big, n_big, cap, keys);
     }
     const int64_t gb = std::min<int64_t>(((int64_t)px + 255) / 256, (int64_t)num_sms * 16);
     k_gbuffer<<<(unsigned)gb, 256, 0, s>>>(S, C, F, keys, orig_to_leaf, G);
