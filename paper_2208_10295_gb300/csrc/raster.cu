@@ -9,12 +9,13 @@
 // n_y = c - f y/z) and goes through the same noise, Eq. 4 lookup, Eq. 5
 // capability test and intensity as the ray-cast path.
 //
-// Rasterisation: one thread per (camera, triangle) clips the triangle at the
-// near plane, projects it and bounds the pixel centres it can cover; each of
-// those pixels tests its centre ray against the triangle with the watertight
-// test of the ray-cast path and keeps the closest (t, original index) by a
-// 64-bit atomicMin — the z-buffer.  Small boxes are tested by that thread;
-// larger ones go to a list whose pixels are spread evenly over the grid.
+// Rasterisation: one thread per triangle finds the cameras whose azimuth
+// sectors its horizontal extent can reach, and for each clips the triangle at
+// the near plane, projects it and bounds the pixel centres it can cover; each
+// of those pixels tests its centre ray against the triangle with the
+// watertight test of the ray-cast path and keeps the closest (t, original
+// index) by a 64-bit atomicMin — the z-buffer.  Small boxes are tested by that
+// thread; larger ones go to a list of row bands that warps take.
 #include "common.cuh"
 #include "philox.cuh"
 #include "trace.cuh"
@@ -127,42 +128,95 @@ __device__ __forceinline__ void triangle_box(const RasterCams& C, const RasterFr
 // many warps without a scan or a search.
 constexpr int kChunkPixels = 256;
 
+// Cameras (bit k = camera k) whose azimuth sector [-pi + k 2pi/K, -pi + (k+1)
+// 2pi/K) the triangle can reach: camera k's pixel centres see only directions
+// of azimuth inside its sector (u = tan of the azimuth off its axis), so a
+// triangle whose horizontal projection, seen from the sensor axis, spans the
+// arc [lo, lo + len] (len < pi: the projection leaves out the axis) reaches
+// the sectors that arc meets.  Widened by 1e-3 rad against rounding; every
+// camera when a vertex lies (nearly) on the axis or the arc cannot be bounded.
+__device__ __forceinline__ unsigned long long camera_mask(const RasterCams& C, const float* pose, float4 a, float4 b,
+                                                          float4 c)
+{
+    const unsigned long long all = C.K >= 64 ? ~0ull : ((1ull << C.K) - 1ull);
+    const float vx[3] = {a.x - pose[3], b.x - pose[3], c.x - pose[3]};
+    const float vy[3] = {a.y - pose[7], b.y - pose[7], c.y - pose[7]};
+    const float vz[3] = {a.z - pose[11], b.z - pose[11], c.z - pose[11]};
+    float az[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        // sensor-frame x and y: the pose's rotation transposed
+        const float sx = vx[j] * pose[0] + vy[j] * pose[4] + vz[j] * pose[8];
+        const float sy = vx[j] * pose[1] + vy[j] * pose[5] + vz[j] * pose[9];
+        // sx, sy carry rounding errors of ~2e-7 of the vertex's distance: keep
+        // their angle's error below the margin, else take every camera
+        if (fabsf(sx) + fabsf(sy) < 1e-3f * (fabsf(vx[j]) + fabsf(vy[j]) + fabsf(vz[j])) + 1e-6f) return all;
+        az[j] = atan2f(sy, sx);
+    }
+    // sort the three azimuths, then the arc is the circle minus the largest gap
+    float t;
+    if (az[0] > az[1]) { t = az[0]; az[0] = az[1]; az[1] = t; }
+    if (az[1] > az[2]) { t = az[1]; az[1] = az[2]; az[2] = t; }
+    if (az[0] > az[1]) { t = az[0]; az[0] = az[1]; az[1] = t; }
+    const float two_pi = 6.28318530717958648f;
+    const float g0 = az[1] - az[0], g1 = az[2] - az[1], g2 = az[0] + two_pi - az[2];
+    float lo, gap;
+    if (g0 >= g1 && g0 >= g2) { gap = g0; lo = az[1]; }
+    else if (g1 >= g2) { gap = g1; lo = az[2]; }
+    else { gap = g2; lo = az[0]; }
+    if (gap <= 3.14159265358979324f + 2e-3f) return all;  // the projection may surround the axis
+    const float eps = 1e-3f;
+    const float sector = two_pi / (float)C.K;
+    const float start = lo - eps + 3.14159265358979324f;  // measured from -pi
+    const float len = two_pi - gap + 2.0f * eps;
+    int k0 = (int)floorf(start / sector);
+    const int k1 = (int)floorf((start + len) / sector);
+    const int count = min(k1 - k0 + 1, C.K);
+    k0 = ((k0 % C.K) + C.K) % C.K;
+    unsigned long long m = 0;
+    for (int i = 0; i < count; ++i) m |= 1ull << ((k0 + i) % C.K);
+    return m;
+}
+
 __global__ void __launch_bounds__(256) k_raster_tris(SceneDev S, RasterCams C, RasterFrame F,
                                                      unsigned long long* keys, BigBox* big,
                                                      unsigned long long* n_big, unsigned big_cap)
 {
-    const int64_t n = (int64_t)C.K * S.n_tris;
-    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n; w += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(w / S.n_tris);
-        const int leaf = (int)(w - (int64_t)k * S.n_tris);
-        const float4 a = __ldg(&S.tris[3 * (int64_t)leaf]);
-        const float4 b = __ldg(&S.tris[3 * (int64_t)leaf + 1]);
-        const float4 c = __ldg(&S.tris[3 * (int64_t)leaf + 2]);
-        int x0, x1, y0, y1;
-        triangle_box(C, F, k, a, b, c, x0, x1, y0, y1);
-        if (x1 < x0 || y1 < y0) continue;
-        const int nx = x1 - x0 + 1, ny = y1 - y0 + 1;
-        int y_here = y0;  // rows from here on are tested by this thread
-        if (nx * ny > kSmallBox) {
-            const int rows = max(1, kChunkPixels / nx);
-            const int n_chunks = (ny + rows - 1) / rows;
-            // a 64-bit counter cannot wrap; every slot below the capacity is
-            // written by the box that took it, the bands past it are tested here
-            const unsigned long long slot = atomicAdd(n_big, (unsigned long long)n_chunks);
-            const int fit = slot >= big_cap ? 0 : (int)min((unsigned long long)n_chunks, big_cap - slot);
-            for (int q = 0; q < fit; ++q) {
-                const int r0 = q * rows;
-                BigBox& e = big[slot + q];
-                e.cam_leaf = ((uint32_t)k << 26) | (uint32_t)leaf;
-                e.x0 = (uint16_t)x0;
-                e.y0 = (uint16_t)(y0 + r0);
-                e.nx = (uint16_t)nx;
-                e.ny = (uint16_t)min(rows, ny - r0);
+    for (int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; leaf < S.n_tris;
+         leaf += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldg(&S.tris[3 * leaf]);
+        const float4 b = __ldg(&S.tris[3 * leaf + 1]);
+        const float4 c = __ldg(&S.tris[3 * leaf + 2]);
+        unsigned long long cams = camera_mask(C, F.pose, a, b, c);
+        while (cams) {
+            const int k = __ffsll((long long)cams) - 1;
+            cams &= cams - 1;
+            int x0, x1, y0, y1;
+            triangle_box(C, F, k, a, b, c, x0, x1, y0, y1);
+            if (x1 < x0 || y1 < y0) continue;
+            const int nx = x1 - x0 + 1, ny = y1 - y0 + 1;
+            int y_here = y0;  // rows from here on are tested by this thread
+            if (nx * ny > kSmallBox) {
+                const int rows = max(1, kChunkPixels / nx);
+                const int n_chunks = (ny + rows - 1) / rows;
+                // a 64-bit counter cannot wrap; every slot below the capacity is
+                // written by the box that took it, the bands past it are tested here
+                const unsigned long long slot = atomicAdd(n_big, (unsigned long long)n_chunks);
+                const int fit = slot >= big_cap ? 0 : (int)min((unsigned long long)n_chunks, big_cap - slot);
+                for (int q = 0; q < fit; ++q) {
+                    const int r0 = q * rows;
+                    BigBox& e = big[slot + q];
+                    e.cam_leaf = ((uint32_t)k << 26) | (uint32_t)leaf;
+                    e.x0 = (uint16_t)x0;
+                    e.y0 = (uint16_t)(y0 + r0);
+                    e.nx = (uint16_t)nx;
+                    e.ny = (uint16_t)min(rows, ny - r0);
+                }
+                y_here = y0 + min(ny, fit * rows);
             }
-            y_here = y0 + min(ny, fit * rows);
+            for (int iy = y_here; iy <= y1; ++iy)
+                for (int ix = x0; ix <= x1; ++ix) raster_pixel(S, C, F, k, (int)leaf, ix, iy, keys);
         }
-        for (int iy = y_here; iy <= y1; ++iy)
-            for (int ix = x0; ix <= x1; ++ix) raster_pixel(S, C, F, k, leaf, ix, iy, keys);
     }
 }
 
@@ -369,8 +423,7 @@ cudaError_t launch_rasterise(cudaStream_t s, const SceneDev& S, const RasterCams
     e = cudaMemsetAsync(n_big, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if (S.n_tris > 0) {
-        const int64_t work = (int64_t)C.K * S.n_tris;
-        const int64_t blocks = std::min<int64_t>((work + 255) / 256, (int64_t)num_sms * 16);
+        const int64_t blocks = std::min<int64_t>((S.n_tris + 255) / 256, (int64_t)num_sms * 16);
         k_raster_tris<<<(unsigned)blocks, 256, 0, s>>>(S, C, F, keys, big, n_big, cap);
         k_raster_big<<<(unsigned)num_sms * 16, 256, 0, s>>>(S, C, F, big, n_big, cap, keys);
     }
