@@ -102,7 +102,7 @@ def _pick(g, w, samples):
     return {k: v[idx] for k, v in g.items()}
 
 
-@pytest.mark.parametrize("width,n_cameras", [(512, 6), (300, 5)])
+@pytest.mark.parametrize("width,n_cameras", [(512, 6), (300, 5), (256, 3), (96, 64)])
 def test_raster_cfg0_every_beam(L, width, n_cameras):
     w = synth.cfg0()
     g, _ = gpu_raster(L, w, width, n_cameras)
