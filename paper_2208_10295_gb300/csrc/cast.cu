@@ -306,14 +306,27 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
     }
     if (cc.counts && fused) {
         // cooperative launch: every block of the grid is resident, so the grid
-        // can wait for the cast, scan the tile counts, then scatter the points
+        // can wait until every kept return is counted; then each block
+        // scatters a contiguous run of tiles, whose first offset is the sum of
+        // the (final) counts before the run — no scan and no second wait
         if (!grid_barrier(cc.done, 1, status)) return;
-        if (blockIdx.x == 0) scan_counts_block(cc);
-        if (!grid_barrier(cc.done, 2, status)) return;
         __shared__ uint32_t s_warp[kScatterItems * 8];
-        for (int64_t t = blockIdx.x; t < cc.n_tiles; t += gridDim.x)
-            scatter_tile(sensors, frames, n_frames, n_beams_total, out, t, __ldcg(&cc.offsets[t]), pts, status,
-                         s_warp);
+        __shared__ long long s_red[8];
+        const int64_t t0 = (int64_t)blockIdx.x * cc.n_tiles / gridDim.x;
+        const int64_t t1 = ((int64_t)blockIdx.x + 1) * cc.n_tiles / gridDim.x;
+        long long before = 0;
+        for (int64_t i = threadIdx.x; i < t0; i += blockDim.x) before += __ldcg(&cc.counts[i]);
+        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+        if (lane == 0) s_red[threadIdx.x >> 5] = before;
+        __syncthreads();
+        long long run = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) run += s_red[w];
+        for (int64_t t = t0; t < t1; ++t) {
+            scatter_tile(sensors, frames, n_frames, n_beams_total, out, t, run, pts, status, s_warp);
+            run += __ldcg(&cc.counts[t]);
+        }
+        // the block holding the last tile knows the total
+        if (t1 == cc.n_tiles && threadIdx.x == 0 && cc.total) *cc.total = run;
     } else if (cc.counts) {
         __shared__ bool s_last;
         __syncthreads();
