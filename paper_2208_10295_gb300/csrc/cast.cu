@@ -159,6 +159,13 @@ struct CompactCounts {
     int64_t n_tiles;
 };
 
+// byte offset, from the tile counts, of the cast's 64-bit work counter: after
+// the counts and the finished-block word, 8-byte aligned
+static size_t compact_counter_offset(int64_t n_tiles)
+{
+    return (size_t)(((n_tiles + 1) * 4 + 7) / 8 * 8);
+}
+
 __device__ __forceinline__ void count_kept_warp(const CompactCounts& cc, bool kept, int64_t dense_index, int lane)
 {
     const unsigned vm = __ballot_sync(0xffffffffu, kept);
@@ -460,7 +467,6 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
 {
     if (scattered) *scattered = false;
     if (n_tiles == 0) return cudaSuccess;
-    cudaMemsetAsync(work_counter, 0, sizeof(unsigned long long), s);
     const int64_t warps = cfg.block_threads / 32;
     int64_t grid = (int64_t)num_sms * cfg.blocks_per_sm;
     if (grid > (n_tiles + warps - 1) / warps) grid = (n_tiles + warps - 1) / warps;
@@ -490,11 +496,16 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
         a.cc.counts = (unsigned*)((char*)compact_scratch + ((nt * 8 + 255) / 256) * 256);
         a.cc.done = a.cc.counts + nt;
         a.cc.total = n_points_dev;
-        cudaMemsetAsync(a.cc.counts, 0, (nt + 1) * sizeof(unsigned), s);
+        // the work counter sits behind the tile counts: one memset clears all
+        const size_t wc_off = compact_counter_offset(nt);
+        a.work_counter = (unsigned long long*)((char*)a.cc.counts + wc_off);
+        cudaMemsetAsync(a.cc.counts, 0, wc_off + sizeof(unsigned long long), s);
         if (points && cfg.fused_scatter) {
             a.pts = *points;
             a.fused = 1;
         }
+    } else {
+        cudaMemsetAsync(work_counter, 0, sizeof(unsigned long long), s);
     }
     // dynamic shared memory: the per-lane traversals keep kSharedStack stack
     // entries per thread there; the warp-synchronous one uses none.  It
@@ -567,7 +578,7 @@ cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_word
 size_t fused_compact_scratch_bytes(int64_t n)
 {
     const int64_t nt = (n + kCompactTileBeams - 1) / kCompactTileBeams;
-    return ((nt * 8 + 255) / 256) * 256 + (((nt + 1) * 4 + 255) / 256) * 256;
+    return ((nt * 8 + 255) / 256) * 256 + ((compact_counter_offset(nt) + 8 + 255) / 256) * 256;
 }
 
 cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev, int n_frames,
