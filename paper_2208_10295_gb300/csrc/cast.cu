@@ -244,19 +244,23 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                                               const int64_t* __restrict__ tile_prefix, int64_t n_tiles,
                                               TableDev T, uint64_t seed, BeamsOut out, int* status,
                                               unsigned long long* work_counter, int tile_rays, WorkCount wc,
-                                              CompactCounts cc, lidar_points pts, int64_t n_beams_total, int fused)
+                                              CompactCounts cc, lidar_points pts, int64_t n_beams_total, int fused,
+                                              const __grid_constant__ InlineFrames inl)
 {
     const int lane = threadIdx.x & 31;
+    // frames and their first tiles: from the launch parameters when they came inline
+    const FrameDev* fr_tab = inl.n ? inl.f : frames;
+    const int64_t* tile_first = inl.n ? inl.prefix : tile_prefix;
     extern __shared__ int2 sh_stack[];  // [kSharedStack][blockDim.x]
     while (true) {
         unsigned long long claimed = 0;
         if (lane == 0) claimed = atomicAdd(work_counter, 1ull);
         const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, claimed, 0);
         if (tile >= n_tiles) break;
-        const int fi = find_frame(tile_prefix, n_frames, tile);
-        const FrameDev& fr = frames[fi];
+        const int fi = find_frame(tile_first, n_frames, tile);
+        const FrameDev& fr = fr_tab[fi];
         const SensorDev& sd = sensors[fr.sensor];
-        const int64_t base = (tile - tile_prefix[fi]) * tile_rays;
+        const int64_t base = (tile - tile_first[fi]) * tile_rays;
         for (int j0 = 0; j0 < tile_rays; j0 += 32) {
             const int64_t pos = base + j0 + lane;
             const bool active = pos < sd.n_beams;
@@ -329,7 +333,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
         long long run = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) run += s_red[w];
         for (int64_t t = t0; t < t1; ++t) {
-            scatter_tile(sensors, frames, n_frames, n_beams_total, out, t, run, pts, status, s_warp);
+            scatter_tile(sensors, fr_tab, n_frames, n_beams_total, out, t, run, pts, status, s_warp);
             run += __ldcg(&cc.counts[t]);
         }
         // the block holding the last tile knows the total
@@ -359,10 +363,12 @@ static_assert(kCompactTile == kCompactTileBeams, "the scatter tiles are the cast
 // One compaction tile (kCompactTileBeams beams) per block.
 __global__ void __launch_bounds__(kCompactThreads) k_scatter_points(
     const SensorDev* __restrict__ sensors, const FrameDev* __restrict__ frames, int n_frames, int64_t n,
-    BeamsOut dense, const int64_t* __restrict__ tile_offsets, lidar_points pts, int* status)
+    BeamsOut dense, const int64_t* __restrict__ tile_offsets, lidar_points pts, int* status,
+    const __grid_constant__ InlineFrames inl)
 {
     __shared__ uint32_t s_warp[kScatterItems * 8];
-    scatter_tile(sensors, frames, n_frames, n, dense, blockIdx.x, tile_offsets[blockIdx.x], pts, status, s_warp);
+    scatter_tile(sensors, inl.n ? inl.f : frames, n_frames, n, dense, blockIdx.x, tile_offsets[blockIdx.x], pts,
+                 status, s_warp);
 }
 
 // ------------------------------------------------------------------ ray order
@@ -419,6 +425,7 @@ struct CastArgs {
     lidar_points pts;
     int64_t n_total;
     int fused;
+    InlineFrames inl;
 };
 
 template <bool C, int V, int W>
@@ -447,12 +454,12 @@ cudaError_t launch_one(cudaStream_t s, CastArgs a, int64_t grid, int block, size
         if (grid > (int64_t)per_sm * num_sms) grid = (int64_t)per_sm * num_sms;
         void* args[] = {&a.scene, &a.sensors, &a.frames, &a.n_frames, &a.prefix, &a.n_tiles, &a.table, &a.seed,
                         &a.out, &a.status, &a.work_counter, &a.tile_rays, &a.wc, &a.cc, &a.pts, &a.n_total,
-                        &a.fused};
+                        &a.fused, &a.inl};
         return cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)grid), dim3(block), args, smem, s);
     }
     fn<<<(unsigned)grid, block, smem, s>>>(a.scene, a.sensors, a.frames, a.n_frames, a.prefix, a.n_tiles, a.table,
                                             a.seed, a.out, a.status, a.work_counter, a.tile_rays, a.wc, a.cc, a.pts,
-                                            a.n_total, a.fused);
+                                            a.n_total, a.fused, a.inl);
     return cudaGetLastError();
 }
 
@@ -463,7 +470,8 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                         int64_t n_tiles, TableDev table, uint64_t seed, BeamsOut out, int* status,
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
                         int64_t n_beams_total, const WorkCount* count, void* compact_scratch,
-                        int64_t* n_points_dev, const lidar_points* points, bool* scattered)
+                        int64_t* n_points_dev, const lidar_points* points, bool* scattered,
+                        const InlineFrames* inline_frames)
 {
     if (scattered) *scattered = false;
     if (n_tiles == 0) return cudaSuccess;
@@ -489,6 +497,7 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     a.tile_rays = cfg.tile_rays;
     a.wc = count ? *count : WorkCount{nullptr, nullptr, nullptr, nullptr};
     a.n_total = n_beams_total;
+    if (inline_frames) a.inl = *inline_frames;  // else n == 0: the device table
     if (compact_scratch) {
         const int64_t nt = (n_beams_total + kCompactTileBeams - 1) / kCompactTileBeams;
         a.cc.n_tiles = nt;
@@ -582,12 +591,15 @@ size_t fused_compact_scratch_bytes(int64_t n)
 }
 
 cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev, int n_frames,
-                           int64_t n, BeamsOut dense, const lidar_points& pts, void* compact_scratch, int* status)
+                           int64_t n, BeamsOut dense, const lidar_points& pts, void* compact_scratch, int* status,
+                           const InlineFrames* inline_frames)
 {
     const int64_t tiles = (n + kCompactTile - 1) / kCompactTile;
     if (tiles == 0) return cudaSuccess;
+    InlineFrames inl{};
+    if (inline_frames) inl = *inline_frames;
     k_scatter_points<<<(unsigned)tiles, kCompactThreads, 0, s>>>(sensors_dev, frames_dev, n_frames, n, dense,
-                                                                 (const int64_t*)compact_scratch, pts, status);
+                                                                 (const int64_t*)compact_scratch, pts, status, inl);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,15 @@ struct FrameDev {
     float pose[12];
 };
 
+// A few frames travel inside the kernel's launch parameters instead of a
+// device table (no copy ahead of the launch); n == 0: use the device table.
+constexpr int kInlineFrames = 4;
+struct InlineFrames {
+    FrameDev f[kInlineFrames];
+    int64_t prefix[kInlineFrames];  // first tile of each frame
+    int n;
+};
+
 struct TableDev {
     const float* table;       // [n_mat][91]
     int32_t n_mat;
@@ -155,7 +164,7 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
                         int64_t n_beams_total, const WorkCount* count = nullptr, void* compact_scratch = nullptr,
                         int64_t* n_points_dev = nullptr, const lidar_points* points = nullptr,
-                        bool* scattered = nullptr);
+                        bool* scattered = nullptr, const InlineFrames* inline_frames = nullptr);
 // ordered compaction fused with the cast: the cast counts kept returns per
 // 1024-beam tile and scans them (compact_scratch of fused_compact_scratch_bytes);
 // with `points` and cfg.fused_scatter it also writes the points after a
@@ -164,7 +173,7 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
 size_t fused_compact_scratch_bytes(int64_t n_beams_total);
 cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev, int n_frames,
                            int64_t n_beams_total, BeamsOut dense, const lidar_points& pts, void* compact_scratch,
-                           int* status);
+                           int* status, const InlineFrames* inline_frames = nullptr);
 cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_words, unsigned long long* total);
 // frames[i].pose = poses[12 i .. 12 i + 11]
 cudaError_t launch_set_poses(cudaStream_t s, FrameDev* frames, int n_frames, const float* poses);

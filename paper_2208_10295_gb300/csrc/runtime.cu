@@ -567,8 +567,11 @@ lidar_status lidar_set_materials(lidar_ctx* c, const float* table, int32_t M)
 }
 
 // shared front half of the cast entry points
+// Frame records and tile prefix of a cast.  With `inl` and at most
+// kInlineFrames frames they go into *inl (the launch parameters) and nothing
+// is copied to the device; otherwise into the device table.
 static lidar_status prepare_frames(lidar_ctx* c, const lidar_frame* frames, int32_t n_frames, int64_t* n_beams_total,
-                                   int64_t* n_tiles)
+                                   int64_t* n_tiles, InlineFrames* inl = nullptr)
 {
     LIDAR_CHECK_ARG(frames != nullptr && n_frames > 0, "lidar_cast: need at least one frame");
     std::vector<FrameDev> fd((size_t)n_frames);
@@ -590,6 +593,17 @@ static lidar_status prepare_frames(lidar_ctx* c, const lidar_frame* frames, int3
         prefix[k] = tiles;
         off += c->slots[s].n_beams;
         tiles += (c->slots[s].n_beams + tr - 1) / tr;
+    }
+    if (inl) inl->n = 0;
+    if (inl && n_frames <= kInlineFrames) {
+        for (int32_t k = 0; k < n_frames; ++k) {
+            inl->f[k] = fd[k];
+            inl->prefix[k] = prefix[k];
+        }
+        inl->n = n_frames;
+        *n_beams_total = off;
+        *n_tiles = tiles;
+        return LIDAR_OK;
     }
     // frame table and tile prefix travel as one block: frames, then the prefix at a 256-byte boundary
     const size_t prefix_at = ((size_t)n_frames * sizeof(FrameDev) + 255) / 256 * 256;
@@ -658,7 +672,7 @@ static lidar_status traversal_available(const lidar_ctx* c, const lidar_scene* s
 static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const FrameDev* frames_dev,
                               const int64_t* prefix_dev, int32_t n_frames, int64_t n_total, int64_t n_tiles,
                               uint64_t seed, const lidar_beams* beams, const lidar_points* points,
-                              int64_t* n_points_dev, bool may_alloc)
+                              int64_t* n_points_dev, bool may_alloc, const InlineFrames* inl = nullptr)
 {
     lidar_status tst = traversal_available(c, scene, "cast");
     if (tst != LIDAR_OK) return tst;
@@ -697,10 +711,10 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
     bool scattered = false;
     LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, frames_dev, n_frames, prefix_dev, n_tiles, c->table, seed,
                            out, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total, nullptr, comp,
-                           n_points_dev, points, &scattered));
+                           n_points_dev, points, &scattered, inl));
     if (points && !scattered)
         LIDAR_CUDA(launch_scatter(c->stream, c->sensors_dev, frames_dev, n_frames, n_total, out, *points, comp,
-                                  c->status_dev));
+                                  c->status_dev, inl));
     return LIDAR_OK;
 }
 
@@ -725,10 +739,11 @@ lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_fram
     if (st != LIDAR_OK) return st;
     DeviceGuard g(c->device);
     int64_t n_total = 0, n_tiles = 0;
-    st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles);
+    InlineFrames inl;
+    st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles, &inl);
     if (st != LIDAR_OK) return st;
     return cast_impl(c, scene, c->frames_dev, c->tile_prefix_dev, n_frames, n_total, n_tiles, seed, beams, points,
-                     n_points_dev, true);
+                     n_points_dev, true, &inl);
 }
 
 }  // extern "C"
