@@ -245,9 +245,13 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                                               TableDev T, uint64_t seed, BeamsOut out, int* status,
                                               unsigned long long* work_counter, int tile_rays, WorkCount wc,
                                               CompactCounts cc, lidar_points pts, int64_t n_beams_total, int fused,
-                                              const __grid_constant__ InlineFrames inl)
+                                              const __grid_constant__ InlineFrames inl, unsigned* zero_next,
+                                              int64_t zero_words)
 {
     const int lane = threadIdx.x & 31;
+    // clear the counter region of the cast before this one, for the cast after it
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < zero_words; i += (int64_t)gridDim.x * blockDim.x)
+        zero_next[i] = 0u;
     // frames and their first tiles: from the launch parameters when they came inline
     const FrameDev* fr_tab = inl.n ? inl.f : frames;
     const int64_t* tile_first = inl.n ? inl.prefix : tile_prefix;
@@ -426,6 +430,8 @@ struct CastArgs {
     int64_t n_total;
     int fused;
     InlineFrames inl;
+    unsigned* zero_next;
+    int64_t zero_words;
 };
 
 template <bool C, int V, int W>
@@ -454,12 +460,12 @@ cudaError_t launch_one(cudaStream_t s, CastArgs a, int64_t grid, int block, size
         if (grid > (int64_t)per_sm * num_sms) grid = (int64_t)per_sm * num_sms;
         void* args[] = {&a.scene, &a.sensors, &a.frames, &a.n_frames, &a.prefix, &a.n_tiles, &a.table, &a.seed,
                         &a.out, &a.status, &a.work_counter, &a.tile_rays, &a.wc, &a.cc, &a.pts, &a.n_total,
-                        &a.fused, &a.inl};
+                        &a.fused, &a.inl, &a.zero_next, &a.zero_words};
         return cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)grid), dim3(block), args, smem, s);
     }
     fn<<<(unsigned)grid, block, smem, s>>>(a.scene, a.sensors, a.frames, a.n_frames, a.prefix, a.n_tiles, a.table,
                                             a.seed, a.out, a.status, a.work_counter, a.tile_rays, a.wc, a.cc, a.pts,
-                                            a.n_total, a.fused, a.inl);
+                                            a.n_total, a.fused, a.inl, a.zero_next, a.zero_words);
     return cudaGetLastError();
 }
 
@@ -471,7 +477,7 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
                         int64_t n_beams_total, const WorkCount* count, void* compact_scratch,
                         int64_t* n_points_dev, const lidar_points* points, bool* scattered,
-                        const InlineFrames* inline_frames)
+                        const InlineFrames* inline_frames, const CounterRegion* region)
 {
     if (scattered) *scattered = false;
     if (n_tiles == 0) return cudaSuccess;
@@ -498,21 +504,29 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     a.wc = count ? *count : WorkCount{nullptr, nullptr, nullptr, nullptr};
     a.n_total = n_beams_total;
     if (inline_frames) a.inl = *inline_frames;  // else n == 0: the device table
+    const bool clean = region && region->clean;
+    if (region) {
+        a.zero_next = region->zero_next;
+        a.zero_words = region->zero_next ? region->zero_words : 0;
+    }
     if (compact_scratch) {
         const int64_t nt = (n_beams_total + kCompactTileBeams - 1) / kCompactTileBeams;
         a.cc.n_tiles = nt;
         a.cc.offsets = (int64_t*)compact_scratch;
-        a.cc.counts = (unsigned*)((char*)compact_scratch + ((nt * 8 + 255) / 256) * 256);
+        a.cc.counts = region ? region->base : (unsigned*)((char*)compact_scratch + ((nt * 8 + 255) / 256) * 256);
         a.cc.done = a.cc.counts + nt;
         a.cc.total = n_points_dev;
         // the work counter sits behind the tile counts: one memset clears all
         const size_t wc_off = compact_counter_offset(nt);
         a.work_counter = (unsigned long long*)((char*)a.cc.counts + wc_off);
-        cudaMemsetAsync(a.cc.counts, 0, wc_off + sizeof(unsigned long long), s);
+        if (!clean) cudaMemsetAsync(a.cc.counts, 0, wc_off + sizeof(unsigned long long), s);
         if (points && cfg.fused_scatter) {
             a.pts = *points;
             a.fused = 1;
         }
+    } else if (region) {
+        a.work_counter = (unsigned long long*)region->base;
+        if (!clean) cudaMemsetAsync(a.work_counter, 0, sizeof(unsigned long long), s);
     } else {
         cudaMemsetAsync(work_counter, 0, sizeof(unsigned long long), s);
     }
@@ -582,6 +596,12 @@ cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_word
     if (n_words == 0) return cudaSuccess;
     k_popcount<<<256, 256, 0, s>>>(bits, n_words, total);
     return cudaGetLastError();
+}
+
+size_t cast_counter_bytes(int64_t n_total, bool compact)
+{
+    if (!compact) return sizeof(unsigned long long);
+    return compact_counter_offset((n_total + kCompactTileBeams - 1) / kCompactTileBeams) + sizeof(unsigned long long);
 }
 
 size_t fused_compact_scratch_bytes(int64_t n)

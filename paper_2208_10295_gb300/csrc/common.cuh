@@ -96,6 +96,19 @@ struct InlineFrames {
     int n;
 };
 
+// The counters of a direct cast (tile counts, finished-block word, work
+// counter) in a region the caller keeps all zero between casts: the launch
+// needs no memset when `clean`, and clears `zero_next` (the region of the cast
+// before it, zero_words words) at its start for the cast after it.
+struct CounterRegion {
+    unsigned* base;
+    bool clean;
+    unsigned* zero_next;
+    int64_t zero_words;
+};
+// bytes of a CounterRegion a cast of n_total dense beams uses
+size_t cast_counter_bytes(int64_t n_total, bool compact);
+
 struct TableDev {
     const float* table;       // [n_mat][91]
     int32_t n_mat;
@@ -164,7 +177,8 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
                         unsigned long long* work_counter, const LaunchCfg& cfg, int num_sms,
                         int64_t n_beams_total, const WorkCount* count = nullptr, void* compact_scratch = nullptr,
                         int64_t* n_points_dev = nullptr, const lidar_points* points = nullptr,
-                        bool* scattered = nullptr, const InlineFrames* inline_frames = nullptr);
+                        bool* scattered = nullptr, const InlineFrames* inline_frames = nullptr,
+                        const CounterRegion* region = nullptr);
 // ordered compaction fused with the cast: the cast counts kept returns per
 // 1024-beam tile and scans them (compact_scratch of fused_compact_scratch_bytes);
 // with `points` and cfg.fused_scatter it also writes the points after a

@@ -99,6 +99,12 @@ struct lidar_ctx {
     size_t sweeps_cap = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // two counter regions of direct casts, used alternately: a cast clears
+    // the other one, so the next needs no memset (cnt_clean)
+    unsigned* cnt_dev = nullptr;
+    int64_t cnt_words = 0;  // per region
+    bool cnt_clean[2] = {false, false};
+    int cnt_cur = 0;
     LaunchCfg cfg{128, 4, 32, 1, 2, 1};
     int build_method = 1;     // 0 Karras LBVH, 1 PLOC clustering (fewer node fetches per ray)
     int ploc_radius = 16;
@@ -256,6 +262,7 @@ void lidar_destroy(lidar_ctx* c)
         if (c->stage_done[i]) cudaEventDestroy(c->stage_done[i]);
     }
     cudaFree(c->scratch);
+    cudaFree(c->cnt_dev);
     cudaFree(c->status_dev);
     delete c;
 }
@@ -669,10 +676,38 @@ static lidar_status traversal_available(const lidar_ctx* c, const lidar_scene* s
 
 // Cast over frames already on the device.  `may_alloc` false: fail instead of
 // growing the scratch (stream capture, batches).
+// The counter region of a direct cast (`direct`: not captured, not a batch):
+// the region the previous cast did not use, which that cast cleared.
+static lidar_status counter_region(lidar_ctx* c, int64_t n_total, bool compact, CounterRegion* R)
+{
+    const int64_t need = ((int64_t)cast_counter_bytes(n_total, compact) + 3) / 4;
+    if (c->cnt_words < need) {
+        LIDAR_CUDA(cudaStreamSynchronize(c->stream));
+        cudaFree(c->cnt_dev);
+        c->cnt_dev = nullptr;
+        c->cnt_words = 0;
+        const int64_t words = (std::max<int64_t>(need, 256) + 63) / 64 * 64;
+        if (dev_alloc((void**)&c->cnt_dev, (size_t)(2 * words) * sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cast: device allocation failed (counters)");
+            return LIDAR_ENOMEM;
+        }
+        c->cnt_words = words;
+        c->cnt_clean[0] = c->cnt_clean[1] = false;
+    }
+    const int r = c->cnt_cur ^ 1;
+    R->base = c->cnt_dev + (int64_t)r * c->cnt_words;
+    R->clean = c->cnt_clean[r];
+    R->zero_next = c->cnt_dev + (int64_t)(r ^ 1) * c->cnt_words;
+    R->zero_words = c->cnt_words;
+    return LIDAR_OK;
+}
+
 static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const FrameDev* frames_dev,
                               const int64_t* prefix_dev, int32_t n_frames, int64_t n_total, int64_t n_tiles,
                               uint64_t seed, const lidar_beams* beams, const lidar_points* points,
-                              int64_t* n_points_dev, bool may_alloc, const InlineFrames* inl = nullptr)
+                              int64_t* n_points_dev, bool may_alloc, const InlineFrames* inl = nullptr,
+                              bool direct = false)
 {
     lidar_status tst = traversal_available(c, scene, "cast");
     if (tst != LIDAR_OK) return tst;
@@ -709,9 +744,29 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
     SceneDev S = scene_dev(scene);
     char* comp = points ? dense_base + dense_bytes : nullptr;
     bool scattered = false;
-    LIDAR_CUDA(launch_cast(c->stream, S, c->sensors_dev, frames_dev, n_frames, prefix_dev, n_tiles, c->table, seed,
-                           out, c->status_dev, c->work_counter, c->cfg, c->num_sms, n_total, nullptr, comp,
-                           n_points_dev, points, &scattered, inl));
+    CounterRegion R{};
+    bool use_region = false;
+    if (direct) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        LIDAR_CUDA(cudaStreamIsCapturing(c->stream, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            lidar_status rs = counter_region(c, n_total, points != nullptr, &R);
+            if (rs != LIDAR_OK) return rs;
+            use_region = true;
+        }
+    }
+    const cudaError_t le = launch_cast(c->stream, S, c->sensors_dev, frames_dev, n_frames, prefix_dev, n_tiles,
+                                       c->table, seed, out, c->status_dev, c->work_counter, c->cfg, c->num_sms,
+                                       n_total, nullptr, comp, n_points_dev, points, &scattered, inl,
+                                       use_region ? &R : nullptr);
+    if (use_region) {
+        // this cast dirtied its region and clears the other one
+        const int r = c->cnt_cur ^ 1;
+        c->cnt_clean[r] = false;
+        c->cnt_clean[r ^ 1] = le == cudaSuccess;
+        c->cnt_cur = r;
+    }
+    LIDAR_CUDA(le);
     if (points && !scattered)
         LIDAR_CUDA(launch_scatter(c->stream, c->sensors_dev, frames_dev, n_frames, n_total, out, *points, comp,
                                   c->status_dev, inl));
@@ -743,7 +798,7 @@ lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_fram
     st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles, &inl);
     if (st != LIDAR_OK) return st;
     return cast_impl(c, scene, c->frames_dev, c->tile_prefix_dev, n_frames, n_total, n_tiles, seed, beams, points,
-                     n_points_dev, true, &inl);
+                     n_points_dev, true, &inl, true);
 }
 
 }  // extern "C"
