@@ -429,3 +429,43 @@ def test_cfg4_city_subrays_sampled(L):
     # most hit beams have several sub-rays of near-equal intensity on the same
     # surface: those are checked through the ambiguous-choice path
     assert rep["hits"] + rep["subray_ambiguous_checked"] > 100
+
+
+def test_direct_casts_back_to_back_with_reused_counters(L):
+    """Direct casts alternate between two counter regions, each clearing the
+    other for the next cast: a sequence of casts with and without a point
+    cloud, of growing sizes (the regions are reallocated) and in both launch
+    modes (fused scatter or not) reproduces the first cast's point cloud."""
+    w = synth.small_terrain(seed=21, n_frames=1, n_az=256)
+    big = synth.small_terrain(seed=22, n_frames=4, n_az=1024)
+    scene, _ = setup(L, w)
+    n = L.total_beams(w.frames)
+
+    def points_of(frames, nb):
+        pts = L.alloc_points(nb)
+        L.cast_into(scene, frames, w.seed, None, pts)
+        assert L.sync_status() == 0
+        c = int(pts["count"].item())
+        return c, {k: v[:c].clone() for k, v in pts.items() if k != "count"}
+
+    c0, p0 = points_of(w.frames, n)
+    assert c0 > 1000
+    cfg0 = L.launch_config()
+    try:
+        for step in range(6):
+            if step == 2:
+                L.set_sensor(0, big.sensors[0])
+                points_of(big.frames, L.total_beams(big.frames))   # larger: new regions
+                L.set_sensor(0, w.sensors[0])
+            if step == 4:
+                L.set_launch_config(fused_scatter=0)
+            dense = L.alloc_beams(n, ("valid",))
+            L.cast_into(scene, w.frames, w.seed, dense)               # no point cloud
+            assert L.sync_status() == 0
+            assert int(dense["valid"].sum().item()) == c0
+            c, p = points_of(w.frames, n)
+            assert c == c0, step
+            for k in p0:
+                assert torch.equal(p[k], p0[k]), (step, k)
+    finally:
+        L.set_launch_config(**cfg0)
