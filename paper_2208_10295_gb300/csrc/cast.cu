@@ -256,6 +256,17 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
     const FrameDev* fr_tab = inl.n ? inl.f : frames;
     const int64_t* tile_first = inl.n ? inl.prefix : tile_prefix;
     extern __shared__ int2 sh_stack[];  // [kSharedStack][blockDim.x]
+    // closest hit of one ray with the instantiated traversal (the warp-synchronous
+    // one needs every lane; the others run on the active lanes)
+    auto trace = [&](const RayPre& p, float t_max, HitRec& h, bool active, unsigned* cost) -> bool {
+        if (kTrav == 1) return trace_closest_warp<kCount>(S, p, t_max, h, active, &wc);
+        if (!active) return true;
+        if (kTrav == 3)
+            return trace_closest8<kCount>(S, p, t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x, cost);
+        if (kTrav == 2)
+            return trace_closest4<kCount>(S, p, t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x, cost);
+        return trace_closest<kCount>(S, p, t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x, cost);
+    };
     while (true) {
         unsigned long long claimed = 0;
         if (lane == 0) claimed = atomicAdd(work_counter, 1ull);
@@ -265,6 +276,54 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
         const FrameDev& fr = fr_tab[fi];
         const SensorDev& sd = sensors[fr.sensor];
         const int64_t base = (tile - tile_first[fi]) * tile_rays;
+        if (!kCount && sd.n_sub > 1) {
+            // a beam's sub-rays on neighbouring lanes (32 / n_sub beams per warp
+            // step): they take nearly the same path through the tree, so the warp
+            // stays converged and shares its node fetches; the strongest return
+            // (ties to the lower sub-ray, sub-ray 0 when none is kept) is picked
+            // across the beam's lanes and written by its lane
+            const int ns = sd.n_sub;
+            const int G = 32 / ns;
+            const int g = lane / ns, k = lane - g * ns;
+            for (int j0 = 0; j0 < tile_rays; j0 += G) {
+                const int64_t pos = base + j0 + g;
+                const bool active = g < G && j0 + g < tile_rays && pos < sd.n_beams;
+                if (!__any_sync(0xffffffffu, active)) break;
+                uint32_t beam = 0;
+                float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f;
+                if (active) {
+                    beam = sd.order ? __ldg(&sd.order[pos]) : (uint32_t)pos;
+                    d0 = __ldg(&sd.dirs[3 * (int64_t)beam]);
+                    d1 = __ldg(&sd.dirs[3 * (int64_t)beam + 1]);
+                    d2 = __ldg(&sd.dirs[3 * (int64_t)beam + 2]);
+                }
+                RayW r = world_ray(fr.pose, d0, d1, d2);
+                if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
+                const RayPre p = prepare_ray(r);
+                HitRec h;
+                if (!trace(p, sd.t_max, h, active, nullptr)) raise_status(status, ST_STACK);
+                BeamResult res;
+                res.valid = 0;
+                res.intensity = 0.0f;
+                if (active)
+                    shade(S, h, r, sd, T, seed, beam, (uint32_t)fr.frame, (uint32_t)fr.sensor, (uint32_t)k, res);
+                const float score = active ? (res.valid ? res.intensity : -1.0f) : -2.0f;
+                float top = -3.0f;
+                int arg = 0;
+                for (int m = 0; m < ns; ++m) {
+                    const float sm = __shfl_sync(0xffffffffu, score, min(g * ns + m, 31));
+                    if (sm > top) {
+                        top = sm;
+                        arg = m;
+                    }
+                }
+                const bool winner = active && k == arg;
+                if (cc.counts) count_kept_warp(cc, winner && res.valid, fr.beam_offset + beam, lane);
+                if (winner) write_beam(out, fr.beam_offset + beam, res, fr.pose, k);
+            }
+            continue;
+        }
+        // one beam per lane, its sub-rays in turn (the counting launch: per-beam costs)
         for (int j0 = 0; j0 < tile_rays; j0 += 32) {
             const int64_t pos = base + j0 + lane;
             const bool active = pos < sd.n_beams;
@@ -287,21 +346,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                 if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
                 const RayPre p = prepare_ray(r);
                 HitRec h;
-                bool ok = true;
-                if (kTrav == 1) {
-                    ok = trace_closest_warp<kCount>(S, p, sd.t_max, h, active, &wc);
-                } else if (active) {
-                    if (kTrav == 3)
-                        ok = trace_closest8<kCount>(S, p, sd.t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x,
-                                                    &cost);
-                    else if (kTrav == 2)
-                        ok = trace_closest4<kCount>(S, p, sd.t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x,
-                                                    &cost);
-                    else
-                        ok = trace_closest<kCount>(S, p, sd.t_max, h, &wc, sh_stack + threadIdx.x, blockDim.x,
-                                                   &cost);
-                }
-                if (!ok) raise_status(status, ST_STACK);
+                if (!trace(p, sd.t_max, h, active, &cost)) raise_status(status, ST_STACK);
                 if (active) {
                     BeamResult res;
                     shade(S, h, r, sd, T, seed, beam, (uint32_t)fr.frame, (uint32_t)fr.sensor, (uint32_t)k, res);
