@@ -6,8 +6,8 @@
 // step of Sec. II-A, here per beam.  From the returns of a beam's sub-rays it
 // also reports several echoes (Sec. IV: multiple returns are future work):
 // mode 0 the n strongest apart by at least `separation` in range, mode 1 the
-// first and the last.  Persistent warp tiles like the frame cast's, 4-wide
-// traversal.
+// first and the last.  Persistent warp tiles like the frame cast's (a beam's
+// sub-rays on neighbouring lanes), 4-wide traversal.
 #include "common.cuh"
 #include "philox.cuh"
 #include "trace.cuh"
@@ -119,6 +119,69 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_sweep_tiles(SceneDev S, con
         const SweepDev f = frames[lo];
         const SensorDev& sd = sensors[f.sensor];
         const int64_t base = (tile - tile_prefix[lo]) * tile_rays;
+        if (sd.n_sub > 1) {
+            // a beam's sub-rays on neighbouring lanes (as in the frame cast): the
+            // strongest return is picked across the beam's lanes and written by its
+            // lane; the beam's first lane gathers the returns for the echoes
+            const int ns = sd.n_sub;
+            const int G = 32 / ns;
+            const int g = lane / ns, k = lane - g * ns;
+            for (int j0 = 0; j0 < tile_rays; j0 += G) {
+                const int64_t pos = base + j0 + g;
+                const bool active = g < G && j0 + g < tile_rays && pos < sd.n_beams;
+                if (!__any_sync(0xffffffffu, active)) break;
+                uint32_t beam = 0;
+                float P[12];
+                float d0 = 0.0f, d1 = 0.0f, d2 = 1.0f, sfrac = 0.0f;
+                if (active) {
+                    beam = sd.order ? __ldg(&sd.order[pos]) : (uint32_t)pos;
+                    sfrac = __ldg(&sd.sweep[beam]);
+                    d0 = __ldg(&sd.dirs[3 * (int64_t)beam]);
+                    d1 = __ldg(&sd.dirs[3 * (int64_t)beam + 1]);
+                    d2 = __ldg(&sd.dirs[3 * (int64_t)beam + 2]);
+                }
+                sweep_pose(f, sfrac, P);
+                RayW r = world_ray(P, d0, d1, d2);
+                if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
+                const RayPre p = prepare_ray(r);
+                HitRec h;
+                if (active && !trace_closest4<false>(S, p, sd.t_max, h, nullptr, nullptr, 0))
+                    raise_status(status, ST_STACK);
+                BeamResult res;
+                res.valid = 0;
+                res.intensity = 0.0f;
+                res.range = 0.0f;
+                res.tri = LIDAR_NO_HIT;
+                if (active)
+                    shade(S, h, r, sd, T, seed, beam, (uint32_t)f.frame, (uint32_t)f.sensor, (uint32_t)k, res);
+                const float score = active ? (res.valid ? res.intensity : -1.0f) : -2.0f;
+                float top = -3.0f;
+                int arg = 0;
+                for (int m = 0; m < ns; ++m) {
+                    const float sm = __shfl_sync(0xffffffffu, score, min(g * ns + m, 31));
+                    if (sm > top) {
+                        top = sm;
+                        arg = m;
+                    }
+                }
+                const int64_t gi = f.beam_offset + beam;
+                if (active && k == arg) write_beam(out, gi, res, P, k);
+                if (kEcho) {
+                    float sub_range[LIDAR_MAX_SUBRAYS], sub_I[LIDAR_MAX_SUBRAYS];
+                    uint32_t sub_tri[LIDAR_MAX_SUBRAYS];
+                    bool sub_ok[LIDAR_MAX_SUBRAYS];
+                    for (int m = 0; m < ns; ++m) {
+                        const int src = min(g * ns + m, 31);
+                        sub_range[m] = __shfl_sync(0xffffffffu, res.range, src);
+                        sub_I[m] = __shfl_sync(0xffffffffu, res.intensity, src);
+                        sub_tri[m] = __shfl_sync(0xffffffffu, res.tri, src);
+                        sub_ok[m] = __shfl_sync(0xffffffffu, res.valid, src) != 0;
+                    }
+                    if (active && k == 0) write_echoes(echo, gi, ns, sub_range, sub_I, sub_tri, sub_ok);
+                }
+            }
+            continue;
+        }
         for (int j0 = 0; j0 < tile_rays; j0 += 32) {
             const int64_t pos = base + j0 + lane;
             const bool active = pos < sd.n_beams;
