@@ -4,8 +4,9 @@
 //   ray generation -> closest-hit BVH traversal -> surface attributes ->
 //   incidence angle -> reflectance lerp -> Philox range noise -> cut-offs ->
 //   intensity -> strongest of the sub-rays
-// writing a dense per-beam record.  A second stage compacts the kept returns
-// in (frame, beam) order.
+// writing a dense per-beam record (a beam's sub-rays on neighbouring lanes).
+// The kept returns are then compacted in (frame, beam) order, in the same
+// launch after one grid-wide wait, or by a second kernel.
 
 #include "common.cuh"
 
@@ -148,9 +149,10 @@ __device__ void scatter_tile(const SensorDev* __restrict__ sensors, const FrameD
 }
 
 // Counts of kept returns per compaction tile of kCompactTileBeams dense
-// indices, gathered by the cast itself (warp-aggregated atomics); the last
-// block to finish turns them into exclusive offsets, so the ordered
-// compaction needs only one more kernel.
+// indices, gathered by the cast itself (warp-aggregated atomics).  With the
+// scatter fused into the cast, every block waits once for all counts and
+// scatters a run of tiles; otherwise the last block to finish turns them into
+// exclusive offsets for one more kernel (k_scatter_points).
 struct CompactCounts {
     unsigned* counts;     // [n_tiles], zeroed before the cast; NULL: not counting
     unsigned* done;       // finished-block counter, zeroed before the cast
