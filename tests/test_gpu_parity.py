@@ -86,11 +86,12 @@ def test_small_terrain_range_exponent(L):
     _report(compare(gpu, ref, label="small terrain, I ~ 1/R^2"))
 
 
-def test_small_terrain_subrays(L):
-    w = synth.small_terrain(seed=9, n_frames=2, n_az=128, n_subrays=7, divergence=2e-3)
+@pytest.mark.parametrize("n_subrays", [7, 3, 8])
+def test_small_terrain_subrays(L, n_subrays):
+    w = synth.small_terrain(seed=9, n_frames=2, n_az=128, n_subrays=n_subrays, divergence=2e-3)
     gpu, _ = gpu_cast(L, w)
     ref = oracle_cast(w)
-    _report(compare_subray(gpu, ref, label="small terrain, 7 sub-rays"))
+    _report(compare_subray(gpu, ref, label=f"small terrain, {n_subrays} sub-rays"))
 
 
 def test_cfg1_full_frame_sampled(L):
@@ -121,8 +122,14 @@ def test_cfg2_batched_sampled(L):
     _report(compare(pick(gpu, w, samples), ref, label="cfg2 8 sensors x 64 frames, 1024 sampled beams"))
 
 
-def test_ray_order_and_launch_shapes_bit_identical(L):
-    w = synth.small_terrain(seed=3, n_frames=2, n_az=256)
+@pytest.mark.parametrize("n_subrays", [1, 7, 3])
+def test_ray_order_and_launch_shapes_bit_identical(L, n_subrays):
+    """Ray order, launch shape, traversal variant and cost schedule change
+    timing only.  With several sub-rays per beam a beam's sub-rays run on
+    neighbouring lanes (7: four beams per warp step, 3: ten), checked here
+    with every traversal, the warp-synchronous one included."""
+    w = synth.small_terrain(seed=3, n_frames=2, n_az=256, n_subrays=n_subrays,
+                            divergence=2e-3 if n_subrays > 1 else 0.0)
     base, scene = gpu_cast(L, w)
     cfg0 = L.launch_config()
     try:
