@@ -556,6 +556,38 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
                                     "unit": "GB/s", "frac": city_bytes / (c_ms / 1e3) / 1e9 / hbm,
                                     "note": "algorithmic node and triangle bytes of the traversal (as the "
                                             "headline roofline), per sub-ray from four frames"}}
+        # forward with tape (each beam's strongest sub-ray) + fused-MSE adjoint to the 64 x 91 table, the
+        # widths and the gain, targets from the hidden table
+        del pts4
+        tf = ("valid", "intensity", "mat", "theta_deg", "rf")
+        tgt4 = L.alloc_beams(B4.n_beams, tf)
+        L.set_materials(L.build_tables(torch.tensor(w4.hidden_params, device=L.device)))
+        B4.cast_into(scene4, w4.seed, tgt4)
+        tape4 = L.alloc_beams(B4.n_beams, tf)
+        tp4 = torch.tensor(w4.params, device=L.device)
+        loss4 = torch.zeros(1, device=L.device)
+        gT4 = torch.zeros((tp4.shape[0], 91), device=L.device)
+        gg4 = torch.zeros(1, device=L.device)
+
+        def fwd4():
+            L.set_materials(L.build_tables(tp4))
+            B4.cast_into(scene4, w4.seed, tape4)
+
+        def fwd_bwd4():
+            fwd4()
+            gT4.zero_()
+            gg4.zero_()
+            L.cast_backward_mse(tape4, 1.0, tgt4["intensity"], tgt4["valid"], loss4, gT4, gg4)
+            L.build_tables_backward(tp4, gT4)
+
+        f4_ms = event_time(torch, stream, fwd4, None, reps=3, warm=1)
+        fb4_ms = event_time(torch, stream, fwd_bwd4, None, reps=3, warm=1)
+        out["city"]["forward_adjoint"] = {"workload": "cfg4: the 32 frames with tape (strongest sub-ray per beam) "
+                                                      "+ fused-MSE adjoint to the 64x91 table, widths and gain",
+                                          "fwd_ms": f4_ms, "fwd_bwd_ms": fb4_ms, "bwd_ms": fb4_ms - f4_ms,
+                                          "loss": float(loss4.item())}
+        del tgt4, tape4
+        L.set_materials(t4)
         B4.free()
         # multi-echo (first and last of the 7 sub-ray returns, 0.5 m apart) over sweeps of the same trajectory
         sw4 = synth.make_sweep_frames([(0, int(a["frame"]), a["pose"], b["pose"])

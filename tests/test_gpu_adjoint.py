@@ -40,7 +40,7 @@ def L():
     lid.close()
 
 
-def _gpu_tape(L, w, scene=None):
+def _gpu_tape(L, w, scene=None, fields=("valid", "intensity", "mat", "theta_deg", "rf")):
     if scene is None:
         scene = L.build_scene(w.scene.verts, w.scene.tris, w.scene.mat, w.scene.inst)
     for s, spec in enumerate(w.sensors):
@@ -49,7 +49,7 @@ def _gpu_tape(L, w, scene=None):
     table = L.build_tables(params)
     L.set_materials(table)
     n = L.total_beams(w.frames)
-    tape = L.alloc_beams(n, ("valid", "intensity", "mat", "theta_deg", "rf"))
+    tape = L.alloc_beams(n, fields)
     L.cast_into(scene, w.frames, w.seed, tape)
     assert L.sync_status() == 0
     return scene, params, table, tape, n
@@ -213,3 +213,33 @@ def test_adjoint_unaligned_tape_matches_aligned(L):
     (la, ga, gga), (lb, gb, ggb) = outs
     assert np.array_equal(ga.view(np.uint32), gb.view(np.uint32)) and gga == ggb
     assert la == pytest.approx(lb, rel=1e-12)
+
+
+def test_adjoint_city_sampled(L):
+    """cfg4 forward + adjoint: the 10.7M-triangle city, all 32 frames with 7
+    sub-rays per beam on the GPU (tape of each beam's strongest sub-ray); the
+    mask keeps a seeded sample of beams that the oracle recomputes, where both
+    pick the same sub-ray and nothing is exempt; targets from the hidden
+    64-material table.  Loss and gradients against the oracle's adjoint."""
+    w = synth.cfg4()
+    scene, params, table, tape, n = _gpu_tape(L, w, fields=("valid", "intensity", "mat", "theta_deg", "rf", "sub"))
+    samples = stratified_sample(w, 256, seed=6)
+    fwd = oracle_cast(w, samples)
+    tgt = oracle_cast(w, samples, table=oracle.build_tables(w.hidden_params))
+    idx = frame_offsets(w)[samples[0]] + samples[1]
+    gsub = tape["sub"].cpu().numpy()[idx].astype(np.int64)
+    r = np.arange(idx.size)
+    ok = (((fwd.flags & 7) == 0) & ((tgt.flags & 7) == 0) & (tgt.valid != 0) & (gsub == fwd.sub) &
+          ((fwd.sub_flags[r, np.clip(fwd.sub, 0, None)] & 7) == 0))
+    tI = np.zeros(n, np.float32)
+    tv = np.zeros(n, np.uint8)
+    tI[idx] = tgt.intensity.astype(np.float32)
+    tv[idx] = ok.astype(np.uint8)
+    loss, gT, gg = _gpu_backward_mse(L, tape, table, 1.0, tI, tv)
+    L_ref, gT_ref, gg_ref, N = oracle.cast_backward(fwd.valid, fwd.mat, fwd.theta_deg, fwd.rf,
+                                                    oracle.build_tables(w.params), 1.0,
+                                                    tI[idx].astype(np.float64), tv[idx])
+    assert N > 30
+    assert loss == pytest.approx(L_ref, rel=NORM_RTOL)
+    close_grad(gT, gT_ref, "city dL/dT")
+    assert gg == pytest.approx(gg_ref, rel=NORM_RTOL)
