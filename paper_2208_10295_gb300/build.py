@@ -2,6 +2,9 @@
 
 Each translation unit is compiled by its own nvcc process (in parallel), then
 linked into one shared library with the C ABI of include/lidar.h.
+build_checked() makes the bounds-checked variant (-DLIDAR_BOUNDS: every
+traversal tests each node and triangle index before reading it and reports a
+bad one in the status word) in _build_checked/, for debugging scene data.
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblidar.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -45,18 +49,21 @@ def _digest(extra_flags):
     return h.hexdigest()
 
 
-def build(force: bool = False, extra_flags=(), verbose: bool = False) -> str:
-    """Build (if sources changed) and return the path of liblidar.so."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "liblidar.stamp")
+def build(force: bool = False, extra_flags=(), verbose: bool = False, build_dir: str = None) -> str:
+    """Build (if sources changed) and return the path of liblidar.so (in
+    `build_dir`, default _build/)."""
+    build_dir = build_dir or BUILD
+    lib = os.path.join(build_dir, "liblidar.so")
+    os.makedirs(build_dir, exist_ok=True)
+    stamp = os.path.join(build_dir, "liblidar.stamp")
     dig = _digest(extra_flags)
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.exists(stamp) and open(stamp).read() == dig:
+        return lib
     nvcc = _nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -68,15 +75,20 @@ def build(force: bool = False, extra_flags=(), verbose: bool = False) -> str:
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as f:
         f.write(dig)
-    return LIB
+    return lib
+
+
+def build_checked(force: bool = False) -> str:
+    """The bounds-checked library: _build_checked/liblidar.so."""
+    return build(force=force, extra_flags=["-DLIDAR_BOUNDS"], build_dir=BUILD_CHECKED)
 
 
 if __name__ == "__main__":

@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                 if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
                 const RayPre p = prepare_ray(r);
                 HitRec h;
-                if (!trace(p, sd.t_max, h, active, nullptr)) raise_status(status, ST_STACK);
+                if (!trace(p, sd.t_max, h, active, nullptr))
+                    raise_status(status, h.leaf == kBadIndex ? ST_BOUNDS : ST_STACK);
                 BeamResult res;
                 res.valid = 0;
                 res.intensity = 0.0f;
@@ -348,7 +349,8 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                 if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
                 const RayPre p = prepare_ray(r);
                 HitRec h;
-                if (!trace(p, sd.t_max, h, active, &cost)) raise_status(status, ST_STACK);
+                if (!trace(p, sd.t_max, h, active, &cost))
+                    raise_status(status, h.leaf == kBadIndex ? ST_BOUNDS : ST_STACK);
                 if (active) {
                     BeamResult res;
                     shade(S, h, r, sd, T, seed, beam, (uint32_t)fr.frame, (uint32_t)fr.sensor, (uint32_t)k, res);

@@ -33,7 +33,7 @@ void set_error(const std::string& msg);
     } while (0)
 
 // device status word codes (first error wins)
-enum : int { ST_OK = 0, ST_CAPACITY = 1, ST_STACK = 2, ST_TIMEOUT = 3, ST_INDEX = 4 };
+enum : int { ST_OK = 0, ST_CAPACITY = 1, ST_STACK = 2, ST_TIMEOUT = 3, ST_INDEX = 4, ST_BOUNDS = 5 };
 
 __device__ __forceinline__ void raise_status(int* status, int code)
 {

@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -12,13 +13,43 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace lidar {
 
 static thread_local std::string g_last_error;
 
-void set_error(const std::string& msg) { g_last_error = msg; }
+// LIDAR_LOG=1 prints every error message to stderr as it is set, 2 also one
+// line per scene build and per cast entry (read once per process).
+static int log_level()
+{
+    static const int level = [] {
+        const char* v = getenv("LIDAR_LOG");
+        return v ? atoi(v) : 0;
+    }();
+    return level;
+}
+
+void set_error(const std::string& msg)
+{
+    g_last_error = msg;
+    if (log_level() >= 1) fprintf(stderr, "lidar: error: %s\n", msg.c_str());
+}
+
+static void log_info(const std::string& msg)
+{
+    if (log_level() >= 2) fprintf(stderr, "lidar: %s\n", msg.c_str());
+}
+
+// NVTX range over one entry point (a profiler's timeline; no cost without a tool)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Host-side allocation fault injection for tests: LIDAR_FAULT_ALLOC_AT=n makes
 // the n-th device allocation of the process (1-based) fail with ENOMEM.
@@ -160,6 +191,9 @@ lidar_status status_from_word(int w)
     case ST_STACK: set_error("BVH traversal stack overflow"); return LIDAR_ESTACK;
     case ST_TIMEOUT: set_error("a bounded device wait timed out"); return LIDAR_ETIMEOUT;
     case ST_INDEX: set_error("triangle vertex index out of range"); return LIDAR_EINVAL;
+    case ST_BOUNDS:
+        set_error("a traversal index outside its array (bounds-checked build): corrupt scene data");
+        return LIDAR_EINVAL;
     default: set_error("unknown device status"); return LIDAR_ECUDA;
     }
 }
@@ -281,6 +315,7 @@ lidar_status lidar_sync_status(lidar_ctx* c)
 lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts, const uint32_t* tris,
                                int64_t n_tris, const uint16_t* mat, const uint32_t* inst, lidar_scene** out)
 {
+    NvtxRange nvtx_("lidar_scene_build");
     LIDAR_CHECK_ARG(c != nullptr && out != nullptr, "lidar_scene_build: ctx/out is NULL");
     *out = nullptr;
     LIDAR_CHECK_ARG(n_tris >= 0 && n_verts >= 0, "lidar_scene_build: negative size");
@@ -384,6 +419,8 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
     }
     c->scenes.insert(s);
     *out = s;
+    log_info("scene built: " + std::to_string(n_tris) + " triangles, " + std::to_string(s->n_nodes4) +
+             " 4-wide and " + std::to_string(s->n_nodes8) + " 8-wide nodes, " + std::to_string(s->build_ms) + " ms");
     return LIDAR_OK;
 }
 
@@ -790,6 +827,7 @@ static lidar_status cast_checks(lidar_ctx* c, const lidar_scene* scene, const li
 lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
                         uint64_t seed, const lidar_beams* beams, const lidar_points* points, int64_t* n_points_dev)
 {
+    NvtxRange nvtx_("lidar_cast");
     lidar_status st = cast_checks(c, scene, beams, points);
     if (st != LIDAR_OK) return st;
     DeviceGuard g(c->device);
@@ -797,6 +835,9 @@ lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_fram
     InlineFrames inl;
     st = prepare_frames(c, frames, n_frames, &n_total, &n_tiles, &inl);
     if (st != LIDAR_OK) return st;
+    if (log_level() >= 2)
+        log_info("cast: " + std::to_string(n_frames) + " frames, " + std::to_string(n_total) + " beams, traversal " +
+                 std::to_string(c->cfg.traversal) + (points ? ", point cloud" : ""));
     return cast_impl(c, scene, c->frames_dev, c->tile_prefix_dev, n_frames, n_total, n_tiles, seed, beams, points,
                      n_points_dev, true, &inl, true);
 }
@@ -860,6 +901,7 @@ extern "C" {
 lidar_status lidar_raster_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
                                uint64_t seed, const lidar_raster_config* cfg, const lidar_beams* beams)
 {
+    NvtxRange nvtx_("lidar_raster_cast");
     LIDAR_CHECK_ARG(beams != nullptr, "lidar_raster_cast: beams is NULL");
     LIDAR_CHECK_ARG(frames != nullptr && n_frames > 0, "lidar_raster_cast: need at least one frame");
     lidar_status st = cast_checks(c, scene, beams, nullptr);
@@ -921,6 +963,7 @@ static void rotation_quaternion(const float* P, double q[4])
 lidar_status lidar_cast_sweep(lidar_ctx* c, const lidar_scene* scene, const lidar_sweep_frame* frames,
                               int32_t n_frames, uint64_t seed, const lidar_beams* beams, const lidar_echoes* echoes)
 {
+    NvtxRange nvtx_("lidar_cast_sweep");
     LIDAR_CHECK_ARG(c != nullptr && scene != nullptr, "lidar_cast_sweep: ctx/scene is NULL");
     LIDAR_CHECK_ARG(scene->ctx == c, "lidar_cast_sweep: scene belongs to another context");
     LIDAR_CHECK_ARG(frames != nullptr && n_frames > 0, "lidar_cast_sweep: need at least one frame");
@@ -1005,6 +1048,7 @@ lidar_status lidar_raster_gbuffer(lidar_ctx* c, const lidar_scene* scene, const 
                                   const lidar_raster_config* cfg, uint32_t* depth_dev, uint32_t* angle_mat_dev,
                                   uint32_t* inst_dev, uint32_t* tri_dev)
 {
+    NvtxRange nvtx_("lidar_raster_gbuffer");
     LIDAR_CHECK_ARG(c != nullptr && frame != nullptr, "lidar_raster_gbuffer: NULL argument");
     const int s = frame->sensor;
     LIDAR_CHECK_ARG(s >= 0 && s < LIDAR_MAX_SENSORS, "lidar_raster_gbuffer: sensor slot out of range");
@@ -1135,6 +1179,7 @@ static lidar_status batch_valid(lidar_ctx* c, const lidar_batch* b)
 lidar_status lidar_cast_batch(lidar_ctx* c, const lidar_scene* scene, const lidar_batch* b, uint64_t seed,
                               const lidar_beams* beams, const lidar_points* points, int64_t* n_points_dev)
 {
+    NvtxRange nvtx_("lidar_cast_batch");
     lidar_status st = cast_checks(c, scene, beams, points);
     if (st != LIDAR_OK) return st;
     st = batch_valid(c, b);
@@ -1187,6 +1232,7 @@ lidar_status lidar_graph_create(lidar_ctx* c, const lidar_scene* scene, lidar_ba
 
 lidar_status lidar_graph_launch(lidar_graph* gr)
 {
+    NvtxRange nvtx_("lidar_graph_launch");
     LIDAR_CHECK_ARG(gr != nullptr, "lidar_graph_launch: graph is NULL");
     DeviceGuard g(gr->ctx->device);
     LIDAR_CUDA(cudaGraphLaunch(gr->exec, gr->ctx->stream));
@@ -1227,6 +1273,7 @@ static lidar_status backward_common(lidar_ctx* c, int64_t n, const lidar_beams* 
 lidar_status lidar_cast_backward(lidar_ctx* c, int64_t n, const lidar_beams* tape, float gain, const float* grad_I,
                                  float* grad_table, float* grad_gain)
 {
+    NvtxRange nvtx_("lidar_cast_backward");
     LIDAR_CHECK_ARG(n == 0 || grad_I != nullptr, "lidar_cast_backward: grad_I is NULL");
     return backward_common(c, n, tape, gain, grad_I, nullptr, nullptr, nullptr, grad_table, grad_gain);
 }
@@ -1235,6 +1282,7 @@ lidar_status lidar_cast_backward_mse(lidar_ctx* c, int64_t n, const lidar_beams*
                                      const float* target_I, const uint8_t* target_valid, float* loss,
                                      float* grad_table, float* grad_gain)
 {
+    NvtxRange nvtx_("lidar_cast_backward_mse");
     LIDAR_CHECK_ARG(n == 0 || (target_I != nullptr && target_valid != nullptr),
                     "lidar_cast_backward_mse: targets are NULL");
     return backward_common(c, n, tape, gain, nullptr, target_I, target_valid, loss, grad_table, grad_gain);
@@ -1250,6 +1298,7 @@ lidar_status lidar_cast_backward_mse_noalloc(void* cuda_stream, int64_t n, const
                                              float gain, const float* target_I, const uint8_t* target_valid,
                                              float* loss, float* grad_table, float* grad_gain)
 {
+    NvtxRange nvtx_("lidar_cast_backward_mse_noalloc");
     LIDAR_CHECK_ARG(n >= 0, "lidar_cast_backward_mse_noalloc: negative beam count");
     LIDAR_CHECK_ARG(table != nullptr && M >= 1, "lidar_cast_backward_mse_noalloc: need a reflectance table");
     if (M > LIDAR_NOALLOC_MAX_MATERIALS) {
@@ -1337,6 +1386,7 @@ static lidar_status counting_cast(lidar_ctx* c, const lidar_scene* scene, const 
 lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
                               uint64_t seed, lidar_work_counts* out, uint32_t* beam_cost_dev)
 {
+    NvtxRange nvtx_("lidar_count_work");
     LIDAR_CHECK_ARG(c != nullptr && scene != nullptr && out != nullptr, "lidar_count_work: NULL argument");
     DeviceGuard g(c->device);
     unsigned long long h[4];
@@ -1367,6 +1417,7 @@ lidar_status lidar_count_work(lidar_ctx* c, const lidar_scene* scene, const lida
 lidar_status lidar_schedule_by_cost(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frame, uint64_t seed,
                                     int32_t mode)
 {
+    NvtxRange nvtx_("lidar_schedule_by_cost");
     LIDAR_CHECK_ARG(mode == 0 || mode == 1, "lidar_schedule_by_cost: mode is 0 or 1");
     LIDAR_CHECK_ARG(c != nullptr && scene != nullptr && frame != nullptr, "lidar_schedule_by_cost: NULL argument");
     const int slot = frame->sensor;

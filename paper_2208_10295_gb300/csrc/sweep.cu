@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_sweep_tiles(SceneDev S, con
                 const RayPre p = prepare_ray(r);
                 HitRec h;
                 if (active && !trace_closest4<false>(S, p, sd.t_max, h, nullptr, nullptr, 0))
-                    raise_status(status, ST_STACK);
+                    raise_status(status, h.leaf == kBadIndex ? ST_BOUNDS : ST_STACK);
                 BeamResult res;
                 res.valid = 0;
                 res.intensity = 0.0f;
@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_sweep_tiles(SceneDev S, con
                 if (k > 0) subray_dir(r.dx, r.dy, r.dz, sd.alpha[k], sd.beta[k]);
                 const RayPre p = prepare_ray(r);
                 HitRec h;
-                if (!trace_closest4<false>(S, p, sd.t_max, h, nullptr, nullptr, 0)) raise_status(status, ST_STACK);
+                if (!trace_closest4<false>(S, p, sd.t_max, h, nullptr, nullptr, 0))
+                    raise_status(status, h.leaf == kBadIndex ? ST_BOUNDS : ST_STACK);
                 BeamResult res;
                 shade(S, h, r, sd, T, seed, beam, (uint32_t)f.frame, (uint32_t)f.sensor, (uint32_t)k, res);
                 if (kEcho) {

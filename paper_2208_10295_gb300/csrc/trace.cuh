@@ -14,6 +14,23 @@ constexpr float kFarScale = 1.0f + 4.76837158203125e-07f;
 // pruning against the current closest hit keeps a slightly wider margin
 constexpr float kBestScale = 1.0f + 9.5367431640625e-07f;
 
+// Checked builds (-DLIDAR_BOUNDS): every traversal tests each node and
+// triangle index against its array before reading it.  A bad index (corrupt
+// scene data) ends the traversal with h.leaf = kBadIndex and false, which the
+// cast reports as a bounds error in the status word, instead of reading
+// outside the arrays.  Normal builds compile the tests away.
+#ifdef LIDAR_BOUNDS
+constexpr bool kBoundsChecks = true;
+#else
+constexpr bool kBoundsChecks = false;
+#endif
+constexpr int kBadIndex = -2;
+
+__device__ __forceinline__ bool index_ok(int64_t i, int64_t n)
+{
+    return !kBoundsChecks || (i >= 0 && i < n);
+}
+
 struct RayW {
     float ox, oy, oz;
     float dx, dy, dz;
@@ -226,6 +243,10 @@ __device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p
             ++n_nodes;
             atomicOr(&wc->node_bits[node >> 5], 1u << (node & 31));
         }
+        if (!index_ok(node, S.n_nodes)) {
+            h.leaf = kBadIndex;
+            return false;
+        }
         const float4 n0 = __ldg(&S.nodes[4 * (int64_t)node + 0]);
         const float4 n1 = __ldg(&S.nodes[4 * (int64_t)node + 1]);
         const float4 n2 = __ldg(&S.nodes[4 * (int64_t)node + 2]);
@@ -234,6 +255,10 @@ __device__ __forceinline__ bool trace_closest(const SceneDev& S, const RayPre& p
         float tL, tR;
         child_boxes(n0, n1, n2, p, h.cull, hitL, hitR, tL, tR);
         const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+        if (!index_ok(hitL && cl < 0 ? ~cl : 0, S.n_tris) || !index_ok(hitR && cr < 0 ? ~cr : 0, S.n_tris)) {
+            h.leaf = kBadIndex;
+            return false;
+        }
         if (hitL && cl < 0) {
             if (kCount) {
                 ++n_tris;
@@ -389,6 +414,10 @@ __device__ __forceinline__ bool trace_closest4(const SceneDev& S, const RayPre& 
             ++n_nodes;
             atomicOr(&wc->node_bits[node >> 5], 1u << (node & 31));
         }
+        if (!index_ok(node, S.n_nodes4)) {
+            h.leaf = kBadIndex;
+            return false;
+        }
         const float4* q = S.nodes4 + 8 * (int64_t)node;
         const int2 meta = __ldg(reinterpret_cast<const int2*>(q + 7));
         float4 kn, kf;
@@ -407,6 +436,10 @@ __device__ __forceinline__ bool trace_closest4(const SceneDev& S, const RayPre& 
                 const unsigned j = (unsigned)(__ffs(leaves) - 1);
                 leaves &= leaves - 1;
                 const int leaf = ~((j & 2u) ? ((j & 1u) ? c.w : c.z) : ((j & 1u) ? c.y : c.x));
+                if (!index_ok(leaf, S.n_tris)) {
+                    h.leaf = kBadIndex;
+                    return false;
+                }
                 if (kCount) {
                     ++n_tris;
                     atomicOr(&wc->leaf_bits[leaf >> 5], 1u << (leaf & 31));
@@ -502,6 +535,10 @@ __device__ __forceinline__ bool trace_closest8(const SceneDev& S, const RayPre& 
             ++n_nodes;
             atomicOr(&wc->node_bits[node >> 5], 1u << (node & 31));
         }
+        if (!index_ok(node, S.n_nodes8)) {
+            h.leaf = kBadIndex;
+            return false;
+        }
         const float4* q = S.nodes8 + 16 * (int64_t)node;
         const int2 meta = __ldg(reinterpret_cast<const int2*>(q + 14));
         float4 ka, fa, kb, fb;
@@ -524,6 +561,10 @@ __device__ __forceinline__ bool trace_closest8(const SceneDev& S, const RayPre& 
                 const unsigned j = (unsigned)(__ffs(leaves) - 1);
                 leaves &= leaves - 1;
                 const int leaf = ~code8(ca, cb, j);
+                if (!index_ok(leaf, S.n_tris)) {
+                    h.leaf = kBadIndex;
+                    return false;
+                }
                 if (kCount) {
                     ++n_tris;
                     atomicOr(&wc->leaf_bits[leaf >> 5], 1u << (leaf & 31));
@@ -612,12 +653,18 @@ __device__ __forceinline__ bool trace_closest_warp(const SceneDev& S, const RayP
     float node_t = 0.0f;  // entry distance of `node` (culled when it exceeds the best hit)
     int pend0 = -1, pend1 = -1;
     bool ok = true;
+    bool bad = false;  // a bounds check failed (checked builds)
     while (__any_sync(0xffffffffu, node >= 0 || pend0 >= 0)) {
         // descend until this lane holds a leaf or has nothing left
         while (__any_sync(0xffffffffu, node >= 0 && pend0 < 0)) {
             if (node >= 0 && pend0 < 0) {
                 if (node_t > h.cull) {
                     node = -1;
+                } else if (!index_ok(node, S.n_nodes)) {
+                    ok = false;
+                    bad = true;
+                    node = -1;
+                    sp = 0;
                 } else {
                     if (kCount) {
                         ++n_nodes;
@@ -631,6 +678,12 @@ __device__ __forceinline__ bool trace_closest_warp(const SceneDev& S, const RayP
                     float tL, tR;
                     child_boxes(n0, n1, n2, p, h.cull, hitL, hitR, tL, tR);
                     const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+                    if (!index_ok(hitL && cl < 0 ? ~cl : 0, S.n_tris) ||
+                        !index_ok(hitR && cr < 0 ? ~cr : 0, S.n_tris)) {
+                        ok = false;
+                        bad = true;
+                        hitL = hitR = false;
+                    }
                     if (hitL && cl < 0) { pend0 = ~cl; hitL = false; }
                     if (hitR && cr < 0) {
                         if (pend0 < 0) pend0 = ~cr; else pend1 = ~cr;
@@ -691,6 +744,7 @@ __device__ __forceinline__ bool trace_closest_warp(const SceneDev& S, const RayP
         atomicAdd(&wc->totals[0], n_nodes);
         atomicAdd(&wc->totals[1], n_tris);
     }
+    if (bad) h.leaf = kBadIndex;
     return ok;
 }
 
