@@ -476,3 +476,33 @@ def test_direct_casts_back_to_back_with_reused_counters(L):
                 assert torch.equal(p[k], p0[k]), (step, k)
     finally:
         L.set_launch_config(**cfg0)
+
+
+def test_degenerate_triangles_change_nothing(L):
+    """Zero-area triangles (one point three times; two equal vertices and a
+    third) appended to cfg0 on the beams' own paths, 5 and 12 m out: every
+    dense field is bit for bit that of plain cfg0 (the original triangles keep
+    their indices) and matches the oracle on every beam; none is ever hit."""
+    w = synth.cfg0()
+    base, _ = gpu_cast(L, w)
+    dirs = L.beam_dirs(0).astype(np.float32)
+    o = np.asarray(w.frames[0]["pose"], np.float32).reshape(3, 4)[:, 3]
+    pick_b = np.arange(0, dirs.shape[0], 97)
+    tris = []
+    for s_ in (np.float32(5.0), np.float32(12.0)):
+        p = o[None, :] + s_ * dirs[pick_b]
+        tris += [[q, q, q] for q in p]
+        tris += [[q, q, q + np.float32([0.0, 0.0, 2.0])] for q in p]
+    v0 = w.scene.verts.shape[0]
+    k = len(tris)
+    sc = synth.Scene(np.concatenate([w.scene.verts, np.asarray(tris, np.float32).reshape(-1, 3)]),
+                     np.concatenate([w.scene.tris, (v0 + np.arange(3 * k, dtype=np.uint32)).reshape(k, 3)]),
+                     np.concatenate([w.scene.mat, np.zeros(k, np.uint16)]),
+                     np.concatenate([w.scene.inst, np.full(k, 999, np.uint32)]))
+    wd = synth.Workload("cfg0_degenerate", sc, w.sensors, w.frames, w.params, w.seed)
+    got, _ = gpu_cast(L, wd)
+    for key in base:
+        assert np.array_equal(base[key].view(np.uint8), got[key].view(np.uint8)), key
+    hit = got["tri"] != 0xFFFFFFFF
+    assert np.all(got["tri"][hit] < w.scene.n_tris)
+    _report(compare(got, oracle_cast(wd), label=f"cfg0 + {k} degenerate triangles on beam paths, every beam"))

@@ -343,3 +343,35 @@ def test_range_scaled_noise_search_range(oracle_lib):
         s = sensor(np.zeros(1), np.zeros(1), r_min=0.5, r_max=dlim, d_max=dlim, RL_max=1e-6, sigma=sig, sigma_k=sk)
         r = oracle_lib.cast(scene, [s], identity_frame(), const_table(0.5), seed=1)
         assert (r.tri[0] != oracle_lib.NO_HIT) == hit
+
+
+def _with_degenerates(scene, tris_xyz):
+    """`scene` plus triangles given by their three vertices (appended after it,
+    so the original triangles keep their indices)."""
+    v0 = scene.verts.shape[0]
+    verts = np.concatenate([scene.verts, np.asarray(tris_xyz, np.float32).reshape(-1, 3)])
+    k = len(tris_xyz)
+    tris = np.concatenate([scene.tris, (v0 + np.arange(3 * k, dtype=np.uint32)).reshape(k, 3)])
+    mat = np.concatenate([scene.mat, np.zeros(k, np.uint16)])
+    inst = np.concatenate([scene.inst, np.full(k, 99, np.uint32)])
+    return synth.Scene(verts, tris, mat, inst)
+
+
+def test_degenerate_triangles_are_never_hit(oracle_lib):
+    """Zero-area triangles — one point three times, or two equal vertices and a
+    third — placed exactly on the beams' paths are never hit: the beams reach
+    the wall x = 20 behind them (range 20 / cos of the azimuth in the plane)."""
+    wall = quads_scene([wall_x(20.0, half=200.0)])
+    az = np.radians([0.0, 0.0, 10.0, -7.5])
+    el = np.zeros(4)
+    s = sensor(az, el, r_min=0.1, r_max=500.0, d_max=500.0, RL_max=1e-6)
+    d = oracle_lib.beam_dirs(s.az_rad, s.el_rad).astype(np.float64)
+    pts = [np.float32(10.0) * d[i].astype(np.float32) for i in range(4)]      # points on (or next to) the beams
+    degs = [[p, p, p] for p in pts] + [[p, p, p + np.float32([0.0, 0.0, 3.0])] for p in pts] + \
+        [[(10.0, -5.0, 0.0), (10.0, 5.0, 0.0), (10.0, -5.0, 0.0)]]             # a repeated-vertex segment across beam 0
+    scene = _with_degenerates(wall, degs)
+    r = oracle_lib.cast(scene, [s], identity_frame(), const_table(0.5), 1)
+    assert np.all(r.tri < 2)                                                  # a wall triangle, never a degenerate one
+    assert np.allclose(r.range, 20.0 / d[:, 0], rtol=1e-12)
+    base = oracle_lib.cast(wall, [s], identity_frame(), const_table(0.5), 1)
+    assert np.array_equal(r.tri, base.tri) and np.array_equal(r.range, base.range)
