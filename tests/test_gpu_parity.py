@@ -506,3 +506,57 @@ def test_degenerate_triangles_change_nothing(L):
     hit = got["tri"] != 0xFFFFFFFF
     assert np.all(got["tri"][hit] < w.scene.n_tris)
     _report(compare(got, oracle_cast(wd), label=f"cfg0 + {k} degenerate triangles on beam paths, every beam"))
+
+
+def _sixteen_sensor_workload():
+    """Every sensor slot filled, with what varies between sensors varying:
+    spinning 16/32-channel and raster patterns whose beam counts are not
+    multiples of 32, 1..8 sub-rays, noise with and without the range term,
+    range exponent, gain, range limits and Eq. 5 constants.  Two frames per
+    slot at different poses, the frame records in a shuffled slot order."""
+    base = synth.small_terrain(seed=41, n_frames=4)
+    rng = np.random.default_rng(4141)
+    sensors = []
+    for s in range(16):
+        ns = 1 + s % 8
+        kw = dict(r_min=float(rng.uniform(0.3, 1.0)), r_max=float(rng.uniform(25.0, 40.0)),
+                  d_max=float(rng.uniform(20.0, 45.0)), RL_max=float(rng.uniform(0.2, 0.9)),
+                  sigma=float(rng.choice([0.0, 0.01, 0.03])), sigma_k=float(rng.choice([0.0, 0.002])),
+                  gain=float(rng.uniform(0.5, 2.0)), range_exp=float(rng.choice([0.0, 2.0])),
+                  n_subrays=ns, divergence_rad=2e-3 if ns > 1 else 0.0)
+        if s % 3 == 0:
+            spec = synth.sensors.sensor_16ch(int(rng.integers(40, 90)), **kw)
+        elif s % 3 == 1:
+            spec = synth.sensors.sensor_32ch(int(rng.integers(20, 45)), **kw)
+        else:
+            spec = synth.sensors.sensor_raster(int(rng.integers(20, 40)), int(rng.integers(9, 23)),
+                                               fov_h=100.0, fov_v=30.0, **kw)
+        sensors.append(spec)
+    poses = base.frames["pose"]
+    entries = []
+    for k, s in enumerate(rng.permutation(np.repeat(np.arange(16), 2))):
+        entries.append((int(s), 100 + k, poses[k % len(poses)]))
+    return synth.Workload("sixteen_sensors", base.scene, sensors, synth.workloads.make_frames(entries),
+                          base.params, base.seed)
+
+
+def test_all_sensor_slots_mixed_batch_every_beam(L):
+    """One cast over frames of all 16 sensor slots (the most the context
+    holds), mixed sub-ray counts and sensor constants, ragged beam counts:
+    every beam against the oracle, and the point cloud in (frame, beam) order
+    against the dense output."""
+    w = _sixteen_sensor_workload()
+    assert len(w.sensors) == 16
+    gpu, scene = gpu_cast(L, w)
+    ref = oracle_cast(w)
+    gmax = max(s.gain for s in w.sensors)
+    rep = compare_subray(gpu, ref, gain=gmax, label=f"16 sensor slots, 32 frames, {len(gpu['valid'])} beams, 1-8 sub-rays")
+    _report(rep)
+    assert rep["returns"] > 1000
+    beams, points = L.cast(scene, w.frames, w.seed, points_capacity=L.total_beams(w.frames))
+    n = int(points["count"].item())
+    v = np.flatnonzero(gpu["valid"] != 0)
+    assert n == v.size
+    assert np.array_equal(points["range"][:n].cpu().numpy().view(np.uint32), gpu["range"][v].view(np.uint32))
+    assert np.array_equal(points["intensity"][:n].cpu().numpy().view(np.uint32), gpu["intensity"][v].view(np.uint32))
+    scene.free()
