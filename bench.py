@@ -45,7 +45,8 @@ POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal,
 # the cast kernel as the roofline times it (cfg1 frame, dense valid flags out,
 # L2 flushed before the launch), from one ncu capture, with the digest of the
 # kernel sources the capture ran.  Reported only while the sources still match.
-NCU_TRAFFIC = {"sources": "874d188715b92447", "bytes": 10_482_688}   # profiles/k_cast_cfg1_ncu_full.md
+NCU_TRAFFIC = {"sources": "874d188715b92447", "bytes": 10_482_688, "l2_bytes": 3_975_268 * 32,
+               "l1_global_load_bytes": 7_811_641 * 32}   # profiles/k_cast_cfg1_ncu_full.md
 KERNEL_SOURCES = ("cast.cu", "shade.cuh", "trace.cuh", "common.cuh", "philox.cuh")
 
 
@@ -344,7 +345,8 @@ def run_ours(args, rank, world, local_rank):
     visit_bytes = counters["node_visits"] * counters["node_bytes"] + counters["tri_tests"] * 48 + counters["io_bytes"]
     uniq_bytes = counters["unique_node_bytes"] + counters["unique_tri_bytes"] + counters["io_bytes"]
     achieved = visit_bytes / (kernel_ms / 1e3) / 1e9
-    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["sources"] == kernel_digest() else None
+    same_kernel = NCU_TRAFFIC["sources"] == kernel_digest()
+    traffic = NCU_TRAFFIC["bytes"] if same_kernel else None
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
     # FP32 ops per node fetch: 12 (binary) or 24 (4-wide) slab subtract+multiply pairs; 40 per triangle test
     flops = counters["node_visits"] * (counters["node_bytes"] // 64) * 2 * 24 + counters["tri_tests"] * 40
@@ -370,6 +372,11 @@ def run_ours(args, rank, world, local_rank):
                      "note": "algorithmic bytes = node fetches x node size + triangle tests x 48 B + 17 B/ray I/O; "
                              "L1/L2 serve most of them (compulsory DRAM bytes in compulsory_bytes_per_launch)",
                      "compulsory_bytes_per_launch": uniq_bytes,
+                     # per ray from the same ncu capture: DRAM, L2 and L1 (global-load sector) bytes
+                     "ncu_bytes_per_ray": ({"dram": traffic / n_beams,
+                                            "l2": NCU_TRAFFIC["l2_bytes"] / n_beams,
+                                            "l1_global_load": NCU_TRAFFIC["l1_global_load_bytes"] / n_beams}
+                                           if same_kernel else None),
                      "compulsory_frac": uniq_bytes / (kernel_ms / 1e3) / 1e9 / hbm},
         "work_per_ray": {k: (v if k == "node_bytes" else v / n_beams) for k, v in counters.items()},
         "alu": {"flops_per_launch": flops, "achieved_tflops": alu_tf, "peak_tflops": fp32_peak_tflops(torch, sm_mhz),
