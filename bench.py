@@ -627,7 +627,7 @@ def cpu_baseline(w, args, n_beams=None):
     t0 = time.perf_counter()
     oracle.cast(w.scene, w.sensors, w.frames, T, w.seed, samples=samples, n_threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": nb / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": nb / dt, "unit": UNIT, "cores": cores, "per_core": nb / dt / cores, "kind": "oracle",
             "sample": f"{nb} seeded beams of the same frame (brute force FP64 over all {w.scene.n_tris} tris), "
                       f"{dt:.1f} s"}
 
@@ -652,8 +652,8 @@ def run_reference(args, rank, world):
             "impl": "reference",
             "config": {"workload": "cfg1: 128-ch x 2048 az over the 1,036,288-tri scene; each step a bounded "
                                    f"sample of {args.ref_beams} beams"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                             "sample": f"{args.ref_beams} seeded beams per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "per_core": value / cb["cores"],
+                             "kind": "oracle", "sample": f"{args.ref_beams} seeded beams per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
 
