@@ -348,8 +348,10 @@ def run_ours(args, rank, world, local_rank):
     same_kernel = NCU_TRAFFIC["sources"] == kernel_digest()
     traffic = NCU_TRAFFIC["bytes"] if same_kernel else None
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
-    # FP32 ops per node fetch: 12 (binary) or 24 (4-wide) slab subtract+multiply pairs; 40 per triangle test
-    flops = counters["node_visits"] * (counters["node_bytes"] // 64) * 2 * 24 + counters["tri_tests"] * 40
+    # FP32 ops per child box of a fetched node: 6 slab subtracts + 6 multiplies, 3 max (entry, with t_eps),
+    # 2 min (exit), the far-scale multiply, the min with the best hit and the compare = 20; a node holds
+    # node_bytes / 32 children (2, 4 or 8); 40 per watertight triangle test
+    flops = counters["node_visits"] * (counters["node_bytes"] // 32) * 20 + counters["tri_tests"] * 40
     alu_tf = flops / (kernel_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
