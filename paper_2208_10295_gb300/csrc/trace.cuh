@@ -341,6 +341,23 @@ __device__ __forceinline__ void slab4_planes(float4 e, float4 x, unsigned long l
     unpack2(slab2(pack2(x.z, x.w), o2, i2), tout.z, tout.w);
 }
 
+// Three-input FP32 max / min (sm_100+): the same result as the two-input
+// fmaxf / fminf chains, NaN inputs ignored unless all are NaN, in one
+// instruction and one dependent step instead of two.
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Near and far slab distances of four child boxes (entry and exit planes per
 // axis already chosen by the direction signs): near = max(axis entries,
 // t_eps), far = min(axis exits) * kFarScale, each slab distance rounded as
@@ -350,16 +367,14 @@ __device__ __forceinline__ void near_far4(float4 xe, float4 xx, float4 ye, float
                                           unsigned long long ix2, unsigned long long iy2, unsigned long long iz2,
                                           float4& kn, float4& kf)
 {
-    float4 tin, tout, ti, to;
-    slab4_planes(xe, xx, ox2, ix2, tin, tout);
-    slab4_planes(ye, yx, oy2, iy2, ti, to);
-    tin = make_float4(fmaxf(tin.x, ti.x), fmaxf(tin.y, ti.y), fmaxf(tin.z, ti.z), fmaxf(tin.w, ti.w));
-    tout = make_float4(fminf(tout.x, to.x), fminf(tout.y, to.y), fminf(tout.z, to.z), fminf(tout.w, to.w));
-    slab4_planes(ze, zx, oz2, iz2, ti, to);
-    kn = make_float4(fmaxf(fmaxf(tin.x, ti.x), kTEps), fmaxf(fmaxf(tin.y, ti.y), kTEps),
-                     fmaxf(fmaxf(tin.z, ti.z), kTEps), fmaxf(fmaxf(tin.w, ti.w), kTEps));
-    kf = make_float4(fminf(tout.x, to.x) * kFarScale, fminf(tout.y, to.y) * kFarScale,
-                     fminf(tout.z, to.z) * kFarScale, fminf(tout.w, to.w) * kFarScale);
+    float4 xi, xo, yi, yo, zi, zo;
+    slab4_planes(xe, xx, ox2, ix2, xi, xo);
+    slab4_planes(ye, yx, oy2, iy2, yi, yo);
+    slab4_planes(ze, zx, oz2, iz2, zi, zo);
+    kn = make_float4(max3f(xi.x, yi.x, fmaxf(zi.x, kTEps)), max3f(xi.y, yi.y, fmaxf(zi.y, kTEps)),
+                     max3f(xi.z, yi.z, fmaxf(zi.z, kTEps)), max3f(xi.w, yi.w, fmaxf(zi.w, kTEps)));
+    kf = make_float4(min3f(xo.x, yo.x, zo.x) * kFarScale, min3f(xo.y, yo.y, zo.y) * kFarScale,
+                     min3f(xo.z, yo.z, zo.z) * kFarScale, min3f(xo.w, yo.w, zo.w) * kFarScale);
 }
 
 // child code of slot j (0..7) of an 8-wide node
