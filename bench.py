@@ -45,7 +45,7 @@ POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal,
 # the cast kernel as the roofline times it (cfg1 frame, dense valid flags out,
 # L2 flushed before the launch), from one ncu capture, with the digest of the
 # kernel sources the capture ran.  Reported only while the sources still match.
-NCU_TRAFFIC = {"sources": "874d188715b92447", "bytes": 10_482_688, "l2_bytes": 3_975_268 * 32,
+NCU_TRAFFIC = {"sources": "e5800d28009b0135", "bytes": 10_460_416, "l2_bytes": 3_981_372 * 32,
                "l1_global_load_bytes": 7_811_641 * 32}   # profiles/k_cast_cfg1_ncu_full.md
 KERNEL_SOURCES = ("cast.cu", "shade.cuh", "trace.cuh", "common.cuh", "philox.cuh")
 
