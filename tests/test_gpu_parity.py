@@ -560,3 +560,83 @@ def test_all_sensor_slots_mixed_batch_every_beam(L):
     assert np.array_equal(points["range"][:n].cpu().numpy().view(np.uint32), gpu["range"][v].view(np.uint32))
     assert np.array_equal(points["intensity"][:n].cpu().numpy().view(np.uint32), gpu["intensity"][v].view(np.uint32))
     scene.free()
+
+
+def _box_tris(lo, hi):
+    """12 triangles (outward winding) of the axis-aligned box [lo, hi]."""
+    x0, y0, z0 = lo
+    x1, y1, z1 = hi
+    v = np.array([[x0, y0, z0], [x1, y0, z0], [x1, y1, z0], [x0, y1, z0],
+                  [x0, y0, z1], [x1, y0, z1], [x1, y1, z1], [x0, y1, z1]], np.float32)
+    f = np.array([[0, 2, 1], [0, 3, 2], [4, 5, 6], [4, 6, 7], [0, 1, 5], [0, 5, 4],
+                  [1, 2, 6], [1, 6, 5], [2, 3, 7], [2, 7, 6], [3, 0, 4], [3, 4, 7]], np.uint32)
+    return v, f
+
+
+def _in_plane_workload():
+    """Beams lying exactly in box planes.  The sensor sits at (0, 0, 1); its
+    horizontal beams (elevation 0: direction z exactly 0) run in the plane
+    z = 1, which is the top of some boxes and the bottom of others, and its
+    azimuth-0 beams (direction y exactly 0) run in the plane y = 0, a face of
+    some boxes.  Their slab distances there are 0 * inf = NaN, which the box
+    test must ignore (the axis is then unconstrained) in the leaves' boxes and
+    in every union box above them.  Four walls close the arena so every
+    horizontal beam ends on a surface."""
+    rng = np.random.default_rng(5150)
+    verts, tris = [], []
+
+    def add(v, f):
+        tris.append(f + sum(len(x) for x in verts))
+        verts.append(v)
+    add(np.array([[-40, -40, 0], [40, -40, 0], [40, 40, 0], [-40, 40, 0]], np.float32),
+        np.array([[0, 1, 2], [0, 2, 3]], np.uint32))
+    for lo, hi in (((30, -40, 0), (31, 40, 6)), ((-31, -40, 0), (-30, 40, 6)),
+                   ((-40, 30, 0), (40, 31, 6)), ((-40, -31, 0), (40, -30, 6))):
+        add(*_box_tris(lo, hi))
+    for k in range(40):
+        x0 = float(rng.integers(3, 25)) * (1 if k % 2 else -1)
+        y0 = 0.0 if k % 5 == 0 else float(rng.integers(-25, 25))
+        sx, sy = float(rng.integers(1, 4)), float(rng.integers(1, 4))
+        z0, z1 = (0.0, 1.0) if k % 3 == 0 else ((1.0, 2.5) if k % 3 == 1 else (0.0, float(rng.integers(2, 4))))
+        add(*_box_tris((x0, y0, z0), (x0 + sx, y0 + sy, z1)))
+    V = np.concatenate(verts)
+    T = np.concatenate(tris)
+    n = T.shape[0]
+    scene = synth.Scene(V, T, (np.arange(n) % 2).astype(np.uint16), (1 + np.arange(n) // 12).astype(np.uint32))
+    el = np.array([-10.0, -1.0, 0.0, 1.0, 10.0])
+    az, elv = synth.sensors.spinning_pattern(el, 720)
+    sensor = synth.SensorSpec("in_plane", az, elv, r_min=0.3, r_max=80.0, d_max=80.0, RL_max=0.5, sigma=0.0)
+    frames = synth.workloads.make_frames([(0, 0, synth.workloads.pose_rows(np.eye(3), [0.0, 0.0, 1.0]))])
+    params = synth.material_params(np.random.default_rng(5151), 2)
+    return synth.Workload("in_plane", scene, [sensor], frames, params, 77)
+
+
+def test_beams_lying_in_box_planes(L):
+    """Beams in the planes of box faces (NaN slab distances): every traversal
+    (binary per lane, warp-synchronous, 4-wide and 8-wide, whose box tests take
+    the near and far distances by different min/max sequences) gives the same
+    records bit for bit, and they match the oracle's brute force on every beam
+    outside the counted exemptions."""
+    w = _in_plane_workload()
+    d = w.sensors[0]
+    dirs = None
+    cfg0 = L.launch_config()
+    try:
+        L.set_launch_config(traversal=2)
+        base, scene = gpu_cast(L, w)
+        dirs = L.beam_dirs(0)
+        for tv in (0, 1, 3):
+            L.set_launch_config(traversal=tv)
+            other, _ = gpu_cast(L, w, scene)
+            for k in base:
+                assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), (tv, k)
+    finally:
+        L.set_launch_config(**cfg0)
+    # the premise: exact zeros in the directions of the in-plane beams
+    horiz = d.el_rad == 0.0
+    assert np.all(dirs[horiz, 2] == 0.0) and np.all(dirs[d.az_rad == 0.0, 1] == 0.0)
+    rep = compare(base, oracle_cast(w), label=f"beams in box planes, {d.n_beams} beams")
+    _report(rep)
+    assert np.all(base["tri"][horiz] != 0xFFFFFFFF)
+    assert rep["hits"] > 0.9 * d.n_beams
+    scene.free()
