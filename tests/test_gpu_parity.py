@@ -635,9 +635,11 @@ def test_beams_lying_in_box_planes(L):
     # the premise: exact zeros in the directions of the in-plane beams
     horiz = d.el_rad == 0.0
     assert np.all(dirs[horiz, 2] == 0.0) and np.all(dirs[d.az_rad == 0.0, 1] == 0.0)
-    rep = compare(base, oracle_cast(w), label=f"beams in box planes, {d.n_beams} beams")
+    ref = oracle_cast(w)
+    rep = compare(base, ref, label=f"beams in box planes, {d.n_beams} beams")
     _report(rep)
     assert np.all(base["tri"][horiz] != 0xFFFFFFFF)
-    # every beam but the +10 deg channel (which clears the 6 m walls) ends on a surface
-    assert rep["hits"] >= 0.8 * d.n_beams - 720
+    # every beam up to +1 deg ends on a surface (the +10 deg channel clears the 6 m walls)
+    low = d.el_rad < np.deg2rad(5.0)
+    assert np.all(ref["tri"][low] != 0xFFFFFFFF) and np.all(base["tri"][low] != 0xFFFFFFFF)
     scene.free()
