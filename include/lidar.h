@@ -260,6 +260,18 @@ lidar_status lidar_cast(lidar_ctx* ctx, const lidar_scene* scene, const lidar_fr
                         int32_t n_frames, uint64_t seed, const lidar_beams* beams,
                         const lidar_points* points, int64_t* n_points_dev);
 
+/* Copies the first `count` points of a cast's point cloud to the host: for
+ * every field that both `dev` (device arrays, as passed to the cast) and
+ * `host` (host arrays; pinned memory makes the copies asynchronous) have
+ * non-NULL, one device-to-host copy queued on `stream` (a cudaStream_t; NULL:
+ * the context's stream), in one call.  `count` is the number of kept returns
+ * as read back from the cast's n_points_dev, already on the host (the copies
+ * are ordered after the cast only by the stream).  Returns without copying
+ * when count is 0.  LIDAR_EINVAL: a NULL ctx, dev or host, or count < 0 or
+ * above either capacity; LIDAR_ECUDA: a copy could not be queued. */
+lidar_status lidar_points_download(lidar_ctx* ctx, const lidar_points* dev, const lidar_points* host,
+                                   int64_t count, void* stream);
+
 /* -------------------------------------------------------- batches and graphs */
 
 /* A device-resident list of frames for repeated casts (many frames along a

@@ -120,6 +120,8 @@ _PROTOS = [
     ("lidar_set_materials", ctypes.c_int, [c_vp, c_vp, ctypes.c_int32]),
     ("lidar_cast", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, ctypes.c_uint64,
                                   ctypes.POINTER(lidar_beams), ctypes.POINTER(lidar_points), c_vp]),
+    ("lidar_points_download", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_points), ctypes.POINTER(lidar_points),
+                                             ctypes.c_int64, c_vp]),
     ("lidar_batch_create", ctypes.c_int, [c_vp, c_vp, ctypes.c_int32, ctypes.POINTER(c_vp)]),
     ("lidar_batch_free", None, [c_vp]),
     ("lidar_batch_set_poses", ctypes.c_int, [c_vp, c_vp, c_vp]),
@@ -206,6 +208,7 @@ lidar_build_tables = _fwd("lidar_build_tables")
 lidar_build_tables_backward = _fwd("lidar_build_tables_backward")
 lidar_set_materials = _fwd("lidar_set_materials")
 lidar_cast = _fwd("lidar_cast")
+lidar_points_download = _fwd("lidar_points_download")
 lidar_batch_create = _fwd("lidar_batch_create")
 lidar_batch_free = _fwd("lidar_batch_free")
 lidar_batch_set_poses = _fwd("lidar_batch_set_poses")

@@ -824,6 +824,32 @@ static lidar_status cast_checks(lidar_ctx* c, const lidar_scene* scene, const li
     return LIDAR_OK;
 }
 
+lidar_status lidar_points_download(lidar_ctx* c, const lidar_points* dev, const lidar_points* host, int64_t count,
+                                   void* stream)
+{
+    NvtxRange nvtx_("lidar_points_download");
+    LIDAR_CHECK_ARG(c != nullptr && dev != nullptr && host != nullptr, "lidar_points_download: NULL argument");
+    LIDAR_CHECK_ARG(count >= 0 && count <= dev->capacity && count <= host->capacity,
+                    "lidar_points_download: count must be in [0, both capacities]");
+    if (count == 0) return LIDAR_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const size_t n = (size_t)count;
+    auto copy = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+        if (dst == nullptr || src == nullptr) return cudaSuccess;
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    };
+    LIDAR_CUDA(copy(host->xyz, dev->xyz, 3 * n * sizeof(float)));
+    LIDAR_CUDA(copy(host->range, dev->range, n * sizeof(float)));
+    LIDAR_CUDA(copy(host->intensity, dev->intensity, n * sizeof(float)));
+    LIDAR_CUDA(copy(host->normal, dev->normal, 3 * n * sizeof(float)));
+    LIDAR_CUDA(copy(host->material, dev->material, n * sizeof(uint16_t)));
+    LIDAR_CUDA(copy(host->instance, dev->instance, n * sizeof(uint32_t)));
+    LIDAR_CUDA(copy(host->beam, dev->beam, n * sizeof(uint32_t)));
+    LIDAR_CUDA(copy(host->frame, dev->frame, n * sizeof(uint32_t)));
+    return LIDAR_OK;
+}
+
 lidar_status lidar_cast(lidar_ctx* c, const lidar_scene* scene, const lidar_frame* frames, int32_t n_frames,
                         uint64_t seed, const lidar_beams* beams, const lidar_points* points, int64_t* n_points_dev)
 {

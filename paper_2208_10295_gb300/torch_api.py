@@ -201,6 +201,16 @@ class Lidar:
                           _ptr(points["count"]) if points is not None else None)
         C.check(st, "lidar_cast")
 
+    def download_points(self, points, host, count: int, stream=None):
+        """Queues the copy of the first `count` points of every field present in
+        both `points` (device tensors of a cast) and `host` (host tensors,
+        pinned for asynchronous copies) on `stream` (default: the context's
+        stream); one native call for all fields."""
+        ds, hs = self.points_struct(points), self.points_struct(host)
+        sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        C.check(C.lidar_points_download(self.handle, ctypes.byref(ds), ctypes.byref(hs), int(count), sp),
+                "lidar_points_download")
+
     def cast(self, scene: Scene, frames, seed: int, dense=True, points_capacity=None):
         """Returns (beams dict, points dict or None)."""
         n = self.total_beams(frames)

@@ -643,3 +643,36 @@ def test_beams_lying_in_box_planes(L):
     low = d.el_rad < np.deg2rad(5.0)
     assert np.all(ref["tri"][low] != 0xFFFFFFFF) and np.all(base["tri"][low] != 0xFFFFFFFF)
     scene.free()
+
+
+def test_points_download(L):
+    """lidar_points_download copies the first `count` points of every field
+    present on both sides (pinned host tensors, a side stream) bit for bit as
+    the device holds them, leaves the rest of the host buffers alone, skips
+    fields missing on either side, and rejects a count above a capacity."""
+    w = synth.small_terrain(seed=12, n_frames=2, n_az=200)
+    scene, _ = setup(L, w)
+    n = L.total_beams(w.frames)
+    _, pts = L.cast(scene, w.frames, w.seed, dense=False, points_capacity=n)
+    assert L.sync_status() == 0
+    cnt = int(pts["count"].item())
+    assert 0 < cnt < n
+    host = {k: torch.full(v.shape, 0x5A, dtype=v.dtype, pin_memory=True) for k, v in pts.items()}
+    del host["normal"]
+    s = torch.cuda.Stream(device=L.device)
+    s.wait_stream(L.stream)
+    L.download_points(pts, host, cnt, stream=s)
+    s.synchronize()
+    for k, h in host.items():
+        if k == "count":
+            continue
+        d = pts[k].cpu()
+        assert torch.equal(h[:cnt], d[:cnt]), k
+        assert bool((h[cnt:] == 0x5A).all()), k
+    L.download_points(pts, host, 0)
+    from paper_2208_10295_gb300 import capi
+    for bad in (n + 1, -1):
+        with pytest.raises(capi.LidarError) as e:
+            L.download_points(pts, host, bad)
+        assert e.value.status == capi.LIDAR_EINVAL
+    scene.free()
