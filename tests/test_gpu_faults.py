@@ -2,7 +2,6 @@
 argument checks, calls in the wrong state, capacity overflow, and allocation
 failures injected on the host (LIDAR_FAULT_ALLOC_AT, in a child process so
 the allocation count starts from zero)."""
-import ctypes
 import os
 import subprocess
 import sys

@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import frame_offsets, gpu_cast, oracle_cast, setup, stratified_sample
+from gpu_util import gpu_cast, oracle_cast, setup
 from parity import compare, compare_subray, to_numpy
 
 torch = pytest.importorskip("torch")

@@ -2,12 +2,11 @@
 Python's libm, exact-rational replay of FP32 operations, numpy's Philox,
 distributional properties, and finite differences."""
 import math
-from fractions import Fraction
 
 import numpy as np
 import pytest
 
-from exact import F, f32_add, f32_div, f32_fma, f32_mul, f32_sqrt, f32_sub
+from exact import f32_add, f32_div, f32_fma, f32_mul, f32_sqrt, f32_sub
 
 
 def test_beam_dirs_follow_spherical_definition(oracle_lib):

@@ -7,7 +7,7 @@ import math
 import numpy as np
 
 import synth
-from scenes_tiny import const_table, identity_frame, quads_scene, sensor, wall_x
+from scenes_tiny import const_table, quads_scene, sensor, wall_x
 
 
 def _rot(axis, ang):
