@@ -326,12 +326,12 @@ lidar_status lidar_cast_backward_mse(lidar_ctx* ctx, int64_t n_beams, const lida
                                      float* loss_dev, float* grad_table_dev, float* grad_gain_dev);
 
 /* Allocation-free variant of lidar_cast_backward_mse (no counterpart in the
- * paper; it exists for callers that must not allocate device memory, such as
- * code that runs while a CUDA graph is being captured in global capture mode,
- * sensor loops with hard real-time deadlines that cannot afford cudaMalloc's
- * implicit synchronisation, or host applications whose memory pool already
- * holds the device's memory).  It needs no context either: the caller passes
- * the stream, the tape arrays and the reflectance table directly.
+ * paper; it exists for callers that must not allocate device memory: sensor
+ * loops with hard real-time deadlines that cannot afford cudaMalloc's implicit
+ * device synchronisation, host applications or plugins whose own memory pool
+ * already holds the device's memory, and code that may not create a context).
+ * It needs no context either: the caller passes the stream, the tape arrays
+ * and the reflectance table directly.
  *   cuda_stream    cudaStream_t to enqueue on (NULL = legacy default stream),
  *                  on the device that is current on the calling thread
  *   valid_dev, mat_dev, theta_deg_dev, rf_dev
@@ -347,10 +347,13 @@ lidar_status lidar_cast_backward_mse(lidar_ctx* ctx, int64_t n_beams, const lida
  * until the process exits).  The entry point calls no cudaMalloc, cudaFree or
  * allocating library routine.  Its first call on a device looks up that
  * array's device address (cudaGetSymbolAddress, once per device, cached), so
- * make that first call before any stream capture.  All calls share the one
- * array: the accumulators are cleared on the stream at the start of every call,
- * and calls whose work overlaps on the GPU (other streams, other threads) race
- * on it and must be serialised by the caller. */
+ * make that first call before any stream capture.  The cached address belongs
+ * to the device's primary context as it was then: after cudaDeviceReset on
+ * that device the array may move, and this entry point must not be called
+ * again in that process.  All calls share the one array: the accumulators are
+ * cleared on the stream at the start of every call, and calls whose work
+ * overlaps on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller. */
 #define LIDAR_NOALLOC_MAX_MATERIALS 64
 #define LIDAR_NOALLOC_SCRATCH_BYTES 55296
 lidar_status lidar_cast_backward_mse_noalloc(void* cuda_stream, int64_t n_beams, const uint8_t* valid_dev,
@@ -507,6 +510,19 @@ typedef struct {
 
 lidar_status lidar_get_launch_config(lidar_ctx* ctx, lidar_launch_config* out);
 lidar_status lidar_set_launch_config(lidar_ctx* ctx, const lidar_launch_config* cfg);
+
+/* Limit, in nanoseconds of GPU time (the device's global timer), of every
+ * bounded device-side wait in the context's kernels: the grid-wide wait of a
+ * cast whose point-cloud scatter runs inside the cast kernel, and the waits of
+ * the one-pass adjoint.  A wait that runs out records LIDAR_ETIMEOUT in the
+ * status word (read by lidar_sync_status) and its block leaves the kernel
+ * without the work after the wait, so that call's outputs past the wait are
+ * incomplete; nothing hangs and the context stays usable.  Default
+ * 2,000,000,000 (2 s), far beyond any legitimate wait; 0 gives up at the first
+ * check that finds the wait unfinished (exercises the timeout path).  Applies
+ * to launches made afterwards. */
+lidar_status lidar_set_wait_limit(lidar_ctx* ctx, uint64_t nanoseconds);
+lidar_status lidar_get_wait_limit(lidar_ctx* ctx, uint64_t* nanoseconds);
 
 #ifdef __cplusplus
 }

@@ -153,6 +153,8 @@ _PROTOS = [
     ("lidar_get_build_options", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_build_options)]),
     ("lidar_get_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
     ("lidar_set_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
+    ("lidar_set_wait_limit", ctypes.c_int, [c_vp, ctypes.c_uint64]),
+    ("lidar_get_wait_limit", ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_uint64)]),
 ]
 
 EXPORTED = [p[0] for p in _PROTOS]
@@ -229,3 +231,5 @@ lidar_schedule_by_cost = _fwd("lidar_schedule_by_cost")
 lidar_reset_schedule = _fwd("lidar_reset_schedule")
 lidar_get_launch_config = _fwd("lidar_get_launch_config")
 lidar_set_launch_config = _fwd("lidar_set_launch_config")
+lidar_set_wait_limit = _fwd("lidar_set_wait_limit")
+lidar_get_wait_limit = _fwd("lidar_get_wait_limit")

@@ -373,7 +373,9 @@ cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid
     unsigned long long* acc = (unsigned long long*)p;
     p += (((size_t)n_acc * 8 + 255) / 256) * 256;
     double* partials = (double*)p;
-    cudaMemsetAsync(scratch, 0, 256 + (((size_t)n_acc * 8 + 255) / 256) * 256, s);
+    // every call starts from zeroed accumulators (the scratch may hold the last call's)
+    const cudaError_t me = cudaMemsetAsync(scratch, 0, 256 + (((size_t)n_acc * 8 + 255) / 256) * 256, s);
+    if (me != cudaSuccess) return me;
     // one wave of resident blocks (at most kAdjBlocks), no more than the tape needs
     int device = 0, sms = 0;
     cudaGetDevice(&device);

@@ -211,11 +211,10 @@ __device__ __forceinline__ uint64_t global_ns()
 
 // Grid-wide barrier number `k` (1, 2, ...) over a counter zeroed before the
 // launch, for cooperative launches only (all blocks co-resident).  The wait
-// is bounded: after kBarrierTimeoutNs it raises ST_TIMEOUT and returns false
-// in every thread of the block, which then leaves the kernel.
-constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;
-
-__device__ bool grid_barrier(unsigned* counter, unsigned k, int* status)
+// is bounded: after wait_ns nanoseconds (the context's wait limit, 2 s by
+// default) it raises ST_TIMEOUT and returns false in every thread of the
+// block, which then leaves the kernel.
+__device__ bool grid_barrier(unsigned* counter, unsigned k, int* status, uint64_t wait_ns)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -226,7 +225,7 @@ __device__ bool grid_barrier(unsigned* counter, unsigned k, int* status)
         const uint64_t t0 = global_ns();
         int ok = 1;
         while (*(volatile unsigned*)counter < target) {
-            if (global_ns() - t0 > kBarrierTimeoutNs) {
+            if (global_ns() - t0 > wait_ns) {
                 raise_status(status, ST_TIMEOUT);
                 ok = 0;
                 break;
@@ -248,7 +247,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                                               unsigned long long* work_counter, int tile_rays, WorkCount wc,
                                               CompactCounts cc, lidar_points pts, int64_t n_beams_total, int fused,
                                               const __grid_constant__ InlineFrames inl, unsigned* zero_next,
-                                              int64_t zero_words)
+                                              int64_t zero_words, uint64_t wait_ns)
 {
     const int lane = threadIdx.x & 31;
     // clear the counter region of the cast before this one, for the cast after it
@@ -373,7 +372,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
         // can wait until every kept return is counted; then each block
         // scatters a contiguous run of tiles, whose first offset is the sum of
         // the (final) counts before the run — no scan and no second wait
-        if (!grid_barrier(cc.done, 1, status)) return;
+        if (!grid_barrier(cc.done, 1, status, wait_ns)) return;
         __shared__ uint32_t s_warp[kScatterItems * 8];
         __shared__ long long s_red[8];
         const int64_t t0 = (int64_t)blockIdx.x * cc.n_tiles / gridDim.x;
@@ -481,6 +480,7 @@ struct CastArgs {
     InlineFrames inl;
     unsigned* zero_next;
     int64_t zero_words;
+    uint64_t wait_ns;
 };
 
 template <bool C, int V, int W>
@@ -509,12 +509,12 @@ cudaError_t launch_one(cudaStream_t s, CastArgs a, int64_t grid, int block, size
         if (grid > (int64_t)per_sm * num_sms) grid = (int64_t)per_sm * num_sms;
         void* args[] = {&a.scene, &a.sensors, &a.frames, &a.n_frames, &a.prefix, &a.n_tiles, &a.table, &a.seed,
                         &a.out, &a.status, &a.work_counter, &a.tile_rays, &a.wc, &a.cc, &a.pts, &a.n_total,
-                        &a.fused, &a.inl, &a.zero_next, &a.zero_words};
+                        &a.fused, &a.inl, &a.zero_next, &a.zero_words, &a.wait_ns};
         return cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)grid), dim3(block), args, smem, s);
     }
     fn<<<(unsigned)grid, block, smem, s>>>(a.scene, a.sensors, a.frames, a.n_frames, a.prefix, a.n_tiles, a.table,
                                             a.seed, a.out, a.status, a.work_counter, a.tile_rays, a.wc, a.cc, a.pts,
-                                            a.n_total, a.fused, a.inl, a.zero_next, a.zero_words);
+                                            a.n_total, a.fused, a.inl, a.zero_next, a.zero_words, a.wait_ns);
     return cudaGetLastError();
 }
 
@@ -552,6 +552,7 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     a.tile_rays = cfg.tile_rays;
     a.wc = count ? *count : WorkCount{nullptr, nullptr, nullptr, nullptr};
     a.n_total = n_beams_total;
+    a.wait_ns = cfg.wait_ns;
     if (inline_frames) a.inl = *inline_frames;  // else n == 0: the device table
     const bool clean = region && region->clean;
     if (region) {

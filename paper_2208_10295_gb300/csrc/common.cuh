@@ -135,6 +135,7 @@ struct LaunchCfg {
     int ray_order;
     int traversal;
     int fused_scatter;   // compaction scatter inside the cast (cooperative launch)
+    uint64_t wait_ns = 2000000000ull;  // limit of every bounded device-side wait
 };
 
 // ------------------------------------------------------------------ kernel launchers

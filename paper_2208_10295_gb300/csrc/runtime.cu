@@ -1546,4 +1546,18 @@ lidar_status lidar_set_launch_config(lidar_ctx* c, const lidar_launch_config* cf
     return LIDAR_OK;
 }
 
+lidar_status lidar_set_wait_limit(lidar_ctx* c, uint64_t ns)
+{
+    LIDAR_CHECK_ARG(c != nullptr, "lidar_set_wait_limit: NULL context");
+    c->cfg.wait_ns = ns;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_get_wait_limit(lidar_ctx* c, uint64_t* ns)
+{
+    LIDAR_CHECK_ARG(c != nullptr && ns != nullptr, "lidar_get_wait_limit: NULL argument");
+    *ns = c->cfg.wait_ns;
+    return LIDAR_OK;
+}
+
 }  // extern "C"

@@ -341,6 +341,15 @@ class Lidar:
         c = C.lidar_launch_config(**cur)
         C.check(C.lidar_set_launch_config(self.handle, ctypes.byref(c)), "lidar_set_launch_config")
 
+    def wait_limit(self) -> int:
+        """Limit (ns) of the bounded device-side waits."""
+        v = ctypes.c_uint64()
+        C.check(C.lidar_get_wait_limit(self.handle, ctypes.byref(v)), "lidar_get_wait_limit")
+        return int(v.value)
+
+    def set_wait_limit(self, ns: int):
+        C.check(C.lidar_set_wait_limit(self.handle, int(ns)), "lidar_set_wait_limit")
+
 
 class Batch:
     """Device-resident frames: casts without host copies, CUDA-graph capture."""
@@ -406,10 +415,15 @@ class LidarCast(torch.autograd.Function):
     """Intensities of every beam as a differentiable function of the material
     parameters (a, s, w) [M,3] and the sensor gain, with hits and masks held
     fixed from the forward pass (the per-beam model of Sec. II with the
-    table builder in front of it)."""
+    table builder in front of it).  The gain is that of one sensor slot, so
+    every frame must name that slot (frames of other slots would keep their
+    own gains in the forward pass while the backward applied this one)."""
 
     @staticmethod
     def forward(ctx, params, gain, lidar: Lidar, scene: Scene, frames, seed: int, slot: int):
+        fr = _frames_array(frames)
+        if np.any(fr["sensor"] != slot):
+            raise ValueError(f"LidarCast differentiates the gain of sensor slot {slot}: every frame must name it")
         table = lidar.build_tables(params.detach())
         lidar.set_materials(table)
         lidar.set_sensor_gain(slot, float(gain.detach().cpu()))

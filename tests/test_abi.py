@@ -90,3 +90,27 @@ def test_oracle_and_cuda_path_are_independent():
         if f.endswith(".py"):
             mods = _imports(os.path.join(ROOT, "synth", f))
             assert "oracle" not in mods and "paper_2208_10295_gb300" not in mods
+
+
+def test_wait_limit_argument_checks(libpath):
+    from paper_2208_10295_gb300 import capi
+    capi.load(libpath)
+    assert capi.lidar_set_wait_limit(None, 0) == capi.LIDAR_EINVAL
+    assert capi.lidar_get_wait_limit(None, None) == capi.LIDAR_EINVAL
+
+
+def test_autograd_function_rejects_frames_of_other_slots():
+    """LidarCast differentiates one sensor slot's gain: frames naming another
+    slot are refused before anything reaches the device."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2208_10295_gb300 import LidarCast
+    w = synth.small_terrain(seed=1, n_frames=2, n_az=8)
+    fr = w.frames.copy()
+    fr["sensor"][1] = 3
+    p = torch.tensor(np.asarray(w.params, np.float32), requires_grad=True)
+    g = torch.tensor(1.0, requires_grad=True)
+    with pytest.raises(ValueError, match="slot 0"):
+        LidarCast.apply(p, g, None, None, fr, w.seed, 0)

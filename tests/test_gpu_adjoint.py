@@ -137,6 +137,19 @@ def test_adjoint_cfg3_sampled(L):
     assert loss == pytest.approx(L_ref, rel=NORM_RTOL)
     close_grad(gT, gT_ref, "cfg3 dL/dT")
     assert gg == pytest.approx(gg_ref, rel=NORM_RTOL)
+    _check_params_grad(L, params, gT, w.params, gT_ref, "cfg3")
+
+
+def _check_params_grad(L, params, gT, params_np, gT_ref, label):
+    """dL/d(a, s, w) through the table builder's chain rule: the GPU's builder
+    backward applied to the GPU's dL/dT against the oracle's FP64 builder
+    backward applied to the oracle's dL/dT, for the three columns together
+    and for the specular width on its own (its gradient is an order of
+    magnitude below the albedo's, so the joint check alone would not see it)."""
+    gp = L.build_tables_backward(params, torch.tensor(gT, device=L.device)).cpu().numpy()
+    gp_ref = oracle.build_tables_backward(params_np, gT_ref)
+    close_grad(gp, gp_ref, f"{label} dL/d(a,s,w)")
+    close_grad(gp[:, 2], gp_ref[:, 2], f"{label} dL/dw (specular width)")
 
 
 def test_cfg3_finite_differences_full_size(L):
@@ -243,3 +256,4 @@ def test_adjoint_city_sampled(L):
     assert loss == pytest.approx(L_ref, rel=NORM_RTOL)
     close_grad(gT, gT_ref, "city dL/dT")
     assert gg == pytest.approx(gg_ref, rel=NORM_RTOL)
+    _check_params_grad(L, params, gT, w.params, gT_ref, "city")

@@ -122,3 +122,46 @@ def test_injected_allocation_failure(L, nth):
     assert status in (capi.LIDAR_ENOMEM, capi.LIDAR_ECAPACITY, capi.LIDAR_OK), status
     if nth <= 3:
         assert status == capi.LIDAR_ENOMEM
+
+
+def test_grid_wait_runs_out_and_recovers(L):
+    """The bounded grid-wide wait of a cast with the point-cloud scatter fused
+    into the cast kernel, made to run out: with a wait limit of 0 ns every
+    block that arrives before the last one gives up at its first check, records
+    LIDAR_ETIMEOUT and leaves the kernel (no hang, no fault).  The dense
+    records, written before the wait, are intact; with the default limit
+    restored the next cast reproduces the reference point cloud bit for bit."""
+    from paper_2208_10295_gb300 import capi
+    w = synth.small_terrain(seed=43, n_frames=4, n_az=1024)
+    scene = L.build_scene(w.scene.verts, w.scene.tris, w.scene.mat, w.scene.inst)
+    L.set_sensor(0, w.sensors[0])
+    L.set_materials(L.build_tables(torch.tensor(w.params, device=L.device)))
+    n = L.total_beams(w.frames)
+    cfg0 = L.launch_config()
+    limit0 = L.wait_limit()
+    assert limit0 == 2_000_000_000
+    try:
+        L.set_launch_config(fused_scatter=1)
+        if not L.launch_config()["fused_scatter"]:
+            pytest.skip("no cooperative launch on this device")
+        ref_beams, ref_pts = L.cast(scene, w.frames, w.seed, dense=True, points_capacity=n)
+        assert L.sync_status() == 0
+        c0 = int(ref_pts["count"].item())
+        assert c0 > 1000
+        L.set_wait_limit(0)
+        beams, _ = L.cast(scene, w.frames, w.seed, dense=True, points_capacity=n)
+        assert L.sync_status() == capi.LIDAR_ETIMEOUT
+        assert "timed out" in capi.last_error()
+        for k in ref_beams:
+            assert torch.equal(beams[k], ref_beams[k]), k
+        L.set_wait_limit(limit0)
+        _, pts = L.cast(scene, w.frames, w.seed, dense=False, points_capacity=n)
+        assert L.sync_status() == 0
+        assert int(pts["count"].item()) == c0
+        for k in ref_pts:
+            if k != "count":
+                assert torch.equal(pts[k][:c0], ref_pts[k][:c0]), k
+    finally:
+        L.set_wait_limit(limit0)
+        L.set_launch_config(**cfg0)
+        scene.free()

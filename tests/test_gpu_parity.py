@@ -94,13 +94,18 @@ def test_small_terrain_subrays(L, n_subrays):
     _report(compare_subray(gpu, ref, label=f"small terrain, {n_subrays} sub-rays"))
 
 
-def test_cfg1_full_frame_sampled(L):
+def test_cfg1_full_frame_every_beam(L):
+    """The headline frame (262,144 beams over 1,036,288 triangles), every beam
+    against the oracle's brute force (about 3.5 minutes of oracle time on 16
+    host cores), the GPU in the benchmark's launch configuration."""
     w = synth.cfg1()
     gpu, _ = gpu_cast(L, w)
-    samples = stratified_sample(w, 1536, seed=1)
-    ref = oracle_cast(w, samples)
-    rep = compare(pick(gpu, w, samples), ref, label="cfg1 full frame, 1536 sampled beams")
+    ref = oracle_cast(w)
+    rep = compare(gpu, ref, label="cfg1 full frame, every beam")
     _report(rep)
+    assert rep["beams"] == 262144
+    # exemptions stay a small, counted minority
+    assert rep["exempt"] <= 1e-3 * rep["beams"]
     # whole-frame properties that hold at any size
     v = gpu["valid"] != 0
     assert v.sum() > 50000
@@ -429,13 +434,15 @@ def test_cfg4_city_subrays_sampled(L):
     against every triangle)."""
     w = synth.cfg4()
     gpu, _ = gpu_cast(L, w, fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst", "sub"))
-    samples = stratified_sample(w, 192, seed=4)
+    samples = stratified_sample(w, 1280, seed=4)
     ref = oracle_cast(w, samples)
-    rep = compare_subray(pick(gpu, w, samples), ref, label="cfg4 city, 7 sub-rays, 192 sampled beams")
+    rep = compare_subray(pick(gpu, w, samples), ref, label="cfg4 city, 7 sub-rays, 1280 sampled beams")
+    rep["strict"] = rep["beams"] - rep["exempt"]
     _report(rep)
-    # most hit beams have several sub-rays of near-equal intensity on the same
-    # surface: those are checked through the ambiguous-choice path
-    assert rep["hits"] + rep["subray_ambiguous_checked"] > 100
+    # many hit beams have several sub-rays of near-equal intensity on the same
+    # surface: those are checked through the ambiguous-choice path; the rest
+    # (a unique strongest sub-ray, or a miss) are compared field by field
+    assert rep["strict"] >= 300, rep
 
 
 def test_direct_casts_back_to_back_with_reused_counters(L):

@@ -1,6 +1,7 @@
 """The allocation-free adjoint entry point, for callers that must not allocate
-device memory (graph capture in global mode, hard real-time loops, hosts whose
-memory pool owns the device).  Its scratch is a fixed array inside the library.
+device memory (hard real-time loops that cannot take cudaMalloc's implicit
+synchronisation, hosts whose memory pool owns the device).  Its scratch is a
+fixed array inside the library.
 
 Checked through the C ABI against lidar_cast_backward_mse on the same tape and
 targets, on two calls in a row (the shared scratch must be cleared between
