@@ -47,6 +47,14 @@ POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal,
 # kernel sources the capture ran.  Reported only while the sources still match.
 NCU_TRAFFIC = {"sources": "e5800d28009b0135", "bytes": 10_460_416, "l2_bytes": 3_981_372 * 32,
                "l1_global_load_bytes": 7_811_641 * 32}   # profiles/k_cast_cfg1_ncu_full.md
+# Binding-unit fractions of the same capture (ncu --set full of one launch):
+# L1/TEX throughput, issue-active and SM-active shares.
+NCU_UNITS = {"l1tex_throughput_pct": 42.6, "issue_active_pct": 43.1, "sm_active_pct": 67.0}
+# FP32 work of one launch of the cast kernel from ncu's SASS instruction
+# counters (sm__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,
+# fp32}_pred_on), FLOPs = 2 ffma + fadd + fmul + 4 ffma2 + 2 fadd2 + 2 fmul2 +
+# the remaining FP32 instructions (min/max, compares) once each.
+NCU_FP32 = {"sources": None, "fp32_flops": None}
 KERNEL_SOURCES = ("cast.cu", "shade.cuh", "trace.cuh", "common.cuh", "philox.cuh")
 
 
@@ -131,9 +139,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def fp32_peak_tflops(torch, sm_mhz):
-    props = torch.cuda.get_device_properties(0)
-    return props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+def measure_fp32_peak(L, gpu_index, seconds=1.0):
+    """FP32 FMA rate measured on this GPU (the library's probe kernel: every SM
+    running independent fused multiply-add chains), repeated for about
+    `seconds` while nvidia-smi samples the SM clock; the best rate and the
+    median clock it ran at."""
+    best = None
+    with ClockSampler(gpu_index) as clk:
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end or best is None:
+            r = L.measure_fp32_rate(1 << 24)
+            if best is None or r["flops_per_s"] > best["flops_per_s"]:
+                best = r
+    c = clk.summary() or {}
+    return {"tflops": best["flops_per_s"] / 1e12, "probe_kernel_ms": best["kernel_ms"],
+            "packed_pairs": best["packed"], "sm_mhz": c.get("sm_mhz"), "clock_reasons": c.get("reasons")}
 
 
 def event_time(torch, stream, fn, flush=None, reps=10, warm=2):
@@ -331,6 +351,17 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- algorithmic work of one launch (instrumented run of the same kernel)
     counters = L.count_work(scene, frames, w.seed)
+    fp32_peak = measure_fp32_peak(L, local_rank) if rank == 0 else None
+    # ---- dense records of the timed frame for the parity check against the oracle's sample
+    parity_dense = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        pf = ("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst")
+        pd = L.alloc_beams(n_beams, pf)
+        L.cast_into(scene, frames, w.seed, pd)
+        if L.sync_status() != 0:
+            raise RuntimeError("device status")
+        parity_dense = {k: v.cpu().numpy() for k, v in pd.items()}
+        del pd
 
     extras = {}
     if not args.no_extras and world == 1:
@@ -355,6 +386,11 @@ def run_ours(args, rank, world, local_rank):
     # node_bytes / 32 children (2, 4 or 8); 40 per watertight triangle test
     flops = counters["node_visits"] * (counters["node_bytes"] // 32) * 20 + counters["tri_tests"] * 40
     alu_tf = flops / (kernel_ms / 1e3) / 1e12
+    # the measured FP32 rate, scaled from the probe's clock to the clock the cast ran at
+    fp_probe = fp32_peak
+    fp_peak = fp_probe["tflops"] * (sm_mhz / fp_probe["sm_mhz"] if fp_probe.get("sm_mhz") else 1.0)
+    ncu_ok = NCU_FP32["sources"] == kernel_digest()
+    ncu_fp32_tf = NCU_FP32["fp32_flops"] / (kernel_ms / 1e3) / 1e12 if ncu_ok else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -374,8 +410,14 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": f"{peaks_src} hbm_gbs (STREAM-style copy)",
                      "bytes_per_launch": visit_bytes, "kernel": "k_cast", "kernel_ms": kernel_ms,
-                     "note": "algorithmic bytes = node fetches x node size + triangle tests x 48 B + 17 B/ray I/O; "
-                             "L1/L2 serve most of them (compulsory DRAM bytes in compulsory_bytes_per_launch)",
+                     "achieved_is": "the traversal's consumption rate of algorithmic bytes (node fetches x node "
+                                    "size + triangle tests x 48 B + 17 B/ray I/O) against the HBM copy peak, the "
+                                    "roofline model of the traversal; L1 and L2 serve most of these bytes, so this "
+                                    "is not an HBM traffic rate (that is compulsory_frac and ncu_bytes_per_ray.dram)",
+                     "binding_unit": (dict(NCU_UNITS, what="latency of dependent node fetches (L1/L2) and "
+                                                           "instruction issue; fractions of one ncu-captured "
+                                                           "launch of this kernel")
+                                      if same_kernel else None),
                      "compulsory_bytes_per_launch": uniq_bytes,
                      # per ray from the same ncu capture: DRAM, L2 and L1 (global-load sector) bytes
                      "ncu_bytes_per_ray": ({"dram": traffic / n_beams,
@@ -384,14 +426,24 @@ def run_ours(args, rank, world, local_rank):
                                            if same_kernel else None),
                      "compulsory_frac": uniq_bytes / (kernel_ms / 1e3) / 1e9 / hbm},
         "work_per_ray": {k: (v if k == "node_bytes" else v / n_beams) for k, v in counters.items()},
-        "alu": {"flops_per_launch": flops, "achieved_tflops": alu_tf, "peak_tflops": fp32_peak_tflops(torch, sm_mhz),
-                "frac": alu_tf / fp32_peak_tflops(torch, sm_mhz), "peak_source": "152 SMs x 128 FP32 lanes x 2 x "
-                                                                                "median SM clock under load"},
+        "alu": {"bound": "alu", "flops_per_launch_alg": flops, "achieved_tflops_alg": alu_tf,
+                "flops_per_launch_ncu": NCU_FP32["fp32_flops"] if ncu_ok else None,
+                "achieved_tflops_ncu": ncu_fp32_tf, "peak_tflops": fp_peak,
+                "frac": (ncu_fp32_tf if ncu_ok else alu_tf) / fp_peak,
+                "frac_alg": alu_tf / fp_peak,
+                "peak_source": "measured: FP32 FMA probe kernel on this GPU, "
+                               f"{fp_probe['tflops']:.1f} TFLOP/s at {fp_probe.get('sm_mhz')} MHz median, scaled "
+                               f"to the {sm_mhz:.0f} MHz median of the timed casts",
+                "probe": fp_probe,
+                "ops": "alg: 20 FP32 ops per child box of a fetched node, 40 per triangle test (from the "
+                       "source); ncu: FP32 thread instructions of one captured launch, packed pairs and FMAs "
+                       "counted as two FLOPs"},
         "clocks": clocks,
     }
     line.update(extras)
     if world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(w, args)
+        line["cpu_baseline"], ref = cpu_baseline(w, args, want_result=True)
+        line["parity"] = parity_check(parity_dense, ref, w)
     if world > 1:
         torch.distributed.destroy_process_group()
     return line
@@ -518,8 +570,8 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
     f_ms = event_time(torch, stream, d3["fwd"], flush, reps=10, warm=2)
     fb_ms = event_time(torch, stream, d3["fwd_bwd"], flush, reps=10, warm=2)
     b_ms = event_time(torch, stream, d3["bwd"], flush, reps=20, warm=3)
-    # the backward's two passes each read the tape and the targets
-    b_bytes = 2 * TAPE_BYTES_PER_BEAM * d3["n"]
+    # algorithmic bytes: the tape and the targets, read once
+    b_bytes = TAPE_BYTES_PER_BEAM * d3["n"]
     hbm = float(load_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS))
     out["differentiation"] = {"workload": "cfg3: 128-ch x 2048 az x 16 frames (4,194,304 beams), forward with tape + "
                                           "fused MSE adjoint to the 32x91 table, widths and gain",
@@ -530,9 +582,8 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
                                                "peak": hbm, "unit": "GB/s",
                                                "frac": b_bytes / (b_ms / 1e3) / 1e9 / hbm,
                                                "bytes_per_launch": b_bytes,
-                                               "note": "tape + targets (16 B/beam) read by both passes (the "
-                                                       "scale pass, then the fixed-point accumulation); L2 "
-                                                       "flushed before each backward"}}
+                                               "note": "tape + targets, 16 B/beam, each read once by the "
+                                                       "algorithm; L2 flushed before each backward"}}
     L.set_materials(table)
     L.set_sensor(0, w1.sensors[0])
     del d3
@@ -564,10 +615,17 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
                                            "tri_tests": cw["tri_tests"] / cw["rays"],
                                            "node_bytes": cw["node_bytes"],
                                            "unique_bytes_4_frames": cw["unique_node_bytes"] + cw["unique_tri_bytes"]},
-                       "roofline": {"bound": "hbm", "achieved": city_bytes / (c_ms / 1e3) / 1e9, "peak": hbm,
-                                    "unit": "GB/s", "frac": city_bytes / (c_ms / 1e3) / 1e9 / hbm,
-                                    "note": "algorithmic node and triangle bytes of the traversal (as the "
-                                            "headline roofline), per sub-ray from four frames"}}
+                       "traversal_bytes": {
+                           "rate_gbs": city_bytes / (c_ms / 1e3) / 1e9, "bytes_per_launch": city_bytes,
+                           "hbm_peak_gbs": hbm, "frac_of_hbm": None,
+                           "note": "algorithmic node and triangle bytes of the traversal per sub-ray (from four "
+                                   "frames), at a rate above the HBM copy peak: a beam's seven sub-rays and its "
+                                   "neighbours walk the same nodes, so L1 serves ~93 % of them and no fraction of "
+                                   "HBM is claimed; what binds is instruction issue",
+                           "binding_unit": {"issue_active_pct": 74.1, "l1tex_throughput_pct": 67.4,
+                                            "fma_pipe_pct": 42.6, "alu_pipe_pct": 55.1,
+                                            "source": "ncu --set full of one city frame launch "
+                                                      "(profiles/k_cast_city_ncu_full.md)"}}}
         # forward with tape (each beam's strongest sub-ray) + fused-MSE adjoint to the 64 x 91 table, the
         # widths and the gain, targets from the hidden table
         del pts4
@@ -619,7 +677,7 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
     return out
 
 
-def cpu_baseline(w, args, n_beams=None):
+def cpu_baseline(w, args, n_beams=None, want_result=False):
     import oracle
     oracle.build()
     nb = n_beams or args.cpu_beams
@@ -630,11 +688,33 @@ def cpu_baseline(w, args, n_beams=None):
     T = oracle.build_tables(w.params)
     cores = len(os.sched_getaffinity(0))
     t0 = time.perf_counter()
-    oracle.cast(w.scene, w.sensors, w.frames, T, w.seed, samples=samples, n_threads=cores)
+    ref = oracle.cast(w.scene, w.sensors, w.frames, T, w.seed, samples=samples, n_threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": nb / dt, "unit": UNIT, "cores": cores, "per_core": nb / dt / cores, "kind": "oracle",
-            "sample": f"{nb} seeded beams of the same frame (brute force FP64 over all {w.scene.n_tris} tris), "
-                      f"{dt:.1f} s"}
+    cb = {"value": nb / dt, "unit": UNIT, "cores": cores, "per_core": nb / dt / cores, "kind": "oracle",
+          "sample": f"{nb} seeded beams of the same frame (brute force FP64 over all {w.scene.n_tris} tris), "
+                    f"{dt:.1f} s"}
+    return (cb, ref) if want_result else cb
+
+
+def parity_check(dense, ref, w):
+    """The timed frame's dense GPU records against the oracle on the CPU
+    baseline's sample of beams (untimed): exemption counts and largest errors,
+    with the tolerances of the parity tests."""
+    if dense is None:
+        return None
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import compare
+    idx = ref["sample_beam"]
+    got = {k: (v.view(np.uint32) if k in ("tri", "inst") else (v.view(np.uint16) if k == "mat" else v))[idx]
+           for k, v in dense.items()}
+    try:
+        rep = compare(got, ref, gain=max(s.gain for s in w.sensors), label="cfg1 frame, CPU-baseline sample")
+        rep["ok"] = True
+    except AssertionError as e:
+        rep = {"ok": False, "mismatch": str(e), "beams": int(idx.size)}
+    rep["tolerances"] = "tri, instance, material, valid bit-exact outside counted exemptions; range rel 1e-5; " \
+                        "intensity rel 1e-4 (floor 1e-7 g); normal abs 1e-5"
+    return rep
 
 
 def run_reference(args, rank, world):

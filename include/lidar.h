@@ -385,6 +385,19 @@ typedef struct {
 lidar_status lidar_count_work(lidar_ctx* ctx, const lidar_scene* scene, const lidar_frame* frames_host,
                               int32_t n_frames, uint64_t seed, lidar_work_counts* out, uint32_t* beam_cost_dev);
 
+/* Measured FP32 arithmetic rate of the context's device, the denominator of
+ * the traversal's ALU fraction (its box and triangle tests are FP32 adds,
+ * multiplies, fused multiply-adds and min/max).  Runs a kernel of independent
+ * fused multiply-add chains on every SM (eight warps per scheduler, no memory
+ * traffic), fma_per_thread FMAs per thread (>= 64; about 8e6 runs for tens of
+ * milliseconds), once as scalar FMAs and once as packed FP32 pairs, and
+ * returns the faster: *flops_per_s (2 FLOPs per FMA, CUDA-event time),
+ * *kernel_ms and *packed (1 if the packed form was faster).  The rate follows
+ * the SM clock of the moment, which the caller should sample alongside.
+ * Synchronises. */
+lidar_status lidar_measure_fp32_rate(lidar_ctx* ctx, int64_t fma_per_thread, double* flops_per_s,
+                                     double* kernel_ms, int32_t* packed);
+
 /* --------------------------------------------------------------- scheduling */
 
 /* Ray schedule of a sensor slot.  The cast kernel's warps take groups of 32

@@ -206,6 +206,10 @@ cudaError_t launch_bucket_schedule(cudaStream_t s, const uint32_t* cost, const u
                                    uint32_t* new_order, void* scratch, size_t scratch_bytes);
 size_t bucket_schedule_scratch_bytes(int64_t n_beams);
 
+// probe.cu: FP32 fused multiply-add rate over every SM (sink: 4 bytes per SM x 4)
+cudaError_t measure_fp32_rate(cudaStream_t s, int num_sms, int64_t fma_per_thread, void* sink_dev,
+                              double* flops_per_s, double* ms, int* form);
+
 // adjoint.cu
 cudaError_t launch_build_tables(cudaStream_t s, const float* params, int M, float* table);
 cudaError_t launch_build_tables_backward(cudaStream_t s, const float* params, const float* grad_table, int M,

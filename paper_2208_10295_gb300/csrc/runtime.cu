@@ -1546,6 +1546,22 @@ lidar_status lidar_set_launch_config(lidar_ctx* c, const lidar_launch_config* cf
     return LIDAR_OK;
 }
 
+lidar_status lidar_measure_fp32_rate(lidar_ctx* c, int64_t fma_per_thread, double* flops_per_s, double* kernel_ms,
+                                     int32_t* packed)
+{
+    LIDAR_CHECK_ARG(c != nullptr && flops_per_s != nullptr && kernel_ms != nullptr && packed != nullptr,
+                    "lidar_measure_fp32_rate: NULL argument");
+    LIDAR_CHECK_ARG(fma_per_thread >= 64 && fma_per_thread <= ((int64_t)1 << 40),
+                    "lidar_measure_fp32_rate: fma_per_thread in [64, 2^40]");
+    DeviceGuard g(c->device);
+    lidar_status st = ensure_scratch(c, (size_t)c->num_sms * 4 * sizeof(float));
+    if (st != LIDAR_OK) return st;
+    int form = 0;
+    LIDAR_CUDA(measure_fp32_rate(c->stream, c->num_sms, fma_per_thread, c->scratch, flops_per_s, kernel_ms, &form));
+    *packed = form;
+    return LIDAR_OK;
+}
+
 lidar_status lidar_set_wait_limit(lidar_ctx* c, uint64_t ns)
 {
     LIDAR_CHECK_ARG(c != nullptr, "lidar_set_wait_limit: NULL context");

@@ -347,6 +347,13 @@ class Lidar:
         C.check(C.lidar_get_wait_limit(self.handle, ctypes.byref(v)), "lidar_get_wait_limit")
         return int(v.value)
 
+    def measure_fp32_rate(self, fma_per_thread: int = 1 << 23) -> dict:
+        """FP32 FMA rate of the device (FLOP/s, 2 per FMA) and the probe's kernel time."""
+        r, t, pk = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        C.check(C.lidar_measure_fp32_rate(self.handle, int(fma_per_thread), ctypes.byref(r), ctypes.byref(t),
+                                          ctypes.byref(pk)), "lidar_measure_fp32_rate")
+        return {"flops_per_s": r.value, "kernel_ms": t.value, "packed": bool(pk.value)}
+
     def set_wait_limit(self, ns: int):
         C.check(C.lidar_set_wait_limit(self.handle, int(ns)), "lidar_set_wait_limit")
 
