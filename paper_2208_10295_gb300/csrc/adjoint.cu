@@ -13,6 +13,11 @@
 // result does not depend on scheduling.
 #include "common.cuh"
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace lidar {
 namespace {
 
@@ -317,6 +322,411 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_adj_finalize(
 
 constexpr int kAdjBlocks = 1024;
 
+// ------------------------------------------------------------ one-pass adjoint
+//
+// The same sums as the passes above with the tape read once.  One block per
+// SM (cooperative launch) owns a contiguous run of chunks of kOneChunk beams.
+// Its chunks stream into shared memory by bulk asynchronous copies (TMA,
+// cp.async.bulk) kOneStages deep, completion tracked by one mbarrier per
+// stage; with tape arrays the copy engine cannot address (not 16-byte
+// aligned) and for the tape's last, partial chunk the threads load the beams
+// themselves.  The block sums its contributions exactly in 64-bit fixed point
+// in shared memory at its own power-of-two scale, chosen from the largest
+// contribution seen so far and the block's beam count; when a chunk raises
+// that maximum past the scale's headroom, the accumulators are rescaled
+// (a rounding shift) before the chunk is added.  After one bounded grid-wide
+// wait every block knows every block's maximum, converts its sums to the
+// common scale of the whole tape (a rounding shift) and adds them into the
+// global accumulators with integer atomics; the last block to finish turns
+// them into the gradients and sums the per-block loss partials in block
+// order.  Every step is a deterministic function of the tape and the grid
+// size, so the result is bit-reproducible run to run.
+
+constexpr int kOneThreads = 512;
+constexpr int kOneBPT = 4;                          // consecutive beams per thread per chunk
+constexpr int kOneChunk = kOneThreads * kOneBPT;    // 2048 beams
+constexpr int kOneStages = 4;
+constexpr int kOneStageBytes = kOneChunk * 16;      // valid 1, target valid 1, mat 2, theta 4, rf 4, g 4
+constexpr int kOneWarps = kOneThreads / 32;
+
+struct OneArgs {
+    int64_t n;
+    const uint8_t* valid;
+    const uint16_t* mat;
+    const float* theta;
+    const float* rf;
+    const float* g;             // target intensities (MSE) or dL/dI
+    const uint8_t* tvalid;      // target valid flags, NULL: all valid
+    TableDev T;
+    float gain;
+    int mse;
+    int n_acc;                  // table entries + the gain
+    unsigned long long* acc;    // [n_acc] global accumulators, cleared in the kernel
+    float* blk_max;             // [grid] per block: largest contribution
+    int* blk_sh;                // [grid] its fixed-point shift
+    double* blk_loss;           // [grid] sum of squared residuals
+    unsigned long long* blk_n;  // [grid] beams used
+    unsigned* ctl;              // [0] grid-wait arrivals, [1] finished blocks; 0 between calls
+    int* status;
+    uint64_t wait_ns;
+    float* loss;
+    float* grad_table;
+    float* grad_gain;
+};
+
+__device__ __forceinline__ uint64_t adj_global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// fixed-point shift for sums of up to `count` terms of magnitude <= m: every
+// partial sum stays below 2^61 (m < 2^em, count + 1 <= 2^ec)
+__device__ __forceinline__ int one_shift(float m, int64_t count)
+{
+    int em;
+    frexpf(m, &em);
+    const int ec = 64 - __clzll((long long)(count + 1));
+    int sh = 61 - em - ec;
+    return sh > 126 ? 126 : (sh < -126 ? -126 : sh);
+}
+
+// v / 2^d rounded to nearest (ties up), d >= 0
+__device__ __forceinline__ long long round_shift(long long v, int d)
+{
+    if (d == 0) return v;
+    if (d > 62) return 0;
+    return (v + (1ll << (d - 1))) >> d;
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a));
+}
+
+__device__ __forceinline__ void bar_expect(uint64_t* bar, unsigned bytes)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+// waits for the stage's phase `parity` to complete; false after wait_ns
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity, uint64_t wait_ns)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    uint64_t t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it == 0) t0 = adj_global_ns();
+        else if (adj_global_ns() - t0 > wait_ns) return false;
+    }
+}
+
+template <bool kTma>
+__global__ void __launch_bounds__(kOneThreads, 1) k_adj_onepass(const __grid_constant__ OneArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* stages = smem;
+    unsigned long long* s_acc = (unsigned long long*)(smem + (kTma ? kOneStages * kOneStageBytes : 0));
+    uint64_t* s_bar = (uint64_t*)(s_acc + ((a.n_acc + 1) & ~1));
+    __shared__ float s_wmax[2][kOneWarps];
+    __shared__ double s_red[kOneWarps];
+    __shared__ unsigned long long s_cnt[kOneWarps];
+    __shared__ int s_flag;
+    __shared__ float s_gmax;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, blk = blockIdx.x;
+    const int64_t n = a.n;
+    const int64_t n_chunks = (n + kOneChunk - 1) / kOneChunk;
+    const int64_t k0 = (int64_t)blk * n_chunks / G, k1 = ((int64_t)blk + 1) * n_chunks / G;
+    const int64_t first = k0 * kOneChunk;
+    const int64_t last = min(k1 * kOneChunk, n);
+    const int64_t L = last > first ? last - first : 0;   // beams of this block
+    const bool has_tv = a.tvalid != nullptr;
+
+    for (int j = tid; j < a.n_acc; j += kOneThreads) s_acc[j] = 0ull;
+    for (int64_t j = (int64_t)blk * kOneThreads + tid; j < a.n_acc; j += (int64_t)G * kOneThreads) a.acc[j] = 0ull;
+    if (kTma && tid == 0) {
+        for (int st = 0; st < kOneStages; ++st) bar_init(&s_bar[st]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // a chunk is copied by the copy engine iff it is whole (the tape's last
+    // chunk may be partial: its byte counts need not be multiples of 16)
+    auto whole = [&](int64_t k) { return (k + 1) * (int64_t)kOneChunk <= n; };
+    auto issue = [&](int64_t k) {
+        const int slot = (int)((k - k0) % kOneStages);
+        unsigned char* d = stages + slot * kOneStageBytes;
+        const int64_t c0 = k * kOneChunk;
+        const unsigned bytes = kOneChunk * (has_tv ? 16u : 15u);
+        bar_expect(&s_bar[slot], bytes);
+        bulk_copy(d, a.valid + c0, kOneChunk, &s_bar[slot]);
+        if (has_tv) bulk_copy(d + kOneChunk, a.tvalid + c0, kOneChunk, &s_bar[slot]);
+        bulk_copy(d + 2 * kOneChunk, a.mat + c0, 2 * kOneChunk, &s_bar[slot]);
+        bulk_copy(d + 4 * kOneChunk, a.theta + c0, 4 * kOneChunk, &s_bar[slot]);
+        bulk_copy(d + 8 * kOneChunk, a.rf + c0, 4 * kOneChunk, &s_bar[slot]);
+        bulk_copy(d + 12 * kOneChunk, a.g + c0, 4 * kOneChunk, &s_bar[slot]);
+    };
+    int64_t issued = k0;  // next chunk to copy (meaningful in thread 0)
+    if (kTma && tid == 0)
+        for (; issued < k1 && issued < k0 + kOneStages && whole(issued); ++issued) issue(issued);
+
+    float blk_max = 0.0f;
+    int sh = 126;
+    float loss32 = 0.0f;
+    unsigned cnt = 0;
+    bool failed = false;
+    int64_t k_fail = k1;  // first chunk whose stage wait ran out
+    const float* Tt = a.T.table;
+    for (int64_t k = k0; k < k1; ++k) {
+        const int64_t c0 = k * kOneChunk;
+        TapeIn in;
+        bool ok = true;
+        if (kTma && whole(k)) {
+            const int slot = (int)((k - k0) % kOneStages);
+            ok = bar_wait(&s_bar[slot], (unsigned)(((k - k0) / kOneStages) & 1), a.wait_ns);
+            if (ok) {
+                const unsigned char* d = stages + slot * kOneStageBytes;
+                const uchar4 v = reinterpret_cast<const uchar4*>(d)[tid];
+                const uchar4 tv = has_tv ? reinterpret_cast<const uchar4*>(d + kOneChunk)[tid] : make_uchar4(1, 1, 1, 1);
+                const ushort4 m = reinterpret_cast<const ushort4*>(d + 2 * kOneChunk)[tid];
+                const float4 th = reinterpret_cast<const float4*>(d + 4 * kOneChunk)[tid];
+                const float4 r = reinterpret_cast<const float4*>(d + 8 * kOneChunk)[tid];
+                const float4 gg = reinterpret_cast<const float4*>(d + 12 * kOneChunk)[tid];
+                in.valid[0] = v.x; in.valid[1] = v.y; in.valid[2] = v.z; in.valid[3] = v.w;
+                in.tvalid[0] = tv.x; in.tvalid[1] = tv.y; in.tvalid[2] = tv.z; in.tvalid[3] = tv.w;
+                in.mat[0] = m.x; in.mat[1] = m.y; in.mat[2] = m.z; in.mat[3] = m.w;
+                in.theta[0] = th.x; in.theta[1] = th.y; in.theta[2] = th.z; in.theta[3] = th.w;
+                in.rf[0] = r.x; in.rf[1] = r.y; in.rf[2] = r.z; in.rf[3] = r.w;
+                in.g[0] = gg.x; in.g[1] = gg.y; in.g[2] = gg.z; in.g[3] = gg.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kOneBPT; ++j) {
+                const int64_t b = c0 + kOneBPT * tid + j;
+                const bool inb = b < n;
+                in.valid[j] = inb ? __ldcs(&a.valid[b]) : (uint8_t)0;
+                in.tvalid[j] = (inb && has_tv) ? __ldcs(&a.tvalid[b]) : (uint8_t)1;
+                in.mat[j] = inb ? __ldcs(&a.mat[b]) : (uint16_t)0;
+                in.theta[j] = inb ? __ldcs(&a.theta[b]) : 0.0f;
+                in.rf[j] = inb ? __ldcs(&a.rf[b]) : 0.0f;
+                in.g[j] = inb ? __ldcs(&a.g[b]) : 0.0f;
+            }
+        }
+        float t_lo[kOneBPT], t_hi[kOneBPT], t_g[kOneBPT];
+        int e[kOneBPT];
+        float mx = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kOneBPT; ++j) {
+            e[j] = -1;
+            t_lo[j] = t_hi[j] = t_g[j] = 0.0f;
+            if (!ok) continue;
+            const TapeRow r = tape_row(in, j, TableDev{Tt, a.T.n_mat}, a.gain, a.mse != 0);
+            if (!r.use) continue;
+            const float w = a.gain * r.rf * r.gI;
+            e[j] = r.m * LIDAR_TABLE_SIZE + r.i;
+            t_lo[j] = w * (1.0f - r.f);
+            t_hi[j] = w * r.f;
+            t_g[j] = r.rf * r.R * r.gI;
+            mx = fmaxf(mx, fmaxf(fabsf(t_g[j]), fmaxf(fabsf(t_lo[j]), fabsf(t_hi[j]))));
+            loss32 = __fmaf_rn(r.res, r.res, loss32);
+            ++cnt;
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_wmax[k & 1][warp] = mx;
+        // every thread has read this chunk's stage and published its maximum
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            k_fail = k;
+            break;
+        }
+        if (kTma && tid == 0 && issued < k1 && whole(issued)) {
+            // the stage just read is free: order the generic reads before the
+            // copy engine's writes, then refill it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(issued);
+            ++issued;
+        }
+        float cm = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kOneWarps; ++w) cm = fmaxf(cm, s_wmax[k & 1][w]);
+        if (cm > blk_max) {
+            const int nsh = one_shift(cm, L);
+            if (nsh < sh && blk_max > 0.0f) {
+                const int d = sh - nsh;
+                for (int j = tid; j < a.n_acc; j += kOneThreads)
+                    s_acc[j] = (unsigned long long)round_shift((long long)s_acc[j], d);
+                __syncthreads();
+            }
+            if (nsh < sh) sh = nsh;
+            blk_max = cm;
+        }
+        if (blk_max > 0.0f) {
+            const float scale = ldexpf(1.0f, sh);
+            int cur = -1;
+            unsigned long long a0 = 0, a1 = 0, gsum = 0;
+#pragma unroll
+            for (int j = 0; j < kOneBPT; ++j) {
+                if (e[j] < 0) continue;
+                if (e[j] != cur) {
+                    if (cur >= 0) {
+                        atomicAdd(&s_acc[cur], a0);
+                        atomicAdd(&s_acc[cur + 1], a1);
+                    }
+                    cur = e[j];
+                    a0 = a1 = 0;
+                }
+                a0 += (unsigned long long)__float2ll_rn(t_lo[j] * scale);
+                a1 += (unsigned long long)__float2ll_rn(t_hi[j] * scale);
+                gsum += (unsigned long long)__float2ll_rn(t_g[j] * scale);
+            }
+            if (cur >= 0) {
+                atomicAdd(&s_acc[cur], a0);
+                atomicAdd(&s_acc[cur + 1], a1);
+            }
+            for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+            if (lane == 0 && gsum) atomicAdd(&s_acc[a.n_acc - 1], gsum);
+        }
+    }
+    if (failed && kTma && tid == 0) {
+        // let the copies still in flight (chunks k_fail .. issued - 1, at most one
+        // per stage) land before the block's shared memory goes away; bounded by
+        // at least a second whatever the caller's wait limit
+        const uint64_t drain_ns = a.wait_ns > 1000000000ull ? a.wait_ns : 1000000000ull;
+        for (int64_t k = k_fail; k < issued; ++k) {
+            const int slot = (int)((k - k0) % kOneStages);
+            bar_wait(&s_bar[slot], (unsigned)(((k - k0) / kOneStages) & 1), drain_ns);
+        }
+    }
+    if (failed && tid == 0) raise_status(a.status, ST_TIMEOUT);
+
+    // ---- this block's loss partial (fixed order), beam count, maximum and shift
+    double l = (double)loss32;
+    unsigned long long c = cnt;
+    for (int o = 16; o > 0; o >>= 1) {
+        l += __shfl_down_sync(0xffffffffu, l, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+        s_red[warp] = l;
+        s_cnt[warp] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        unsigned long long ct = 0;
+        for (int w = 0; w < kOneWarps; ++w) {
+            t += s_red[w];
+            ct += s_cnt[w];
+        }
+        a.blk_loss[blk] = t;
+        a.blk_n[blk] = ct;
+        a.blk_max[blk] = failed ? 0.0f : blk_max;
+        a.blk_sh[blk] = sh;
+        // ---- grid-wide wait (cooperative launch: every block is resident)
+        __threadfence();
+        atomicAdd(&a.ctl[0], 1u);
+        int okw = 1;
+        const uint64_t t0 = adj_global_ns();
+        while (*(volatile unsigned*)&a.ctl[0] < (unsigned)G) {
+            if (adj_global_ns() - t0 > a.wait_ns) {
+                raise_status(a.status, ST_TIMEOUT);
+                okw = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_flag = okw;
+    }
+    __syncthreads();
+    if (s_flag && !failed) {
+        // the common scale: the largest contribution of the whole tape
+        float gm = 0.0f;
+        for (int j = tid; j < G; j += kOneThreads) gm = fmaxf(gm, __ldcg(&a.blk_max[j]));
+        for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+        if (lane == 0) s_wmax[0][warp] = gm;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.0f;
+            for (int w = 0; w < kOneWarps; ++w) t = fmaxf(t, s_wmax[0][w]);
+            s_gmax = t;
+        }
+        __syncthreads();
+        if (blk_max > 0.0f) {
+            const int S = one_shift(s_gmax, n);
+            const int d = sh - S;
+            for (int j = tid; j < a.n_acc; j += kOneThreads) {
+                const long long v = round_shift((long long)s_acc[j], d);
+                if (v) atomicAdd(&a.acc[j], (unsigned long long)v);
+            }
+        }
+    }
+    // ---- the last block to finish writes the results
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_flag = atomicAdd(&a.ctl[1], 1u) == (unsigned)G - 1;
+    __syncthreads();
+    if (!s_flag) return;
+    __threadfence();
+    if (tid == 0) {
+        float gm = 0.0f;
+        unsigned long long N = 0;
+        for (int j = 0; j < G; ++j) {
+            gm = fmaxf(gm, __ldcg(&a.blk_max[j]));
+            N += __ldcg(&a.blk_n[j]);
+        }
+        s_gmax = gm;
+        s_cnt[0] = N;
+        if (a.loss) {
+            double t = 0.0;
+            for (int j = 0; j < G; ++j) t += __ldcg(&a.blk_loss[j]);
+            *a.loss = a.mse ? (float)(N ? t / (double)N : 0.0) : 0.0f;
+        }
+    }
+    __syncthreads();
+    const unsigned long long N = s_cnt[0];
+    if (s_gmax > 0.0f) {
+        const float inv_scale = ldexpf(1.0f, -one_shift(s_gmax, n));  // exact: a power of two
+        const float norm = a.mse ? (N ? __frcp_rn((float)N) : 0.0f) : 1.0f;
+        for (int j = tid; j < a.n_acc; j += kOneThreads) {
+            const float v = __fmul_rn(__fmul_rn(__ll2float_rn((long long)__ldcg(&a.acc[j])), inv_scale), norm);
+            if (j < a.n_acc - 1) {
+                if (a.grad_table) a.grad_table[j] += v;
+            } else if (a.grad_gain) {
+                *a.grad_gain += v;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // every block has passed the grid wait and counted itself: ready for the next call
+        a.ctl[0] = 0u;
+        a.ctl[1] = 0u;
+    }
+}
+
 }  // namespace
 
 // Scratch of the allocation-free backward variant: a file-scope device array
@@ -427,6 +837,82 @@ cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid
     k_adj_finalize<<<(n_acc + kFinalizeThreads - 1) / kFinalizeThreads, kFinalizeThreads, 0, s>>>(
         n_acc, acc, absmax, count, target_I != nullptr, partials, blocks, grad_table, grad_gain, loss);
     return cudaGetLastError();
+}
+
+size_t onepass_scratch_bytes(int M, int num_sms)
+{
+    const size_t n_acc = (size_t)M * LIDAR_TABLE_SIZE + 1;
+    const size_t G = (size_t)(num_sms > 0 ? num_sms : 1);
+    return ((n_acc * 8 + 255) / 256) * 256 + ((G * 24 + 255) / 256) * 256;
+}
+
+cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_t* valid, const uint16_t* mat,
+                                         const float* theta_deg, const float* rf, TableDev T, float gain,
+                                         const float* grad_I, const float* target_I, const uint8_t* target_valid,
+                                         float* loss, float* grad_table, float* grad_gain, void* scratch,
+                                         size_t scratch_bytes, unsigned* ctl, int* status, uint64_t wait_ns,
+                                         int num_sms)
+{
+    const int n_acc = T.n_mat * LIDAR_TABLE_SIZE + 1;
+    if (num_sms < 1 || scratch_bytes < onepass_scratch_bytes(T.n_mat, num_sms)) return cudaErrorInvalidValue;
+    const float* g = target_I ? target_I : grad_I;
+    // the copy engine needs 16-byte aligned sources; otherwise the threads load the tape
+    auto al16 = [](const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; };
+    const bool tma = al16(valid) && al16(target_valid) && al16(mat) && al16(theta_deg) && al16(rf) && al16(g);
+    const size_t acc_smem = (size_t)((n_acc + 1) & ~1) * 8;
+    const size_t smem = (tma ? (size_t)kOneStages * kOneStageBytes : 0) + acc_smem + kOneStages * 8;
+    const void* fn = tma ? (const void*)k_adj_onepass<true> : (const void*)k_adj_onepass<false>;
+    {
+        // the shared-memory attribute and the residency are asked once per
+        // (device, kernel, size); a failure means the accumulators do not fit
+        // beside the stages: the caller then takes the separate passes
+        static std::mutex mu;
+        static std::map<std::tuple<int, bool, size_t>, bool> fits;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = fits.find({dev, tma, smem});
+        if (it == fits.end()) {
+            int per_sm = 0;
+            bool ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+                      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kOneThreads, smem) == cudaSuccess &&
+                      per_sm >= 1;
+            if (!ok) cudaGetLastError();
+            it = fits.emplace(std::make_tuple(dev, tma, smem), ok).first;
+        }
+        if (!it->second) return cudaErrorNotSupported;
+    }
+    // one block per SM whatever the occupancy, so the aligned and the unaligned
+    // paths split the tape the same way (and give the same sums)
+    const int64_t n_chunks = (n + kOneChunk - 1) / kOneChunk;
+    int G = (int)std::min<int64_t>(std::max<int64_t>(n_chunks, 1), num_sms);
+    char* p = (char*)scratch;
+    OneArgs a{};
+    a.n = n;
+    a.valid = valid;
+    a.mat = mat;
+    a.theta = theta_deg;
+    a.rf = rf;
+    a.g = g;
+    a.tvalid = target_valid;
+    a.T = T;
+    a.gain = gain;
+    a.mse = target_I != nullptr;
+    a.n_acc = n_acc;
+    a.acc = (unsigned long long*)p;
+    p += (((size_t)n_acc * 8 + 255) / 256) * 256;
+    a.blk_max = (float*)p;
+    a.blk_sh = (int*)(p + (size_t)G * 4);
+    a.blk_loss = (double*)(p + (size_t)G * 8);
+    a.blk_n = (unsigned long long*)(p + (size_t)G * 16);
+    a.ctl = ctl;
+    a.status = status;
+    a.wait_ns = wait_ns;
+    a.loss = loss;
+    a.grad_table = grad_table;
+    a.grad_gain = grad_gain;
+    void* args[] = {&a};
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kOneThreads), args, smem, s);
 }
 
 }  // namespace lidar

@@ -220,6 +220,17 @@ cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid
                                  float* loss, float* grad_table, float* grad_gain, void* scratch,
                                  size_t scratch_bytes);
 size_t backward_scratch_bytes(int M);
+// One-pass variant (one cooperative launch, the tape read once); returns
+// cudaErrorNotSupported when the table's accumulators do not fit in shared
+// memory beside the copy stages (then launch_cast_backward applies).  ctl: two
+// words that are zero between calls (the kernel leaves them so).
+size_t onepass_scratch_bytes(int M, int num_sms);
+cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_t* valid, const uint16_t* mat,
+                                         const float* theta_deg, const float* rf, TableDev table, float gain,
+                                         const float* grad_I, const float* target_I, const uint8_t* target_valid,
+                                         float* loss, float* grad_table, float* grad_gain, void* scratch,
+                                         size_t scratch_bytes, unsigned* ctl, int* status, uint64_t wait_ns,
+                                         int num_sms);
 // address (on the current device) and size of the allocation-free variant's scratch array
 cudaError_t noalloc_scratch(void** ptr, size_t* bytes);
 

@@ -117,6 +117,8 @@ struct lidar_ctx {
     int* status_dev = nullptr;
     unsigned long long* work_counter = nullptr;
     int* aux_dev = nullptr;  // scratch ints (build height)
+    unsigned* adj_ctl = nullptr;  // two words of the one-pass adjoint, zero between calls
+    int coop = 0;                 // the device launches cooperative kernels
     SensorSlot slots[LIDAR_MAX_SENSORS];
     SensorDev* sensors_dev = nullptr;
     TableDev table{nullptr, 0};
@@ -239,6 +241,8 @@ lidar_status lidar_create(int device, void* cuda_stream, lidar_ctx** out)
     c->status_dev = (int*)p;
     c->work_counter = (unsigned long long*)((char*)p + 64);
     c->aux_dev = (int*)((char*)p + 128);
+    c->adj_ctl = (unsigned*)((char*)p + 192);
+    c->coop = coop;
     e = dev_alloc((void**)&c->sensors_dev, sizeof(SensorDev) * LIDAR_MAX_SENSORS);
     if (e != cudaSuccess) {
         cudaFree(p);
@@ -1288,11 +1292,21 @@ static lidar_status backward_common(lidar_ctx* c, int64_t n, const lidar_beams* 
         return LIDAR_ESTATE;
     }
     DeviceGuard g(c->device);
-    lidar_status st = ensure_scratch(c, backward_scratch_bytes(c->table.n_mat));
+    lidar_status st = ensure_scratch(c, std::max(backward_scratch_bytes(c->table.n_mat),
+                                                 onepass_scratch_bytes(c->table.n_mat, c->num_sms)));
     if (st != LIDAR_OK) return st;
-    LIDAR_CUDA(launch_cast_backward(c->stream, n, tape->valid, tape->mat, tape->theta_deg, tape->rf, c->table, gain,
-                                    grad_I, target_I, target_valid, loss, grad_table, grad_gain, c->scratch,
-                                    c->scratch_bytes));
+    // one pass over the tape (cooperative launch) unless its accumulators do
+    // not fit in shared memory or the device cannot launch cooperatively
+    cudaError_t e = cudaErrorNotSupported;
+    if (c->coop)
+        e = launch_cast_backward_onepass(c->stream, n, tape->valid, tape->mat, tape->theta_deg, tape->rf, c->table,
+                                         gain, grad_I, target_I, target_valid, loss, grad_table, grad_gain, c->scratch,
+                                         c->scratch_bytes, c->adj_ctl, c->status_dev, c->cfg.wait_ns, c->num_sms);
+    if (e == cudaErrorNotSupported)
+        e = launch_cast_backward(c->stream, n, tape->valid, tape->mat, tape->theta_deg, tape->rf, c->table, gain,
+                                 grad_I, target_I, target_valid, loss, grad_table, grad_gain, c->scratch,
+                                 c->scratch_bytes);
+    LIDAR_CUDA(e);
     return LIDAR_OK;
 }
 

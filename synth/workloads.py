@@ -362,3 +362,25 @@ def small_terrain(seed=77, n_cells=32, half=16.0, n_objects=12, n_frames=2, n_az
 
 def by_index(i: int) -> Workload:
     return [cfg0, cfg1, cfg2, cfg3, cfg4][i]()
+
+
+def adjoint_tape(n: int, n_materials: int, seed: int, period: int = 1 << 15, octaves: float = 20.0):
+    """A seeded adjoint tape drawn directly (no cast): per beam a forward valid
+    flag (80 % set), a material in [0, n_materials + 3) (ids past the table
+    select its last row), an incidence angle uniform on [0, 90] degrees (every
+    97th an integer, every 1013th exactly 90), a range factor in [0.5, 2], a
+    target intensity and a target valid flag (90 % set).  The targets grow
+    along a sawtooth: within each `period` beams their scale rises by 2^octaves,
+    so a running maximum keeps growing inside any run of consecutive beams."""
+    rng = np.random.default_rng(seed)
+    theta = rng.uniform(0.0, 90.0, n).astype(np.float32)
+    theta[::97] = np.floor(theta[::97])
+    theta[::1013] = 90.0
+    ramp = np.exp2(octaves * (np.arange(n) % period) / period)
+    return {"valid": (rng.uniform(size=n) < 0.8).astype(np.uint8),
+            "mat": rng.integers(0, n_materials + 3, n).astype(np.uint16),
+            "theta_deg": theta,
+            "rf": rng.uniform(0.5, 2.0, n).astype(np.float32),
+            "target_I": (rng.uniform(0.0, 1.0, n) * ramp).astype(np.float32),
+            "target_valid": (rng.uniform(size=n) < 0.9).astype(np.uint8),
+            "params": S.material_params(rng, n_materials)}

@@ -257,3 +257,88 @@ def test_adjoint_city_sampled(L):
     close_grad(gT, gT_ref, "city dL/dT")
     assert gg == pytest.approx(gg_ref, rel=NORM_RTOL)
     _check_params_grad(L, params, gT, w.params, gT_ref, "city")
+
+
+# ----------------------------------------------------------------- synthetic tapes
+# The adjoint alone on tapes drawn directly (no cast), against the oracle's FP64
+# adjoint on the same FP32 inputs: sizes that leave a partial last chunk, enough
+# chunks per SM that every block streams several through its copy stages, a
+# target scale that keeps growing inside each block (its fixed-point sums are
+# rescaled on the way), material ids past the table, a table too large for
+# shared memory (the separate passes), and the empty and one-beam tapes.
+
+def _synthetic(L, n, M, seed):
+    t = synth.adjoint_tape(n, M, seed)
+    dev = L.device
+    params = torch.tensor(t["params"], device=dev)
+    table = L.build_tables(params)
+    L.set_materials(table)
+    tape = {k: torch.tensor(t[k], device=dev) for k in ("valid", "mat", "theta_deg", "rf")}
+    return t, params, table, tape, torch.tensor(t["target_I"], device=dev), torch.tensor(t["target_valid"], device=dev)
+
+
+def _mse(L, tape, table, tI, tv, gain):
+    loss = torch.zeros(1, device=L.device)
+    gT = torch.zeros_like(table)
+    gg = torch.zeros(1, device=L.device)
+    L.cast_backward_mse(tape, gain, tI, tv, loss, gT, gg)
+    st = L.sync_status()
+    assert st == 0, st
+    return loss.item(), gT.cpu().numpy(), gg.item()
+
+
+@pytest.mark.parametrize("n,M", [(2_500_001, 32), (4_194_304, 64), (3000, 64), (2048, 4), (1, 8), (0, 8),
+                                 (200_003, 200)])
+def test_adjoint_synthetic_tape_vs_oracle(L, n, M):
+    t, params, table, tape, tI, tv = _synthetic(L, n, M, seed=7000 + M + n % 97)
+    gain = 1.25
+    loss, gT, gg = _mse(L, tape, table, tI, tv, gain)
+    T = table.cpu().numpy().astype(np.float64)
+    L_ref, gT_ref, gg_ref, N = oracle.cast_backward(t["valid"], t["mat"], t["theta_deg"], t["rf"], T, gain,
+                                                    t["target_I"].astype(np.float64), t["target_valid"])
+    if N == 0:
+        assert loss == 0.0 and gg == 0.0 and not gT.any()
+        return
+    assert loss == pytest.approx(L_ref, rel=NORM_RTOL)
+    close_grad(gT, gT_ref, f"synthetic n={n} M={M} dL/dT")
+    assert gg == pytest.approx(gg_ref, rel=NORM_RTOL)
+
+
+def test_adjoint_synthetic_unaligned_and_repeat_bit_identical(L):
+    """Tape views one element past an aligned address (the threads load the
+    tape; no copy engine) give the gradients of aligned copies of the same
+    beams (copied by the copy engine) bit for bit, and a repeated call gives
+    the same bits again."""
+    n = 1_500_007
+    t, params, table, tape, tI, tv = _synthetic(L, n, 32, seed=7100)
+    off = {k: v[1:] for k, v in tape.items()}
+    same = {k: v[1:].clone() for k, v in tape.items()}
+    a = _mse(L, off, table, tI[1:], tv[1:], 1.0)
+    b = _mse(L, same, table, tI[1:].clone(), tv[1:].clone(), 1.0)
+    c = _mse(L, same, table, tI[1:].clone(), tv[1:].clone(), 1.0)
+    assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32)) and a[2] == b[2]
+    assert np.array_equal(b[1].view(np.uint32), c[1].view(np.uint32)) and b[2] == c[2] and b[0] == c[0]
+    assert a[0] == pytest.approx(b[0], rel=1e-12)
+
+
+def test_adjoint_wait_runs_out_and_recovers(L):
+    """The adjoint's bounded waits (copy stages, grid-wide wait) made to run
+    out with a 0 ns limit: the call reports LIDAR_ETIMEOUT through the status
+    word, nothing hangs, and with the default limit back the next call gives
+    the reference result bit for bit."""
+    from paper_2208_10295_gb300 import capi
+    t, params, table, tape, tI, tv = _synthetic(L, 2_000_000, 32, seed=7200)
+    ref = _mse(L, tape, table, tI, tv, 1.0)
+    limit0 = L.wait_limit()
+    try:
+        L.set_wait_limit(0)
+        loss = torch.zeros(1, device=L.device)
+        gT = torch.zeros_like(table)
+        gg = torch.zeros(1, device=L.device)
+        L.cast_backward_mse(tape, 1.0, tI, tv, loss, gT, gg)
+        assert L.sync_status() == capi.LIDAR_ETIMEOUT
+    finally:
+        L.set_wait_limit(limit0)
+    again = _mse(L, tape, table, tI, tv, 1.0)
+    assert again[0] == ref[0] and again[2] == ref[2]
+    assert np.array_equal(again[1].view(np.uint32), ref[1].view(np.uint32))
