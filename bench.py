@@ -54,16 +54,24 @@ NCU_UNITS = {"l1tex_throughput_pct": 42.6, "issue_active_pct": 43.1, "sm_active_
 # counters (sm__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,
 # fp32}_pred_on), FLOPs = 2 ffma + fadd + fmul + 4 ffma2 + 2 fadd2 + 2 fmul2 +
 # the remaining FP32 instructions (min/max, compares) once each.
-NCU_FP32 = {"sources": None, "fp32_flops": None}
+NCU_FP32 = {"sources": "b3f41d743257cfe8", "fp32_flops": 509_197_113, "fp32_ops": 487_615_621,
+            "counters": {"ffma": 21_581_492, "fadd": 10_683_339, "fmul": 33_692_596, "ffma2": 0,
+                         "fadd2": 70_207_356, "fmul2": 70_207_356, "fp32_all": 347_200_909}}
+# profiles/k_cast_cfg1_fp32_counts.md
 KERNEL_SOURCES = ("cast.cu", "shade.cuh", "trace.cuh", "common.cuh", "philox.cuh")
 
 
 def kernel_digest():
+    """Digest of the sources that make up the cast kernel (of common.cuh only
+    the device-side layout above its host launcher declarations)."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2208_10295_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+            data = fh.read()
+        if f == "common.cuh":
+            data = data[:data.find(b"// ------------------------------------------------------------------ kernel launchers")]
+        h.update(data)
     return h.hexdigest()[:16]
 
 
@@ -426,18 +434,19 @@ def run_ours(args, rank, world, local_rank):
                                            if same_kernel else None),
                      "compulsory_frac": uniq_bytes / (kernel_ms / 1e3) / 1e9 / hbm},
         "work_per_ray": {k: (v if k == "node_bytes" else v / n_beams) for k, v in counters.items()},
-        "alu": {"bound": "alu", "flops_per_launch_alg": flops, "achieved_tflops_alg": alu_tf,
-                "flops_per_launch_ncu": NCU_FP32["fp32_flops"] if ncu_ok else None,
+        "alu": {"bound": "alu", "flops_per_launch_ncu": NCU_FP32["fp32_flops"] if ncu_ok else None,
                 "achieved_tflops_ncu": ncu_fp32_tf, "peak_tflops": fp_peak,
                 "frac": (ncu_fp32_tf if ncu_ok else alu_tf) / fp_peak,
-                "frac_alg": alu_tf / fp_peak,
+                "achieved_tops_alg": alu_tf,
                 "peak_source": "measured: FP32 FMA probe kernel on this GPU, "
                                f"{fp_probe['tflops']:.1f} TFLOP/s at {fp_probe.get('sm_mhz')} MHz median, scaled "
                                f"to the {sm_mhz:.0f} MHz median of the timed casts",
                 "probe": fp_probe,
+                "ops_per_launch_alg": flops, "ops_per_launch_ncu": NCU_FP32["fp32_ops"] if ncu_ok else None,
                 "ops": "alg: 20 FP32 ops per child box of a fetched node, 40 per triangle test (from the "
-                       "source); ncu: FP32 thread instructions of one captured launch, packed pairs and FMAs "
-                       "counted as two FLOPs"},
+                       "source, each operation once); ncu: FP32 thread instructions of one captured launch "
+                       "(sm__sass_thread_inst_executed_op_*_pred_on), each lane operation once (ops) or with "
+                       "FMAs and packed pairs counted as two (flops, the unit of the measured peak)"},
         "clocks": clocks,
     }
     line.update(extras)
