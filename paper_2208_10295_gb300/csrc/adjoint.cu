@@ -6,11 +6,18 @@
 // a specular lobe): T[m][k] = a cos(k deg) + s exp(-k^2 / (2 w^2)), k = 0..90.
 //
 // Adjoint accumulation is deterministic: every contribution is converted to a
-// 64-bit fixed-point integer with a per-call power-of-two scale (chosen from
-// the largest contribution, so the sum cannot overflow) and summed with
-// integer atomics, first in a block-private shared-memory copy of the
-// gradient, then into a global copy; integer addition is associative, so the
-// result does not depend on scheduling.
+// 64-bit fixed-point integer at a power-of-two scale chosen from the largest
+// contribution (so no sum can overflow) and summed with integer atomics, first
+// in a block-private shared-memory copy of the gradient; integer addition is
+// associative, so the result does not depend on scheduling.  Two forms:
+//   - one pass (the default): one cooperative launch reads the tape once
+//     (copy-engine stages), each block sums at its own scale, rescaled as its
+//     maximum grows, and the blocks meet at the common scale after a bounded
+//     grid-wide wait;
+//   - separate passes (tables too large for shared memory beside the copy
+//     stages, devices without cooperative launch, the allocation-free entry
+//     point): a scale pass over the tape, the fixed-point accumulation at
+//     the global scale, and a finalize kernel.
 #include "common.cuh"
 
 #include <algorithm>
@@ -343,9 +350,10 @@ constexpr int kAdjBlocks = 1024;
 // size, so the result is bit-reproducible run to run.
 
 constexpr int kOneThreads = 512;
-constexpr int kOneBPT = 4;                          // consecutive beams per thread per chunk
+constexpr int kOneBPT = 4;                          // beams per thread per chunk (one per warp step)
 constexpr int kOneChunk = kOneThreads * kOneBPT;    // 2048 beams
-constexpr int kOneStages = 4;
+constexpr int kOneStages = 2;
+constexpr int kOneBlocksPerSm = 2;
 constexpr int kOneStageBytes = kOneChunk * 16;      // valid 1, target valid 1, mat 2, theta 4, rf 4, g 4
 constexpr int kOneWarps = kOneThreads / 32;
 
@@ -361,12 +369,12 @@ struct OneArgs {
     float gain;
     int mse;
     int n_acc;                  // table entries + the gain
-    unsigned long long* acc;    // [n_acc] global accumulators, cleared in the kernel
+    long long* rows;            // [grid][n_acc] each block's sums at the common scale
     float* blk_max;             // [grid] per block: largest contribution
     int* blk_sh;                // [grid] its fixed-point shift
     double* blk_loss;           // [grid] sum of squared residuals
     unsigned long long* blk_n;  // [grid] beams used
-    unsigned* ctl;              // [0] grid-wait arrivals, [1] finished blocks; 0 between calls
+    unsigned* ctl;              // [0] arrivals at the grid-wide waits, [1] finished blocks; 0 between calls
     int* status;
     uint64_t wait_ns;
     float* loss;
@@ -390,6 +398,19 @@ __device__ __forceinline__ int one_shift(float m, int64_t count)
     const int ec = 64 - __clzll((long long)(count + 1));
     int sh = 61 - em - ec;
     return sh > 126 ? 126 : (sh < -126 ? -126 : sh);
+}
+
+// round(x 2^sh) as a 64-bit integer for |x| 2^sh < 2^61: y = x 2^sh is exact
+// (a power-of-two scale), q = y / 2^31 rounded and r = y - q 2^31 are exact
+// in FP32 (|q| < 2^30, |r| <= 2^30), and both convert to 32-bit integers; the
+// FP32-to-int64 conversion would run on the FP64 pipe, which is narrow on
+// this part.  Ties of r round to even.
+__device__ __forceinline__ long long fixed_of(float x, float scale)
+{
+    const float y = x * scale;
+    const float q = rintf(y * 4.656612873077393e-10f);  // 2^-31
+    const float r = fmaf(-q, 2147483648.0f, y);
+    return ((long long)__float2int_rn(q) << 31) + (long long)__float2int_rn(r);
 }
 
 // v / 2^d rounded to nearest (ties up), d >= 0
@@ -430,7 +451,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity, uint64_
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 2000;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
             : "r"(a), "r"(parity)
@@ -441,15 +462,79 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity, uint64_
     }
 }
 
+// Shared-memory accumulators of the one-pass kernel: each 64-bit two's
+// complement fixed-point sum is kept as a low and a high 32-bit word in two
+// arrays and added with native 32-bit atomics, the carry out of the low word
+// (seen in the value the atomic returns) added into the high word.  Every add
+// is exact modulo 2^64 and the adds commute, so the sum is the 64-bit sum.
+struct Acc32 {
+    unsigned* lo;
+    unsigned* hi;
+    __device__ __forceinline__ void add(int j, long long v) const
+    {
+        const unsigned l = (unsigned)(unsigned long long)v;
+        const unsigned h = (unsigned)((unsigned long long)v >> 32);
+        const unsigned old = atomicAdd(&lo[j], l);
+        const unsigned carry = (old + l < old) ? 1u : 0u;
+        if (h + carry) atomicAdd(&hi[j], h + carry);
+    }
+    __device__ __forceinline__ long long get(int j) const
+    {
+        return (long long)(((unsigned long long)hi[j] << 32) | lo[j]);
+    }
+    __device__ __forceinline__ void set(int j, long long v) const
+    {
+        lo[j] = (unsigned)(unsigned long long)v;
+        hi[j] = (unsigned)((unsigned long long)v >> 32);
+    }
+};
+
+// Grid-wide wait of a cooperative launch in two halves: every block arrives
+// once per wait (thread 0 publishes the block's writes first), then waits
+// until the counter reaches k x grid for wait number k, bounded by wait_ns
+// (then ST_TIMEOUT, and false in every thread of the block).
+__device__ __forceinline__ void grid_arrive(unsigned* ctl)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&ctl[0], 1u);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait_for(unsigned* ctl, unsigned target, int* status, uint64_t wait_ns,
+                                              int* s_flag)
+{
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint64_t t0 = adj_global_ns();
+        while (*(volatile unsigned*)&ctl[0] < target) {
+            if (adj_global_ns() - t0 > wait_ns) {
+                raise_status(status, ST_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
 template <bool kTma>
-__global__ void __launch_bounds__(kOneThreads, 1) k_adj_onepass(const __grid_constant__ OneArgs a)
+__global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_constant__ OneArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* stages = smem;
-    unsigned long long* s_acc = (unsigned long long*)(smem + (kTma ? kOneStages * kOneStageBytes : 0));
-    uint64_t* s_bar = (uint64_t*)(s_acc + ((a.n_acc + 1) & ~1));
-    __shared__ float s_wmax[2][kOneWarps];
-    __shared__ double s_red[kOneWarps];
+    const int n_acc_pad = (a.n_acc + 3) & ~3;
+    unsigned* s_words = (unsigned*)(smem + (kTma ? kOneStages * kOneStageBytes : 0));
+    const Acc32 acc{s_words, s_words + n_acc_pad};
+    uint64_t* s_bar = (uint64_t*)(s_words + 2 * n_acc_pad);
+    float* s_table = (float*)(s_bar + kOneStages);  // the reflectance table, [n_mat][91]
+    __shared__ __align__(16) float s_wmax[2][kOneWarps];
+    __shared__ double s_red[kOneThreads];
     __shared__ unsigned long long s_cnt[kOneWarps];
     __shared__ int s_flag;
     __shared__ float s_gmax;
@@ -457,100 +542,139 @@ __global__ void __launch_bounds__(kOneThreads, 1) k_adj_onepass(const __grid_con
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, blk = blockIdx.x;
     const int64_t n = a.n;
-    const int64_t n_chunks = (n + kOneChunk - 1) / kOneChunk;
-    const int64_t k0 = (int64_t)blk * n_chunks / G, k1 = ((int64_t)blk + 1) * n_chunks / G;
-    const int64_t first = k0 * kOneChunk;
-    const int64_t last = min(k1 * kOneChunk, n);
-    const int64_t L = last > first ? last - first : 0;   // beams of this block
+    // this block's beams: an even share of the tape in whole 16-beam groups
+    // (16-byte aligned copies of every array), taken in chunks of kOneChunk
+    // beams; only the last chunk of a block may be shorter
+    const int64_t n16 = (n + 15) / 16;
+    const int64_t first = ((int64_t)blk * n16 / G) * 16;
+    const int64_t last = min((((int64_t)blk + 1) * n16 / G) * 16, n);
+    const int64_t L = last > first ? last - first : 0;
+    const int64_t n_chunks = (L + kOneChunk - 1) / kOneChunk;
     const bool has_tv = a.tvalid != nullptr;
 
-    for (int j = tid; j < a.n_acc; j += kOneThreads) s_acc[j] = 0ull;
-    for (int64_t j = (int64_t)blk * kOneThreads + tid; j < a.n_acc; j += (int64_t)G * kOneThreads) a.acc[j] = 0ull;
+    for (int j = tid; j < 2 * n_acc_pad; j += kOneThreads) s_words[j] = 0u;
+    for (int j = tid; j < a.T.n_mat * LIDAR_TABLE_SIZE; j += kOneThreads) s_table[j] = __ldg(&a.T.table[j]);
     if (kTma && tid == 0) {
         for (int st = 0; st < kOneStages; ++st) bar_init(&s_bar[st]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // a chunk is copied by the copy engine iff it is whole (the tape's last
-    // chunk may be partial: its byte counts need not be multiples of 16)
-    auto whole = [&](int64_t k) { return (k + 1) * (int64_t)kOneChunk <= n; };
+    // beams of chunk k, and how many of them the copy engine brings (whole
+    // 16-beam groups: only the tape's last few beams are loaded by the threads)
+    auto chunk_beams = [&](int64_t k) { return (int)min((int64_t)kOneChunk, L - k * kOneChunk); };
+    auto chunk_copied = [&](int64_t k) { return chunk_beams(k) & ~15; };
     auto issue = [&](int64_t k) {
-        const int slot = (int)((k - k0) % kOneStages);
+        const int slot = (int)(k % kOneStages);
         unsigned char* d = stages + slot * kOneStageBytes;
-        const int64_t c0 = k * kOneChunk;
-        const unsigned bytes = kOneChunk * (has_tv ? 16u : 15u);
-        bar_expect(&s_bar[slot], bytes);
-        bulk_copy(d, a.valid + c0, kOneChunk, &s_bar[slot]);
-        if (has_tv) bulk_copy(d + kOneChunk, a.tvalid + c0, kOneChunk, &s_bar[slot]);
-        bulk_copy(d + 2 * kOneChunk, a.mat + c0, 2 * kOneChunk, &s_bar[slot]);
-        bulk_copy(d + 4 * kOneChunk, a.theta + c0, 4 * kOneChunk, &s_bar[slot]);
-        bulk_copy(d + 8 * kOneChunk, a.rf + c0, 4 * kOneChunk, &s_bar[slot]);
-        bulk_copy(d + 12 * kOneChunk, a.g + c0, 4 * kOneChunk, &s_bar[slot]);
+        const int64_t c0 = first + k * kOneChunk;
+        const unsigned nb = (unsigned)chunk_copied(k);
+        bar_expect(&s_bar[slot], nb * (has_tv ? 16u : 15u));
+        if (nb == 0) return;
+        bulk_copy(d, a.valid + c0, nb, &s_bar[slot]);
+        if (has_tv) bulk_copy(d + kOneChunk, a.tvalid + c0, nb, &s_bar[slot]);
+        bulk_copy(d + 2 * kOneChunk, a.mat + c0, 2 * nb, &s_bar[slot]);
+        bulk_copy(d + 4 * kOneChunk, a.theta + c0, 4 * nb, &s_bar[slot]);
+        bulk_copy(d + 8 * kOneChunk, a.rf + c0, 4 * nb, &s_bar[slot]);
+        bulk_copy(d + 12 * kOneChunk, a.g + c0, 4 * nb, &s_bar[slot]);
     };
-    int64_t issued = k0;  // next chunk to copy (meaningful in thread 0)
+    int64_t issued = 0;  // next chunk to copy (meaningful in thread 0)
     if (kTma && tid == 0)
-        for (; issued < k1 && issued < k0 + kOneStages && whole(issued); ++issued) issue(issued);
+        for (; issued < n_chunks && issued < kOneStages; ++issued) issue(issued);
 
     float blk_max = 0.0f;
     int sh = 126;
-    float loss32 = 0.0f;
+    float loss32 = 0.0f, gain32 = 0.0f;  // this thread's squared residuals and gain terms, in its order
     unsigned cnt = 0;
     bool failed = false;
-    int64_t k_fail = k1;  // first chunk whose stage wait ran out
-    const float* Tt = a.T.table;
-    for (int64_t k = k0; k < k1; ++k) {
-        const int64_t c0 = k * kOneChunk;
+    int64_t k_fail = n_chunks;  // first chunk whose stage wait ran out
+    for (int64_t k = 0; k < n_chunks; ++k) {
+        const int64_t c0 = first + k * kOneChunk;
+        const int nb = chunk_beams(k);
         TapeIn in;
         bool ok = true;
-        if (kTma && whole(k)) {
-            const int slot = (int)((k - k0) % kOneStages);
-            ok = bar_wait(&s_bar[slot], (unsigned)(((k - k0) / kOneStages) & 1), a.wait_ns);
-            if (ok) {
-                const unsigned char* d = stages + slot * kOneStageBytes;
-                const uchar4 v = reinterpret_cast<const uchar4*>(d)[tid];
-                const uchar4 tv = has_tv ? reinterpret_cast<const uchar4*>(d + kOneChunk)[tid] : make_uchar4(1, 1, 1, 1);
-                const ushort4 m = reinterpret_cast<const ushort4*>(d + 2 * kOneChunk)[tid];
-                const float4 th = reinterpret_cast<const float4*>(d + 4 * kOneChunk)[tid];
-                const float4 r = reinterpret_cast<const float4*>(d + 8 * kOneChunk)[tid];
-                const float4 gg = reinterpret_cast<const float4*>(d + 12 * kOneChunk)[tid];
-                in.valid[0] = v.x; in.valid[1] = v.y; in.valid[2] = v.z; in.valid[3] = v.w;
-                in.tvalid[0] = tv.x; in.tvalid[1] = tv.y; in.tvalid[2] = tv.z; in.tvalid[3] = tv.w;
-                in.mat[0] = m.x; in.mat[1] = m.y; in.mat[2] = m.z; in.mat[3] = m.w;
-                in.theta[0] = th.x; in.theta[1] = th.y; in.theta[2] = th.z; in.theta[3] = th.w;
-                in.rf[0] = r.x; in.rf[1] = r.y; in.rf[2] = r.z; in.rf[3] = r.w;
-                in.g[0] = gg.x; in.g[1] = gg.y; in.g[2] = gg.z; in.g[3] = gg.w;
-            }
+        const unsigned char* d = nullptr;
+        if (kTma) {
+            const int slot = (int)(k % kOneStages);
+            ok = bar_wait(&s_bar[slot], (unsigned)((k / kOneStages) & 1), a.wait_ns);
+            d = stages + slot * kOneStageBytes;
+        }
+        const int r0 = kOneBPT * tid;  // this thread's first beam in the chunk
+        if (kTma && ok && r0 + kOneBPT <= chunk_copied(k)) {
+            const uchar4 v = reinterpret_cast<const uchar4*>(d)[tid];
+            const uchar4 tv = has_tv ? reinterpret_cast<const uchar4*>(d + kOneChunk)[tid] : make_uchar4(1, 1, 1, 1);
+            const ushort4 m = reinterpret_cast<const ushort4*>(d + 2 * kOneChunk)[tid];
+            const float4 th = reinterpret_cast<const float4*>(d + 4 * kOneChunk)[tid];
+            const float4 r = reinterpret_cast<const float4*>(d + 8 * kOneChunk)[tid];
+            const float4 gg = reinterpret_cast<const float4*>(d + 12 * kOneChunk)[tid];
+            in.valid[0] = v.x; in.valid[1] = v.y; in.valid[2] = v.z; in.valid[3] = v.w;
+            in.tvalid[0] = tv.x; in.tvalid[1] = tv.y; in.tvalid[2] = tv.z; in.tvalid[3] = tv.w;
+            in.mat[0] = m.x; in.mat[1] = m.y; in.mat[2] = m.z; in.mat[3] = m.w;
+            in.theta[0] = th.x; in.theta[1] = th.y; in.theta[2] = th.z; in.theta[3] = th.w;
+            in.rf[0] = r.x; in.rf[1] = r.y; in.rf[2] = r.z; in.rf[3] = r.w;
+            in.g[0] = gg.x; in.g[1] = gg.y; in.g[2] = gg.z; in.g[3] = gg.w;
         } else {
+            // the ragged end of the tape, a tape the copy engine cannot address,
+            // or a wait that ran out
+            const int cp = kTma && ok ? chunk_copied(k) : 0;
 #pragma unroll
             for (int j = 0; j < kOneBPT; ++j) {
-                const int64_t b = c0 + kOneBPT * tid + j;
-                const bool inb = b < n;
-                in.valid[j] = inb ? __ldcs(&a.valid[b]) : (uint8_t)0;
-                in.tvalid[j] = (inb && has_tv) ? __ldcs(&a.tvalid[b]) : (uint8_t)1;
-                in.mat[j] = inb ? __ldcs(&a.mat[b]) : (uint16_t)0;
-                in.theta[j] = inb ? __ldcs(&a.theta[b]) : 0.0f;
-                in.rf[j] = inb ? __ldcs(&a.rf[b]) : 0.0f;
-                in.g[j] = inb ? __ldcs(&a.g[b]) : 0.0f;
+                const int rr = r0 + j;
+                in.valid[j] = 0;
+                in.tvalid[j] = 1;
+                in.mat[j] = 0;
+                in.theta[j] = in.rf[j] = in.g[j] = 0.0f;
+                if (!ok || rr >= nb) continue;
+                if (rr < cp) {
+                    in.valid[j] = d[rr];
+                    if (has_tv) in.tvalid[j] = d[kOneChunk + rr];
+                    in.mat[j] = reinterpret_cast<const uint16_t*>(d + 2 * kOneChunk)[rr];
+                    in.theta[j] = reinterpret_cast<const float*>(d + 4 * kOneChunk)[rr];
+                    in.rf[j] = reinterpret_cast<const float*>(d + 8 * kOneChunk)[rr];
+                    in.g[j] = reinterpret_cast<const float*>(d + 12 * kOneChunk)[rr];
+                } else {
+                    const int64_t b = c0 + rr;
+                    in.valid[j] = __ldcs(&a.valid[b]);
+                    if (has_tv) in.tvalid[j] = __ldcs(&a.tvalid[b]);
+                    in.mat[j] = __ldcs(&a.mat[b]);
+                    in.theta[j] = __ldcs(&a.theta[b]);
+                    in.rf[j] = __ldcs(&a.rf[b]);
+                    in.g[j] = __ldcs(&a.g[b]);
+                }
             }
         }
-        float t_lo[kOneBPT], t_hi[kOneBPT], t_g[kOneBPT];
+        float t_lo[kOneBPT], t_hi[kOneBPT];
         int e[kOneBPT];
         float mx = 0.0f;
+        const int n_mat = a.T.n_mat;
+        const float gain = a.gain;
+        const bool mse = a.mse != 0;
 #pragma unroll
         for (int j = 0; j < kOneBPT; ++j) {
             e[j] = -1;
-            t_lo[j] = t_hi[j] = t_g[j] = 0.0f;
-            if (!ok) continue;
-            const TapeRow r = tape_row(in, j, TableDev{Tt, a.T.n_mat}, a.gain, a.mse != 0);
-            if (!r.use) continue;
-            const float w = a.gain * r.rf * r.gI;
-            e[j] = r.m * LIDAR_TABLE_SIZE + r.i;
-            t_lo[j] = w * (1.0f - r.f);
-            t_hi[j] = w * r.f;
-            t_g[j] = r.rf * r.R * r.gI;
-            mx = fmaxf(mx, fmaxf(fabsf(t_g[j]), fmaxf(fabsf(t_lo[j]), fabsf(t_hi[j]))));
-            loss32 = __fmaf_rn(r.res, r.res, loss32);
+            t_lo[j] = t_hi[j] = 0.0f;
+            if (!(in.valid[j] != 0 && in.tvalid[j] != 0)) continue;
+            // the forward pass's lerp of the table row (Sec. III), then dL/dI
+            const int m = in.mat[j] < n_mat ? in.mat[j] : n_mat - 1;
+            const float th = in.theta[j];
+            int i = (int)th;
+            if (i > LIDAR_TABLE_SIZE - 2) i = LIDAR_TABLE_SIZE - 2;
+            const float f = th - (float)i;
+            const int ei = m * LIDAR_TABLE_SIZE + i;
+            const float R = s_table[ei] * (1.0f - f) + s_table[ei + 1] * f;
+            const float rf = in.rf[j];
+            float res = 0.0f, gI = in.g[j];
+            if (mse) {
+                res = gain * R * rf - in.g[j];
+                gI = 2.0f * res;
+            }
+            const float w = gain * rf * gI;
+            e[j] = ei;
+            t_lo[j] = w * (1.0f - f);
+            t_hi[j] = w * f;
+            gain32 += rf * R * gI;
+            mx = fmaxf(mx, fmaxf(fabsf(t_lo[j]), fabsf(t_hi[j])));
+            loss32 = __fmaf_rn(res, res, loss32);
             ++cnt;
         }
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -561,7 +685,7 @@ __global__ void __launch_bounds__(kOneThreads, 1) k_adj_onepass(const __grid_con
             k_fail = k;
             break;
         }
-        if (kTma && tid == 0 && issued < k1 && whole(issued)) {
+        if (kTma && tid == 0 && issued < n_chunks) {
             // the stage just read is free: order the generic reads before the
             // copy engine's writes, then refill it
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -570,158 +694,211 @@ __global__ void __launch_bounds__(kOneThreads, 1) k_adj_onepass(const __grid_con
         }
         float cm = 0.0f;
 #pragma unroll
-        for (int w = 0; w < kOneWarps; ++w) cm = fmaxf(cm, s_wmax[k & 1][w]);
+        for (int w = 0; w < kOneWarps; w += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(&s_wmax[k & 1][w]);
+            cm = fmaxf(fmaxf(cm, fmaxf(q.x, q.y)), fmaxf(q.z, q.w));
+        }
         if (cm > blk_max) {
             const int nsh = one_shift(cm, L);
             if (nsh < sh && blk_max > 0.0f) {
-                const int d = sh - nsh;
-                for (int j = tid; j < a.n_acc; j += kOneThreads)
-                    s_acc[j] = (unsigned long long)round_shift((long long)s_acc[j], d);
+                const int dd = sh - nsh;
+                for (int j = tid; j < a.n_acc; j += kOneThreads) acc.set(j, round_shift(acc.get(j), dd));
                 __syncthreads();
             }
             if (nsh < sh) sh = nsh;
             blk_max = cm;
         }
         if (blk_max > 0.0f) {
+            // a thread's neighbouring beams that share a table bin are added once
+            // (integer sums: the grouping does not change the result)
             const float scale = ldexpf(1.0f, sh);
             int cur = -1;
-            unsigned long long a0 = 0, a1 = 0, gsum = 0;
+            long long a0 = 0, a1 = 0;
 #pragma unroll
             for (int j = 0; j < kOneBPT; ++j) {
                 if (e[j] < 0) continue;
                 if (e[j] != cur) {
                     if (cur >= 0) {
-                        atomicAdd(&s_acc[cur], a0);
-                        atomicAdd(&s_acc[cur + 1], a1);
+                        acc.add(cur, a0);
+                        acc.add(cur + 1, a1);
                     }
                     cur = e[j];
                     a0 = a1 = 0;
                 }
-                a0 += (unsigned long long)__float2ll_rn(t_lo[j] * scale);
-                a1 += (unsigned long long)__float2ll_rn(t_hi[j] * scale);
-                gsum += (unsigned long long)__float2ll_rn(t_g[j] * scale);
+                a0 += fixed_of(t_lo[j], scale);
+                a1 += fixed_of(t_hi[j], scale);
             }
             if (cur >= 0) {
-                atomicAdd(&s_acc[cur], a0);
-                atomicAdd(&s_acc[cur + 1], a1);
+                acc.add(cur, a0);
+                acc.add(cur + 1, a1);
             }
-            for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
-            if (lane == 0 && gsum) atomicAdd(&s_acc[a.n_acc - 1], gsum);
         }
     }
+    __syncthreads();  // every thread is done with the last chunk's maxima
     if (failed && kTma && tid == 0) {
         // let the copies still in flight (chunks k_fail .. issued - 1, at most one
         // per stage) land before the block's shared memory goes away; bounded by
         // at least a second whatever the caller's wait limit
         const uint64_t drain_ns = a.wait_ns > 1000000000ull ? a.wait_ns : 1000000000ull;
-        for (int64_t k = k_fail; k < issued; ++k) {
-            const int slot = (int)((k - k0) % kOneStages);
-            bar_wait(&s_bar[slot], (unsigned)(((k - k0) / kOneStages) & 1), drain_ns);
-        }
+        for (int64_t k = k_fail; k < issued; ++k)
+            bar_wait(&s_bar[k % kOneStages], (unsigned)((k / kOneStages) & 1), drain_ns);
     }
     if (failed && tid == 0) raise_status(a.status, ST_TIMEOUT);
 
-    // ---- this block's loss partial (fixed order), beam count, maximum and shift
-    double l = (double)loss32;
-    unsigned long long c = cnt;
+    // ---- this block's gain-term maximum, loss partial (fixed order), beam count:
+    // FP32 within a warp (a fixed shuffle tree), FP64 across warps
+    float gmx = fabsf(gain32);
+    float l = loss32;
+    unsigned c = cnt;
     for (int o = 16; o > 0; o >>= 1) {
+        gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, o));
         l += __shfl_down_sync(0xffffffffu, l, o);
         c += __shfl_down_sync(0xffffffffu, c, o);
     }
     if (lane == 0) {
-        s_red[warp] = l;
+        s_red[warp] = (double)l;
         s_cnt[warp] = c;
+        s_wmax[0][warp] = gmx;
     }
     __syncthreads();
     if (tid == 0) {
         double t = 0.0;
         unsigned long long ct = 0;
+        float gm = 0.0f;
         for (int w = 0; w < kOneWarps; ++w) {
             t += s_red[w];
             ct += s_cnt[w];
+            gm = fmaxf(gm, s_wmax[0][w]);
         }
+        s_gmax = gm;
         a.blk_loss[blk] = t;
         a.blk_n[blk] = ct;
+    }
+    __syncthreads();
+    // the threads' gain sums join the fixed-point sums: widen the scale first
+    // if one of them is larger than every term seen
+    if (s_gmax > blk_max && !failed) {
+        const int nsh = one_shift(s_gmax, L);
+        if (nsh < sh && blk_max > 0.0f) {
+            const int dd = sh - nsh;
+            for (int j = tid; j < a.n_acc; j += kOneThreads) acc.set(j, round_shift(acc.get(j), dd));
+        }
+        if (nsh < sh) sh = nsh;
+        blk_max = s_gmax;
+    }
+    __syncthreads();
+    if (blk_max > 0.0f) {
+        long long gq = fixed_of(gain32, ldexpf(1.0f, sh));
+        for (int o = 16; o > 0; o >>= 1) gq += __shfl_xor_sync(0xffffffffu, gq, o);
+        if (lane == 0 && gq) acc.add(a.n_acc - 1, gq);
+    }
+    __syncthreads();
+    if (tid == 0) {
         a.blk_max[blk] = failed ? 0.0f : blk_max;
         a.blk_sh[blk] = sh;
-        // ---- grid-wide wait (cooperative launch: every block is resident)
-        __threadfence();
-        atomicAdd(&a.ctl[0], 1u);
-        int okw = 1;
-        const uint64_t t0 = adj_global_ns();
-        while (*(volatile unsigned*)&a.ctl[0] < (unsigned)G) {
-            if (adj_global_ns() - t0 > a.wait_ns) {
-                raise_status(a.status, ST_TIMEOUT);
-                okw = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-        s_flag = okw;
     }
-    __syncthreads();
-    if (s_flag && !failed) {
-        // the common scale: the largest contribution of the whole tape
-        float gm = 0.0f;
-        for (int j = tid; j < G; j += kOneThreads) gm = fmaxf(gm, __ldcg(&a.blk_max[j]));
-        for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
-        if (lane == 0) s_wmax[0][warp] = gm;
-        __syncthreads();
-        if (tid == 0) {
-            float t = 0.0f;
-            for (int w = 0; w < kOneWarps; ++w) t = fmaxf(t, s_wmax[0][w]);
-            s_gmax = t;
-        }
-        __syncthreads();
-        if (blk_max > 0.0f) {
-            const int S = one_shift(s_gmax, n);
-            const int d = sh - S;
-            for (int j = tid; j < a.n_acc; j += kOneThreads) {
-                const long long v = round_shift((long long)s_acc[j], d);
-                if (v) atomicAdd(&a.acc[j], (unsigned long long)v);
-            }
-        }
-    }
-    // ---- the last block to finish writes the results
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_flag = atomicAdd(&a.ctl[1], 1u) == (unsigned)G - 1;
-    __syncthreads();
-    if (!s_flag) return;
-    __threadfence();
-    if (tid == 0) {
+    // ---- grid-wide wait 1: every block's maximum, count and loss partial are out
+    grid_arrive(a.ctl);
+    if (!grid_wait_for(a.ctl, (unsigned)G, a.status, a.wait_ns, &s_flag)) failed = true;
+    // the common scale (the largest contribution of the whole tape) and the
+    // number of beams used, reduced in a fixed order by every block
+    {
         float gm = 0.0f;
         unsigned long long N = 0;
-        for (int j = 0; j < G; ++j) {
+        for (int j = tid; j < G; j += kOneThreads) {
             gm = fmaxf(gm, __ldcg(&a.blk_max[j]));
             N += __ldcg(&a.blk_n[j]);
         }
-        s_gmax = gm;
-        s_cnt[0] = N;
-        if (a.loss) {
-            double t = 0.0;
-            for (int j = 0; j < G; ++j) t += __ldcg(&a.blk_loss[j]);
-            *a.loss = a.mse ? (float)(N ? t / (double)N : 0.0) : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) {
+            gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+            N += __shfl_xor_sync(0xffffffffu, N, o);
         }
-    }
-    __syncthreads();
-    const unsigned long long N = s_cnt[0];
-    if (s_gmax > 0.0f) {
-        const float inv_scale = ldexpf(1.0f, -one_shift(s_gmax, n));  // exact: a power of two
-        const float norm = a.mse ? (N ? __frcp_rn((float)N) : 0.0f) : 1.0f;
-        for (int j = tid; j < a.n_acc; j += kOneThreads) {
-            const float v = __fmul_rn(__fmul_rn(__ll2float_rn((long long)__ldcg(&a.acc[j])), inv_scale), norm);
-            if (j < a.n_acc - 1) {
-                if (a.grad_table) a.grad_table[j] += v;
-            } else if (a.grad_gain) {
-                *a.grad_gain += v;
+        if (lane == 0) {
+            s_wmax[1][warp] = gm;
+            s_cnt[warp] = N;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float g2 = 0.0f;
+            unsigned long long n2 = 0;
+            for (int w = 0; w < kOneWarps; ++w) {
+                g2 = fmaxf(g2, s_wmax[1][w]);
+                n2 += s_cnt[w];
             }
+            s_gmax = g2;
+            s_cnt[0] = n2;
+        }
+        __syncthreads();
+    }
+    const float gmax = s_gmax;
+    const unsigned long long N = s_cnt[0];
+    const int S = one_shift(gmax, n);
+    // this block's sums at the common scale, one dense row
+    {
+        long long* row = a.rows + (int64_t)blk * a.n_acc;
+        const int dd = sh - S;
+        for (int j = tid; j < a.n_acc; j += kOneThreads)
+            row[j] = (failed || blk_max <= 0.0f) ? 0ll : round_shift(acc.get(j), dd);
+    }
+    // ---- grid-wide wait 2: every row is out
+    grid_arrive(a.ctl);
+    // block 0 writes the loss (the partials in block order, a fixed tree)
+    // between its arrival and its wait
+    if (blk == 0 && a.loss) {
+        double t = 0.0;
+        for (int j = tid; j < G; j += kOneThreads) t += __ldcg(&a.blk_loss[j]);
+        s_red[tid] = t;
+        __syncthreads();
+        for (int w = kOneThreads / 2; w > 0; w >>= 1) {
+            if (tid < w) s_red[tid] += s_red[tid + w];
+            __syncthreads();
+        }
+        if (tid == 0) *a.loss = a.mse ? (float)(N ? s_red[0] / (double)N : 0.0) : 0.0f;
+    }
+    if (!grid_wait_for(a.ctl, 2u * (unsigned)G, a.status, a.wait_ns, &s_flag)) failed = true;
+    // each block sums the rows over its slice of the entries and writes those
+    // gradients: warp w reads rows w, w + kOneWarps, ..., lane l entry j0 + l of
+    // each (contiguous: one row's slice per warp load), then the warps' sums
+    // meet in shared memory (integer sums: the order is free)
+    if (!failed && gmax > 0.0f) {
+        const int j0 = (int)((int64_t)blk * a.n_acc / G), j1 = (int)(((int64_t)blk + 1) * a.n_acc / G);
+        const float inv_scale = ldexpf(1.0f, -S);  // exact: a power of two
+        const float norm = a.mse ? (N ? __frcp_rn((float)N) : 0.0f) : 1.0f;
+        long long* s_part = reinterpret_cast<long long*>(s_red);  // [kOneWarps][32]
+        for (int e0 = j0; e0 < j1; e0 += 32) {
+            const int j = e0 + lane;
+            long long t = 0;
+            if (j < j1) {
+                constexpr int kUnroll = 8;
+                for (int r0 = warp; r0 < G; r0 += kOneWarps * kUnroll) {
+                    long long v[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int r = r0 + u * kOneWarps;
+                        v[u] = r < G ? __ldcg(&a.rows[(int64_t)r * a.n_acc + j]) : 0ll;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) t += v[u];
+                }
+            }
+            s_part[warp * 32 + lane] = t;
+            __syncthreads();
+            if (warp == 0 && j < j1) {
+                long long tot = 0;
+                for (int w = 0; w < kOneWarps; ++w) tot += s_part[w * 32 + lane];
+                const float v = __fmul_rn(__fmul_rn(__ll2float_rn(tot), inv_scale), norm);
+                if (j < a.n_acc - 1) {
+                    if (a.grad_table) a.grad_table[j] += v;
+                } else if (a.grad_gain) {
+                    *a.grad_gain += v;
+                }
+            }
+            __syncthreads();
         }
     }
+    // ---- the last block to finish clears the wait counters for the next call
     __syncthreads();
-    if (tid == 0) {
-        // every block has passed the grid wait and counted itself: ready for the next call
+    if (tid == 0 && atomicAdd(&a.ctl[1], 1u) == (unsigned)G - 1) {
         a.ctl[0] = 0u;
         a.ctl[1] = 0u;
     }
@@ -842,8 +1019,8 @@ cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid
 size_t onepass_scratch_bytes(int M, int num_sms)
 {
     const size_t n_acc = (size_t)M * LIDAR_TABLE_SIZE + 1;
-    const size_t G = (size_t)(num_sms > 0 ? num_sms : 1);
-    return ((n_acc * 8 + 255) / 256) * 256 + ((G * 24 + 255) / 256) * 256;
+    const size_t G = (size_t)(num_sms > 0 ? num_sms : 1) * kOneBlocksPerSm;
+    return ((G * n_acc * 8 + 255) / 256) * 256 + ((G * 24 + 255) / 256) * 256;
 }
 
 cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_t* valid, const uint16_t* mat,
@@ -859,33 +1036,60 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
     // the copy engine needs 16-byte aligned sources; otherwise the threads load the tape
     auto al16 = [](const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; };
     const bool tma = al16(valid) && al16(target_valid) && al16(mat) && al16(theta_deg) && al16(rf) && al16(g);
-    const size_t acc_smem = (size_t)((n_acc + 1) & ~1) * 8;
-    const size_t smem = (tma ? (size_t)kOneStages * kOneStageBytes : 0) + acc_smem + kOneStages * 8;
-    const void* fn = tma ? (const void*)k_adj_onepass<true> : (const void*)k_adj_onepass<false>;
+    const size_t acc_smem = (size_t)((n_acc + 3) & ~3) * 8;  // low and high words, 16-byte aligned
+    const size_t table_smem = (size_t)T.n_mat * LIDAR_TABLE_SIZE * 4;
+    const size_t smem_tma = (size_t)kOneStages * kOneStageBytes + acc_smem + kOneStages * 8 + table_smem;
+    const size_t smem_direct = acc_smem + kOneStages * 8 + table_smem;
+    const size_t smem = tma ? smem_tma : smem_direct;
+    const void* fn_tma = (const void*)k_adj_onepass<true>;
+    const void* fn = tma ? fn_tma : (const void*)k_adj_onepass<false>;
+    // blocks per SM: as many as the copy-engine variant can keep resident (up to
+    // kOneBlocksPerSm), whichever variant runs, so that the aligned and the
+    // unaligned paths split the tape the same way (and give the same sums)
+    int bps = 0;
     {
-        // the shared-memory attribute and the residency are asked once per
-        // (device, kernel, size); a failure means the accumulators do not fit
-        // beside the stages: the caller then takes the separate passes
+        // the kernel may take up to the device's opt-in shared memory (set once
+        // per device and kernel: the attribute is the function's, whatever the
+        // size of a launch); residency is asked once per (device, kernel, size).
+        // No room for one block means the accumulators do not fit beside the
+        // stages: the caller then takes the separate passes.
         static std::mutex mu;
-        static std::map<std::tuple<int, bool, size_t>, bool> fits;
+        static std::map<std::pair<int, const void*>, bool> opted;
+        static std::map<std::tuple<int, const void*, size_t>, int> resident;
         int dev = 0;
         cudaGetDevice(&dev);
         std::lock_guard<std::mutex> lk(mu);
-        auto it = fits.find({dev, tma, smem});
-        if (it == fits.end()) {
-            int per_sm = 0;
-            bool ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
-                      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kOneThreads, smem) == cudaSuccess &&
-                      per_sm >= 1;
+        auto opt_in = [&](const void* f) {
+            auto it = opted.find({dev, f});
+            if (it != opted.end()) return it->second;
+            int optin = 0;
+            cudaFuncAttributes fa{};
+            bool ok = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+                      cudaFuncGetAttributes(&fa, f) == cudaSuccess &&
+                      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           optin - (int)fa.sharedSizeBytes) == cudaSuccess;
             if (!ok) cudaGetLastError();
-            it = fits.emplace(std::make_tuple(dev, tma, smem), ok).first;
-        }
-        if (!it->second) return cudaErrorNotSupported;
+            opted[{dev, f}] = ok;
+            return ok;
+        };
+        auto per_sm = [&](const void* f, size_t bytes) {
+            auto it = resident.find({dev, f, bytes});
+            if (it != resident.end()) return it->second;
+            int r = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, f, kOneThreads, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                r = 0;
+            }
+            resident[{dev, f, bytes}] = r;
+            return r;
+        };
+        if (!opt_in(fn_tma) || !opt_in(fn)) return cudaErrorNotSupported;
+        bps = std::min(per_sm(fn_tma, smem_tma), kOneBlocksPerSm);
+        if (bps < 1 || per_sm(fn, smem) < bps) return cudaErrorNotSupported;
     }
-    // one block per SM whatever the occupancy, so the aligned and the unaligned
-    // paths split the tape the same way (and give the same sums)
+    // about a chunk per block at least; a block's share is whole 16-beam groups
     const int64_t n_chunks = (n + kOneChunk - 1) / kOneChunk;
-    int G = (int)std::min<int64_t>(std::max<int64_t>(n_chunks, 1), num_sms);
+    int G = (int)std::min<int64_t>(std::max<int64_t>(n_chunks, 1), (int64_t)bps * num_sms);
     char* p = (char*)scratch;
     OneArgs a{};
     a.n = n;
@@ -899,8 +1103,8 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
     a.gain = gain;
     a.mse = target_I != nullptr;
     a.n_acc = n_acc;
-    a.acc = (unsigned long long*)p;
-    p += (((size_t)n_acc * 8 + 255) / 256) * 256;
+    a.rows = (long long*)p;
+    p += (((size_t)G * n_acc * 8 + 255) / 256) * 256;
     a.blk_max = (float*)p;
     a.blk_sh = (int*)(p + (size_t)G * 4);
     a.blk_loss = (double*)(p + (size_t)G * 8);
@@ -912,7 +1116,9 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
     a.grad_table = grad_table;
     a.grad_gain = grad_gain;
     void* args[] = {&a};
-    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kOneThreads), args, smem, s);
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kOneThreads), args, smem, s);
+    if (e != cudaSuccess) cudaGetLastError();  // leave no stale launch error for the next call
+    return e;
 }
 
 }  // namespace lidar
