@@ -45,11 +45,11 @@ POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal,
 # the cast kernel as the roofline times it (cfg1 frame, dense valid flags out,
 # L2 flushed before the launch), from one ncu capture, with the digest of the
 # kernel sources the capture ran.  Reported only while the sources still match.
-NCU_TRAFFIC = {"sources": "e5800d28009b0135", "bytes": 10_460_416, "l2_bytes": 3_981_372 * 32,
+NCU_TRAFFIC = {"sources": "b3f41d743257cfe8", "bytes": 10_468_864, "l2_bytes": 3_961_926 * 32,
                "l1_global_load_bytes": 7_811_641 * 32}   # profiles/k_cast_cfg1_ncu_full.md
 # Binding-unit fractions of the same capture (ncu --set full of one launch):
 # L1/TEX throughput, issue-active and SM-active shares.
-NCU_UNITS = {"l1tex_throughput_pct": 42.6, "issue_active_pct": 43.1, "sm_active_pct": 67.0}
+NCU_UNITS = {"l1tex_throughput_pct": 42.5, "issue_active_pct": 43.3, "sm_active_pct": 72.4}
 # FP32 work of one launch of the cast kernel from ncu's SASS instruction
 # counters (sm__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,
 # fp32}_pred_on), FLOPs = 2 ffma + fadd + fmul + 4 ffma2 + 2 fadd2 + 2 fmul2 +
