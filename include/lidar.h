@@ -524,6 +524,20 @@ typedef struct {
 lidar_status lidar_get_launch_config(lidar_ctx* ctx, lidar_launch_config* out);
 lidar_status lidar_set_launch_config(lidar_ctx* ctx, const lidar_launch_config* cfg);
 
+/* Overlap of consecutive direct casts (lidar_cast calls on the context's
+ * stream, outside a stream capture; enable 1 by default, 0 to cast one after
+ * the other).  A cast then starts on the SMs the cast before it leaves idle
+ * once that cast's work queue is empty (its last, longest traversals still
+ * running), by programmatic dependent launch; the library orders everything
+ * the two share (counter regions, dense scratch).  Results are bit-identical
+ * either way.  Anything else on the stream between two casts (a copy, an event
+ * wait, another kernel) lets the second start only when the first has
+ * finished, as usual.  Callers must not let the point or dense buffers of one
+ * cast be read by later stream work that does not follow that cast on the
+ * stream. */
+lidar_status lidar_set_cast_overlap(lidar_ctx* ctx, int32_t enable);
+lidar_status lidar_get_cast_overlap(lidar_ctx* ctx, int32_t* enable);
+
 /* Limit, in nanoseconds of GPU time (the device's global timer), of every
  * bounded device-side wait in the context's kernels: the grid-wide wait of a
  * cast whose point-cloud scatter runs inside the cast kernel, and the waits of

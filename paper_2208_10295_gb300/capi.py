@@ -154,6 +154,8 @@ _PROTOS = [
     ("lidar_get_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
     ("lidar_set_launch_config", ctypes.c_int, [c_vp, ctypes.POINTER(lidar_launch_config)]),
     ("lidar_set_wait_limit", ctypes.c_int, [c_vp, ctypes.c_uint64]),
+    ("lidar_set_cast_overlap", ctypes.c_int, [c_vp, ctypes.c_int32]),
+    ("lidar_get_cast_overlap", ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_int32)]),
     ("lidar_measure_fp32_rate", ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     ("lidar_get_wait_limit", ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_uint64)]),
@@ -236,3 +238,5 @@ lidar_set_launch_config = _fwd("lidar_set_launch_config")
 lidar_set_wait_limit = _fwd("lidar_set_wait_limit")
 lidar_get_wait_limit = _fwd("lidar_get_wait_limit")
 lidar_measure_fp32_rate = _fwd("lidar_measure_fp32_rate")
+lidar_set_cast_overlap = _fwd("lidar_set_cast_overlap")
+lidar_get_cast_overlap = _fwd("lidar_get_cast_overlap")

@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -247,12 +248,15 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
                                               unsigned long long* work_counter, int tile_rays, WorkCount wc,
                                               CompactCounts cc, lidar_points pts, int64_t n_beams_total, int fused,
                                               const __grid_constant__ InlineFrames inl, unsigned* zero_next,
-                                              int64_t zero_words, uint64_t wait_ns)
+                                              int64_t zero_words, uint64_t wait_ns, int pdl)
 {
     const int lane = threadIdx.x & 31;
-    // clear the counter region of the cast before this one, for the cast after it
+    // clear the counter region of the cast after this one
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < zero_words; i += (int64_t)gridDim.x * blockDim.x)
         zero_next[i] = 0u;
+    // overlapped casts: the block's clearing is done before any of its warps
+    // lets the next cast start
+    if (pdl) __syncthreads();
     // frames and their first tiles: from the launch parameters when they came inline
     const FrameDev* fr_tab = inl.n ? inl.f : frames;
     const int64_t* tile_first = inl.n ? inl.prefix : tile_prefix;
@@ -272,7 +276,18 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_cast(SceneDev S, const Sens
         unsigned long long claimed = 0;
         if (lane == 0) claimed = atomicAdd(work_counter, 1ull);
         const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, claimed, 0);
-        if (tile >= n_tiles) break;
+        if (tile >= n_tiles) {
+            if (pdl && lane == 0) {
+                // the work queue is empty: once the cast before this one has
+                // completed (its counter region and dense records are then free
+                // for the cast after this one), the next cast may start on the
+                // SMs this cast's last tiles leave idle
+                __threadfence();
+                asm volatile("griddepcontrol.wait;" ::: "memory");
+                asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+            }
+            break;
+        }
         const int fi = find_frame(tile_first, n_frames, tile);
         const FrameDev& fr = fr_tab[fi];
         const SensorDev& sd = sensors[fr.sensor];
@@ -412,15 +427,22 @@ constexpr int kCompactItems = 4;
 constexpr int kCompactTile = kCompactThreads * kCompactItems;
 static_assert(kCompactTile == kCompactTileBeams, "the scatter tiles are the cast's counting tiles");
 
-// One compaction tile (kCompactTileBeams beams) per block.
+// Compaction tiles (kCompactTileBeams beams) blockIdx.x, blockIdx.x + gridDim.x, ...
+// With `pdl` (an overlapped cast's scatter) the block first lets the next
+// cast start, then waits for its own cast to complete.
 __global__ void __launch_bounds__(kCompactThreads) k_scatter_points(
     const SensorDev* __restrict__ sensors, const FrameDev* __restrict__ frames, int n_frames, int64_t n,
     BeamsOut dense, const int64_t* __restrict__ tile_offsets, lidar_points pts, int* status,
-    const __grid_constant__ InlineFrames inl)
+    const __grid_constant__ InlineFrames inl, int pdl)
 {
+    if (pdl) {
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+    }
     __shared__ uint32_t s_warp[kScatterItems * 8];
-    scatter_tile(sensors, inl.n ? inl.f : frames, n_frames, n, dense, blockIdx.x, tile_offsets[blockIdx.x], pts,
-                 status, s_warp);
+    const int64_t n_tiles = (n + kCompactTileBeams - 1) / kCompactTileBeams;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x)
+        scatter_tile(sensors, inl.n ? inl.f : frames, n_frames, n, dense, t, tile_offsets[t], pts, status, s_warp);
 }
 
 // ------------------------------------------------------------------ ray order
@@ -481,12 +503,17 @@ struct CastArgs {
     unsigned* zero_next;
     int64_t zero_words;
     uint64_t wait_ns;
+    int pdl;
 };
 
 template <bool C, int V, int W>
-cudaError_t launch_one(cudaStream_t s, CastArgs a, int64_t grid, int block, size_t smem, int num_sms)
+cudaError_t launch_one(cudaStream_t s, CastArgs a, int64_t grid, int block, size_t smem, int num_sms,
+                       cudaError_t* refused)
 {
     auto fn = k_cast<C, V, W>;
+    void* args[] = {&a.scene, &a.sensors, &a.frames, &a.n_frames, &a.prefix, &a.n_tiles, &a.table, &a.seed,
+                    &a.out, &a.status, &a.work_counter, &a.tile_rays, &a.wc, &a.cc, &a.pts, &a.n_total,
+                    &a.fused, &a.inl, &a.zero_next, &a.zero_words, &a.wait_ns, &a.pdl};
     if (a.fused) {
         // every block must be resident for the grid-wide waits; the occupancy
         // of this instantiation depends only on the block size and the shared
@@ -507,14 +534,33 @@ cudaError_t launch_one(cudaStream_t s, CastArgs a, int64_t grid, int block, size
         }
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         if (grid > (int64_t)per_sm * num_sms) grid = (int64_t)per_sm * num_sms;
-        void* args[] = {&a.scene, &a.sensors, &a.frames, &a.n_frames, &a.prefix, &a.n_tiles, &a.table, &a.seed,
-                        &a.out, &a.status, &a.work_counter, &a.tile_rays, &a.wc, &a.cc, &a.pts, &a.n_total,
-                        &a.fused, &a.inl, &a.zero_next, &a.zero_words, &a.wait_ns};
-        return cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)grid), dim3(block), args, smem, s);
     }
+    if (a.pdl) {
+        // programmatic dependent launch: this cast may start before the one
+        // ahead of it in the stream has finished (the kernel orders what must be
+        // ordered, see k_cast); refused combinations fall back to a plain launch
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)grid);
+        lc.blockDim = dim3(block);
+        lc.dynamicSmemBytes = smem;
+        lc.stream = s;
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        attr[1].id = cudaLaunchAttributeCooperative;
+        attr[1].val.cooperative = 1;
+        lc.attrs = attr;
+        lc.numAttrs = a.fused ? 2 : 1;
+        const cudaError_t pe = cudaLaunchKernelExC(&lc, (const void*)fn, args);
+        if (pe == cudaSuccess) return cudaSuccess;
+        cudaGetLastError();
+        if (refused) *refused = pe;
+        a.pdl = 0;
+    }
+    if (a.fused) return cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)grid), dim3(block), args, smem, s);
     fn<<<(unsigned)grid, block, smem, s>>>(a.scene, a.sensors, a.frames, a.n_frames, a.prefix, a.n_tiles, a.table,
                                             a.seed, a.out, a.status, a.work_counter, a.tile_rays, a.wc, a.cc, a.pts,
-                                            a.n_total, a.fused, a.inl, a.zero_next, a.zero_words, a.wait_ns);
+                                            a.n_total, a.fused, a.inl, a.zero_next, a.zero_words, a.wait_ns, a.pdl);
     return cudaGetLastError();
 }
 
@@ -555,9 +601,11 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     a.wait_ns = cfg.wait_ns;
     if (inline_frames) a.inl = *inline_frames;  // else n == 0: the device table
     const bool clean = region && region->clean;
+    cudaError_t* refused = region ? region->overlap_refused : nullptr;
     if (region) {
         a.zero_next = region->zero_next;
         a.zero_words = region->zero_next ? region->zero_words : 0;
+        a.pdl = region->overlap ? 1 : 0;
     }
     if (compact_scratch) {
         const int64_t nt = (n_beams_total + kCompactTileBeams - 1) / kCompactTileBeams;
@@ -570,7 +618,9 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
         const size_t wc_off = compact_counter_offset(nt);
         a.work_counter = (unsigned long long*)((char*)a.cc.counts + wc_off);
         if (!clean) cudaMemsetAsync(a.cc.counts, 0, wc_off + sizeof(unsigned long long), s);
-        if (points && cfg.fused_scatter) {
+        // an overlapped cast compacts in the scatter kernel that follows it (a
+        // cooperative grid could not start before the cast ahead of it ends)
+        if (points && cfg.fused_scatter && !(region && region->overlap)) {
             a.pts = *points;
             a.fused = 1;
         }
@@ -590,25 +640,25 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
     if (count) {
         // the work counted depends on the tree the traversal walks, not on the launch shape
         a.fused = 0;
-        e = cfg.traversal == 3   ? launch_one<true, 4, 3>(s, a, grid, bt, stack_bytes, num_sms)
-            : cfg.traversal == 2 ? launch_one<true, 4, 2>(s, a, grid, bt, stack_bytes, num_sms)
-                                 : launch_one<true, 4, 0>(s, a, grid, bt, stack_bytes, num_sms);
+        e = cfg.traversal == 3   ? launch_one<true, 4, 3>(s, a, grid, bt, stack_bytes, num_sms, refused)
+            : cfg.traversal == 2 ? launch_one<true, 4, 2>(s, a, grid, bt, stack_bytes, num_sms, refused)
+                                 : launch_one<true, 4, 0>(s, a, grid, bt, stack_bytes, num_sms, refused);
     } else if (cfg.traversal == 1) {
-        e = variant == 2   ? launch_one<false, 2, 1>(s, a, grid, bt, 0, num_sms)
-            : variant == 3 ? launch_one<false, 3, 1>(s, a, grid, bt, 0, num_sms)
-                           : launch_one<false, 4, 1>(s, a, grid, bt, 0, num_sms);
+        e = variant == 2   ? launch_one<false, 2, 1>(s, a, grid, bt, 0, num_sms, refused)
+            : variant == 3 ? launch_one<false, 3, 1>(s, a, grid, bt, 0, num_sms, refused)
+                           : launch_one<false, 4, 1>(s, a, grid, bt, 0, num_sms, refused);
     } else if (cfg.traversal == 2) {
-        e = variant == 2   ? launch_one<false, 2, 2>(s, a, grid, bt, stack_bytes, num_sms)
-            : variant == 3 ? launch_one<false, 3, 2>(s, a, grid, bt, stack_bytes, num_sms)
-                           : launch_one<false, 4, 2>(s, a, grid, bt, stack_bytes, num_sms);
+        e = variant == 2   ? launch_one<false, 2, 2>(s, a, grid, bt, stack_bytes, num_sms, refused)
+            : variant == 3 ? launch_one<false, 3, 2>(s, a, grid, bt, stack_bytes, num_sms, refused)
+                           : launch_one<false, 4, 2>(s, a, grid, bt, stack_bytes, num_sms, refused);
     } else if (cfg.traversal == 3) {
-        e = variant == 2   ? launch_one<false, 2, 3>(s, a, grid, bt, stack_bytes, num_sms)
-            : variant == 3 ? launch_one<false, 3, 3>(s, a, grid, bt, stack_bytes, num_sms)
-                           : launch_one<false, 4, 3>(s, a, grid, bt, stack_bytes, num_sms);
+        e = variant == 2   ? launch_one<false, 2, 3>(s, a, grid, bt, stack_bytes, num_sms, refused)
+            : variant == 3 ? launch_one<false, 3, 3>(s, a, grid, bt, stack_bytes, num_sms, refused)
+                           : launch_one<false, 4, 3>(s, a, grid, bt, stack_bytes, num_sms, refused);
     } else {
-        e = variant == 2   ? launch_one<false, 2, 0>(s, a, grid, bt, stack_bytes, num_sms)
-            : variant == 3 ? launch_one<false, 3, 0>(s, a, grid, bt, stack_bytes, num_sms)
-                           : launch_one<false, 4, 0>(s, a, grid, bt, stack_bytes, num_sms);
+        e = variant == 2   ? launch_one<false, 2, 0>(s, a, grid, bt, stack_bytes, num_sms, refused)
+            : variant == 3 ? launch_one<false, 3, 0>(s, a, grid, bt, stack_bytes, num_sms, refused)
+                           : launch_one<false, 4, 0>(s, a, grid, bt, stack_bytes, num_sms, refused);
     }
     if (e == cudaSuccess && scattered) *scattered = a.fused != 0;
     return e;
@@ -662,14 +712,35 @@ size_t fused_compact_scratch_bytes(int64_t n)
 
 cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev, int n_frames,
                            int64_t n, BeamsOut dense, const lidar_points& pts, void* compact_scratch, int* status,
-                           const InlineFrames* inline_frames)
+                           const InlineFrames* inline_frames, int num_sms, bool pdl)
 {
     const int64_t tiles = (n + kCompactTile - 1) / kCompactTile;
     if (tiles == 0) return cudaSuccess;
     InlineFrames inl{};
     if (inline_frames) inl = *inline_frames;
+    const int64_t* offsets = (const int64_t*)compact_scratch;
+    int flag = 0;
+    if (pdl && num_sms > 0) {
+        // an overlapped cast's scatter: a small grid (one 128-thread block per SM
+        // fits beside the cast's blocks) that lets the next cast start at once
+        // and then waits for its own cast
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)std::min<int64_t>(tiles, num_sms));
+        lc.blockDim = dim3(128);
+        lc.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        flag = 1;
+        void* args[] = {&sensors_dev, &frames_dev, &n_frames, &n, &dense, &offsets, (void*)&pts, &status, &inl, &flag};
+        if (cudaLaunchKernelExC(&lc, (const void*)k_scatter_points, args) == cudaSuccess) return cudaSuccess;
+        cudaGetLastError();
+        flag = 0;
+    }
     k_scatter_points<<<(unsigned)tiles, kCompactThreads, 0, s>>>(sensors_dev, frames_dev, n_frames, n, dense,
-                                                                 (const int64_t*)compact_scratch, pts, status, inl);
+                                                                 offsets, pts, status, inl, flag);
     return cudaGetLastError();
 }
 

@@ -99,12 +99,16 @@ struct InlineFrames {
 // The counters of a direct cast (tile counts, finished-block word, work
 // counter) in a region the caller keeps all zero between casts: the launch
 // needs no memset when `clean`, and clears `zero_next` (the region of the cast
-// before it, zero_words words) at its start for the cast after it.
+// after it, zero_words words) at its start.  Direct casts rotate through three
+// regions, so that with overlapped casts the region being cleared was last
+// used by a cast that has completed.
 struct CounterRegion {
     unsigned* base;
     bool clean;
     unsigned* zero_next;
     int64_t zero_words;
+    bool overlap;   // launch with programmatic dependent launch (consecutive direct casts overlap)
+    cudaError_t* overlap_refused;  // nullable: the launch's answer when it refused the overlapped launch
 };
 // bytes of a CounterRegion a cast of n_total dense beams uses
 size_t cast_counter_bytes(int64_t n_total, bool compact);
@@ -188,7 +192,8 @@ cudaError_t launch_cast(cudaStream_t s, const SceneDev& scene, const SensorDev* 
 size_t fused_compact_scratch_bytes(int64_t n_beams_total);
 cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const FrameDev* frames_dev, int n_frames,
                            int64_t n_beams_total, BeamsOut dense, const lidar_points& pts, void* compact_scratch,
-                           int* status, const InlineFrames* inline_frames = nullptr);
+                           int* status, const InlineFrames* inline_frames = nullptr, int num_sms = 0,
+                           bool pdl = false);
 cudaError_t launch_popcount(cudaStream_t s, const uint32_t* bits, int64_t n_words, unsigned long long* total);
 // frames[i].pose = poses[12 i .. 12 i + 11]
 cudaError_t launch_set_poses(cudaStream_t s, FrameDev* frames, int n_frames, const float* poses);

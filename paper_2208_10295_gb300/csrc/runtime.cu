@@ -132,12 +132,16 @@ struct lidar_ctx {
     size_t sweeps_cap = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
-    // two counter regions of direct casts, used alternately: a cast clears
-    // the other one, so the next needs no memset (cnt_clean)
+    // three counter regions of direct casts, used in turn: a cast clears the
+    // next one, so the next cast needs no memset (cnt_clean); with overlapped
+    // casts the region a cast clears was last used by a completed cast
     unsigned* cnt_dev = nullptr;
     int64_t cnt_words = 0;  // per region
-    bool cnt_clean[2] = {false, false};
+    bool cnt_clean[3] = {false, false, false};
     int cnt_cur = 0;
+    int overlap = 1;         // consecutive direct casts may overlap (programmatic dependent launch)
+    int dense_cur = 0;       // which half of the scratch the next direct cast's dense records use
+    std::vector<std::pair<uintptr_t, uintptr_t>> last_out;  // output byte ranges of the last direct cast
     LaunchCfg cfg{128, 4, 32, 1, 2, 1};
     int build_method = 1;     // 0 Karras LBVH, 1 PLOC clustering (fewer node fetches per ray)
     int ploc_radius = 16;
@@ -728,19 +732,20 @@ static lidar_status counter_region(lidar_ctx* c, int64_t n_total, bool compact, 
         c->cnt_dev = nullptr;
         c->cnt_words = 0;
         const int64_t words = (std::max<int64_t>(need, 256) + 63) / 64 * 64;
-        if (dev_alloc((void**)&c->cnt_dev, (size_t)(2 * words) * sizeof(unsigned)) != cudaSuccess) {
+        if (dev_alloc((void**)&c->cnt_dev, (size_t)(3 * words) * sizeof(unsigned)) != cudaSuccess) {
             cudaGetLastError();
             set_error("cast: device allocation failed (counters)");
             return LIDAR_ENOMEM;
         }
         c->cnt_words = words;
-        c->cnt_clean[0] = c->cnt_clean[1] = false;
+        c->cnt_clean[0] = c->cnt_clean[1] = c->cnt_clean[2] = false;
     }
-    const int r = c->cnt_cur ^ 1;
+    const int r = (c->cnt_cur + 1) % 3;
     R->base = c->cnt_dev + (int64_t)r * c->cnt_words;
     R->clean = c->cnt_clean[r];
-    R->zero_next = c->cnt_dev + (int64_t)(r ^ 1) * c->cnt_words;
+    R->zero_next = c->cnt_dev + (int64_t)((r + 1) % 3) * c->cnt_words;
     R->zero_words = c->cnt_words;
+    R->overlap = c->overlap != 0;
     return LIDAR_OK;
 }
 
@@ -753,6 +758,15 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
     lidar_status tst = traversal_available(c, scene, "cast");
     if (tst != LIDAR_OK) return tst;
     BeamsOut out = to_beams_out(beams);
+    // a direct cast outside a stream capture counts in its own counter region
+    // and may overlap the direct cast before it
+    bool use_region = false;
+    if (direct) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        LIDAR_CUDA(cudaStreamIsCapturing(c->stream, &cs));
+        use_region = cs == cudaStreamCaptureStatusNone;
+    }
+    const bool overlapped = use_region && c->overlap != 0;
     // compaction reads the dense records: provide the ones the points need
     char* dense_base = nullptr;
     size_t dense_bytes = 0;
@@ -765,15 +779,24 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
                       (need_int ? al(4 * n_total) : 0) + (need_norm ? al(12 * n_total) : 0) +
                       (need_mat ? al(2 * n_total) : 0) + (need_inst ? al(4 * n_total) : 0);
         const size_t need = dense_bytes + fused_compact_scratch_bytes(n_total);
-        if (c->scratch_bytes < need) {
+        // overlapped casts use the two halves of the scratch in turn, so a cast
+        // does not overwrite the records the cast before it still compacts
+        const size_t half = (need + 255) / 256 * 256;
+        const size_t total = overlapped ? 2 * half : need;
+        if (c->scratch_bytes < total) {
             if (!may_alloc) {
                 set_error("cast: scratch too small for this batch (recreate the batch)");
                 return LIDAR_ESTATE;
             }
-            lidar_status st = ensure_scratch(c, need);
+            lidar_status st = ensure_scratch(c, total);
             if (st != LIDAR_OK) return st;
         }
         char* p = (char*)c->scratch;
+        if (overlapped) {
+            // the halves split the scratch at a fixed point, whatever each cast needs
+            p += (size_t)c->dense_cur * (c->scratch_bytes / 2 / 256 * 256);
+            c->dense_cur ^= 1;
+        }
         dense_base = p;
         if (need_valid) { out.valid = (uint8_t*)p; p += al(n_total); }
         if (need_range) { out.range = (float*)p; p += al(4 * n_total); }
@@ -786,31 +809,55 @@ static lidar_status cast_impl(lidar_ctx* c, const lidar_scene* scene, const Fram
     char* comp = points ? dense_base + dense_bytes : nullptr;
     bool scattered = false;
     CounterRegion R{};
-    bool use_region = false;
-    if (direct) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        LIDAR_CUDA(cudaStreamIsCapturing(c->stream, &cs));
-        if (cs == cudaStreamCaptureStatusNone) {
-            lidar_status rs = counter_region(c, n_total, points != nullptr, &R);
-            if (rs != LIDAR_OK) return rs;
-            use_region = true;
+    if (use_region) {
+        lidar_status rs = counter_region(c, n_total, points != nullptr, &R);
+        if (rs != LIDAR_OK) return rs;
+        // overlap the previous direct cast only when no output of this cast
+        // shares memory with one of its outputs (else plain stream order)
+        std::vector<std::pair<uintptr_t, uintptr_t>> mine;
+        auto add = [&](const void* p, size_t bytes) {
+            if (p && bytes) mine.emplace_back((uintptr_t)p, (uintptr_t)p + bytes);
+        };
+        if (beams) {
+            const size_t n = (size_t)n_total;
+            add(beams->valid, n); add(beams->tri, 4 * n); add(beams->t, 4 * n); add(beams->range, 4 * n);
+            add(beams->intensity, 4 * n); add(beams->normal, 12 * n); add(beams->mat, 2 * n); add(beams->inst, 4 * n);
+            add(beams->sub, n); add(beams->theta_deg, 4 * n); add(beams->rf, 4 * n);
         }
+        if (points) {
+            const size_t m = (size_t)points->capacity;
+            add(points->xyz, 12 * m); add(points->range, 4 * m); add(points->intensity, 4 * m);
+            add(points->normal, 12 * m); add(points->material, 2 * m); add(points->instance, 4 * m);
+            add(points->beam, 4 * m); add(points->frame, 4 * m);
+        }
+        add(n_points_dev, sizeof(int64_t));
+        bool shared = false;
+        for (const auto& a : mine)
+            for (const auto& b : c->last_out)
+                if (a.first < b.second && b.first < a.second) shared = true;
+        R.overlap = R.overlap && !shared;
+        c->last_out.swap(mine);
     }
+    cudaError_t refused = cudaSuccess;
+    R.overlap_refused = &refused;
     const cudaError_t le = launch_cast(c->stream, S, c->sensors_dev, frames_dev, n_frames, prefix_dev, n_tiles,
                                        c->table, seed, out, c->status_dev, c->work_counter, c->cfg, c->num_sms,
                                        n_total, nullptr, comp, n_points_dev, points, &scattered, inl,
                                        use_region ? &R : nullptr);
+    if (refused != cudaSuccess)
+        log_info(std::string("cast: overlapped launch refused (") + cudaGetErrorString(refused) +
+                 "), launched after the previous cast instead");
     if (use_region) {
-        // this cast dirtied its region and clears the other one
-        const int r = c->cnt_cur ^ 1;
+        // this cast dirtied its region and clears the next one
+        const int r = (c->cnt_cur + 1) % 3;
         c->cnt_clean[r] = false;
-        c->cnt_clean[r ^ 1] = le == cudaSuccess;
+        c->cnt_clean[(r + 1) % 3] = le == cudaSuccess;
         c->cnt_cur = r;
     }
     LIDAR_CUDA(le);
     if (points && !scattered)
         LIDAR_CUDA(launch_scatter(c->stream, c->sensors_dev, frames_dev, n_frames, n_total, out, *points, comp,
-                                  c->status_dev, inl));
+                                  c->status_dev, inl, c->num_sms, use_region && R.overlap && refused == cudaSuccess));
     return LIDAR_OK;
 }
 
@@ -1573,6 +1620,21 @@ lidar_status lidar_measure_fp32_rate(lidar_ctx* c, int64_t fma_per_thread, doubl
     int form = 0;
     LIDAR_CUDA(measure_fp32_rate(c->stream, c->num_sms, fma_per_thread, c->scratch, flops_per_s, kernel_ms, &form));
     *packed = form;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_set_cast_overlap(lidar_ctx* c, int32_t enable)
+{
+    LIDAR_CHECK_ARG(c != nullptr, "lidar_set_cast_overlap: NULL context");
+    LIDAR_CHECK_ARG(enable == 0 || enable == 1, "lidar_set_cast_overlap: enable is 0 or 1");
+    c->overlap = enable;
+    return LIDAR_OK;
+}
+
+lidar_status lidar_get_cast_overlap(lidar_ctx* c, int32_t* enable)
+{
+    LIDAR_CHECK_ARG(c != nullptr && enable != nullptr, "lidar_get_cast_overlap: NULL argument");
+    *enable = c->overlap;
     return LIDAR_OK;
 }
 

@@ -354,6 +354,15 @@ class Lidar:
                                           ctypes.byref(pk)), "lidar_measure_fp32_rate")
         return {"flops_per_s": r.value, "kernel_ms": t.value, "packed": bool(pk.value)}
 
+    def cast_overlap(self) -> bool:
+        v = ctypes.c_int32()
+        C.check(C.lidar_get_cast_overlap(self.handle, ctypes.byref(v)), "lidar_get_cast_overlap")
+        return bool(v.value)
+
+    def set_cast_overlap(self, enable: bool):
+        """Consecutive direct casts may overlap (bit-identical results either way)."""
+        C.check(C.lidar_set_cast_overlap(self.handle, int(bool(enable))), "lidar_set_cast_overlap")
+
     def set_wait_limit(self, ns: int):
         C.check(C.lidar_set_wait_limit(self.handle, int(ns)), "lidar_set_wait_limit")
 

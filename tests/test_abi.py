@@ -114,3 +114,10 @@ def test_autograd_function_rejects_frames_of_other_slots():
     g = torch.tensor(1.0, requires_grad=True)
     with pytest.raises(ValueError, match="slot 0"):
         LidarCast.apply(p, g, None, None, fr, w.seed, 0)
+
+
+def test_cast_overlap_argument_checks(libpath):
+    from paper_2208_10295_gb300 import capi
+    capi.load(libpath)
+    assert capi.lidar_set_cast_overlap(None, 1) == capi.LIDAR_EINVAL
+    assert capi.lidar_get_cast_overlap(None, None) == capi.LIDAR_EINVAL

@@ -684,3 +684,64 @@ def test_points_download(L):
             L.download_points(pts, host, bad)
         assert e.value.status == capi.LIDAR_EINVAL
     scene.free()
+
+
+def _points_np(p):
+    c = int(p["count"].item())
+    return c, {k: v[:c].cpu().numpy() for k, v in p.items() if k != "count"}
+
+
+def test_overlapped_direct_casts_match_serial(L):
+    """Consecutive direct casts whose outputs share no memory may overlap (the
+    next cast starts on the SMs the previous one's last traversals leave idle).
+    Six casts of three frames in rotation into three sets of buffers, with no
+    synchronisation between them (one of the repeat casts writes no dense
+    records), give bit for bit what casts one after the other give; so do
+    back-to-back casts of different frames into the same buffers (those the
+    library orders one after the other)."""
+    w = synth.small_terrain(seed=23, n_frames=3, n_az=512)
+    scene, _ = setup(L, w)
+    nb = w.sensors[0].n_beams
+    frames = [w.frames[k:k + 1] for k in range(3)]
+    fields = ("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst")
+    assert L.cast_overlap()
+    try:
+        L.set_cast_overlap(False)
+        ref = []
+        for k in range(3):
+            d, p = L.alloc_beams(nb, fields), L.alloc_points(nb)
+            L.cast_into(scene, frames[k], w.seed, d, p)
+            assert L.sync_status() == 0
+            ref.append((to_numpy(d), _points_np(p)))
+        L.set_cast_overlap(True)
+        bufs = [(L.alloc_beams(nb, fields), L.alloc_points(nb)) for _ in range(3)]
+        for i in range(6):
+            d, p = bufs[i % 3]
+            L.cast_into(scene, frames[i % 3], w.seed, d if i % 3 != 1 or i < 3 else None, p)
+        torch.cuda.synchronize()
+        assert L.sync_status() == 0
+        for k in range(3):
+            d, p = bufs[k]
+            gd = to_numpy(d)
+            for f in fields:
+                assert np.array_equal(gd[f].view(np.uint8), ref[k][0][f].view(np.uint8)), (k, f)
+            c, pts = _points_np(p)
+            assert c == ref[k][1][0], k
+            for f in pts:
+                assert np.array_equal(pts[f].view(np.uint8), ref[k][1][1][f].view(np.uint8)), (k, f)
+        # the same buffers for every cast: each cast follows the one before it
+        d, p = bufs[0]
+        for k in (1, 2, 0, 2):
+            L.cast_into(scene, frames[k], w.seed, d, p)
+        torch.cuda.synchronize()
+        assert L.sync_status() == 0
+        gd = to_numpy(d)
+        for f in fields:
+            assert np.array_equal(gd[f].view(np.uint8), ref[2][0][f].view(np.uint8)), f
+        c, pts = _points_np(p)
+        assert c == ref[2][1][0]
+        for f in pts:
+            assert np.array_equal(pts[f].view(np.uint8), ref[2][1][1][f].view(np.uint8)), f
+    finally:
+        L.set_cast_overlap(True)
+        scene.free()
