@@ -314,7 +314,13 @@ void lidar_graph_free(lidar_graph* graph);
  * with i = min(floor(theta), 89), f = theta - i, R the interpolated table
  * value and g = gain.  grad_table_dev [M][91] and grad_gain_dev [1] are
  * accumulated into (not overwritten).  Accumulation uses 64-bit fixed point,
- * so the result is bit-reproducible run to run. */
+ * so the result is bit-reproducible run to run.  The tape is read once by one
+ * cooperative kernel whose device-side waits are bounded by the context's
+ * wait limit (LIDAR_ETIMEOUT in the status word if one runs out); tables of
+ * more than about 130 materials, and devices without cooperative launch, take
+ * three kernels (two reads of the tape) instead.  Tape arrays that start on
+ * a 16-byte boundary are streamed by the copy engine; others are read by the
+ * threads, with the same result. */
 lidar_status lidar_cast_backward(lidar_ctx* ctx, int64_t n_beams, const lidar_beams* tape, float gain,
                                  const float* grad_I_dev, float* grad_table_dev, float* grad_gain_dev);
 

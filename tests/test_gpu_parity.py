@@ -123,9 +123,9 @@ def test_cfg1_full_frame_every_beam(L):
 def test_cfg2_batched_sampled(L):
     w = synth.cfg2()
     gpu, _ = gpu_cast(L, w, fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst"))
-    samples = stratified_sample(w, 1024, seed=2)
+    samples = stratified_sample(w, 4096, seed=2)
     ref = oracle_cast(w, samples)
-    _report(compare(pick(gpu, w, samples), ref, label="cfg2 8 sensors x 64 frames, 1024 sampled beams"))
+    _report(compare(pick(gpu, w, samples), ref, label="cfg2 8 sensors x 64 frames, 4096 sampled beams"))
 
 
 @pytest.mark.parametrize("n_subrays", [1, 7, 3])
