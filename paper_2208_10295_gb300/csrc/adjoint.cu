@@ -356,6 +356,7 @@ constexpr int kOneStages = 2;
 constexpr int kOneBlocksPerSm = 2;
 constexpr int kOneStageBytes = kOneChunk * 16;      // valid 1, target valid 1, mat 2, theta 4, rf 4, g 4
 constexpr int kOneWarps = kOneThreads / 32;
+constexpr int kOneMaxGrid = 1024;  // blocks of one launch (two per SM on up to 512 SMs)
 
 struct OneArgs {
     int64_t n;
@@ -369,7 +370,7 @@ struct OneArgs {
     float gain;
     int mse;
     int n_acc;                  // table entries + the gain
-    long long* rows;            // [grid][n_acc] each block's sums at the common scale
+    long long* rows;            // [grid][n_acc] each block's sums at its own scale
     float* blk_max;             // [grid] per block: largest contribution
     int* blk_sh;                // [grid] its fixed-point shift
     double* blk_loss;           // [grid] sum of squared residuals
@@ -413,10 +414,10 @@ __device__ __forceinline__ long long fixed_of(float x, float scale)
     return ((long long)__float2int_rn(q) << 31) + (long long)__float2int_rn(r);
 }
 
-// v / 2^d rounded to nearest (ties up), d >= 0
+// v / 2^d rounded to nearest (ties up), d >= 0 (d <= 0 returns v unchanged)
 __device__ __forceinline__ long long round_shift(long long v, int d)
 {
-    if (d == 0) return v;
+    if (d <= 0) return v;
     if (d > 62) return 0;
     return (v + (1ll << (d - 1))) >> d;
 }
@@ -538,6 +539,7 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
     __shared__ unsigned long long s_cnt[kOneWarps];
     __shared__ int s_flag;
     __shared__ float s_gmax;
+    __shared__ int s_sh[kOneMaxGrid];  // every block's fixed-point shift
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, blk = blockIdx.x;
@@ -792,22 +794,28 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
         for (int o = 16; o > 0; o >>= 1) gq += __shfl_xor_sync(0xffffffffu, gq, o);
         if (lane == 0 && gq) acc.add(a.n_acc - 1, gq);
     }
-    __syncthreads();
+    // this block's sums at its own scale, one dense row, with its maximum and shift
+    {
+        long long* row = a.rows + (int64_t)blk * a.n_acc;
+        for (int j = tid; j < a.n_acc; j += kOneThreads) row[j] = failed ? 0ll : acc.get(j);
+    }
     if (tid == 0) {
         a.blk_max[blk] = failed ? 0.0f : blk_max;
         a.blk_sh[blk] = sh;
     }
-    // ---- grid-wide wait 1: every block's maximum, count and loss partial are out
+    // ---- the grid-wide wait: every block's row, maximum, shift, count and loss partial are out
     grid_arrive(a.ctl);
     if (!grid_wait_for(a.ctl, (unsigned)G, a.status, a.wait_ns, &s_flag)) failed = true;
     // the common scale (the largest contribution of the whole tape) and the
-    // number of beams used, reduced in a fixed order by every block
+    // number of beams used, reduced in a fixed order by every block; every
+    // block's shift into shared memory
     {
         float gm = 0.0f;
         unsigned long long N = 0;
         for (int j = tid; j < G; j += kOneThreads) {
             gm = fmaxf(gm, __ldcg(&a.blk_max[j]));
             N += __ldcg(&a.blk_n[j]);
+            s_sh[j] = __ldcg(&a.blk_sh[j]);
         }
         for (int o = 16; o > 0; o >>= 1) {
             gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
@@ -833,33 +841,20 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
     const float gmax = s_gmax;
     const unsigned long long N = s_cnt[0];
     const int S = one_shift(gmax, n);
-    // this block's sums at the common scale, one dense row
-    {
-        long long* row = a.rows + (int64_t)blk * a.n_acc;
-        const int dd = sh - S;
-        for (int j = tid; j < a.n_acc; j += kOneThreads)
-            row[j] = (failed || blk_max <= 0.0f) ? 0ll : round_shift(acc.get(j), dd);
-    }
-    // ---- grid-wide wait 2: every row is out
-    grid_arrive(a.ctl);
-    // block 0 writes the loss (the partials in block order, a fixed tree)
-    // between its arrival and its wait
-    if (blk == 0 && a.loss) {
+    // block 0's first warp writes the loss: the partials in a fixed order (lane
+    // l takes blocks l, l + 32, ..., then a fixed shuffle tree)
+    if (blk == 0 && warp == 0 && a.loss) {
         double t = 0.0;
-        for (int j = tid; j < G; j += kOneThreads) t += __ldcg(&a.blk_loss[j]);
-        s_red[tid] = t;
-        __syncthreads();
-        for (int w = kOneThreads / 2; w > 0; w >>= 1) {
-            if (tid < w) s_red[tid] += s_red[tid + w];
-            __syncthreads();
-        }
-        if (tid == 0) *a.loss = a.mse ? (float)(N ? s_red[0] / (double)N : 0.0) : 0.0f;
+        for (int j = lane; j < G; j += 32) t += __ldcg(&a.blk_loss[j]);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) *a.loss = a.mse ? (float)(N ? t / (double)N : 0.0) : 0.0f;
     }
-    if (!grid_wait_for(a.ctl, 2u * (unsigned)G, a.status, a.wait_ns, &s_flag)) failed = true;
-    // each block sums the rows over its slice of the entries and writes those
-    // gradients: warp w reads rows w, w + kOneWarps, ..., lane l entry j0 + l of
-    // each (contiguous: one row's slice per warp load), then the warps' sums
-    // meet in shared memory (integer sums: the order is free)
+    // each block sums the rows over its slice of the entries, each row shifted
+    // from its block's scale to the common one (a rounding shift, as the block
+    // would have made), and writes those gradients: warp w reads rows w,
+    // w + kOneWarps, ..., lane l entry j0 + l of each (contiguous: one row's
+    // slice per warp load), then the warps' sums meet in shared memory
+    // (integer sums: the order is free)
     if (!failed && gmax > 0.0f) {
         const int j0 = (int)((int64_t)blk * a.n_acc / G), j1 = (int)(((int64_t)blk + 1) * a.n_acc / G);
         const float inv_scale = ldexpf(1.0f, -S);  // exact: a power of two
@@ -878,7 +873,10 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
                         v[u] = r < G ? __ldcg(&a.rows[(int64_t)r * a.n_acc + j]) : 0ll;
                     }
 #pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) t += v[u];
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int r = r0 + u * kOneWarps;
+                        if (r < G) t += round_shift(v[u], s_sh[r] - S);
+                    }
                 }
             }
             s_part[warp * 32 + lane] = t;
@@ -1090,6 +1088,7 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
     // about a chunk per block at least; a block's share is whole 16-beam groups
     const int64_t n_chunks = (n + kOneChunk - 1) / kOneChunk;
     int G = (int)std::min<int64_t>(std::max<int64_t>(n_chunks, 1), (int64_t)bps * num_sms);
+    if (G > kOneMaxGrid) G = kOneMaxGrid;
     char* p = (char*)scratch;
     OneArgs a{};
     a.n = n;
