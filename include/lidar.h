@@ -127,6 +127,11 @@ lidar_status lidar_get_scene_info(const lidar_scene* scene, lidar_scene_info* ou
 typedef struct {
     int32_t method;        /* 0 LBVH, 1 PLOC (default: about a third fewer node fetches per ray) */
     int32_t ploc_radius;   /* 1..64, default 16 */
+    int32_t collapse;      /* children of the wide nodes: 0 (default) each node opens its largest-area
+                              child until it is full; 1 the surface-area-heuristic optimum over the
+                              binary tree (a bottom-up dynamic program, Ylitie, Karras and Laine 2017) */
+    float tri_cost;        /* collapse 1: a triangle test's cost relative to a wide-node visit, (0, 100],
+                              default 1 */
 } lidar_build_options;
 
 lidar_status lidar_set_build_options(lidar_ctx* ctx, const lidar_build_options* options);

@@ -624,15 +624,150 @@ __device__ int gather_children(const float4* __restrict__ bn, int b, ChildBox ch
     return internal;
 }
 
+// ---- SAH-optimal choice of a wide node's children (a dynamic program over the
+// binary tree, in the manner of Ylitie, Karras and Laine, HPG 2017).  Expected
+// cost of a tree: c_node x SA(N) summed over its wide nodes N plus c_tri x
+// SA(t) over its triangle children t (surface areas relative to the root's).
+// For binary node n and a budget of i child slots (i = 1..W):
+//   D(n, i) = min over j of C(left, j) + C(right, i - j)   (n spread over i slots)
+//   C(n, 1) = c_node SA(n) + D(n, W)                        (n one slot: a wide node)
+//   C(n, i) = min(C(n, 1), D(n, i)),  i >= 2
+// with C(t, i) = c_tri SA(t) for a triangle.  Per node the argmin split of
+// D(n, i) and whether C(n, 1) won are kept; a wide node at n takes the slots
+// D(n, W)'s split gives its two children, expanded while they win.
+struct CollapseDP {
+    const int* parent_node;   // [n_binary] parent of each internal node (-1: root)
+    const int* parent_leaf;   // [n_leaves] parent of each triangle
+    float* cost;              // [n_binary][W] C(n, i)
+    uint8_t* split;           // [n_binary][W] argmin j of D(n, i) (i >= 2)
+    uint16_t* single;         // [n_binary] bit i: C(n, 1) <= D(n, i)
+    unsigned* visits;         // [n_binary] children finished, bottom-up
+    float c_node, c_tri;
+};
+
+__global__ void k_parents(const float4* __restrict__ bn, int n_binary, int* parent_node, int* parent_leaf)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_binary) return;
+    const float4 n3 = bn[4 * (int64_t)n + 3];
+    const int c[2] = {__float_as_int(n3.x), __float_as_int(n3.y)};
+    for (int k = 0; k < 2; ++k) {
+        if (c[k] >= 0) parent_node[c[k]] = n;
+        else parent_leaf[~c[k]] = n;
+    }
+}
+
+// one thread per triangle climbs towards the root; the second child to finish
+// computes its parent's table, so every node is computed once, after both
+// children
+template <int W>
+__global__ void k_collapse_dp(const float4* __restrict__ bn, int n_leaves, CollapseDP dp)
+{
+    const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+    if (leaf >= n_leaves) return;
+    int node = dp.parent_leaf[leaf];
+    while (node >= 0) {
+        __threadfence();
+        if (atomicAdd(&dp.visits[node], 1u) == 0u) return;  // the other child is still running
+        __threadfence();
+        ChildBox cb[2];
+        float cc[2][W];
+        for (int side = 0; side < 2; ++side) {
+            binary_child(bn, node, side, cb[side]);
+            if (cb[side].ref < 0) {
+                const float v = dp.c_tri * half_area(cb[side]);
+                for (int i = 0; i < W; ++i) cc[side][i] = v;
+            } else {
+                for (int i = 0; i < W; ++i) cc[side][i] = __ldcg(&dp.cost[(int64_t)cb[side].ref * W + i]);
+            }
+        }
+        ChildBox u;
+        for (int a = 0; a < 3; ++a) {
+            u.lo[a] = fminf(cb[0].lo[a], cb[1].lo[a]);
+            u.hi[a] = fmaxf(cb[0].hi[a], cb[1].hi[a]);
+        }
+        float D[W + 1];
+        int J[W + 1];
+        for (int i = 2; i <= W; ++i) {
+            D[i] = INFINITY;
+            J[i] = 1;
+            for (int j = 1; j < i; ++j) {
+                const float v = cc[0][j - 1] + cc[1][i - j - 1];
+                if (v < D[i]) {
+                    D[i] = v;
+                    J[i] = j;
+                }
+            }
+        }
+        const float c1 = dp.c_node * half_area(u) + D[W];
+        unsigned mask = 0;
+        float* out = dp.cost + (int64_t)node * W;
+        uint8_t* sp = dp.split + (int64_t)node * W;
+        out[0] = c1;
+        sp[0] = 0;
+        for (int i = 2; i <= W; ++i) {
+            if (c1 <= D[i]) {
+                out[i - 1] = c1;
+                mask |= 1u << i;
+            } else {
+                out[i - 1] = D[i];
+            }
+            sp[i - 1] = (uint8_t)J[i];
+        }
+        dp.single[node] = (uint16_t)mask;
+        node = dp.parent_node[node];
+    }
+}
+
+// children of binary node b chosen by the dynamic program; returns the number
+// of internal ones
+template <int W>
+__device__ int gather_children_dp(const float4* __restrict__ bn, int b, const CollapseDP& dp, ChildBox ch[W],
+                                  int& count)
+{
+    int budget[W];
+    binary_child(bn, b, 0, ch[0]);
+    binary_child(bn, b, 1, ch[1]);
+    const int j = dp.split[(int64_t)b * W + W - 1];
+    budget[0] = j;
+    budget[1] = W - j;
+    count = 2;
+    for (bool more = true; more;) {
+        more = false;
+        for (int k = 0; k < count; ++k) {
+            const int x = ch[k].ref, i = budget[k];
+            if (x < 0 || i < 2 || ((dp.single[x] >> i) & 1u)) continue;
+            const int jx = dp.split[(int64_t)x * W + i - 1];
+            binary_child(bn, x, 0, ch[k]);
+            binary_child(bn, x, 1, ch[count]);
+            budget[k] = jx;
+            budget[count] = i - jx;
+            ++count;
+            more = true;
+            break;
+        }
+    }
+    int internal = 0;
+    for (int k = 0; k < count; ++k) internal += ch[k].ref >= 0;
+    return internal;
+}
+
+template <int W>
+__device__ __forceinline__ int gather(const float4* __restrict__ bn, int b, const CollapseDP* dp, ChildBox ch[W],
+                                      int& count)
+{
+    return dp ? gather_children_dp<W>(bn, b, *dp, ch, count) : gather_children<W>(bn, b, ch, count);
+}
+
 template <int W>
 __global__ void k_collapse_count(const float4* __restrict__ bn, const int* __restrict__ frontier, int n,
-                                 uint32_t* __restrict__ n_internal)
+                                 uint32_t* __restrict__ n_internal, const CollapseDP dp, int use_dp)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     ChildBox ch[W];
     int count;
-    n_internal[i] = (uint32_t)gather_children<W>(bn, frontier[i], ch, count);
+    n_internal[i] = (uint32_t)gather<W>(bn, frontier[i], use_dp ? &dp : nullptr, ch, count);
 }
 
 __global__ void __launch_bounds__(1024) k_collapse_scan(uint32_t* __restrict__ v, int n, uint32_t* total)
@@ -666,14 +801,15 @@ template <int W>
 __global__ void k_collapse_write(const float4* __restrict__ bn, const int* __restrict__ frontier,
                                  const int* __restrict__ pushes_in, int n, const uint32_t* __restrict__ offset,
                                  int slot_base, int next_base, float4* __restrict__ nodes,
-                                 int* __restrict__ next_frontier, int* __restrict__ pushes_out, int* stack_need)
+                                 int* __restrict__ next_frontier, int* __restrict__ pushes_out, int* stack_need,
+                                 const CollapseDP dp, int use_dp)
 {
     constexpr int G = W / 4;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     ChildBox ch[W];
     int count;
-    const int internal = gather_children<W>(bn, frontier[i], ch, count);
+    const int internal = gather<W>(bn, frontier[i], use_dp ? &dp : nullptr, ch, count);
     const int below = pushes_in[i] + (internal > 0 ? internal - 1 : 0);
     atomicMax(stack_need, below);
     {
@@ -729,11 +865,16 @@ size_t collapse_scratch_bytes(int64_t n_binary)
 {
     const int64_t m = n_binary > 0 ? n_binary : 1;
     const size_t arr = ((m * sizeof(int) + 255) / 256) * 256;
-    return 5 * arr + 256;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    // frontier and push arrays, counts, total; then the dynamic program's
+    // parents (nodes, triangles), costs and splits for up to 8 slots, flags, visits
+    return 5 * arr + 256 + arr + al((m + 1) * sizeof(int)) + al(m * 8 * sizeof(float)) + al(m * 8) +
+           al(m * sizeof(uint16_t)) + arr;
 }
 
 cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, int64_t n_binary, float4* nodes,
-                         int64_t* n_wide, int* levels, int* stack_need, void* scratch, size_t scratch_bytes)
+                         int64_t* n_wide, int* levels, int* stack_need, void* scratch, size_t scratch_bytes,
+                         int sah_dp, float tri_cost)
 {
     *n_wide = 0;
     *levels = 0;
@@ -749,6 +890,39 @@ cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, 
     uint32_t* counts = (uint32_t*)((char*)scratch + 4 * arr);
     uint32_t* total = (uint32_t*)((char*)scratch + 5 * arr);
     int* need = (int*)(total + 1);
+    CollapseDP dp{};
+    if (sah_dp && n_binary < 2) sah_dp = 0;  // a single triangle: nothing to choose
+    if (sah_dp) {
+        auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+        char* q = (char*)scratch + 5 * arr + 256;
+        int* parent_node = (int*)q;
+        q += arr;
+        int* parent_leaf = (int*)q;
+        q += al((n_binary + 1) * sizeof(int));
+        dp.cost = (float*)q;
+        q += al(n_binary * 8 * sizeof(float));
+        dp.split = (uint8_t*)q;
+        q += al(n_binary * 8);
+        dp.single = (uint16_t*)q;
+        q += al(n_binary * sizeof(uint16_t));
+        dp.visits = (unsigned*)q;
+        dp.parent_node = parent_node;
+        dp.parent_leaf = parent_leaf;
+        dp.c_node = 1.0f;
+        dp.c_tri = tri_cost;
+        cudaError_t e0 = cudaMemsetAsync(parent_node, 0xFF, (size_t)n_binary * sizeof(int), s);
+        if (e0 == cudaSuccess) e0 = cudaMemsetAsync(dp.visits, 0, (size_t)n_binary * sizeof(unsigned), s);
+        if (e0 != cudaSuccess) return e0;
+        const int nb = (int)n_binary;
+        k_parents<<<(nb + 255) / 256, 256, 0, s>>>(binary_nodes, nb, parent_node, parent_leaf);
+        if (width == 4)
+            k_collapse_dp<4><<<(nb + 1 + 255) / 256, 256, 0, s>>>(binary_nodes, nb + 1, dp);
+        else
+            k_collapse_dp<8><<<(nb + 1 + 255) / 256, 256, 0, s>>>(binary_nodes, nb + 1, dp);
+        e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
+    const int use_dp = sah_dp ? 1 : 0;
     const int init[2] = {0, 0};  // root, no pushes above it
     cudaError_t e = cudaMemcpyAsync(fa, &init[0], sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pa, &init[1], sizeof(int), cudaMemcpyHostToDevice, s);
@@ -763,15 +937,15 @@ cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, 
     while (n > 0) {
         const int blocks = (n + 255) / 256;
         if (width == 4) {
-            k_collapse_count<4><<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts);
+            k_collapse_count<4><<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts, dp, use_dp);
             k_collapse_scan<<<1, 1024, 0, s>>>(counts, n, total);
             k_collapse_write<4><<<blocks, 256, 0, s>>>(binary_nodes, cur, pcur, n, counts, slot_base,
-                                                      (int)allocated, nodes, nxt, pnxt, need);
+                                                      (int)allocated, nodes, nxt, pnxt, need, dp, use_dp);
         } else {
-            k_collapse_count<8><<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts);
+            k_collapse_count<8><<<blocks, 256, 0, s>>>(binary_nodes, cur, n, counts, dp, use_dp);
             k_collapse_scan<<<1, 1024, 0, s>>>(counts, n, total);
             k_collapse_write<8><<<blocks, 256, 0, s>>>(binary_nodes, cur, pcur, n, counts, slot_base,
-                                                      (int)allocated, nodes, nxt, pnxt, need);
+                                                      (int)allocated, nodes, nxt, pnxt, need, dp, use_dp);
         }
         uint32_t next_n = 0;
         e = cudaMemcpyAsync(&next_n, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);

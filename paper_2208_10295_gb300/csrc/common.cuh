@@ -157,8 +157,11 @@ size_t build_scratch_bytes(int64_t n_tris);
 // deterministic); synchronises once per level.  `nodes` may be NULL to count
 // only.  *n_wide = wide nodes, *levels = height of the wide tree, *stack_need =
 // deepest traversal stack the tree can require.
+// sah_dp: children chosen by the SAH dynamic program (triangle test cost
+// tri_cost relative to a wide-node visit) instead of opening the largest child
 cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, int64_t n_binary, float4* nodes,
-                         int64_t* n_wide, int* levels, int* stack_need, void* scratch, size_t scratch_bytes);
+                         int64_t* n_wide, int* levels, int* stack_need, void* scratch, size_t scratch_bytes,
+                         int sah_dp = 0, float tri_cost = 1.0f);
 size_t collapse_scratch_bytes(int64_t n_binary);
 
 // sort.cu: stable LSD radix sort of (key, value) pairs, keys of `key_bits` bits

@@ -145,6 +145,8 @@ struct lidar_ctx {
     LaunchCfg cfg{128, 4, 32, 1, 2, 1};
     int build_method = 1;     // 0 Karras LBVH, 1 PLOC clustering (fewer node fetches per ray)
     int ploc_radius = 16;
+    int collapse = 0;         // wide nodes: 0 open the largest child, 1 SAH dynamic program
+    float tri_cost = 1.0f;    // a triangle test's cost relative to a wide-node visit (collapse 1)
     std::set<lidar_scene*> scenes;
 };
 
@@ -393,7 +395,7 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         cudaEventRecord(e0, c->stream);
         int need4 = 0;
         cudaError_t e4 = collapse_bvh(c->stream, 4, s->nodes, s->n_nodes, s->nodes4, &s->n_nodes4, &s->levels4,
-                                      &need4, c->scratch, c->scratch_bytes);
+                                      &need4, c->scratch, c->scratch_bytes, c->collapse, c->tri_cost);
         // the 8-wide tree: count its nodes and the stack it could need, then
         // write it into an exact allocation; a tree that could need more than
         // the traversal stack is not kept (the 4-wide and binary ones serve)
@@ -401,7 +403,7 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         int levels8 = 0, need8 = 0;
         if (e4 == cudaSuccess)
             e4 = collapse_bvh(c->stream, 8, s->nodes, s->n_nodes, nullptr, &n8, &levels8, &need8, c->scratch,
-                              c->scratch_bytes);
+                              c->scratch_bytes, c->collapse, c->tri_cost);
         if (e4 == cudaSuccess && need8 <= kTraversalStack && n8 > 0) {
             if (dev_alloc((void**)&s->nodes8, (size_t)n8 * 16 * sizeof(float4)) != cudaSuccess) {
                 cudaGetLastError();
@@ -409,7 +411,7 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
                 return fail(LIDAR_ENOMEM);
             }
             e4 = collapse_bvh(c->stream, 8, s->nodes, s->n_nodes, s->nodes8, &s->n_nodes8, &s->levels8, &need8,
-                              c->scratch, c->scratch_bytes);
+                              c->scratch, c->scratch_bytes, c->collapse, c->tri_cost);
             s->bytes += s->n_nodes8 * 256;
         }
         cudaEventRecord(e1, c->stream);
@@ -1553,8 +1555,12 @@ lidar_status lidar_set_build_options(lidar_ctx* c, const lidar_build_options* o)
     LIDAR_CHECK_ARG(c != nullptr && o != nullptr, "lidar_set_build_options: NULL argument");
     LIDAR_CHECK_ARG(o->method == 0 || o->method == 1, "lidar_set_build_options: method is 0 or 1");
     LIDAR_CHECK_ARG(o->ploc_radius >= 1 && o->ploc_radius <= 64, "lidar_set_build_options: ploc_radius in [1, 64]");
+    LIDAR_CHECK_ARG(o->collapse == 0 || o->collapse == 1, "lidar_set_build_options: collapse is 0 or 1");
+    LIDAR_CHECK_ARG(o->tri_cost > 0.0f && o->tri_cost <= 100.0f, "lidar_set_build_options: tri_cost in (0, 100]");
     c->build_method = o->method;
     c->ploc_radius = o->ploc_radius;
+    c->collapse = o->collapse;
+    c->tri_cost = o->tri_cost;
     return LIDAR_OK;
 }
 
@@ -1563,6 +1569,8 @@ lidar_status lidar_get_build_options(lidar_ctx* c, lidar_build_options* o)
     LIDAR_CHECK_ARG(c != nullptr && o != nullptr, "lidar_get_build_options: NULL argument");
     o->method = c->build_method;
     o->ploc_radius = c->ploc_radius;
+    o->collapse = c->collapse;
+    o->tri_cost = c->tri_cost;
     return LIDAR_OK;
 }
 

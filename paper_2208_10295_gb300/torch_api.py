@@ -319,15 +319,20 @@ class Lidar:
         return g
 
     # ----------------------------------------------------------- build options
-    def set_build_options(self, method: int = 1, ploc_radius: int = 16):
-        """Hierarchy of scenes built afterwards: 0 Karras LBVH, 1 PLOC (default)."""
-        o = C.lidar_build_options(method, ploc_radius)
+    def set_build_options(self, method: int = 1, ploc_radius: int = 16, collapse: int = None, tri_cost: float = None):
+        """Hierarchy of scenes built afterwards: 0 Karras LBVH, 1 PLOC (default);
+        wide-node children by the largest-area rule (collapse 0) or the SAH
+        dynamic program (collapse 1, triangle cost `tri_cost`); unchanged when
+        not given."""
+        cur = self.build_options()
+        o = C.lidar_build_options(method, ploc_radius, cur["collapse"] if collapse is None else collapse,
+                                  cur["tri_cost"] if tri_cost is None else tri_cost)
         C.check(C.lidar_set_build_options(self.handle, ctypes.byref(o)), "lidar_set_build_options")
 
     def build_options(self):
         o = C.lidar_build_options()
         C.check(C.lidar_get_build_options(self.handle, ctypes.byref(o)), "lidar_get_build_options")
-        return {"method": o.method, "ploc_radius": o.ploc_radius}
+        return {"method": o.method, "ploc_radius": o.ploc_radius, "collapse": o.collapse, "tri_cost": o.tri_cost}
 
     # ----------------------------------------------------------- tuning
     def launch_config(self):

@@ -348,16 +348,17 @@ def _wide_tree_invariants(nodes, width, n_tris, lo_t, hi_t):
     assert seen_node[0] == 0 and np.all(seen_node[1:] == 1)
 
 
-@pytest.mark.parametrize("method", [0, 1])
-def test_wide_tree_invariants(L, method):
-    """The 4- and 8-wide trees collapsed from either binary hierarchy hold every
-    leaf once with exact boxes; the 8-wide tree is shallower."""
+@pytest.mark.parametrize("method,collapse", [(0, 0), (1, 0), (1, 1)])
+def test_wide_tree_invariants(L, method, collapse):
+    """The 4- and 8-wide trees collapsed from either binary hierarchy, by the
+    largest-area rule or the SAH dynamic program, hold every leaf once with
+    exact boxes; the 8-wide tree is shallower."""
     w = synth.small_terrain(seed=8, n_cells=48, half=24.0, n_objects=20, n_frames=1, n_az=32)
-    L.set_build_options(method=method)
+    L.set_build_options(method=method, collapse=collapse)
     try:
         scene, _ = setup(L, w)
     finally:
-        L.set_build_options(method=1)
+        L.set_build_options(method=1, collapse=0)
     _, leaf_tri = scene.export()
     V = w.scene.verts[w.scene.tris[leaf_tri]]
     lo_t, hi_t = V.min(1).astype(np.float32), V.max(1).astype(np.float32)
@@ -745,3 +746,27 @@ def test_overlapped_direct_casts_match_serial(L):
     finally:
         L.set_cast_overlap(True)
         scene.free()
+
+
+def test_sah_collapse_casts_bit_identical(L):
+    """The wide trees chosen by the SAH dynamic program give every dense field
+    of the full cfg1 frame and of a small terrain with sub-rays bit for bit as
+    the largest-area collapse does, with both wide traversals."""
+    fields = ("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst", "theta_deg")
+    cfg0 = L.launch_config()
+    try:
+        for w in (synth.cfg1(), synth.small_terrain(seed=9, n_frames=2, n_az=128, n_subrays=7, divergence=2e-3)):
+            for tv in (2, 3):
+                L.set_launch_config(traversal=tv)
+                L.set_build_options(method=1, collapse=0)
+                base, s0 = gpu_cast(L, w, fields=fields)
+                L.set_build_options(method=1, collapse=1)
+                other, s1 = gpu_cast(L, w, fields=fields)
+                for k in fields:
+                    assert np.array_equal(base[k].view(np.uint8), other[k].view(np.uint8)), (w.name, tv, k)
+                assert s1.info()["n_nodes4"] <= s0.info()["n_nodes4"]
+                s0.free()
+                s1.free()
+    finally:
+        L.set_build_options(method=1, collapse=0)
+        L.set_launch_config(**cfg0)
