@@ -46,6 +46,7 @@ __device__ __forceinline__ int frame_of_index(const FrameDev* __restrict__ frame
 
 constexpr int kCompactTileBeams = 1024;
 constexpr int kScatterItems = 4;
+constexpr int kPdlScatterThreads = 64;  // an overlapped cast's scatter blocks
 
 // Ordered scatter of one compaction tile of kCompactTileBeams dense beams by
 // the calling block (blockDim a multiple of 32, at most 256).  A chunk is
@@ -54,12 +55,13 @@ constexpr int kScatterItems = 4;
 // consecutive output slots (coalesced stores); ballots rank them in the warp
 // and one table of per-(row, warp) counts in shared memory orders the rows
 // and warps.  `s_warp` holds kScatterItems * 8 words.
+template <int kItems = kScatterItems>
 __device__ void scatter_tile(const SensorDev* __restrict__ sensors, const FrameDev* __restrict__ frames,
                              int n_frames, int64_t n, const BeamsOut& dense, int64_t tile, int64_t tile_offset,
                              const lidar_points& pts, int* status, uint32_t* s_warp)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-    const int chunk_beams = blockDim.x * kScatterItems;
+    const int chunk_beams = blockDim.x * kItems;
     const unsigned lt_mask = (1u << lane) - 1u;
     int64_t running = tile_offset;
     for (int chunk = 0; chunk < kCompactTileBeams; chunk += chunk_beams) {
@@ -67,13 +69,13 @@ __device__ void scatter_tile(const SensorDev* __restrict__ sensors, const FrameD
         // gather every field of the chunk's beams before the scan and the
         // first store: the point arrays could alias the dense ones as far as
         // the compiler knows, so loads after a store would wait for it
-        bool v[kScatterItems];
-        float rg[kScatterItems], it[kScatterItems], nx[kScatterItems], ny[kScatterItems], nz[kScatterItems];
-        float dx[kScatterItems], dy[kScatterItems], dz[kScatterItems];
-        uint16_t mt[kScatterItems];
-        uint32_t in[kScatterItems], bm[kScatterItems], fk[kScatterItems];
+        bool v[kItems];
+        float rg[kItems], it[kItems], nx[kItems], ny[kItems], nz[kItems];
+        float dx[kItems], dy[kItems], dz[kItems];
+        uint16_t mt[kItems];
+        uint32_t in[kItems], bm[kItems], fk[kItems];
 #pragma unroll
-        for (int k = 0; k < kScatterItems; ++k) {
+        for (int k = 0; k < kItems; ++k) {
             rg[k] = it[k] = nx[k] = ny[k] = nz[k] = dx[k] = dy[k] = dz[k] = 0.0f;
             mt[k] = 0;
             in[k] = bm[k] = fk[k] = 0;
@@ -102,17 +104,17 @@ __device__ void scatter_tile(const SensorDev* __restrict__ sensors, const FrameD
             if (pts.material) mt[k] = __ldcg(&dense.mat[idx]);
             if (pts.instance) in[k] = __ldcg(&dense.inst[idx]);
         }
-        unsigned mask[kScatterItems];
+        unsigned mask[kItems];
 #pragma unroll
-        for (int k = 0; k < kScatterItems; ++k) {
+        for (int k = 0; k < kItems; ++k) {
             mask[k] = __ballot_sync(0xffffffffu, v[k]);
             if (lane == 0) s_warp[k * 8 + warp] = (uint32_t)__popc(mask[k]);
         }
         __syncthreads();
         // slots before row k, warp w: all of rows < k, then warps < w of row k
-        uint32_t before[kScatterItems], total = 0;
+        uint32_t before[kItems], total = 0;
 #pragma unroll
-        for (int k = 0; k < kScatterItems; ++k) {
+        for (int k = 0; k < kItems; ++k) {
             for (int w = 0; w < n_warps; ++w) {
                 const uint32_t c = s_warp[k * 8 + w];
                 if (w == warp) before[k] = total;
@@ -120,7 +122,7 @@ __device__ void scatter_tile(const SensorDev* __restrict__ sensors, const FrameD
             }
         }
 #pragma unroll
-        for (int k = 0; k < kScatterItems; ++k) {
+        for (int k = 0; k < kItems; ++k) {
             if (!v[k]) continue;
             const int64_t pos = running + before[k] + (uint32_t)__popc(mask[k] & lt_mask);
             if (pos >= pts.capacity) {
@@ -430,6 +432,7 @@ static_assert(kCompactTile == kCompactTileBeams, "the scatter tiles are the cast
 // Compaction tiles (kCompactTileBeams beams) blockIdx.x, blockIdx.x + gridDim.x, ...
 // With `pdl` (an overlapped cast's scatter) the block first lets the next
 // cast start, then waits for its own cast to complete.
+template <int kItems>
 __global__ void __launch_bounds__(kCompactThreads) k_scatter_points(
     const SensorDev* __restrict__ sensors, const FrameDev* __restrict__ frames, int n_frames, int64_t n,
     BeamsOut dense, const int64_t* __restrict__ tile_offsets, lidar_points pts, int* status,
@@ -439,10 +442,11 @@ __global__ void __launch_bounds__(kCompactThreads) k_scatter_points(
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         asm volatile("griddepcontrol.wait;" ::: "memory");
     }
-    __shared__ uint32_t s_warp[kScatterItems * 8];
+    __shared__ uint32_t s_warp[kItems * 8];
     const int64_t n_tiles = (n + kCompactTileBeams - 1) / kCompactTileBeams;
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x)
-        scatter_tile(sensors, inl.n ? inl.f : frames, n_frames, n, dense, t, tile_offsets[t], pts, status, s_warp);
+        scatter_tile<kItems>(sensors, inl.n ? inl.f : frames, n_frames, n, dense, t, tile_offsets[t], pts, status,
+                             s_warp);
 }
 
 // ------------------------------------------------------------------ ray order
@@ -721,12 +725,15 @@ cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const F
     const int64_t* offsets = (const int64_t*)compact_scratch;
     int flag = 0;
     if (pdl && num_sms > 0) {
-        // an overlapped cast's scatter: a small grid (one 128-thread block per SM
-        // fits beside the cast's blocks) that lets the next cast start at once
-        // and then waits for its own cast
+        // an overlapped cast's scatter: a small grid that lets the next cast
+        // start at once and then waits for its own cast.  Its blocks must become
+        // resident beside the running cast's (two 256-thread blocks of ~112
+        // registers leave 8,192 registers of an SM free), or the next cast
+        // could not start before the cast's blocks exit: one 64-thread block
+        // per SM at ~80 registers
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3((unsigned)std::min<int64_t>(tiles, num_sms));
-        lc.blockDim = dim3(128);
+        lc.blockDim = dim3(kPdlScatterThreads);
         lc.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -735,12 +742,13 @@ cudaError_t launch_scatter(cudaStream_t s, const SensorDev* sensors_dev, const F
         lc.numAttrs = 1;
         flag = 1;
         void* args[] = {&sensors_dev, &frames_dev, &n_frames, &n, &dense, &offsets, (void*)&pts, &status, &inl, &flag};
-        if (cudaLaunchKernelExC(&lc, (const void*)k_scatter_points, args) == cudaSuccess) return cudaSuccess;
+        if (cudaLaunchKernelExC(&lc, (const void*)k_scatter_points<kScatterItems>, args) == cudaSuccess)
+            return cudaSuccess;
         cudaGetLastError();
         flag = 0;
     }
-    k_scatter_points<<<(unsigned)tiles, kCompactThreads, 0, s>>>(sensors_dev, frames_dev, n_frames, n, dense,
-                                                                 offsets, pts, status, inl, flag);
+    k_scatter_points<kScatterItems><<<(unsigned)tiles, kCompactThreads, 0, s>>>(sensors_dev, frames_dev, n_frames, n,
+                                                                                dense, offsets, pts, status, inl, flag);
     return cudaGetLastError();
 }
 
