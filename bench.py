@@ -45,16 +45,16 @@ POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal,
 # the cast kernel as the roofline times it (cfg1 frame, dense valid flags out,
 # L2 flushed before the launch), from one ncu capture, with the digest of the
 # kernel sources the capture ran.  Reported only while the sources still match.
-NCU_TRAFFIC = {"sources": "b3f41d743257cfe8", "bytes": 10_468_864, "l2_bytes": 3_961_926 * 32,
+NCU_TRAFFIC = {"sources": "43cc999e0fe54cea", "bytes": 10_473_472, "l2_bytes": 3_972_856 * 32,
                "l1_global_load_bytes": 7_811_641 * 32}   # profiles/k_cast_cfg1_ncu_full.md
 # Binding-unit fractions of the same capture (ncu --set full of one launch):
 # L1/TEX throughput, issue-active and SM-active shares.
-NCU_UNITS = {"l1tex_throughput_pct": 42.5, "issue_active_pct": 43.3, "sm_active_pct": 72.4}
+NCU_UNITS = {"l1tex_throughput_pct": 42.7, "issue_active_pct": 43.6, "sm_active_pct": 70.8}
 # FP32 work of one launch of the cast kernel from ncu's SASS instruction
 # counters (sm__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,
 # fp32}_pred_on), FLOPs = 2 ffma + fadd + fmul + 4 ffma2 + 2 fadd2 + 2 fmul2 +
 # the remaining FP32 instructions (min/max, compares) once each.
-NCU_FP32 = {"sources": "b3f41d743257cfe8", "fp32_flops": 509_197_113, "fp32_ops": 487_615_621,
+NCU_FP32 = {"sources": "43cc999e0fe54cea", "fp32_flops": 509_197_113, "fp32_ops": 487_615_621,
             "counters": {"ffma": 21_581_492, "fadd": 10_683_339, "fmul": 33_692_596, "ffma2": 0,
                          "fadd2": 70_207_356, "fmul2": 70_207_356, "fp32_all": 347_200_909}}
 # profiles/k_cast_cfg1_fp32_counts.md
