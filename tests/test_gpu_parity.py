@@ -770,3 +770,38 @@ def test_sah_collapse_casts_bit_identical(L):
     finally:
         L.set_build_options(method=1, collapse=0)
         L.set_launch_config(**cfg0)
+
+
+def test_overlapped_casts_of_many_frames(L):
+    """Casts of more than four frames take their frame table through a copy on
+    the stream (not the launch parameters); back to back into rotating buffers
+    without synchronisation they still give every cast's point cloud bit for
+    bit as casts one after the other do."""
+    w = synth.small_terrain(seed=24, n_frames=6, n_az=256)
+    scene, _ = setup(L, w)
+    n = L.total_beams(w.frames)
+    sets = [w.frames, w.frames[::-1].copy()]
+    try:
+        L.set_cast_overlap(False)
+        ref = []
+        for fr in sets:
+            p = L.alloc_points(n)
+            L.cast_into(scene, fr, w.seed, None, p)
+            assert L.sync_status() == 0
+            ref.append(_points_np(p))
+        L.set_cast_overlap(True)
+        bufs = [L.alloc_points(n) for _ in range(3)]
+        order = [0, 1, 0, 1, 1, 0]
+        for i, k in enumerate(order):
+            L.cast_into(scene, sets[k], w.seed, None, bufs[i % 3])
+        torch.cuda.synchronize()
+        assert L.sync_status() == 0
+        for j in range(3):
+            k = order[3 + j]
+            c, pts = _points_np(bufs[j])
+            assert c == ref[k][0], j
+            for f in pts:
+                assert np.array_equal(pts[f].view(np.uint8), ref[k][1][f].view(np.uint8)), (j, f)
+    finally:
+        L.set_cast_overlap(True)
+        scene.free()
