@@ -341,13 +341,13 @@ constexpr int kAdjBlocks = 1024;
 // in shared memory at its own power-of-two scale, chosen from the largest
 // contribution seen so far and the block's beam count; when a chunk raises
 // that maximum past the scale's headroom, the accumulators are rescaled
-// (a rounding shift) before the chunk is added.  After one bounded grid-wide
-// wait every block knows every block's maximum, converts its sums to the
-// common scale of the whole tape (a rounding shift) and adds them into the
-// global accumulators with integer atomics; the last block to finish turns
-// them into the gradients and sums the per-block loss partials in block
-// order.  Every step is a deterministic function of the tape and the grid
-// size, so the result is bit-reproducible run to run.
+// (a rounding shift) before the chunk is added.  Each block then writes its
+// sums as one row.  After one bounded grid-wide wait every block knows every
+// block's maximum and scale; block b adds, over its own slice of the table
+// entries, every block's row shifted to the common scale of the whole tape (a
+// rounding shift) and writes those gradients; block 0 sums the per-block loss
+// partials in block order.  Every step is a deterministic function of the
+// tape and the grid size, so the result is bit-reproducible run to run.
 
 constexpr int kOneThreads = 512;
 constexpr int kOneBPT = 4;                          // beams per thread per chunk (one per warp step)
@@ -375,7 +375,8 @@ struct OneArgs {
     int* blk_sh;                // [grid] its fixed-point shift
     double* blk_loss;           // [grid] sum of squared residuals
     unsigned long long* blk_n;  // [grid] beams used
-    unsigned* ctl;              // [0] arrivals at the grid-wide waits, [1] finished blocks; 0 between calls
+    unsigned long long* arrivals;  // blocks arrived at the grid-wide wait, over every launch (never reset)
+    unsigned long long base;       // its value when this launch starts
     int* status;
     uint64_t wait_ns;
     float* loss;
@@ -491,25 +492,28 @@ struct Acc32 {
 };
 
 // Grid-wide wait of a cooperative launch in two halves: every block arrives
-// once per wait (thread 0 publishes the block's writes first), then waits
-// until the counter reaches k x grid for wait number k, bounded by wait_ns
-// (then ST_TIMEOUT, and false in every thread of the block).
-__device__ __forceinline__ void grid_arrive(unsigned* ctl)
+// once (thread 0 publishes the block's writes first), then waits until the
+// arrival counter reaches its value at the launch's start plus the grid,
+// bounded by wait_ns (then ST_TIMEOUT, and false in every thread of the
+// block).  The counter only grows: every block of every launch arrives
+// exactly once, timed out or not, so the caller knows its value at the next
+// launch and nothing resets it.
+__device__ __forceinline__ void grid_arrive(unsigned long long* arrivals)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicAdd(&ctl[0], 1u);
+        atomicAdd(arrivals, 1ull);
     }
 }
 
-__device__ __forceinline__ bool grid_wait_for(unsigned* ctl, unsigned target, int* status, uint64_t wait_ns,
-                                              int* s_flag)
+__device__ __forceinline__ bool grid_wait_for(unsigned long long* arrivals, unsigned long long target, int* status,
+                                              uint64_t wait_ns, int* s_flag)
 {
     if (threadIdx.x == 0) {
         int ok = 1;
         const uint64_t t0 = adj_global_ns();
-        while (*(volatile unsigned*)&ctl[0] < target) {
+        while (*(volatile unsigned long long*)arrivals < target) {
             if (adj_global_ns() - t0 > wait_ns) {
                 raise_status(status, ST_TIMEOUT);
                 ok = 0;
@@ -554,13 +558,6 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
     const int64_t n_chunks = (L + kOneChunk - 1) / kOneChunk;
     const bool has_tv = a.tvalid != nullptr;
 
-    for (int j = tid; j < 2 * n_acc_pad; j += kOneThreads) s_words[j] = 0u;
-    for (int j = tid; j < a.T.n_mat * LIDAR_TABLE_SIZE; j += kOneThreads) s_table[j] = __ldg(&a.T.table[j]);
-    if (kTma && tid == 0) {
-        for (int st = 0; st < kOneStages; ++st) bar_init(&s_bar[st]);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
 
     // beams of chunk k, and how many of them the copy engine brings (whole
     // 16-beam groups: only the tape's last few beams are loaded by the threads)
@@ -580,9 +577,18 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
         bulk_copy(d + 8 * kOneChunk, a.rf + c0, 4 * nb, &s_bar[slot]);
         bulk_copy(d + 12 * kOneChunk, a.g + c0, 4 * nb, &s_bar[slot]);
     };
+    // the first copies go out before the accumulators are cleared and the
+    // table is read (the stages are disjoint from both); the block barrier
+    // below orders the barriers' initialisation before any thread waits
     int64_t issued = 0;  // next chunk to copy (meaningful in thread 0)
-    if (kTma && tid == 0)
+    if (kTma && tid == 0) {
+        for (int st = 0; st < kOneStages; ++st) bar_init(&s_bar[st]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (; issued < n_chunks && issued < kOneStages; ++issued) issue(issued);
+    }
+    for (int j = tid; j < 2 * n_acc_pad; j += kOneThreads) s_words[j] = 0u;
+    for (int j = tid; j < a.T.n_mat * LIDAR_TABLE_SIZE; j += kOneThreads) s_table[j] = __ldg(&a.T.table[j]);
+    __syncthreads();
 
     float blk_max = 0.0f;
     int sh = 126;
@@ -794,6 +800,20 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
         for (int o = 16; o > 0; o >>= 1) gq += __shfl_xor_sync(0xffffffffu, gq, o);
         if (lane == 0 && gq) acc.add(a.n_acc - 1, gq);
     }
+    __syncthreads();  // every warp's gain sum is in before the row is read out
+    // this block's slice of the entries, summed over every row after the
+    // wait, and the gradients already in its first 32 entries (read now:
+    // nothing else writes them during the launch)
+    const int j0 = (int)((int64_t)blk * a.n_acc / G), j1 = (int)(((int64_t)blk + 1) * a.n_acc / G);
+    float g_prev = 0.0f;
+    if (warp == 0 && lane < j1 - j0) {
+        const int j = j0 + lane;
+        if (j < a.n_acc - 1) {
+            if (a.grad_table) g_prev = a.grad_table[j];
+        } else if (a.grad_gain) {
+            g_prev = *a.grad_gain;
+        }
+    }
     // this block's sums at its own scale, one dense row, with its maximum and shift
     {
         long long* row = a.rows + (int64_t)blk * a.n_acc;
@@ -804,8 +824,32 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
         a.blk_sh[blk] = sh;
     }
     // ---- the grid-wide wait: every block's row, maximum, shift, count and loss partial are out
-    grid_arrive(a.ctl);
-    if (!grid_wait_for(a.ctl, (unsigned)G, a.status, a.wait_ns, &s_flag)) failed = true;
+    grid_arrive(a.arrivals);
+    if (!grid_wait_for(a.arrivals, a.base + (unsigned long long)G, a.status, a.wait_ns, &s_flag)) failed = true;
+
+    // The merge takes the slice in pieces of up to 32 entries.  For a piece of
+    // P entries a warp load covers R = 32 / P rows (lane l: entry l mod P of
+    // row sub-group l / P); warp w takes rows (i kOneWarps + w) R + sub for
+    // i = 0, 1, ...  The first batch of loads is issued before the per-block
+    // maxima are reduced, so both round trips overlap.
+    constexpr int kRowLoads = 8;
+    auto piece = [&](int e0, int& P, int& R, int& sub, int& j) {
+        P = min(32, j1 - e0);
+        R = 32 / P;
+        sub = lane / P;
+        j = e0 + lane % P;
+    };
+    auto load_batch = [&](int e0, int i0, long long (&v)[kRowLoads]) {
+        int P, R, sub, j;
+        piece(e0, P, R, sub, j);
+#pragma unroll
+        for (int u = 0; u < kRowLoads; ++u) {
+            const int r = ((i0 + u) * kOneWarps + warp) * R + sub;
+            v[u] = (sub < R && r < G) ? __ldcg(&a.rows[(int64_t)r * a.n_acc + j]) : 0ll;
+        }
+    };
+    long long v0[kRowLoads];
+    if (j0 < j1) load_batch(j0, 0, v0);
     // the common scale (the largest contribution of the whole tape) and the
     // number of beams used, reduced in a fixed order by every block; every
     // block's shift into shared memory
@@ -841,64 +885,56 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
     const float gmax = s_gmax;
     const unsigned long long N = s_cnt[0];
     const int S = one_shift(gmax, n);
-    // block 0's first warp writes the loss: the partials in a fixed order (lane
+    // block 0's last warp writes the loss: the partials in a fixed order (lane
     // l takes blocks l, l + 32, ..., then a fixed shuffle tree)
-    if (blk == 0 && warp == 0 && a.loss) {
+    if (blk == 0 && warp == kOneWarps - 1 && a.loss) {
         double t = 0.0;
         for (int j = lane; j < G; j += 32) t += __ldcg(&a.blk_loss[j]);
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
         if (lane == 0) *a.loss = a.mse ? (float)(N ? t / (double)N : 0.0) : 0.0f;
     }
-    // each block sums the rows over its slice of the entries, each row shifted
-    // from its block's scale to the common one (a rounding shift, as the block
-    // would have made), and writes those gradients: warp w reads rows w,
-    // w + kOneWarps, ..., lane l entry j0 + l of each (contiguous: one row's
-    // slice per warp load), then the warps' sums meet in shared memory
-    // (integer sums: the order is free)
+    // each block sums every row over its slice of the entries, each row
+    // shifted from its block's scale to the common one (a rounding shift, as
+    // the block would have made), and writes those gradients; the warps' and
+    // sub-groups' sums meet in shared memory (integer sums: the order is free)
     if (!failed && gmax > 0.0f) {
-        const int j0 = (int)((int64_t)blk * a.n_acc / G), j1 = (int)(((int64_t)blk + 1) * a.n_acc / G);
         const float inv_scale = ldexpf(1.0f, -S);  // exact: a power of two
         const float norm = a.mse ? (N ? __frcp_rn((float)N) : 0.0f) : 1.0f;
         long long* s_part = reinterpret_cast<long long*>(s_red);  // [kOneWarps][32]
         for (int e0 = j0; e0 < j1; e0 += 32) {
-            const int j = e0 + lane;
+            int P, R, sub, j;
+            piece(e0, P, R, sub, j);
             long long t = 0;
-            if (j < j1) {
-                constexpr int kUnroll = 8;
-                for (int r0 = warp; r0 < G; r0 += kOneWarps * kUnroll) {
-                    long long v[kUnroll];
+            for (int i0 = 0; (i0 * kOneWarps + warp) * R < G; i0 += kRowLoads) {
+                long long v[kRowLoads];
+                if (e0 == j0 && i0 == 0) {
 #pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        const int r = r0 + u * kOneWarps;
-                        v[u] = r < G ? __ldcg(&a.rows[(int64_t)r * a.n_acc + j]) : 0ll;
-                    }
+                    for (int u = 0; u < kRowLoads; ++u) v[u] = v0[u];
+                } else {
+                    load_batch(e0, i0, v);
+                }
 #pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        const int r = r0 + u * kOneWarps;
-                        if (r < G) t += round_shift(v[u], s_sh[r] - S);
-                    }
+                for (int u = 0; u < kRowLoads; ++u) {
+                    const int r = ((i0 + u) * kOneWarps + warp) * R + sub;
+                    if (sub < R && r < G) t += round_shift(v[u], s_sh[r] - S);
                 }
             }
             s_part[warp * 32 + lane] = t;
             __syncthreads();
-            if (warp == 0 && j < j1) {
+            if (warp == 0 && lane < P) {
                 long long tot = 0;
-                for (int w = 0; w < kOneWarps; ++w) tot += s_part[w * 32 + lane];
+                for (int w = 0; w < kOneWarps; ++w)
+                    for (int q = 0; q < R; ++q) tot += s_part[w * 32 + q * P + lane];
                 const float v = __fmul_rn(__fmul_rn(__ll2float_rn(tot), inv_scale), norm);
-                if (j < a.n_acc - 1) {
-                    if (a.grad_table) a.grad_table[j] += v;
+                const int jj = e0 + lane;
+                if (jj < a.n_acc - 1) {
+                    if (a.grad_table) a.grad_table[jj] = (e0 == j0 ? g_prev : a.grad_table[jj]) + v;
                 } else if (a.grad_gain) {
-                    *a.grad_gain += v;
+                    *a.grad_gain = (e0 == j0 ? g_prev : *a.grad_gain) + v;
                 }
             }
             __syncthreads();
         }
-    }
-    // ---- the last block to finish clears the wait counters for the next call
-    __syncthreads();
-    if (tid == 0 && atomicAdd(&a.ctl[1], 1u) == (unsigned)G - 1) {
-        a.ctl[0] = 0u;
-        a.ctl[1] = 0u;
     }
 }
 
@@ -1025,8 +1061,8 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
                                          const float* theta_deg, const float* rf, TableDev T, float gain,
                                          const float* grad_I, const float* target_I, const uint8_t* target_valid,
                                          float* loss, float* grad_table, float* grad_gain, void* scratch,
-                                         size_t scratch_bytes, unsigned* ctl, int* status, uint64_t wait_ns,
-                                         int num_sms)
+                                         size_t scratch_bytes, unsigned long long* arrivals,
+                                         unsigned long long* arrivals_base, int* status, uint64_t wait_ns, int num_sms)
 {
     const int n_acc = T.n_mat * LIDAR_TABLE_SIZE + 1;
     if (num_sms < 1 || scratch_bytes < onepass_scratch_bytes(T.n_mat, num_sms)) return cudaErrorInvalidValue;
@@ -1108,7 +1144,8 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
     a.blk_sh = (int*)(p + (size_t)G * 4);
     a.blk_loss = (double*)(p + (size_t)G * 8);
     a.blk_n = (unsigned long long*)(p + (size_t)G * 16);
-    a.ctl = ctl;
+    a.arrivals = arrivals;
+    a.base = *arrivals_base;
     a.status = status;
     a.wait_ns = wait_ns;
     a.loss = loss;
@@ -1116,7 +1153,10 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
     a.grad_gain = grad_gain;
     void* args[] = {&a};
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kOneThreads), args, smem, s);
-    if (e != cudaSuccess) cudaGetLastError();  // leave no stale launch error for the next call
+    if (e != cudaSuccess)
+        cudaGetLastError();  // leave no stale launch error for the next call
+    else
+        *arrivals_base += (unsigned long long)G;  // every block arrives once, whatever happens in the launch
     return e;
 }
 

@@ -237,7 +237,8 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
                                          const float* theta_deg, const float* rf, TableDev table, float gain,
                                          const float* grad_I, const float* target_I, const uint8_t* target_valid,
                                          float* loss, float* grad_table, float* grad_gain, void* scratch,
-                                         size_t scratch_bytes, unsigned* ctl, int* status, uint64_t wait_ns,
+                                         size_t scratch_bytes, unsigned long long* arrivals,
+                                         unsigned long long* arrivals_base, int* status, uint64_t wait_ns,
                                          int num_sms);
 // address (on the current device) and size of the allocation-free variant's scratch array
 cudaError_t noalloc_scratch(void** ptr, size_t* bytes);

@@ -117,7 +117,8 @@ struct lidar_ctx {
     int* status_dev = nullptr;
     unsigned long long* work_counter = nullptr;
     int* aux_dev = nullptr;  // scratch ints (build height)
-    unsigned* adj_ctl = nullptr;  // two words of the one-pass adjoint, zero between calls
+    unsigned long long* adj_arrivals = nullptr;  // the one-pass adjoint's grid-wait counter (only grows)
+    unsigned long long adj_arrivals_base = 0;    // its value once every launch so far has run
     int coop = 0;                 // the device launches cooperative kernels
     SensorSlot slots[LIDAR_MAX_SENSORS];
     SensorDev* sensors_dev = nullptr;
@@ -247,7 +248,7 @@ lidar_status lidar_create(int device, void* cuda_stream, lidar_ctx** out)
     c->status_dev = (int*)p;
     c->work_counter = (unsigned long long*)((char*)p + 64);
     c->aux_dev = (int*)((char*)p + 128);
-    c->adj_ctl = (unsigned*)((char*)p + 192);
+    c->adj_arrivals = (unsigned long long*)((char*)p + 192);
     c->coop = coop;
     e = dev_alloc((void**)&c->sensors_dev, sizeof(SensorDev) * LIDAR_MAX_SENSORS);
     if (e != cudaSuccess) {
@@ -1350,7 +1351,8 @@ static lidar_status backward_common(lidar_ctx* c, int64_t n, const lidar_beams* 
     if (c->coop)
         e = launch_cast_backward_onepass(c->stream, n, tape->valid, tape->mat, tape->theta_deg, tape->rf, c->table,
                                          gain, grad_I, target_I, target_valid, loss, grad_table, grad_gain, c->scratch,
-                                         c->scratch_bytes, c->adj_ctl, c->status_dev, c->cfg.wait_ns, c->num_sms);
+                                         c->scratch_bytes, c->adj_arrivals, &c->adj_arrivals_base, c->status_dev,
+                                         c->cfg.wait_ns, c->num_sms);
     if (e == cudaErrorNotSupported)
         e = launch_cast_backward(c->stream, n, tape->valid, tape->mat, tape->theta_deg, tape->rf, c->table, gain,
                                  grad_I, target_I, target_valid, loss, grad_table, grad_gain, c->scratch,
