@@ -110,6 +110,7 @@ typedef struct {
     int64_t n_nodes8;      /* nodes of the 8-wide hierarchy (same collapse), 0 when not kept because
                               its traversal could need a deeper stack than the kernel's 96 entries */
     int32_t levels8;       /* its height */
+    int64_t treelets;      /* treelets the restructuring rewrote (lidar_build_options.treelet_rounds) */
 } lidar_scene_info;
 
 lidar_status lidar_get_scene_info(const lidar_scene* scene, lidar_scene_info* out);
@@ -130,8 +131,13 @@ typedef struct {
     int32_t collapse;      /* children of the wide nodes: 0 (default) each node opens its largest-area
                               child until it is full; 1 the surface-area-heuristic optimum over the
                               binary tree (a bottom-up dynamic program, Ylitie, Karras and Laine 2017) */
-    float tri_cost;        /* collapse 1: a triangle test's cost relative to a wide-node visit, (0, 100],
-                              default 1 */
+    float tri_cost;        /* a triangle test's cost relative to a node visit, (0, 100], default 1: the
+                              collapse-1 program's and the treelet restructuring's */
+    int32_t treelet_rounds;  /* 0..8, default 0: rounds of treelet restructuring of the binary tree before
+                                the collapse (Karras and Aila, HPG 2013): bottom-up, each node's treelet
+                                of up to 7 leaves (opened largest area first) is rewritten in the
+                                shape of least surface-area cost, found by a dynamic program over the
+                                subsets of its leaves */
 } lidar_build_options;
 
 lidar_status lidar_set_build_options(lidar_ctx* ctx, const lidar_build_options* options);

@@ -40,7 +40,8 @@ class LidarError(RuntimeError):
 class lidar_scene_info(ctypes.Structure):
     _fields_ = [("n_tris", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("max_depth", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double), ("n_nodes4", ctypes.c_int64),
-                ("levels4", ctypes.c_int32), ("n_nodes8", ctypes.c_int64), ("levels8", ctypes.c_int32)]
+                ("levels4", ctypes.c_int32), ("n_nodes8", ctypes.c_int64), ("levels8", ctypes.c_int32),
+                ("treelets", ctypes.c_int64)]
 
 
 class lidar_sensor_desc(ctypes.Structure):
@@ -88,7 +89,7 @@ class lidar_echoes(ctypes.Structure):
 
 class lidar_build_options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("ploc_radius", ctypes.c_int32), ("collapse", ctypes.c_int32),
-                ("tri_cost", ctypes.c_float)]
+                ("tri_cost", ctypes.c_float), ("treelet_rounds", ctypes.c_int32)]
 
 
 class lidar_raster_config(ctypes.Structure):

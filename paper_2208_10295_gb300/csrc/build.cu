@@ -967,3 +967,292 @@ cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, 
 }
 
 }  // namespace lidar
+
+// ---------------------------------------------------------------------------
+// Treelet restructuring of the binary hierarchy (Karras and Aila, "Fast
+// Parallel Construction of High-Quality Bounding Volume Hierarchies", HPG
+// 2013), written here for one thread per treelet.  Cost of a tree under the
+// surface-area model: c_node x A(n) over its internal nodes plus c_tri x A(t)
+// over its triangles (A: half the surface area of the box).  One round climbs
+// the tree bottom-up (the second child to finish processes its parent, so a
+// node is processed after its whole subtree).  At node n the thread forms a
+// treelet: starting from n's two children it replaces the treelet leaf of
+// largest area that is an internal node by that node's children, until there
+// are kTreeletLeaves leaves or none is internal.  A dynamic program over the
+// subsets S of the treelet's leaves gives the cheapest binary tree over them:
+//   c({l}) = cost of leaf l's subtree,
+//   c(S)   = c_node x A(S) + min over partitions S = P + Q of c(P) + c(Q).
+// If that is cheaper than the treelet's current shape, its internal nodes
+// (n first, so n's parent keeps pointing at it) are rewritten in the new
+// shape with exact FP32 min/max child boxes.  Only the topology above the
+// treelet's leaves changes, so the result is again a valid hierarchy over the
+// same triangles.  Every decision depends only on the subtree below the
+// node, so the result does not depend on the order threads run in.
+namespace lidar {
+namespace {
+
+constexpr int kTreeletLeaves = 7;
+
+struct TreeletArgs {
+    const float4* tris;
+    int n_leaves;
+    int n_binary;
+    float4* nodes;            // binary nodes, rewritten in place
+    const int* parent_node;   // [n_binary], -1 at the root
+    const int* parent_leaf;   // [n_leaves]
+    unsigned* visits;         // [n_binary] children finished, zero at the start of a round
+    float* cost;              // [n_binary] surface-area cost of each node's subtree
+    unsigned long long* changed;  // treelets rewritten in the round
+    int* status;              // ST_INDEX: a child reference out of range, or a climb longer than the bound
+    float c_node, c_tri;
+};
+
+// longest climb a valid hierarchy of up to 2^31 triangles can need is far
+// below this; a longer one means a broken tree (a cycle), which ends the climb
+constexpr int kTreeletMaxClimb = 4096;
+
+struct TBox {
+    float lo[3], hi[3];
+};
+
+__device__ __forceinline__ float tbox_area(const TBox& b)
+{
+    const float dx = b.hi[0] - b.lo[0], dy = b.hi[1] - b.lo[1], dz = b.hi[2] - b.lo[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__device__ __forceinline__ void tbox_grow(TBox& a, const TBox& b)
+{
+    for (int k = 0; k < 3; ++k) {
+        a.lo[k] = fminf(a.lo[k], b.lo[k]);
+        a.hi[k] = fmaxf(a.hi[k], b.hi[k]);
+    }
+}
+
+// child `side` of binary node `node` (read through L2: other threads of the
+// round may have written it)
+__device__ __forceinline__ void treelet_child(const float4* nodes, int node, int side, int& ref, TBox& b)
+{
+    const float4 n0 = __ldcg(&nodes[4 * (int64_t)node + 0]), n1 = __ldcg(&nodes[4 * (int64_t)node + 1]);
+    const float4 n2 = __ldcg(&nodes[4 * (int64_t)node + 2]), n3 = __ldcg(&nodes[4 * (int64_t)node + 3]);
+    if (side == 0) {
+        b.lo[0] = n0.x; b.hi[0] = n0.y; b.lo[1] = n0.z; b.hi[1] = n0.w; b.lo[2] = n2.x; b.hi[2] = n2.y;
+        ref = __float_as_int(n3.x);
+    } else {
+        b.lo[0] = n1.x; b.hi[0] = n1.y; b.lo[1] = n1.z; b.hi[1] = n1.w; b.lo[2] = n2.z; b.hi[2] = n2.w;
+        ref = __float_as_int(n3.y);
+    }
+}
+
+__device__ __forceinline__ bool ref_ok(const TreeletArgs& a, int ref)
+{
+    return ref >= 0 ? ref < a.n_binary : ~ref < a.n_leaves;
+}
+
+__device__ __forceinline__ float subtree_cost(const TreeletArgs& a, int ref, const TBox& b)
+{
+    return ref < 0 ? a.c_tri * tbox_area(b) : __ldcg(&a.cost[ref]);
+}
+
+__device__ void treelet_node(const TreeletArgs& a, int node)
+{
+    int lref[kTreeletLeaves];
+    TBox lbox[kTreeletLeaves];
+    float lcost[kTreeletLeaves];
+    int inner[kTreeletLeaves - 1];
+    treelet_child(a.nodes, node, 0, lref[0], lbox[0]);
+    treelet_child(a.nodes, node, 1, lref[1], lbox[1]);
+    if (!ref_ok(a, lref[0]) || !ref_ok(a, lref[1])) {
+        raise_status(a.status, ST_INDEX);
+        return;
+    }
+    lcost[0] = subtree_cost(a, lref[0], lbox[0]);
+    lcost[1] = subtree_cost(a, lref[1], lbox[1]);
+    TBox whole = lbox[0];
+    tbox_grow(whole, lbox[1]);
+    // the node's cost in its current shape
+    const float c_now = a.c_node * tbox_area(whole) + lcost[0] + lcost[1];
+    inner[0] = node;
+    int k = 2, n_inner = 1;
+    while (k < kTreeletLeaves) {
+        int best = -1;
+        float best_a = -1.0f;
+        for (int i = 0; i < k; ++i)
+            if (lref[i] >= 0 && tbox_area(lbox[i]) > best_a) {
+                best_a = tbox_area(lbox[i]);
+                best = i;
+            }
+        if (best < 0) break;
+        const int open = lref[best];
+        inner[n_inner++] = open;
+        treelet_child(a.nodes, open, 0, lref[best], lbox[best]);
+        treelet_child(a.nodes, open, 1, lref[k], lbox[k]);
+        if (!ref_ok(a, lref[best]) || !ref_ok(a, lref[k])) {
+            raise_status(a.status, ST_INDEX);
+            return;
+        }
+        lcost[best] = subtree_cost(a, lref[best], lbox[best]);
+        lcost[k] = subtree_cost(a, lref[k], lbox[k]);
+        ++k;
+    }
+    if (k < 3) {
+        a.cost[node] = c_now;
+        return;
+    }
+    // the cheapest binary tree over the k leaves: subsets in increasing order
+    // (every proper subset of S is smaller than S); each partition once (P
+    // holds S's lowest leaf)
+    float c[1 << kTreeletLeaves];
+    unsigned char split[1 << kTreeletLeaves];
+    const int full = (1 << k) - 1;
+    for (int s = 1; s <= full; ++s) {
+        if ((s & (s - 1)) == 0) {
+            c[s] = lcost[__ffs(s) - 1];
+            split[s] = 0;
+            continue;
+        }
+        TBox u;
+        bool first = true;
+        for (int i = 0; i < k; ++i)
+            if (s & (1 << i)) {
+                if (first) u = lbox[i];
+                else tbox_grow(u, lbox[i]);
+                first = false;
+            }
+        const int low = s & -s;
+        float best = INFINITY;
+        int bp = low;
+        for (int p = (s - 1) & s; p; p = (p - 1) & s) {
+            if (!(p & low)) continue;
+            const float v = c[p] + c[s ^ p];
+            if (v < best) {
+                best = v;
+                bp = p;
+            }
+        }
+        c[s] = a.c_node * tbox_area(u) + best;
+        split[s] = (unsigned char)bp;
+    }
+    // keep the current shape unless the optimum is clearly cheaper (it is
+    // one of the shapes the program compares, so it is never dearer beyond
+    // rounding)
+    if (!(c[full] < c_now * (1.0f - 1e-5f))) {
+        a.cost[node] = c_now;
+        return;
+    }
+    // rewrite: subset S at internal node id, its parts as leaves or the next
+    // internal nodes of the treelet
+    int st_s[kTreeletLeaves], st_id[kTreeletLeaves];
+    int sp = 0, next = 1;
+    st_s[sp] = full;
+    st_id[sp++] = node;
+    while (sp > 0) {
+        --sp;
+        const int s = st_s[sp], id = st_id[sp];
+        const int part[2] = {split[s], s ^ split[s]};
+        int ref[2];
+        TBox box[2];
+        for (int side = 0; side < 2; ++side) {
+            const int x = part[side];
+            bool first = true;
+            for (int i = 0; i < k; ++i)
+                if (x & (1 << i)) {
+                    if (first) box[side] = lbox[i];
+                    else tbox_grow(box[side], lbox[i]);
+                    first = false;
+                }
+            if ((x & (x - 1)) == 0) {
+                ref[side] = lref[__ffs(x) - 1];
+            } else {
+                ref[side] = inner[next++];
+                st_s[sp] = x;
+                st_id[sp++] = ref[side];
+            }
+        }
+        const TBox& L = box[0];
+        const TBox& R = box[1];
+        a.nodes[4 * (int64_t)id + 0] = make_float4(L.lo[0], L.hi[0], L.lo[1], L.hi[1]);
+        a.nodes[4 * (int64_t)id + 1] = make_float4(R.lo[0], R.hi[0], R.lo[1], R.hi[1]);
+        a.nodes[4 * (int64_t)id + 2] = make_float4(L.lo[2], L.hi[2], R.lo[2], R.hi[2]);
+        a.nodes[4 * (int64_t)id + 3] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), 0.0f, 0.0f);
+        a.cost[id] = c[s];
+    }
+    atomicAdd(a.changed, 1ull);
+}
+
+__global__ void __launch_bounds__(128) k_treelet_round(TreeletArgs a)
+{
+    const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+    if (leaf >= a.n_leaves) return;
+    int node = a.parent_leaf[leaf];
+    for (int step = 0; node >= 0; ++step) {
+        if (node >= a.n_binary || step >= kTreeletMaxClimb) {
+            raise_status(a.status, ST_INDEX);
+            return;
+        }
+        __threadfence();
+        if (atomicAdd(&a.visits[node], 1u) == 0u) return;  // the other child is still running
+        __threadfence();
+        treelet_node(a, node);
+        node = a.parent_node[node];
+    }
+}
+
+__global__ void k_parents_reset(int* parent_node, int n_binary)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_binary) parent_node[i] = -1;
+}
+
+}  // namespace
+
+size_t treelet_scratch_bytes(int64_t n_tris)
+{
+    // parents of nodes and leaves, visit counters, costs, heights, node boxes, counter
+    return 5 * align256(n_tris * sizeof(int)) + align256((size_t)n_tris * 2 * sizeof(float4)) + 256;
+}
+
+cudaError_t restructure_treelets(cudaStream_t s, const float4* tris, int64_t n, float4* nodes, int* max_height_dev,
+                                 int rounds, float tri_cost, void* scratch, size_t scratch_bytes,
+                                 unsigned long long* changed_host, int* status)
+{
+    if (changed_host) *changed_host = 0;
+    if (n < 3 || rounds <= 0) return cudaSuccess;
+    if (scratch_bytes < treelet_scratch_bytes(n)) return cudaErrorInvalidValue;
+    const int n_binary = (int)(n - 1);
+    char* p = (char*)scratch;
+    int* parent_node = (int*)p; p += align256(n * sizeof(int));
+    int* parent_leaf = (int*)p; p += align256(n * sizeof(int));
+    unsigned* visits = (unsigned*)p; p += align256(n * sizeof(int));
+    float* cost = (float*)p; p += align256(n * sizeof(float));
+    int* heights = (int*)p; p += align256(n * sizeof(int));
+    float4* node_boxes = (float4*)p; p += align256((size_t)n * 2 * sizeof(float4));
+    unsigned long long* changed = (unsigned long long*)p;
+    const int nb_blocks = (n_binary + 255) / 256;
+    TreeletArgs a{tris, (int)n, n_binary, nodes, parent_node, parent_leaf, visits, cost, changed, status,
+                  1.0f, tri_cost};
+    cudaError_t e = cudaMemsetAsync(changed, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    for (int r = 0; r < rounds; ++r) {
+        k_parents_reset<<<nb_blocks, 256, 0, s>>>(parent_node, n_binary);
+        k_parents<<<nb_blocks, 256, 0, s>>>(nodes, n_binary, parent_node, parent_leaf);
+        e = cudaMemsetAsync(visits, 0, (size_t)n_binary * sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        k_treelet_round<<<(int)((n + 127) / 128), 128, 0, s>>>(a);
+    }
+    // parents, heights and the root height of the final shape (the boxes the
+    // refit writes are the same exact unions)
+    k_parents_reset<<<nb_blocks, 256, 0, s>>>(parent_node, n_binary);
+    k_parents<<<nb_blocks, 256, 0, s>>>(nodes, n_binary, parent_node, parent_leaf);
+    e = cudaMemsetAsync(visits, 0, (size_t)n_binary * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(max_height_dev, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_refit<<<(int)((n + kBuildThreads - 1) / kBuildThreads), kBuildThreads, 0, s>>>(
+        tris, n, nodes, node_boxes, heights, parent_node, parent_leaf, (int*)visits, max_height_dev);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && changed_host)
+        e = cudaMemcpyAsync(changed_host, changed, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    return e;
+}
+
+}  // namespace lidar

@@ -163,6 +163,14 @@ cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, 
                          int64_t* n_wide, int* levels, int* stack_need, void* scratch, size_t scratch_bytes,
                          int sah_dp = 0, float tri_cost = 1.0f);
 size_t collapse_scratch_bytes(int64_t n_binary);
+// treelet restructuring of the binary hierarchy (rounds > 0, n_tris >= 3);
+// recomputes the root height; *changed_host (valid after a stream
+// synchronisation) receives the number of treelets rewritten; a broken input
+// tree records ST_INDEX in *status
+size_t treelet_scratch_bytes(int64_t n_tris);
+cudaError_t restructure_treelets(cudaStream_t s, const float4* tris, int64_t n, float4* nodes, int* max_height_dev,
+                                 int rounds, float tri_cost, void* scratch, size_t scratch_bytes,
+                                 unsigned long long* changed_host, int* status);
 
 // sort.cu: stable LSD radix sort of (key, value) pairs, keys of `key_bits` bits
 size_t radix_sort_scratch_bytes(int64_t n);

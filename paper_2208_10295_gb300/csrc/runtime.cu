@@ -102,6 +102,7 @@ struct lidar_scene {
     int max_depth = 0;
     double build_ms = 0.0;
     int64_t bytes = 0;
+    int64_t treelets = 0;  // treelets the restructuring rewrote
 };
 
 static SceneDev scene_dev(const lidar_scene* scene)
@@ -147,7 +148,8 @@ struct lidar_ctx {
     int build_method = 1;     // 0 Karras LBVH, 1 PLOC clustering (fewer node fetches per ray)
     int ploc_radius = 16;
     int collapse = 0;         // wide nodes: 0 open the largest child, 1 SAH dynamic program
-    float tri_cost = 1.0f;    // a triangle test's cost relative to a wide-node visit (collapse 1)
+    float tri_cost = 1.0f;    // a triangle test's cost relative to a node visit (collapse 1, treelets)
+    int treelet_rounds = 0;   // rounds of treelet restructuring of the binary tree
     std::set<lidar_scene*> scenes;
 };
 
@@ -358,7 +360,8 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         }
         s->bytes = s->n_nodes * 64 + s->n_nodes * 128 + n_tris * 48 + n_tris * 4;
         lidar_status st = ensure_scratch(c, std::max({build_scratch_bytes(n_tris), collapse_scratch_bytes(s->n_nodes),
-                                                      c->build_method == 1 ? ploc_scratch_bytes(n_tris) : (size_t)0}));
+                                                      c->build_method == 1 ? ploc_scratch_bytes(n_tris) : (size_t)0,
+                                                      c->treelet_rounds > 0 ? treelet_scratch_bytes(n_tris) : (size_t)0}));
         if (st != LIDAR_OK) return fail(st);
         struct Events {
             cudaEvent_t a = nullptr, b = nullptr;
@@ -370,6 +373,10 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         cudaError_t e = build_lbvh(c->stream, verts, n_verts, tris, mat, inst, n_tris, s->nodes, s->tris,
                                    s->leaf_tri, c->status_dev, c->aux_dev, c->scratch, c->scratch_bytes,
                                    n_tris >= 2 ? c->build_method : 0, c->ploc_radius);
+        unsigned long long treelets = 0;
+        if (e == cudaSuccess && c->treelet_rounds > 0)
+            e = restructure_treelets(c->stream, s->tris, n_tris, s->nodes, c->aux_dev, c->treelet_rounds, c->tri_cost,
+                                     c->scratch, c->scratch_bytes, &treelets, c->status_dev);
         cudaEventRecord(e1, c->stream);
         if (e != cudaSuccess) {
             set_error(std::string("lidar_scene_build: ") + cudaGetErrorString(e));
@@ -382,6 +389,7 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         s->build_ms = ms;
+        s->treelets = (int64_t)treelets;
         int w = 0, h = 0;
         cudaMemcpy(&w, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost);
         cudaMemcpy(&h, c->aux_dev, sizeof(int), cudaMemcpyDeviceToHost);
@@ -447,6 +455,7 @@ lidar_status lidar_get_scene_info(const lidar_scene* s, lidar_scene_info* out)
     out->levels4 = s->levels4;
     out->n_nodes8 = s->n_nodes8;
     out->levels8 = s->levels8;
+    out->treelets = s->treelets;
     return LIDAR_OK;
 }
 
@@ -1559,10 +1568,13 @@ lidar_status lidar_set_build_options(lidar_ctx* c, const lidar_build_options* o)
     LIDAR_CHECK_ARG(o->ploc_radius >= 1 && o->ploc_radius <= 64, "lidar_set_build_options: ploc_radius in [1, 64]");
     LIDAR_CHECK_ARG(o->collapse == 0 || o->collapse == 1, "lidar_set_build_options: collapse is 0 or 1");
     LIDAR_CHECK_ARG(o->tri_cost > 0.0f && o->tri_cost <= 100.0f, "lidar_set_build_options: tri_cost in (0, 100]");
+    LIDAR_CHECK_ARG(o->treelet_rounds >= 0 && o->treelet_rounds <= 8,
+                    "lidar_set_build_options: treelet_rounds in [0, 8]");
     c->build_method = o->method;
     c->ploc_radius = o->ploc_radius;
     c->collapse = o->collapse;
     c->tri_cost = o->tri_cost;
+    c->treelet_rounds = o->treelet_rounds;
     return LIDAR_OK;
 }
 
@@ -1573,6 +1585,7 @@ lidar_status lidar_get_build_options(lidar_ctx* c, lidar_build_options* o)
     o->ploc_radius = c->ploc_radius;
     o->collapse = c->collapse;
     o->tri_cost = c->tri_cost;
+    o->treelet_rounds = c->treelet_rounds;
     return LIDAR_OK;
 }
 
