@@ -1003,7 +1003,7 @@ struct TreeletArgs {
     unsigned* visits;         // [n_binary] children finished, zero at the start of a round
     float* cost;              // [n_binary] surface-area cost of each node's subtree
     unsigned long long* changed;  // treelets rewritten in the round
-    int* status;              // ST_INDEX: a child reference out of range, or a climb longer than the bound
+    int* status;              // ST_BOUNDS: a child reference out of range, or a climb longer than the bound
     float c_node, c_tri;
 };
 
@@ -1063,7 +1063,7 @@ __device__ void treelet_node(const TreeletArgs& a, int node)
     treelet_child(a.nodes, node, 0, lref[0], lbox[0]);
     treelet_child(a.nodes, node, 1, lref[1], lbox[1]);
     if (!ref_ok(a, lref[0]) || !ref_ok(a, lref[1])) {
-        raise_status(a.status, ST_INDEX);
+        raise_status(a.status, ST_BOUNDS);
         return;
     }
     lcost[0] = subtree_cost(a, lref[0], lbox[0]);
@@ -1088,7 +1088,7 @@ __device__ void treelet_node(const TreeletArgs& a, int node)
         treelet_child(a.nodes, open, 0, lref[best], lbox[best]);
         treelet_child(a.nodes, open, 1, lref[k], lbox[k]);
         if (!ref_ok(a, lref[best]) || !ref_ok(a, lref[k])) {
-            raise_status(a.status, ST_INDEX);
+            raise_status(a.status, ST_BOUNDS);
             return;
         }
         lcost[best] = subtree_cost(a, lref[best], lbox[best]);
@@ -1187,7 +1187,7 @@ __global__ void __launch_bounds__(128) k_treelet_round(TreeletArgs a)
     int node = a.parent_leaf[leaf];
     for (int step = 0; node >= 0; ++step) {
         if (node >= a.n_binary || step >= kTreeletMaxClimb) {
-            raise_status(a.status, ST_INDEX);
+            raise_status(a.status, ST_BOUNDS);
             return;
         }
         __threadfence();

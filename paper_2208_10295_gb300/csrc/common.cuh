@@ -166,7 +166,7 @@ size_t collapse_scratch_bytes(int64_t n_binary);
 // treelet restructuring of the binary hierarchy (rounds > 0, n_tris >= 3);
 // recomputes the root height; *changed_host (valid after a stream
 // synchronisation) receives the number of treelets rewritten; a broken input
-// tree records ST_INDEX in *status
+// tree records ST_BOUNDS in *status
 size_t treelet_scratch_bytes(int64_t n_tris);
 cudaError_t restructure_treelets(cudaStream_t s, const float4* tris, int64_t n, float4* nodes, int* max_height_dev,
                                  int rounds, float tri_cost, void* scratch, size_t scratch_bytes,

@@ -203,7 +203,8 @@ lidar_status status_from_word(int w)
     case ST_TIMEOUT: set_error("a bounded device wait timed out"); return LIDAR_ETIMEOUT;
     case ST_INDEX: set_error("triangle vertex index out of range"); return LIDAR_EINVAL;
     case ST_BOUNDS:
-        set_error("a traversal index outside its array (bounds-checked build): corrupt scene data");
+        set_error("an index outside its array (the bounds-checked traversal, or the treelet restructuring of a "
+                  "broken tree): corrupt scene data");
         return LIDAR_EINVAL;
     default: set_error("unknown device status"); return LIDAR_ECUDA;
     }

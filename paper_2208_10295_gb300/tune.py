@@ -8,7 +8,7 @@ the ordered scatter runs inside the cast (cooperative launch) or as its own
 kernel, timing each candidate with CUDA events on the context stream.  Every
 candidate produces bit-identical results (tested), so the choice is purely a
 performance one.  The winner is cached in a JSON file keyed by GPU name, SM
-count and a hash of the workload's shape.
+count and a hash of the workload's shape and of its hierarchy's size.
 """
 from __future__ import annotations
 
@@ -36,7 +36,11 @@ SPACE = {
 def workload_key(L, scene, frames) -> str:
     props = torch.cuda.get_device_properties(L.device)
     fr = np.ascontiguousarray(frames)
-    shape = [int(scene.n_tris)] + [int(L.n_beams[int(s)]) for s in fr["sensor"]]
+    info = scene.info()
+    # the hierarchy as well as the sizes: a tree built with other options
+    # (another method, treelet rounds) is another workload
+    shape = ([int(scene.n_tris), int(info["n_nodes4"]), int(info["n_nodes8"]), int(info["treelets"])] +
+             [int(L.n_beams[int(s)]) for s in fr["sensor"]])
     h = hashlib.sha256(json.dumps(shape).encode()).hexdigest()[:16]
     return f"{props.name}|{props.multi_processor_count}|{h}"
 

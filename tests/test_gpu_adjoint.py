@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 import synth
+from bench import build_cfg1  # the benchmark's hierarchy of the 1M-triangle scene
 from gpu_util import frame_offsets, oracle_cast, stratified_sample
 
 torch = pytest.importorskip("torch")
@@ -123,7 +124,7 @@ def test_adjoint_cfg3_sampled(L):
     """Full 16-frame workload on the GPU; the mask keeps a seeded sample of
     beams that the oracle computes one by one."""
     w = synth.cfg3()
-    scene, params, table, tape, n = _gpu_tape(L, w)
+    scene, params, table, tape, n = _gpu_tape(L, w, scene=build_cfg1(L, w))
     samples = stratified_sample(w, 1024, seed=3)
     fwd = oracle_cast(w, samples)
     tgt = oracle_cast(w, samples, table=oracle.build_tables(w.hidden_params))
@@ -156,7 +157,7 @@ def test_cfg3_finite_differences_full_size(L):
     """All 4.2M beams: the frozen-hit loss is quadratic in T and g, so central
     differences of the GPU loss match its gradient (rel 1e-3)."""
     w = synth.cfg3()
-    scene, params, table, tape, n = _gpu_tape(L, w)
+    scene, params, table, tape, n = _gpu_tape(L, w, scene=build_cfg1(L, w))
     dev = L.device
     Th = L.build_tables(torch.tensor(w.hidden_params, device=dev))
     L.set_materials(Th)
@@ -234,8 +235,10 @@ def test_adjoint_city_sampled(L):
     mask keeps a seeded sample of beams that the oracle recomputes, where both
     pick the same sub-ray and nothing is exempt; targets from the hidden
     64-material table.  Loss and gradients against the oracle's adjoint."""
+    from bench import build_city  # the benchmark's hierarchy of the city
     w = synth.cfg4()
-    scene, params, table, tape, n = _gpu_tape(L, w, fields=("valid", "intensity", "mat", "theta_deg", "rf", "sub"))
+    scene, params, table, tape, n = _gpu_tape(L, w, scene=build_city(L, w),
+                                              fields=("valid", "intensity", "mat", "theta_deg", "rf", "sub"))
     samples = stratified_sample(w, 256, seed=6)
     fwd = oracle_cast(w, samples)
     tgt = oracle_cast(w, samples, table=oracle.build_tables(w.hidden_params))

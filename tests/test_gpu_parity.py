@@ -98,8 +98,9 @@ def test_cfg1_full_frame_every_beam(L):
     """The headline frame (262,144 beams over 1,036,288 triangles), every beam
     against the oracle's brute force (about 3.5 minutes of oracle time on 16
     host cores), the GPU in the benchmark's launch configuration."""
+    from bench import build_cfg1  # the hierarchy the benchmark walks (PLOC + treelet rounds)
     w = synth.cfg1()
-    gpu, _ = gpu_cast(L, w)
+    gpu, _ = gpu_cast(L, w, scene=build_cfg1(L, w))
     ref = oracle_cast(w)
     rep = compare(gpu, ref, label="cfg1 full frame, every beam")
     _report(rep)
@@ -121,8 +122,10 @@ def test_cfg1_full_frame_every_beam(L):
 
 
 def test_cfg2_batched_sampled(L):
+    from bench import build_cfg1  # the benchmark's hierarchy of the 1M-triangle scene
     w = synth.cfg2()
-    gpu, _ = gpu_cast(L, w, fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst"))
+    gpu, _ = gpu_cast(L, w, scene=build_cfg1(L, w),
+                      fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst"))
     samples = stratified_sample(w, 4096, seed=2)
     ref = oracle_cast(w, samples)
     _report(compare(pick(gpu, w, samples), ref, label="cfg2 8 sensors x 64 frames, 4096 sampled beams"))
@@ -434,8 +437,10 @@ def test_cfg4_city_subrays_sampled(L):
     """The 10.7M-triangle city, 7 sub-rays per beam, all 32 frames cast on the
     GPU; a seeded sample of beams is recomputed by the oracle (every sub-ray
     against every triangle)."""
+    from bench import build_city  # the hierarchy the benchmark walks (PLOC + treelet rounds)
     w = synth.cfg4()
-    gpu, _ = gpu_cast(L, w, fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst", "sub"))
+    gpu, _ = gpu_cast(L, w, scene=build_city(L, w),
+                      fields=("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst", "sub"))
     samples = stratified_sample(w, 1280, seed=4)
     ref = oracle_cast(w, samples)
     rep = compare_subray(pick(gpu, w, samples), ref, label="cfg4 city, 7 sub-rays, 1280 sampled beams")

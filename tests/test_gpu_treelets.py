@@ -170,15 +170,19 @@ def test_rounds_never_raise_the_tree_cost(L):
 
 
 def test_treelet_trees_cast_bit_identical(L):
-    """Every dense field of the full cfg1 frame and of a small terrain with
-    sub-rays, bit for bit, through both wide traversals, with and without the
-    restructuring (the closest hit does not depend on the hierarchy)."""
+    """Every dense field of the full cfg1 frame, of a small terrain with
+    sub-rays and of one city frame (7 sub-rays per beam), bit for bit, through
+    both wide traversals, with and without the restructuring (the closest hit
+    does not depend on the hierarchy)."""
     fields = ("valid", "tri", "t", "range", "intensity", "normal", "mat", "inst", "theta_deg")
     cfg0 = L.launch_config()
     out = {}
     try:
-        for w in (synth.cfg1(), synth.small_terrain(seed=9, n_frames=2, n_az=128, n_subrays=7, divergence=2e-3)):
-            for tv in (2, 3):
+        city = synth.cfg4()
+        city.frames = city.frames[1:2]
+        for w in (synth.cfg1(), synth.small_terrain(seed=9, n_frames=2, n_az=128, n_subrays=7, divergence=2e-3),
+                  city):
+            for tv in ((2, 3) if w is not city else (2,)):
                 L.set_launch_config(traversal=tv)
                 L.set_build_options(method=1, treelet_rounds=0)
                 base, s0 = gpu_cast(L, w, fields=fields)
