@@ -38,11 +38,18 @@ METRIC = "LiDAR rays/sec (128-ch, 1M-tri scene) & roofline %; fwd+bwd vs plain f
 UNIT = "rays/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6800.0
-# The hierarchies the benchmark walks: PLOC plus this many rounds of treelet
-# restructuring, the counts that cast fastest on a GB300 (one frame each, L2
-# flushed; measurements in the design notes)
-CFG1_TREELET_ROUNDS = 1
-CITY_TREELET_ROUNDS = 8
+# The hierarchies the benchmark walks: PLOC plus rounds of treelet
+# restructuring, with the builders' area measure weighting the boxes' top and
+# bottom faces (normal to z) less than their sides — the choices that cast
+# fastest on a GB300 (one frame each, L2 flushed; measurements in the design
+# notes)
+CFG1_TREE = {"treelet_rounds": 2, "area_weight": (1.0, 1.0, 0.23)}
+CITY_TREE = {"treelet_rounds": 8, "area_weight": (1.0, 1.0, 0.35)}
+
+
+def tree_name(tree):
+    return (f"PLOC + {tree['treelet_rounds']} treelet rounds, face weights "
+            f"{'/'.join(f'{v:g}' for v in tree['area_weight'])} (x/y/z), collapsed 4-wide")
 POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal, material, instance, beam, frame
 
 
@@ -50,23 +57,25 @@ POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal,
 # the cast kernel as the roofline times it (cfg1 frame, dense valid flags out,
 # L2 flushed before the launch), from one ncu capture, with the digest of the
 # kernel sources the capture ran.  Reported only while the sources still match.
-NCU_TRAFFIC = {"sources": "43cc999e0fe54cea", "tree_rounds": 1, "bytes": 10_048_256, "l2_bytes": 3_720_117 * 32,
-               "l1_global_load_bytes": 7_460_893 * 32}   # profiles/k_cast_cfg1_ncu_full.md
+NCU_TRAFFIC = {"sources": "43cc999e0fe54cea", "tree": dict(treelet_rounds=2, area_weight=(1.0, 1.0, 0.23)),
+               "bytes": 9_744_640, "l2_bytes": 3_380_907 * 32,
+               "l1_global_load_bytes": 6_591_193 * 32}   # profiles/k_cast_cfg1_ncu_full.md
 # Binding-unit fractions of the same capture (ncu --set full of one launch):
 # L1/TEX throughput, issue-active and SM-active shares.
-NCU_UNITS = {"l1tex_throughput_pct": 43.2, "issue_active_pct": 44.1, "sm_active_pct": 72.7}
+NCU_UNITS = {"l1tex_throughput_pct": 41.1, "issue_active_pct": 43.4, "sm_active_pct": 71.0}
 # FP32 work of one launch of the cast kernel from ncu's SASS instruction
 # counters (sm__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,fadd2,fmul2,
 # fp32}_pred_on), FLOPs = 2 ffma + fadd + fmul + 4 ffma2 + 2 fadd2 + 2 fmul2 +
 # the remaining FP32 instructions (min/max, compares) once each.
-NCU_FP32 = {"sources": "43cc999e0fe54cea", "tree_rounds": 1, "fp32_flops": 545_113_507, "fp32_ops": 523_619_382,
-            "counters": {"ffma": 21_494_125, "fadd": 10_540_873, "fmul": 35_611_705, "ffma2": 0,
-                         "fadd2": 76_209_252, "fmul2": 76_209_252, "fp32_all": 371_200_878}}
+NCU_FP32 = {"sources": "43cc999e0fe54cea", "tree": dict(treelet_rounds=2, area_weight=(1.0, 1.0, 0.23)),
+            "fp32_flops": 497_878_528, "fp32_ops": 476_442_679,
+            "counters": {"ffma": 21_435_849, "fadd": 10_460_945, "fmul": 33_010_988, "ffma2": 0,
+                         "fadd2": 68_563_704, "fmul2": 68_563_704, "fp32_all": 339_315_271}}
 # profiles/k_cast_cfg1_fp32_counts.md
 # Binding-unit fractions of one city frame launch (ncu --set full,
 # profiles/k_cast_city_ncu_full.md), with the sources and tree it ran
-NCU_CITY_UNITS = {"sources": "43cc999e0fe54cea", "tree_rounds": 8, "issue_active_pct": 74.3,
-                  "l1tex_throughput_pct": 63.5, "fma_pipe_pct": 42.9, "alu_pipe_pct": 53.4}
+NCU_CITY_UNITS = {"sources": "43cc999e0fe54cea", "tree": dict(treelet_rounds=8, area_weight=(1.0, 1.0, 0.35)),
+                  "issue_active_pct": 74.8, "l1tex_throughput_pct": 62.9, "fma_pipe_pct": 42.7, "alu_pipe_pct": 53.5}
 KERNEL_SOURCES = ("cast.cu", "shade.cuh", "trace.cuh", "common.cuh", "philox.cuh")
 # DRAM traffic (read + write) of one launch of the one-pass adjoint on the
 # 16-frame tape, from one ncu capture (profiles/k_adj_cfg3_ncu_full.md),
@@ -94,11 +103,11 @@ def adjoint_digest():
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def build_with_rounds(L, w, rounds):
-    """w's scene as a PLOC hierarchy with `rounds` treelet rounds; the
+def build_with_tree(L, w, tree):
+    """w's scene as a PLOC hierarchy with the options in `tree`; the
     context's build options are restored afterwards."""
     opts = L.build_options()
-    L.set_build_options(method=1, ploc_radius=opts["ploc_radius"], treelet_rounds=rounds)
+    L.set_build_options(method=1, ploc_radius=opts["ploc_radius"], **tree)
     try:
         return L.build_scene(w.scene.verts, w.scene.tris, w.scene.mat, w.scene.inst)
     finally:
@@ -107,12 +116,12 @@ def build_with_rounds(L, w, rounds):
 
 def build_cfg1(L, w):
     """The 1.04M-triangle scene (cfg1, and the batches and tapes cast in it)."""
-    return build_with_rounds(L, w, CFG1_TREELET_ROUNDS)
+    return build_with_tree(L, w, CFG1_TREE)
 
 
 def build_city(L, w4):
     """The 10.7M-triangle city (cfg4)."""
-    return build_with_rounds(L, w4, CITY_TREELET_ROUNDS)
+    return build_with_tree(L, w4, CITY_TREE)
 
 
 def dist_env():
@@ -431,7 +440,7 @@ def run_ours(args, rank, world, local_rank):
     visit_bytes = counters["node_visits"] * counters["node_bytes"] + counters["tri_tests"] * 48 + counters["io_bytes"]
     uniq_bytes = counters["unique_node_bytes"] + counters["unique_tri_bytes"] + counters["io_bytes"]
     achieved = visit_bytes / (kernel_ms / 1e3) / 1e9
-    same_kernel = NCU_TRAFFIC["sources"] == kernel_digest() and NCU_TRAFFIC["tree_rounds"] == CFG1_TREELET_ROUNDS
+    same_kernel = NCU_TRAFFIC["sources"] == kernel_digest() and NCU_TRAFFIC["tree"] == CFG1_TREE
     traffic = NCU_TRAFFIC["bytes"] if same_kernel else None
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
     # FP32 ops per child box of a fetched node: 6 slab subtracts + 6 multiplies, 3 max (entry, with t_eps),
@@ -442,7 +451,7 @@ def run_ours(args, rank, world, local_rank):
     # the measured FP32 rate, scaled from the probe's clock to the clock the cast ran at
     fp_probe = fp32_peak
     fp_peak = fp_probe["tflops"] * (sm_mhz / fp_probe["sm_mhz"] if fp_probe.get("sm_mhz") else 1.0)
-    ncu_ok = NCU_FP32["sources"] == kernel_digest() and NCU_FP32["tree_rounds"] == CFG1_TREELET_ROUNDS
+    ncu_ok = NCU_FP32["sources"] == kernel_digest() and NCU_FP32["tree"] == CFG1_TREE
     ncu_fp32_tf = NCU_FP32["fp32_flops"] / (kernel_ms / 1e3) / 1e12 if ncu_ok else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -452,7 +461,7 @@ def run_ours(args, rank, world, local_rank):
                                "scene, one frame per step incl. ordered compaction",
                    "beams_per_step_per_gpu": n_beams, "tris": int(w.scene.n_tris),
                    "l2": "flushed (256 MiB write) before every timed step", "build_ms": build_ms,
-                   "tree": f"PLOC + {CFG1_TREELET_ROUNDS} treelet round(s), collapsed 4-wide",
+                   "tree": tree_name(CFG1_TREE),
                    "points_per_step": n_points, "launch": tuned_cfg},
         "gpu_launches": launches_per_step * args.steps,
         "e2e": {"value": n_beams / (e2e_step_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 56,
@@ -679,7 +688,7 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
                        "tris": int(w4.scene.n_tris), "beams": B4.n_beams, "subrays": B4.n_beams * 7,
                        "ms": c_ms, "subrays_per_s": B4.n_beams * 7 / (c_ms / 1e3),
                        "build_ms": info["build_ms"], "bvh_depth": info["max_depth"],
-                       "tree": f"PLOC + {CITY_TREELET_ROUNDS} treelet rounds ({info['treelets']} treelets rewritten)",
+                       "tree": f"{tree_name(CITY_TREE)} ({info['treelets']} treelets rewritten)",
                        "points": int(pts4["count"].item()), "launch": cfg4,
                        "work_per_subray": {"node_visits": cw["node_visits"] / cw["rays"],
                                            "tri_tests": cw["tri_tests"] / cw["rays"],
@@ -695,7 +704,7 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
                            "binding_unit": (dict(NCU_CITY_UNITS, source="ncu --set full of one city frame "
                                                                          "launch (profiles/k_cast_city_ncu_full.md)")
                                             if NCU_CITY_UNITS["sources"] == kernel_digest() and
-                                            NCU_CITY_UNITS["tree_rounds"] == CITY_TREELET_ROUNDS else None)}}
+                                            NCU_CITY_UNITS["tree"] == CITY_TREE else None)}}
         # forward with tape (each beam's strongest sub-ray) + fused-MSE adjoint to the 64 x 91 table, the
         # widths and the gain, targets from the hidden table
         del pts4

@@ -138,6 +138,13 @@ typedef struct {
                                 of up to 7 leaves (opened largest area first) is rewritten in the
                                 shape of least surface-area cost, found by a dynamic program over the
                                 subsets of its leaves */
+    float area_weight[3];  /* (0, 100] each, default 1, 1, 1: weights of a box's faces normal to x, y and z
+                              in the area that PLOC's nearest-neighbour distance, the collapse's
+                              largest-area rule and both surface-area programs compare; half the
+                              weighted surface of a box is z dx dy + x dy dz + y dz dx.  1, 1, 1 is
+                              the surface area (rays of every direction alike); weights proportional
+                              to the sensors' mean |direction| components (mostly level rays: a
+                              smaller z) fit a LiDAR's beam pattern */
 } lidar_build_options;
 
 lidar_status lidar_set_build_options(lidar_ctx* ctx, const lidar_build_options* options);

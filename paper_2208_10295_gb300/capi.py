@@ -89,7 +89,8 @@ class lidar_echoes(ctypes.Structure):
 
 class lidar_build_options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("ploc_radius", ctypes.c_int32), ("collapse", ctypes.c_int32),
-                ("tri_cost", ctypes.c_float), ("treelet_rounds", ctypes.c_int32)]
+                ("tri_cost", ctypes.c_float), ("treelet_rounds", ctypes.c_int32),
+                ("area_weight", ctypes.c_float * 3)]
 
 
 class lidar_raster_config(ctypes.Structure):

@@ -278,12 +278,12 @@ size_t build_scratch_bytes(int64_t n)
 }
 
 cudaError_t build_ploc(cudaStream_t s, const float4* tris_sorted, int64_t n, float4* nodes_out, int* max_height_dev,
-                       int radius, void* scratch, size_t scratch_bytes, unsigned long long* host_total);
+                       int radius, void* scratch, size_t scratch_bytes, unsigned long long* host_total, AreaW w);
 
 cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, const uint32_t* tris,
                        const uint16_t* mat, const uint32_t* inst, int64_t n, float4* nodes_out,
                        float4* tris_out, uint32_t* leaf_tri_out, int* status, int* max_height_dev,
-                       void* scratch, size_t scratch_bytes, int method, int radius)
+                       void* scratch, size_t scratch_bytes, int method, int radius, AreaW area_w)
 {
     if (n == 0) return cudaSuccess;
     if (scratch_bytes < build_scratch_bytes(n)) return cudaErrorInvalidValue;
@@ -315,7 +315,7 @@ cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, cons
     if (method == 1) {
         // clustering over the Morton-ordered leaves; the sort's buffers are free again
         unsigned long long total = 0;
-        return build_ploc(s, tris_out, n, nodes_out, max_height_dev, radius, scratch, scratch_bytes, &total);
+        return build_ploc(s, tris_out, n, nodes_out, max_height_dev, radius, scratch, scratch_bytes, &total, area_w);
     }
     const int iblocks = (int)((n - 1 + kBuildThreads - 1) / kBuildThreads);
     k_karras<<<iblocks, kBuildThreads, 0, s>>>(keys, n, nodes_out, parent_node, parent_leaf);
@@ -343,12 +343,13 @@ struct PlocClusters {
     int* height;
 };
 
-__device__ __forceinline__ float union_half_area(float4 alo, float4 ahi, float4 blo, float4 bhi)
+// half the weighted surface of the union of two boxes
+__device__ __forceinline__ float union_half_area(float4 alo, float4 ahi, float4 blo, float4 bhi, AreaW w)
 {
     const float dx = fmaxf(ahi.x, bhi.x) - fminf(alo.x, blo.x);
     const float dy = fmaxf(ahi.y, bhi.y) - fminf(alo.y, blo.y);
     const float dz = fmaxf(ahi.z, bhi.z) - fminf(alo.z, blo.z);
-    return dx * dy + dy * dz + dz * dx;
+    return w.z * dx * dy + w.x * dy * dz + w.y * dz * dx;
 }
 
 __global__ void __launch_bounds__(kBuildThreads) k_ploc_init(const float4* __restrict__ tris, int64_t n,
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_ploc_init(const float4* __res
     C.height[i] = 0;
 }
 
-__global__ void __launch_bounds__(kBuildThreads) k_ploc_nearest(PlocClusters C, int n, int radius, int* nn)
+__global__ void __launch_bounds__(kBuildThreads) k_ploc_nearest(PlocClusters C, int n, int radius, int* nn, AreaW w)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_ploc_nearest(PlocClusters C, 
     const int lo = max(i - radius, 0), hi = min(i + radius, n - 1);
     for (int j = lo; j <= hi; ++j) {
         if (j == i) continue;
-        const float d = union_half_area(alo, ahi, C.box[2 * (int64_t)j], C.box[2 * (int64_t)j + 1]);
+        const float d = union_half_area(alo, ahi, C.box[2 * (int64_t)j], C.box[2 * (int64_t)j + 1], w);
         if (d < best_d) {  // ascending j: ties keep the lower position
             best_d = d;
             best = j;
@@ -498,7 +499,7 @@ size_t ploc_scratch_bytes(int64_t n)
 }
 
 cudaError_t build_ploc(cudaStream_t s, const float4* tris_sorted, int64_t n, float4* nodes_out, int* max_height_dev,
-                       int radius, void* scratch, size_t scratch_bytes, unsigned long long* host_total)
+                       int radius, void* scratch, size_t scratch_bytes, unsigned long long* host_total, AreaW w)
 {
     if (n < 2) return cudaErrorInvalidValue;
     if (scratch_bytes < ploc_scratch_bytes(n)) return cudaErrorInvalidValue;
@@ -524,7 +525,7 @@ cudaError_t build_ploc(cudaStream_t s, const float4* tris_sorted, int64_t n, flo
         const int sblocks = (nc + kScanItems - 1) / kScanItems;
         int force = 0;
         for (int attempt = 0; attempt < 2; ++attempt) {
-            k_ploc_nearest<<<blocks, kBuildThreads, 0, s>>>(A, nc, radius, nn);
+            k_ploc_nearest<<<blocks, kBuildThreads, 0, s>>>(A, nc, radius, nn, w);
             k_ploc_flags<<<blocks, kBuildThreads, 0, s>>>(nn, nc, force, flags);
             k_scan_local<<<sblocks, kScanItems, 0, s>>>(flags, nc, prefix, sums);
             k_scan_sums<<<1, kScanItems, 0, s>>>(sums, sblocks);
@@ -592,15 +593,15 @@ __device__ __forceinline__ void binary_child(const float4* __restrict__ bn, int 
     }
 }
 
-__device__ __forceinline__ float half_area(const ChildBox& c)
+__device__ __forceinline__ float half_area(const ChildBox& c, AreaW w)
 {
     const float dx = c.hi[0] - c.lo[0], dy = c.hi[1] - c.lo[1], dz = c.hi[2] - c.lo[2];
-    return dx * dy + dy * dz + dz * dx;
+    return w.z * dx * dy + w.x * dy * dz + w.y * dz * dx;
 }
 
 // children of binary node b; returns the number of internal ones
 template <int W>
-__device__ int gather_children(const float4* __restrict__ bn, int b, ChildBox ch[W], int& count)
+__device__ int gather_children(const float4* __restrict__ bn, int b, ChildBox ch[W], int& count, AreaW w)
 {
     binary_child(bn, b, 0, ch[0]);
     binary_child(bn, b, 1, ch[1]);
@@ -609,8 +610,8 @@ __device__ int gather_children(const float4* __restrict__ bn, int b, ChildBox ch
         int best = -1;
         float best_a = -1.0f;
         for (int k = 0; k < count; ++k)
-            if (ch[k].ref >= 0 && half_area(ch[k]) > best_a) {
-                best_a = half_area(ch[k]);
+            if (ch[k].ref >= 0 && half_area(ch[k], w) > best_a) {
+                best_a = half_area(ch[k], w);
                 best = k;
             }
         if (best < 0) break;
@@ -643,6 +644,7 @@ struct CollapseDP {
     uint16_t* single;         // [n_binary] bit i: C(n, 1) <= D(n, i)
     unsigned* visits;         // [n_binary] children finished, bottom-up
     float c_node, c_tri;
+    AreaW w;                  // face weights of the area measure (also the largest-area rule's)
 };
 
 __global__ void k_parents(const float4* __restrict__ bn, int n_binary, int* parent_node, int* parent_leaf)
@@ -675,7 +677,7 @@ __global__ void k_collapse_dp(const float4* __restrict__ bn, int n_leaves, Colla
         for (int side = 0; side < 2; ++side) {
             binary_child(bn, node, side, cb[side]);
             if (cb[side].ref < 0) {
-                const float v = dp.c_tri * half_area(cb[side]);
+                const float v = dp.c_tri * half_area(cb[side], dp.w);
                 for (int i = 0; i < W; ++i) cc[side][i] = v;
             } else {
                 for (int i = 0; i < W; ++i) cc[side][i] = __ldcg(&dp.cost[(int64_t)cb[side].ref * W + i]);
@@ -699,7 +701,7 @@ __global__ void k_collapse_dp(const float4* __restrict__ bn, int n_leaves, Colla
                 }
             }
         }
-        const float c1 = dp.c_node * half_area(u) + D[W];
+        const float c1 = dp.c_node * half_area(u, dp.w) + D[W];
         unsigned mask = 0;
         float* out = dp.cost + (int64_t)node * W;
         uint8_t* sp = dp.split + (int64_t)node * W;
@@ -753,10 +755,10 @@ __device__ int gather_children_dp(const float4* __restrict__ bn, int b, const Co
 }
 
 template <int W>
-__device__ __forceinline__ int gather(const float4* __restrict__ bn, int b, const CollapseDP* dp, ChildBox ch[W],
-                                      int& count)
+__device__ __forceinline__ int gather(const float4* __restrict__ bn, int b, const CollapseDP& dp, int use_dp,
+                                      ChildBox ch[W], int& count)
 {
-    return dp ? gather_children_dp<W>(bn, b, *dp, ch, count) : gather_children<W>(bn, b, ch, count);
+    return use_dp ? gather_children_dp<W>(bn, b, dp, ch, count) : gather_children<W>(bn, b, ch, count, dp.w);
 }
 
 template <int W>
@@ -767,7 +769,7 @@ __global__ void k_collapse_count(const float4* __restrict__ bn, const int* __res
     if (i >= n) return;
     ChildBox ch[W];
     int count;
-    n_internal[i] = (uint32_t)gather<W>(bn, frontier[i], use_dp ? &dp : nullptr, ch, count);
+    n_internal[i] = (uint32_t)gather<W>(bn, frontier[i], dp, use_dp, ch, count);
 }
 
 __global__ void __launch_bounds__(1024) k_collapse_scan(uint32_t* __restrict__ v, int n, uint32_t* total)
@@ -809,7 +811,7 @@ __global__ void k_collapse_write(const float4* __restrict__ bn, const int* __res
     if (i >= n) return;
     ChildBox ch[W];
     int count;
-    const int internal = gather<W>(bn, frontier[i], use_dp ? &dp : nullptr, ch, count);
+    const int internal = gather<W>(bn, frontier[i], dp, use_dp, ch, count);
     const int below = pushes_in[i] + (internal > 0 ? internal - 1 : 0);
     atomicMax(stack_need, below);
     {
@@ -874,7 +876,7 @@ size_t collapse_scratch_bytes(int64_t n_binary)
 
 cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, int64_t n_binary, float4* nodes,
                          int64_t* n_wide, int* levels, int* stack_need, void* scratch, size_t scratch_bytes,
-                         int sah_dp, float tri_cost)
+                         int sah_dp, float tri_cost, AreaW area_w)
 {
     *n_wide = 0;
     *levels = 0;
@@ -891,6 +893,7 @@ cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, 
     uint32_t* total = (uint32_t*)((char*)scratch + 5 * arr);
     int* need = (int*)(total + 1);
     CollapseDP dp{};
+    dp.w = area_w;  // the largest-area rule reads it too
     if (sah_dp && n_binary < 2) sah_dp = 0;  // a single triangle: nothing to choose
     if (sah_dp) {
         auto al = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -1005,6 +1008,7 @@ struct TreeletArgs {
     unsigned long long* changed;  // treelets rewritten in the round
     int* status;              // ST_BOUNDS: a child reference out of range, or a climb longer than the bound
     float c_node, c_tri;
+    AreaW w;                  // face weights of the area measure
 };
 
 // longest climb a valid hierarchy of up to 2^31 triangles can need is far
@@ -1015,10 +1019,10 @@ struct TBox {
     float lo[3], hi[3];
 };
 
-__device__ __forceinline__ float tbox_area(const TBox& b)
+__device__ __forceinline__ float tbox_area(const TBox& b, AreaW w)
 {
     const float dx = b.hi[0] - b.lo[0], dy = b.hi[1] - b.lo[1], dz = b.hi[2] - b.lo[2];
-    return dx * dy + dy * dz + dz * dx;
+    return w.z * dx * dy + w.x * dy * dz + w.y * dz * dx;
 }
 
 __device__ __forceinline__ void tbox_grow(TBox& a, const TBox& b)
@@ -1051,7 +1055,7 @@ __device__ __forceinline__ bool ref_ok(const TreeletArgs& a, int ref)
 
 __device__ __forceinline__ float subtree_cost(const TreeletArgs& a, int ref, const TBox& b)
 {
-    return ref < 0 ? a.c_tri * tbox_area(b) : __ldcg(&a.cost[ref]);
+    return ref < 0 ? a.c_tri * tbox_area(b, a.w) : __ldcg(&a.cost[ref]);
 }
 
 __device__ void treelet_node(const TreeletArgs& a, int node)
@@ -1071,15 +1075,15 @@ __device__ void treelet_node(const TreeletArgs& a, int node)
     TBox whole = lbox[0];
     tbox_grow(whole, lbox[1]);
     // the node's cost in its current shape
-    const float c_now = a.c_node * tbox_area(whole) + lcost[0] + lcost[1];
+    const float c_now = a.c_node * tbox_area(whole, a.w) + lcost[0] + lcost[1];
     inner[0] = node;
     int k = 2, n_inner = 1;
     while (k < kTreeletLeaves) {
         int best = -1;
         float best_a = -1.0f;
         for (int i = 0; i < k; ++i)
-            if (lref[i] >= 0 && tbox_area(lbox[i]) > best_a) {
-                best_a = tbox_area(lbox[i]);
+            if (lref[i] >= 0 && tbox_area(lbox[i], a.w) > best_a) {
+                best_a = tbox_area(lbox[i], a.w);
                 best = i;
             }
         if (best < 0) break;
@@ -1130,7 +1134,7 @@ __device__ void treelet_node(const TreeletArgs& a, int node)
                 bp = p;
             }
         }
-        c[s] = a.c_node * tbox_area(u) + best;
+        c[s] = a.c_node * tbox_area(u, a.w) + best;
         split[s] = (unsigned char)bp;
     }
     // keep the current shape unless the optimum is clearly cheaper (it is
@@ -1214,7 +1218,7 @@ size_t treelet_scratch_bytes(int64_t n_tris)
 
 cudaError_t restructure_treelets(cudaStream_t s, const float4* tris, int64_t n, float4* nodes, int* max_height_dev,
                                  int rounds, float tri_cost, void* scratch, size_t scratch_bytes,
-                                 unsigned long long* changed_host, int* status)
+                                 unsigned long long* changed_host, int* status, AreaW area_w)
 {
     if (changed_host) *changed_host = 0;
     if (n < 3 || rounds <= 0) return cudaSuccess;
@@ -1230,7 +1234,7 @@ cudaError_t restructure_treelets(cudaStream_t s, const float4* tris, int64_t n, 
     unsigned long long* changed = (unsigned long long*)p;
     const int nb_blocks = (n_binary + 255) / 256;
     TreeletArgs a{tris, (int)n, n_binary, nodes, parent_node, parent_leaf, visits, cost, changed, status,
-                  1.0f, tri_cost};
+                  1.0f, tri_cost, area_w};
     cudaError_t e = cudaMemsetAsync(changed, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     for (int r = 0; r < rounds; ++r) {

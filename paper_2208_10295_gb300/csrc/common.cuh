@@ -144,12 +144,21 @@ struct LaunchCfg {
 
 // ------------------------------------------------------------------ kernel launchers
 
+// Weights of a box's faces in the area measure the builders compare: half the
+// weighted surface of a box of extents (dx, dy, dz) is
+//   z dx dy + x dy dz + y dz dx
+// (x weights the faces normal to x, ...); 1, 1, 1 is half the surface area.
+struct AreaW {
+    float x, y, z;
+};
+
 // build.cu
 struct BuildScratch;
 cudaError_t build_lbvh(cudaStream_t s, const float* verts, int64_t n_verts, const uint32_t* tris,
                        const uint16_t* mat, const uint32_t* inst, int64_t n_tris, float4* nodes_out,
                        float4* tris_out, uint32_t* leaf_tri_out, int* status, int* max_depth_dev,
-                       void* scratch, size_t scratch_bytes, int method = 0, int ploc_radius = 16);
+                       void* scratch, size_t scratch_bytes, int method = 0, int ploc_radius = 16,
+                       AreaW area_w = AreaW{1.0f, 1.0f, 1.0f});
 // scratch of the clustering build (method 1), on top of nothing: it reuses build_lbvh's scratch
 size_t ploc_scratch_bytes(int64_t n_tris);
 size_t build_scratch_bytes(int64_t n_tris);
@@ -161,7 +170,7 @@ size_t build_scratch_bytes(int64_t n_tris);
 // tri_cost relative to a wide-node visit) instead of opening the largest child
 cudaError_t collapse_bvh(cudaStream_t s, int width, const float4* binary_nodes, int64_t n_binary, float4* nodes,
                          int64_t* n_wide, int* levels, int* stack_need, void* scratch, size_t scratch_bytes,
-                         int sah_dp = 0, float tri_cost = 1.0f);
+                         int sah_dp = 0, float tri_cost = 1.0f, AreaW area_w = AreaW{1.0f, 1.0f, 1.0f});
 size_t collapse_scratch_bytes(int64_t n_binary);
 // treelet restructuring of the binary hierarchy (rounds > 0, n_tris >= 3);
 // recomputes the root height; *changed_host (valid after a stream
@@ -170,7 +179,8 @@ size_t collapse_scratch_bytes(int64_t n_binary);
 size_t treelet_scratch_bytes(int64_t n_tris);
 cudaError_t restructure_treelets(cudaStream_t s, const float4* tris, int64_t n, float4* nodes, int* max_height_dev,
                                  int rounds, float tri_cost, void* scratch, size_t scratch_bytes,
-                                 unsigned long long* changed_host, int* status);
+                                 unsigned long long* changed_host, int* status,
+                                 AreaW area_w = AreaW{1.0f, 1.0f, 1.0f});
 
 // sort.cu: stable LSD radix sort of (key, value) pairs, keys of `key_bits` bits
 size_t radix_sort_scratch_bytes(int64_t n);

@@ -150,6 +150,7 @@ struct lidar_ctx {
     int collapse = 0;         // wide nodes: 0 open the largest child, 1 SAH dynamic program
     float tri_cost = 1.0f;    // a triangle test's cost relative to a node visit (collapse 1, treelets)
     int treelet_rounds = 0;   // rounds of treelet restructuring of the binary tree
+    AreaW area_w{1.0f, 1.0f, 1.0f};  // face weights of the builders' area measure
     std::set<lidar_scene*> scenes;
 };
 
@@ -373,11 +374,11 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         cudaEventRecord(e0, c->stream);
         cudaError_t e = build_lbvh(c->stream, verts, n_verts, tris, mat, inst, n_tris, s->nodes, s->tris,
                                    s->leaf_tri, c->status_dev, c->aux_dev, c->scratch, c->scratch_bytes,
-                                   n_tris >= 2 ? c->build_method : 0, c->ploc_radius);
+                                   n_tris >= 2 ? c->build_method : 0, c->ploc_radius, c->area_w);
         unsigned long long treelets = 0;
         if (e == cudaSuccess && c->treelet_rounds > 0)
             e = restructure_treelets(c->stream, s->tris, n_tris, s->nodes, c->aux_dev, c->treelet_rounds, c->tri_cost,
-                                     c->scratch, c->scratch_bytes, &treelets, c->status_dev);
+                                     c->scratch, c->scratch_bytes, &treelets, c->status_dev, c->area_w);
         cudaEventRecord(e1, c->stream);
         if (e != cudaSuccess) {
             set_error(std::string("lidar_scene_build: ") + cudaGetErrorString(e));
@@ -405,7 +406,7 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         cudaEventRecord(e0, c->stream);
         int need4 = 0;
         cudaError_t e4 = collapse_bvh(c->stream, 4, s->nodes, s->n_nodes, s->nodes4, &s->n_nodes4, &s->levels4,
-                                      &need4, c->scratch, c->scratch_bytes, c->collapse, c->tri_cost);
+                                      &need4, c->scratch, c->scratch_bytes, c->collapse, c->tri_cost, c->area_w);
         // the 8-wide tree: count its nodes and the stack it could need, then
         // write it into an exact allocation; a tree that could need more than
         // the traversal stack is not kept (the 4-wide and binary ones serve)
@@ -413,7 +414,7 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
         int levels8 = 0, need8 = 0;
         if (e4 == cudaSuccess)
             e4 = collapse_bvh(c->stream, 8, s->nodes, s->n_nodes, nullptr, &n8, &levels8, &need8, c->scratch,
-                              c->scratch_bytes, c->collapse, c->tri_cost);
+                              c->scratch_bytes, c->collapse, c->tri_cost, c->area_w);
         if (e4 == cudaSuccess && need8 <= kTraversalStack && n8 > 0) {
             if (dev_alloc((void**)&s->nodes8, (size_t)n8 * 16 * sizeof(float4)) != cudaSuccess) {
                 cudaGetLastError();
@@ -421,7 +422,7 @@ lidar_status lidar_scene_build(lidar_ctx* c, const float* verts, int64_t n_verts
                 return fail(LIDAR_ENOMEM);
             }
             e4 = collapse_bvh(c->stream, 8, s->nodes, s->n_nodes, s->nodes8, &s->n_nodes8, &s->levels8, &need8,
-                              c->scratch, c->scratch_bytes, c->collapse, c->tri_cost);
+                              c->scratch, c->scratch_bytes, c->collapse, c->tri_cost, c->area_w);
             s->bytes += s->n_nodes8 * 256;
         }
         cudaEventRecord(e1, c->stream);
@@ -1571,11 +1572,15 @@ lidar_status lidar_set_build_options(lidar_ctx* c, const lidar_build_options* o)
     LIDAR_CHECK_ARG(o->tri_cost > 0.0f && o->tri_cost <= 100.0f, "lidar_set_build_options: tri_cost in (0, 100]");
     LIDAR_CHECK_ARG(o->treelet_rounds >= 0 && o->treelet_rounds <= 8,
                     "lidar_set_build_options: treelet_rounds in [0, 8]");
+    for (int k = 0; k < 3; ++k)
+        LIDAR_CHECK_ARG(o->area_weight[k] > 0.0f && o->area_weight[k] <= 100.0f,
+                        "lidar_set_build_options: area_weight in (0, 100]");
     c->build_method = o->method;
     c->ploc_radius = o->ploc_radius;
     c->collapse = o->collapse;
     c->tri_cost = o->tri_cost;
     c->treelet_rounds = o->treelet_rounds;
+    c->area_w = AreaW{o->area_weight[0], o->area_weight[1], o->area_weight[2]};
     return LIDAR_OK;
 }
 
@@ -1587,6 +1592,9 @@ lidar_status lidar_get_build_options(lidar_ctx* c, lidar_build_options* o)
     o->collapse = c->collapse;
     o->tri_cost = c->tri_cost;
     o->treelet_rounds = c->treelet_rounds;
+    o->area_weight[0] = c->area_w.x;
+    o->area_weight[1] = c->area_w.y;
+    o->area_weight[2] = c->area_w.z;
     return LIDAR_OK;
 }
 

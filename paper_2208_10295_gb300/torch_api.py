@@ -320,24 +320,27 @@ class Lidar:
 
     # ----------------------------------------------------------- build options
     def set_build_options(self, method: int = 1, ploc_radius: int = 16, collapse: int = None, tri_cost: float = None,
-                          treelet_rounds: int = None):
+                          treelet_rounds: int = None, area_weight=None):
         """Hierarchy of scenes built afterwards: 0 Karras LBVH, 1 PLOC (default);
         `treelet_rounds` rounds of treelet restructuring of the binary tree;
         wide-node children by the largest-area rule (collapse 0) or the SAH
         dynamic program (collapse 1); `tri_cost` is a triangle test's cost
-        relative to a node visit in both surface-area programs.  Options not
-        given keep their current values."""
+        relative to a node visit in both surface-area programs; `area_weight`
+        (x, y, z) weights a box's faces in every area the builders compare.
+        Options not given keep their current values."""
         cur = self.build_options()
+        aw = cur["area_weight"] if area_weight is None else tuple(float(v) for v in area_weight)
         o = C.lidar_build_options(method, ploc_radius, cur["collapse"] if collapse is None else collapse,
                                   cur["tri_cost"] if tri_cost is None else tri_cost,
-                                  cur["treelet_rounds"] if treelet_rounds is None else treelet_rounds)
+                                  cur["treelet_rounds"] if treelet_rounds is None else treelet_rounds,
+                                  (ctypes.c_float * 3)(*aw))
         C.check(C.lidar_set_build_options(self.handle, ctypes.byref(o)), "lidar_set_build_options")
 
     def build_options(self):
         o = C.lidar_build_options()
         C.check(C.lidar_get_build_options(self.handle, ctypes.byref(o)), "lidar_get_build_options")
         return {"method": o.method, "ploc_radius": o.ploc_radius, "collapse": o.collapse, "tri_cost": o.tri_cost,
-                "treelet_rounds": o.treelet_rounds}
+                "treelet_rounds": o.treelet_rounds, "area_weight": tuple(o.area_weight)}
 
     # ----------------------------------------------------------- tuning
     def launch_config(self):
