@@ -349,6 +349,18 @@ lidar_status lidar_cast_backward_mse(lidar_ctx* ctx, int64_t n_beams, const lida
                                      const float* target_I_dev, const uint8_t* target_valid_dev,
                                      float* loss_dev, float* grad_table_dev, float* grad_gain_dev);
 
+/* As lidar_cast_backward_mse, and writes N, the number of beams the mean
+ * runs over, to n_used_dev (device, one uint64; LIDAR_EINVAL if NULL).  For a
+ * batch whose beams are split over ranks (data-parallel fitting): rank r
+ * computes its loss L_r and gradients G_r (into zeroed buffers) over its own
+ * beams with its own N_r; the batch's loss and gradients are then
+ * sum_r N_r L_r / sum_r N_r and sum_r N_r G_r / sum_r N_r, one all-reduce of
+ * the (N_r x, N_r) vector. */
+lidar_status lidar_cast_backward_mse_count(lidar_ctx* ctx, int64_t n_beams, const lidar_beams* tape, float gain,
+                                           const float* target_I_dev, const uint8_t* target_valid_dev,
+                                           float* loss_dev, float* grad_table_dev, float* grad_gain_dev,
+                                           uint64_t* n_used_dev);
+
 /* Allocation-free variant of lidar_cast_backward_mse (no counterpart in the
  * paper; it exists for callers that must not allocate device memory: sensor
  * loops with hard real-time deadlines that cannot afford cudaMalloc's implicit

@@ -138,6 +138,8 @@ _PROTOS = [
                                            c_vp, c_vp, c_vp]),
     ("lidar_cast_backward_mse", ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.POINTER(lidar_beams),
                                                ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    ("lidar_cast_backward_mse_count", ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.POINTER(lidar_beams),
+                                                     ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     ("lidar_cast_backward_mse_noalloc", ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, c_vp, c_vp, c_vp, c_vp,
                                                        ctypes.c_int32, ctypes.c_float, c_vp, c_vp, c_vp, c_vp,
                                                        c_vp]),
@@ -227,6 +229,7 @@ lidar_graph_launch = _fwd("lidar_graph_launch")
 lidar_graph_free = _fwd("lidar_graph_free")
 lidar_cast_backward = _fwd("lidar_cast_backward")
 lidar_cast_backward_mse = _fwd("lidar_cast_backward_mse")
+lidar_cast_backward_mse_count = _fwd("lidar_cast_backward_mse_count")
 lidar_cast_backward_mse_noalloc = _fwd("lidar_cast_backward_mse_noalloc")
 lidar_count_work = _fwd("lidar_count_work")
 lidar_raster_cast = _fwd("lidar_raster_cast")

@@ -297,11 +297,12 @@ constexpr int kFinalizeThreads = 256;
 __global__ void __launch_bounds__(kFinalizeThreads) k_adj_finalize(
     int n_acc, const unsigned long long* __restrict__ acc, const unsigned int* __restrict__ absmax_bits,
     const unsigned long long* __restrict__ count, int mse, const double* __restrict__ loss_partials, int n_partials,
-    float* grad_table, float* grad_gain, float* loss)
+    float* grad_table, float* grad_gain, float* loss, unsigned long long* n_used)
 {
     const float scale = fixed_scale(*absmax_bits, *count);
     const float inv_scale = __frcp_rn(scale);  // exact: the scale is a power of two
     const unsigned long long N = *count;
+    if (n_used && blockIdx.x == 0 && threadIdx.x == 0) *n_used = N;
     // FP32 (FP64 is slow on this part): the integer sum rounded once to 24
     // bits, an exact scaling, one rounded normalisation
     const float norm = mse ? (N ? __frcp_rn((float)N) : 0.0f) : 1.0f;
@@ -382,6 +383,7 @@ struct OneArgs {
     float* loss;
     float* grad_table;
     float* grad_gain;
+    unsigned long long* n_used;  // NULL, or the number of beams the mean runs over
 };
 
 __device__ __forceinline__ uint64_t adj_global_ns()
@@ -887,6 +889,7 @@ __global__ void __launch_bounds__(kOneThreads, 2) k_adj_onepass(const __grid_con
     const int S = one_shift(gmax, n);
     // block 0's last warp writes the loss: the partials in a fixed order (lane
     // l takes blocks l, l + 32, ..., then a fixed shuffle tree)
+    if (blk == 0 && tid == 0 && a.n_used) *a.n_used = N;
     if (blk == 0 && warp == kOneWarps - 1 && a.loss) {
         double t = 0.0;
         for (int j = lane; j < G; j += 32) t += __ldcg(&a.blk_loss[j]);
@@ -983,7 +986,7 @@ cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid
                                  const float* theta_deg, const float* rf, TableDev T, float gain,
                                  const float* grad_I, const float* target_I, const uint8_t* target_valid,
                                  float* loss, float* grad_table, float* grad_gain, void* scratch,
-                                 size_t scratch_bytes)
+                                 size_t scratch_bytes, unsigned long long* n_used)
 {
     if (scratch_bytes < backward_scratch_bytes(T.n_mat)) return cudaErrorInvalidValue;
     const int n_acc = T.n_mat * LIDAR_TABLE_SIZE + 1;
@@ -1046,7 +1049,7 @@ cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid
             n, valid, mat, theta_deg, rf, T, gain, grad_I, target_I, target_valid, absmax, count, acc, partials,
             use_shared);
     k_adj_finalize<<<(n_acc + kFinalizeThreads - 1) / kFinalizeThreads, kFinalizeThreads, 0, s>>>(
-        n_acc, acc, absmax, count, target_I != nullptr, partials, blocks, grad_table, grad_gain, loss);
+        n_acc, acc, absmax, count, target_I != nullptr, partials, blocks, grad_table, grad_gain, loss, n_used);
     return cudaGetLastError();
 }
 
@@ -1062,7 +1065,8 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
                                          const float* grad_I, const float* target_I, const uint8_t* target_valid,
                                          float* loss, float* grad_table, float* grad_gain, void* scratch,
                                          size_t scratch_bytes, unsigned long long* arrivals,
-                                         unsigned long long* arrivals_base, int* status, uint64_t wait_ns, int num_sms)
+                                         unsigned long long* arrivals_base, int* status, uint64_t wait_ns, int num_sms,
+                                         unsigned long long* n_used)
 {
     const int n_acc = T.n_mat * LIDAR_TABLE_SIZE + 1;
     if (num_sms < 1 || scratch_bytes < onepass_scratch_bytes(T.n_mat, num_sms)) return cudaErrorInvalidValue;
@@ -1151,6 +1155,7 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
     a.loss = loss;
     a.grad_table = grad_table;
     a.grad_gain = grad_gain;
+    a.n_used = n_used;
     void* args[] = {&a};
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kOneThreads), args, smem, s);
     if (e != cudaSuccess)

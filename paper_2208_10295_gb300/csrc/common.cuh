@@ -244,12 +244,14 @@ cudaError_t launch_cast_backward(cudaStream_t s, int64_t n, const uint8_t* valid
                                  const float* theta_deg, const float* rf, TableDev table, float gain,
                                  const float* grad_I, const float* target_I, const uint8_t* target_valid,
                                  float* loss, float* grad_table, float* grad_gain, void* scratch,
-                                 size_t scratch_bytes);
+                                 size_t scratch_bytes, unsigned long long* n_used = nullptr);
 size_t backward_scratch_bytes(int M);
 // One-pass variant (one cooperative launch, the tape read once); returns
 // cudaErrorNotSupported when the table's accumulators do not fit in shared
-// memory beside the copy stages (then launch_cast_backward applies).  ctl: two
-// words that are zero between calls (the kernel leaves them so).
+// memory beside the copy stages (then launch_cast_backward applies).
+// arrivals: the grid-wait counter, *arrivals_base its value before this
+// launch (advanced by the launcher).  n_used (device, may be NULL) receives
+// the number of beams the mean runs over.
 size_t onepass_scratch_bytes(int M, int num_sms);
 cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_t* valid, const uint16_t* mat,
                                          const float* theta_deg, const float* rf, TableDev table, float gain,
@@ -257,7 +259,7 @@ cudaError_t launch_cast_backward_onepass(cudaStream_t s, int64_t n, const uint8_
                                          float* loss, float* grad_table, float* grad_gain, void* scratch,
                                          size_t scratch_bytes, unsigned long long* arrivals,
                                          unsigned long long* arrivals_base, int* status, uint64_t wait_ns,
-                                         int num_sms);
+                                         int num_sms, unsigned long long* n_used = nullptr);
 // address (on the current device) and size of the allocation-free variant's scratch array
 cudaError_t noalloc_scratch(void** ptr, size_t* bytes);
 

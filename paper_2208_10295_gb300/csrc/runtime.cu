@@ -1342,7 +1342,8 @@ void lidar_graph_free(lidar_graph* gr)
 
 static lidar_status backward_common(lidar_ctx* c, int64_t n, const lidar_beams* tape, float gain,
                                     const float* grad_I, const float* target_I, const uint8_t* target_valid,
-                                    float* loss, float* grad_table, float* grad_gain)
+                                    float* loss, float* grad_table, float* grad_gain,
+                                    unsigned long long* n_used = nullptr)
 {
     LIDAR_CHECK_ARG(c != nullptr && tape != nullptr, "lidar_cast_backward: ctx/tape is NULL");
     LIDAR_CHECK_ARG(n >= 0, "lidar_cast_backward: negative beam count");
@@ -1363,11 +1364,11 @@ static lidar_status backward_common(lidar_ctx* c, int64_t n, const lidar_beams* 
         e = launch_cast_backward_onepass(c->stream, n, tape->valid, tape->mat, tape->theta_deg, tape->rf, c->table,
                                          gain, grad_I, target_I, target_valid, loss, grad_table, grad_gain, c->scratch,
                                          c->scratch_bytes, c->adj_arrivals, &c->adj_arrivals_base, c->status_dev,
-                                         c->cfg.wait_ns, c->num_sms);
+                                         c->cfg.wait_ns, c->num_sms, n_used);
     if (e == cudaErrorNotSupported)
         e = launch_cast_backward(c->stream, n, tape->valid, tape->mat, tape->theta_deg, tape->rf, c->table, gain,
                                  grad_I, target_I, target_valid, loss, grad_table, grad_gain, c->scratch,
-                                 c->scratch_bytes);
+                                 c->scratch_bytes, n_used);
     LIDAR_CUDA(e);
     return LIDAR_OK;
 }
@@ -1388,6 +1389,19 @@ lidar_status lidar_cast_backward_mse(lidar_ctx* c, int64_t n, const lidar_beams*
     LIDAR_CHECK_ARG(n == 0 || (target_I != nullptr && target_valid != nullptr),
                     "lidar_cast_backward_mse: targets are NULL");
     return backward_common(c, n, tape, gain, nullptr, target_I, target_valid, loss, grad_table, grad_gain);
+}
+
+lidar_status lidar_cast_backward_mse_count(lidar_ctx* c, int64_t n, const lidar_beams* tape, float gain,
+                                           const float* target_I, const uint8_t* target_valid, float* loss,
+                                           float* grad_table, float* grad_gain, uint64_t* n_used)
+{
+    NvtxRange nvtx_("lidar_cast_backward_mse_count");
+    LIDAR_CHECK_ARG(n == 0 || (target_I != nullptr && target_valid != nullptr),
+                    "lidar_cast_backward_mse_count: targets are NULL");
+    LIDAR_CHECK_ARG(n_used != nullptr, "lidar_cast_backward_mse_count: n_used is NULL");
+    static_assert(sizeof(uint64_t) == sizeof(unsigned long long), "64-bit count");
+    return backward_common(c, n, tape, gain, nullptr, target_I, target_valid, loss, grad_table, grad_gain,
+                           reinterpret_cast<unsigned long long*>(n_used));
 }
 
 // Device address of the allocation-free variant's scratch array, looked up once

@@ -238,12 +238,22 @@ class Lidar:
         C.check(C.lidar_cast_backward(self.handle, n, ctypes.byref(ts), float(gain), _ptr(grad_I.contiguous()),
                                       _ptr(grad_table), _ptr(grad_gain)), "lidar_cast_backward")
 
-    def cast_backward_mse(self, tape, gain: float, target_I, target_valid, loss, grad_table, grad_gain):
+    def cast_backward_mse(self, tape, gain: float, target_I, target_valid, loss, grad_table, grad_gain,
+                          n_used: torch.Tensor = None):
+        """Fused-MSE adjoint; `n_used` (int64 [1] on the device, optional)
+        receives the number of beams the mean runs over (for combining the
+        partial results of ranks, `combine_mse` / `allreduce_mse`)."""
         n = tape["valid"].shape[0]
         ts = self.beams_struct(tape)
-        C.check(C.lidar_cast_backward_mse(self.handle, n, ctypes.byref(ts), float(gain), _ptr(target_I),
-                                          _ptr(target_valid), _ptr(loss), _ptr(grad_table), _ptr(grad_gain)),
-                "lidar_cast_backward_mse")
+        if n_used is None:
+            C.check(C.lidar_cast_backward_mse(self.handle, n, ctypes.byref(ts), float(gain), _ptr(target_I),
+                                              _ptr(target_valid), _ptr(loss), _ptr(grad_table), _ptr(grad_gain)),
+                    "lidar_cast_backward_mse")
+        else:
+            C.check(C.lidar_cast_backward_mse_count(self.handle, n, ctypes.byref(ts), float(gain), _ptr(target_I),
+                                                    _ptr(target_valid), _ptr(loss), _ptr(grad_table),
+                                                    _ptr(grad_gain), _ptr(n_used)),
+                    "lidar_cast_backward_mse_count")
 
     def count_work(self, scene: Scene, frames, seed: int, beam_cost: torch.Tensor = None):
         """Work of one cast (instrumented kernel): node fetches, triangle tests,
@@ -475,3 +485,49 @@ class LidarCast(torch.autograd.Function):
         lidar.cast_backward(ctx.tape, float(gain), grad_I.contiguous().float(), gT, gg)
         gp = lidar.build_tables_backward(params, gT)
         return gp, gg.reshape(gain.shape), None, None, None, None, None
+
+
+# ------------------------------------------------------- data-parallel fitting
+#
+# When the beams of one batch (frames of a trajectory) are split over ranks,
+# each rank runs the fused-MSE adjoint over its own beams, into zeroed
+# gradient buffers, with `n_used` counting the beams its mean ran over.  The
+# batch's mean-squared loss and gradients are the partial results weighted by
+# their counts: sum_r N_r x_r / sum_r N_r.  `combine_mse` does that for a list
+# of partials held by one process; `allreduce_mse` does it across the ranks of
+# a torch.distributed group with one all-reduce (FP64) of the weighted vector
+# [N L, N dL/dT, N dL/dg, N] — the one exchange step of a sharded fit.
+
+def _mse_vector(loss, grad_table, grad_gain, n_used):
+    n = n_used.reshape(1).to(torch.float64)
+    return torch.cat([loss.reshape(1).double() * n, grad_table.reshape(-1).double() * n,
+                      grad_gain.reshape(1).double() * n, n])
+
+
+def _mse_unpack(vec, loss, grad_table, grad_gain):
+    N = vec[-1]
+    scale = torch.where(N > 0, 1.0 / N, torch.zeros_like(N))
+    loss.copy_((vec[0] * scale).reshape(loss.shape).to(loss.dtype))
+    k = grad_table.numel()
+    grad_table.copy_((vec[1:1 + k] * scale).reshape(grad_table.shape).to(grad_table.dtype))
+    grad_gain.copy_((vec[1 + k] * scale).reshape(grad_gain.shape).to(grad_gain.dtype))
+    return N
+
+
+def combine_mse(parts, loss, grad_table, grad_gain):
+    """Batch loss and gradients from per-part results `parts` = [(loss,
+    grad_table, grad_gain, n_used), ...] (each over its own beams), written
+    into loss, grad_table and grad_gain; returns the total count (a 0-d FP64
+    tensor on the parts' device)."""
+    vec = sum(_mse_vector(*p) for p in parts)
+    return _mse_unpack(vec, loss, grad_table, grad_gain)
+
+
+def allreduce_mse(loss, grad_table, grad_gain, n_used, group=None):
+    """In place on every rank of `group`: this rank's loss, grad_table and
+    grad_gain (over its own n_used beams) become the whole batch's; returns
+    the batch's count (a 0-d FP64 tensor)."""
+    import torch.distributed as dist
+    vec = _mse_vector(loss, grad_table, grad_gain, n_used)
+    dist.all_reduce(vec, op=dist.ReduceOp.SUM, group=group)
+    return _mse_unpack(vec, loss, grad_table, grad_gain)

@@ -307,6 +307,44 @@ def test_adjoint_synthetic_tape_vs_oracle(L, n, M):
     assert gg == pytest.approx(gg_ref, rel=NORM_RTOL)
 
 
+@pytest.mark.parametrize("M", [32, 200])
+def test_adjoint_count_and_split_tape_combined(L, M):
+    """`n_used` is the number of beams valid in both tape and targets (the one
+    -pass kernel for 32 materials, the separate passes for 200), and a tape
+    split in three uneven parts, each part's adjoint combined by its count
+    (`combine_mse`, the arithmetic the ranks of a sharded fit all-reduce),
+    gives the whole tape's loss and gradients."""
+    from paper_2208_10295_gb300.torch_api import combine_mse
+    n = 1_000_003
+    t, params, table, tape, tI, tv = _synthetic(L, n, M, seed=7300 + M)
+    dev = L.device
+
+    def run(lo, hi):
+        loss = torch.zeros(1, device=dev)
+        gT = torch.zeros_like(table)
+        gg = torch.zeros(1, device=dev)
+        cnt = torch.full((1,), -1, dtype=torch.int64, device=dev)
+        L.cast_backward_mse({k: v[lo:hi] for k, v in tape.items()}, 1.25, tI[lo:hi], tv[lo:hi], loss, gT, gg,
+                            n_used=cnt)
+        assert L.sync_status() == 0
+        return loss, gT, gg, cnt
+
+    whole = run(0, n)
+    expect = int(((t["valid"] != 0) & (t["target_valid"] != 0)).sum())
+    assert int(whole[3].item()) == expect
+    cuts = [0, 123_457, 700_001, n]
+    parts = [run(a, b) for a, b in zip(cuts[:-1], cuts[1:])]
+    assert sum(int(p[3].item()) for p in parts) == expect
+    loss = torch.zeros(1, device=dev)
+    gT = torch.zeros_like(table)
+    gg = torch.zeros(1, device=dev)
+    total = combine_mse(parts, loss, gT, gg)
+    assert int(total.item()) == expect
+    assert loss.item() == pytest.approx(whole[0].item(), rel=1e-6)
+    close_grad(gT.cpu().numpy(), whole[1].cpu().numpy(), f"split tape M={M} dL/dT")
+    assert gg.item() == pytest.approx(whole[2].item(), rel=1e-6)
+
+
 def test_adjoint_synthetic_unaligned_and_repeat_bit_identical(L):
     """Tape views one element past an aligned address (the threads load the
     tape; no copy engine) give the gradients of aligned copies of the same
