@@ -38,6 +38,8 @@ METRIC = "LiDAR rays/sec (128-ch, 1M-tri scene) & roofline %; fwd+bwd vs plain f
 UNIT = "rays/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6800.0
+# The launch the headline kernel's ncu captures ran (k_cast<0, 2, 2>)
+HEADLINE_LAUNCH = {"traversal": (2,), "block_threads": (256,), "blocks_per_sm": (2,)}
 # The hierarchies the benchmark walks: PLOC plus rounds of treelet
 # restructuring, with the builders' area measure weighting the boxes' top and
 # bottom faces (normal to z) less than their sides — the choices that cast
@@ -75,6 +77,7 @@ NCU_FP32 = {"sources": "43cc999e0fe54cea", "tree": dict(treelet_rounds=2, area_w
 # Binding-unit fractions of one city frame launch (ncu --set full,
 # profiles/k_cast_city_ncu_full.md), with the sources and tree it ran
 NCU_CITY_UNITS = {"sources": "43cc999e0fe54cea", "tree": dict(treelet_rounds=8, area_weight=(1.0, 1.0, 0.35)),
+                  "kernel": "k_cast<0, 4, 2>",
                   "issue_active_pct": 74.8, "l1tex_throughput_pct": 62.9, "fma_pipe_pct": 42.7, "alu_pipe_pct": 53.5}
 KERNEL_SOURCES = ("cast.cu", "shade.cuh", "trace.cuh", "common.cuh", "philox.cuh")
 # DRAM traffic (read + write) of one launch of the one-pass adjoint on the
@@ -95,6 +98,15 @@ def kernel_digest():
             data = data[:data.find(b"// ------------------------------------------------------------------ kernel launchers")]
         h.update(data)
     return h.hexdigest()[:16]
+
+
+def kernel_name(cfg):
+    """The cast kernel instantiation a launch configuration runs: k_cast<0,
+    register variant, traversal>, the variant from the requested residency
+    (threads x blocks per SM <= 512: 128 registers, <= 768: 85, else 64)."""
+    threads = cfg["block_threads"] * cfg["blocks_per_sm"]
+    variant = 2 if threads <= 512 else (3 if threads <= 768 else 4)
+    return f"k_cast<0, {variant}, {cfg['traversal']}>"
 
 
 def adjoint_digest():
@@ -258,8 +270,13 @@ def run_ours(args, rank, world, local_rank):
     near = frames.copy()
     near[0]["pose"][3] += 1.0
     near[0]["pose"][7] += 0.5
+    # the headline's kernel is the one the ncu captures describe: the 4-wide
+    # walk at 256 threads x 2 blocks per SM (the 8-wide walk and other shapes
+    # measure within a few per cent of it on this tree and would make the
+    # captured traffic and unit fractions another kernel's); ray order,
+    # schedule and the fused scatter are tuned
     tuned_cfg, tuned_ms = autotune(L, scene, frames, w.seed, schedule_frames=near, use_cache=not args.retune,
-                                   points=True)
+                                   points=True, restrict=HEADLINE_LAUNCH)
     n_beams = L.total_beams(frames)
     build_ms = scene.info()["build_ms"]
     pts = L.alloc_points(n_beams)
@@ -440,7 +457,9 @@ def run_ours(args, rank, world, local_rank):
     visit_bytes = counters["node_visits"] * counters["node_bytes"] + counters["tri_tests"] * 48 + counters["io_bytes"]
     uniq_bytes = counters["unique_node_bytes"] + counters["unique_tri_bytes"] + counters["io_bytes"]
     achieved = visit_bytes / (kernel_ms / 1e3) / 1e9
-    same_kernel = NCU_TRAFFIC["sources"] == kernel_digest() and NCU_TRAFFIC["tree"] == CFG1_TREE
+    captured_launch = all(tuned_cfg.get(k) in v for k, v in HEADLINE_LAUNCH.items())
+    same_kernel = (NCU_TRAFFIC["sources"] == kernel_digest() and NCU_TRAFFIC["tree"] == CFG1_TREE and
+                   captured_launch)
     traffic = NCU_TRAFFIC["bytes"] if same_kernel else None
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
     # FP32 ops per child box of a fetched node: 6 slab subtracts + 6 multiplies, 3 max (entry, with t_eps),
@@ -451,7 +470,7 @@ def run_ours(args, rank, world, local_rank):
     # the measured FP32 rate, scaled from the probe's clock to the clock the cast ran at
     fp_probe = fp32_peak
     fp_peak = fp_probe["tflops"] * (sm_mhz / fp_probe["sm_mhz"] if fp_probe.get("sm_mhz") else 1.0)
-    ncu_ok = NCU_FP32["sources"] == kernel_digest() and NCU_FP32["tree"] == CFG1_TREE
+    ncu_ok = NCU_FP32["sources"] == kernel_digest() and NCU_FP32["tree"] == CFG1_TREE and captured_launch
     ncu_fp32_tf = NCU_FP32["fp32_flops"] / (kernel_ms / 1e3) / 1e12 if ncu_ok else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -704,7 +723,8 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
                            "binding_unit": (dict(NCU_CITY_UNITS, source="ncu --set full of one city frame "
                                                                          "launch (profiles/k_cast_city_ncu_full.md)")
                                             if NCU_CITY_UNITS["sources"] == kernel_digest() and
-                                            NCU_CITY_UNITS["tree"] == CITY_TREE else None)}}
+                                            NCU_CITY_UNITS["tree"] == CITY_TREE and
+                                            kernel_name(cfg4) == NCU_CITY_UNITS["kernel"] else None)}}
         # forward with tape (each beam's strongest sub-ray) + fused-MSE adjoint to the 64 x 91 table, the
         # widths and the gain, targets from the hidden table
         del pts4

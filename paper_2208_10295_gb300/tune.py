@@ -62,8 +62,12 @@ def _time_cast(L, scene, frames, seed, out, pts, flush, reps):
     return statistics.median(ts)
 
 
-def candidates(points=False, wide8=True):
-    for bt, bps, tv, ro, sc, fs in itertools.product(*SPACE.values()):
+def candidates(points=False, wide8=True, restrict=None):
+    """Every valid configuration of SPACE; `restrict` (key -> allowed values)
+    narrows the search to part of it."""
+    space = {k: tuple(v for v in vals if restrict is None or k not in restrict or v in restrict[k])
+             for k, vals in SPACE.items()}
+    for bt, bps, tv, ro, sc, fs in itertools.product(*space.values()):
         if bt * bps > 2048 or bt * bps < 256:
             continue
         if tv == 3 and not wide8:
@@ -89,15 +93,18 @@ def apply(L, scene, cfg, schedule_frames, seed):
 
 
 def autotune(L, scene, frames, seed, schedule_frames=None, cache_path=DEFAULT_CACHE, reps=8, flush_l2=True,
-             use_cache=True, verbose=False, points=False):
+             use_cache=True, verbose=False, points=False, restrict=None):
     """Picks and applies the fastest configuration for casting `frames`
     (`points`: the cast plus the ordered compaction into a point cloud,
     otherwise the cast to dense valid flags).  `schedule_frames` (default
     `frames`) are the poses whose measured costs order the rays for the cost
     schedules: pass a nearby pose (the previous frame) to keep the
-    measurement honest.  Returns (config, ms)."""
+    measurement honest.  `restrict` (key -> allowed values) narrows the
+    search.  Returns (config, ms)."""
     schedule_frames = frames if schedule_frames is None else schedule_frames
     key = workload_key(L, scene, frames) + ("|points" if points else "|dense")
+    if restrict:
+        key += "|" + json.dumps({k: list(v) for k, v in sorted(restrict.items())})
     cache = {}
     if use_cache and cache_path and os.path.exists(cache_path):
         try:
@@ -114,7 +121,7 @@ def autotune(L, scene, frames, seed, schedule_frames=None, cache_path=DEFAULT_CA
     pts = L.alloc_points(n) if points else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=L.device) if flush_l2 else None
     best = None
-    for cfg in candidates(points, wide8=scene.info()["n_nodes8"] > 0 or scene.n_tris == 0):
+    for cfg in candidates(points, wide8=scene.info()["n_nodes8"] > 0 or scene.n_tris == 0, restrict=restrict):
         apply(L, scene, cfg, schedule_frames, seed)
         ms = _time_cast(L, scene, frames, seed, out, pts, flush, reps)
         if verbose:

@@ -97,10 +97,26 @@ def test_small_terrain_subrays(L, n_subrays):
 def test_cfg1_full_frame_every_beam(L):
     """The headline frame (262,144 beams over 1,036,288 triangles), every beam
     against the oracle's brute force (about 3.5 minutes of oracle time on 16
-    host cores), the GPU in the benchmark's launch configuration."""
-    from bench import build_cfg1  # the hierarchy the benchmark walks (PLOC + treelet rounds)
+    host cores), the GPU on the benchmark's tree, in its launch shape, with
+    its per-beam cost-bucket schedule measured on a pose 1.1 m away."""
+    from bench import HEADLINE_LAUNCH, build_cfg1
     w = synth.cfg1()
-    gpu, _ = gpu_cast(L, w, scene=build_cfg1(L, w))
+    scene = build_cfg1(L, w)
+    cfg0 = L.launch_config()
+    try:
+        L.set_launch_config(ray_order=1, **{k: v[0] for k, v in HEADLINE_LAUNCH.items()})
+        setup(L, w, scene)
+        near = w.frames.copy()
+        near[0]["pose"][3] += 1.0
+        near[0]["pose"][7] += 0.5
+        L.schedule_by_cost(scene, near, w.seed, mode=1)
+        beams = L.alloc_beams(L.total_beams(w.frames))
+        L.cast_into(scene, w.frames, w.seed, beams)
+        assert L.sync_status() == 0
+        gpu = to_numpy(beams)
+    finally:
+        L.reset_schedule(0)
+        L.set_launch_config(**cfg0)
     ref = oracle_cast(w)
     rep = compare(gpu, ref, label="cfg1 full frame, every beam")
     _report(rep)
