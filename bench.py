@@ -518,6 +518,12 @@ def run_ours(args, rank, world, local_rank):
                                f"{fp_probe['tflops']:.1f} TFLOP/s at {fp_probe.get('sm_mhz')} MHz median, scaled "
                                f"to the {sm_mhz:.0f} MHz median of the timed casts",
                 "probe": fp_probe,
+                # the same measured rate at the maximum SM clock and at the median clock under a
+                # long GEMM load recorded with the HBM and tensor peaks
+                "peak_tflops_at_mhz": ({f"{mhz:.0f}": fp_probe["tflops"] * mhz / fp_probe["sm_mhz"]
+                                        for mhz in (2070.0, float(peaks.get("clocks_under_load", {})
+                                                                  .get("sm_mhz_median", 1455.0)))}
+                                       if fp_probe.get("sm_mhz") else None),
                 "ops_per_launch_alg": flops, "ops_per_launch_ncu": NCU_FP32["fp32_ops"] if ncu_ok else None,
                 "ops": "alg: 20 FP32 ops per child box of a fetched node, 40 per triangle test (from the "
                        "source, each operation once); ncu: FP32 thread instructions of one captured launch "
