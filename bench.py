@@ -315,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
 
     if args.adjoint_only:
         # the cfg3 fused-MSE backward alone (profiling runs)
-        d3 = cfg3_adjoint(torch, L, scene, tuned_cfg)
+        d3 = cfg3_adjoint(torch, L, scene, use_cache=not args.retune)
         d3["fwd"]()
         # the fused-MSE backward call alone: one launch of the one-pass kernel each
         kernel_ms = event_time(torch, stream, d3["bwd_kernel"], flush, reps=args.steps, warm=args.warmup)
@@ -543,15 +543,18 @@ def run_ours(args, rank, world, local_rank):
 TAPE_BYTES_PER_BEAM = 16  # valid 1 + mat 2 + theta 4 + rf 4 (tape) + intensity 4 + valid 1 (targets)
 
 
-def cfg3_adjoint(torch, L, scene, tuned_cfg):
+def cfg3_adjoint(torch, L, scene, use_cache=True):
     """cfg3 (16 frames of the 128-ch sensor): targets from the hidden table, the
     tape of a forward at the model's table, and closures for the forward, the
-    fused-MSE backward alone and both."""
+    fused-MSE backward alone and both.  The 16-frame cast is tuned on its own
+    (a throughput workload: its best launch differs from a single frame's)."""
     import synth
-    from paper_2208_10295_gb300.tune import apply as apply_cfg
+    from paper_2208_10295_gb300.tune import autotune
     w3 = synth.cfg3()
     L.set_sensor(0, w3.sensors[0])
-    apply_cfg(L, scene, tuned_cfg, w3.frames[:1], w3.seed)
+    L.set_materials(L.build_tables(torch.tensor(w3.params, device=L.device)))
+    cfg3, _ = autotune(L, scene, w3.frames, w3.seed, schedule_frames=w3.frames[:1], use_cache=use_cache,
+                       points=False)
     th = L.build_tables(torch.tensor(w3.hidden_params, device=L.device))
     tp = torch.tensor(w3.params, device=L.device)
     n3 = L.total_beams(w3.frames)
@@ -583,7 +586,7 @@ def cfg3_adjoint(torch, L, scene, tuned_cfg):
         L.cast_backward_mse(tape, 1.0, tgt["intensity"], tgt["valid"], loss, gT, gg)
 
     return {"n": n3, "fwd": fwd, "bwd": bwd, "fwd_bwd": fwd_bwd, "bwd_kernel": bwd_kernel, "loss": loss,
-            "tape": tape, "targets": tgt}
+            "tape": tape, "targets": tgt, "launch": cfg3}
 
 
 def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tuned_cfg):
@@ -661,7 +664,7 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
     del sbuf
     L.set_sensor(0, w1.sensors[0])
     # ---- cfg3: 16 frames forward (dense tape) + fused-MSE adjoint vs plain forward
-    d3 = cfg3_adjoint(torch, L, scene, tuned_cfg)
+    d3 = cfg3_adjoint(torch, L, scene, use_cache=not args.retune)
     f_ms = event_time(torch, stream, d3["fwd"], flush, reps=10, warm=2)
     fb_ms = event_time(torch, stream, d3["fwd_bwd"], flush, reps=10, warm=2)
     b_ms = event_time(torch, stream, d3["bwd"], flush, reps=20, warm=3)
@@ -675,7 +678,7 @@ def run_extras(args, torch, L, scene, w1, table, flush, stream, single_step, tun
                                           "fused MSE adjoint to the 32x91 table, widths and gain",
                               "fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "bwd_ms": fb_ms - f_ms,
                               "bwd_alone_ms": b_ms, "plain_single_frame_fwd_ms": single_ms,
-                              "loss": float(d3["loss"].item()),
+                              "loss": float(d3["loss"].item()), "launch": d3["launch"],
                               "bwd_kernel_ms": bk_ms,
                               "bwd_roofline": {"bound": "hbm", "achieved": b_bytes / (bk_ms / 1e3) / 1e9,
                                                "peak": hbm, "unit": "GB/s",

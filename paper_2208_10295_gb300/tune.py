@@ -1,7 +1,8 @@
 """Autotuner for the cast kernel's launch configuration and ray schedule.
 
 Searches threads per block x resident blocks per SM (which also picks the
-register budget), the traversal variant, the ray order (beam order / Morton
+register budget: up to 512 threads per SM 128 registers, up to 768 85, more
+64), the traversal variant, the ray order (beam order / Morton
 order of directions), the schedule (Morton groups / most expensive groups
 first / per-beam cost buckets) and, when the point cloud is timed too, whether
 the ordered scatter runs inside the cast (cooperative launch) or as its own
@@ -25,7 +26,7 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
 
 SPACE = {
     "block_threads": (64, 128, 256),
-    "blocks_per_sm": (2, 4, 8, 12),
+    "blocks_per_sm": (2, 3, 4, 6, 8, 12),
     "traversal": (0, 1, 2, 3),
     "ray_order": (0, 1),
     "schedule": ("morton", "cost", "bucket"),

@@ -160,7 +160,9 @@ def test_ray_order_and_launch_shapes_bit_identical(L, n_subrays):
     try:
         for cfg in ({"ray_order": 0}, {"block_threads": 64, "tile_rays": 64}, {"traversal": 1}, {"traversal": 2},
                     {"traversal": 3}, {"traversal": 3, "block_threads": 128, "blocks_per_sm": 4},
-                    {"block_threads": 256, "tile_rays": 512, "blocks_per_sm": 2}):
+                    {"block_threads": 256, "tile_rays": 512, "blocks_per_sm": 2},
+                    {"block_threads": 256, "blocks_per_sm": 3}, {"block_threads": 128, "blocks_per_sm": 6},
+                    {"block_threads": 256, "blocks_per_sm": 4, "traversal": 2}):
             L.set_launch_config(**cfg)
             other, _ = gpu_cast(L, w, scene)
             for k in base:
