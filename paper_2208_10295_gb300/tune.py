@@ -63,6 +63,24 @@ def _time_cast(L, scene, frames, seed, out, pts, flush, reps):
     return statistics.median(ts)
 
 
+def _time_stream(L, scene, frames, seed, pts_list, reps):
+    """Per-cast time of back-to-back casts into rotating point buffers (no L2
+    flush; consecutive casts overlap): the streaming regime."""
+    stream = L.stream
+    ts = []
+    for i in range(reps + 1):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(8):
+            L.cast_into(scene, frames, seed, None, pts_list[k % len(pts_list)])
+        b.record(stream)
+        b.synchronize()
+        if i >= 1:
+            ts.append(a.elapsed_time(b) / 8)
+    return statistics.median(ts)
+
+
 def candidates(points=False, wide8=True, restrict=None):
     """Every valid configuration of SPACE; `restrict` (key -> allowed values)
     narrows the search to part of it."""
@@ -94,18 +112,22 @@ def apply(L, scene, cfg, schedule_frames, seed):
 
 
 def autotune(L, scene, frames, seed, schedule_frames=None, cache_path=DEFAULT_CACHE, reps=8, flush_l2=True,
-             use_cache=True, verbose=False, points=False, restrict=None):
+             use_cache=True, verbose=False, points=False, restrict=None, streaming=False):
     """Picks and applies the fastest configuration for casting `frames`
     (`points`: the cast plus the ordered compaction into a point cloud,
     otherwise the cast to dense valid flags).  `schedule_frames` (default
     `frames`) are the poses whose measured costs order the rays for the cost
     schedules: pass a nearby pose (the previous frame) to keep the
     measurement honest.  `restrict` (key -> allowed values) narrows the
-    search.  Returns (config, ms)."""
+    search.  `streaming`: time back-to-back casts of the frames into rotating
+    point buffers without an L2 flush (a sensor streaming frames; consecutive
+    casts overlap) instead of one flushed cast.  Returns (config, ms)."""
     schedule_frames = frames if schedule_frames is None else schedule_frames
     key = workload_key(L, scene, frames) + ("|points" if points else "|dense")
     if restrict:
         key += "|" + json.dumps({k: list(v) for k, v in sorted(restrict.items())})
+    if streaming:
+        key += "|stream"
     cache = {}
     if use_cache and cache_path and os.path.exists(cache_path):
         try:
@@ -120,11 +142,13 @@ def autotune(L, scene, frames, seed, schedule_frames=None, cache_path=DEFAULT_CA
     n = L.total_beams(frames)
     out = None if points else L.alloc_beams(n, ("valid",))
     pts = L.alloc_points(n) if points else None
+    pts_list = [pts] + [L.alloc_points(n) for _ in range(2)] if streaming else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=L.device) if flush_l2 else None
     best = None
     for cfg in candidates(points, wide8=scene.info()["n_nodes8"] > 0 or scene.n_tris == 0, restrict=restrict):
         apply(L, scene, cfg, schedule_frames, seed)
-        ms = _time_cast(L, scene, frames, seed, out, pts, flush, reps)
+        ms = (_time_stream(L, scene, frames, seed, pts_list, max(reps // 2, 3)) if streaming
+              else _time_cast(L, scene, frames, seed, out, pts, flush, reps))
         if verbose:
             print(f"{ms * 1e3:9.1f} us  {cfg}", flush=True)
         if best is None or ms < best[1]:
