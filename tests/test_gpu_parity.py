@@ -828,3 +828,36 @@ def test_overlapped_casts_of_many_frames(L):
     finally:
         L.set_cast_overlap(True)
         scene.free()
+
+
+def test_streaming_autotune_gives_the_same_points(L):
+    """The tuner's streaming regime (back-to-back casts into rotating point
+    buffers, no flush) picks a launch among the shapes the end-to-end loop
+    allows; casts in it give the point cloud of the default launch bit for
+    bit, one at a time and back to back."""
+    from bench import STREAM_LAUNCH
+    from paper_2208_10295_gb300.tune import autotune
+    w = synth.small_terrain(seed=29, n_frames=1, n_az=512)
+    scene, _ = setup(L, w)
+    nb = w.sensors[0].n_beams
+    cfg0 = L.launch_config()
+    ref = L.alloc_points(nb)
+    L.cast_into(scene, w.frames, w.seed, None, ref)
+    assert L.sync_status() == 0
+    c_ref, p_ref = _points_np(ref)
+    try:
+        cfg, ms = autotune(L, scene, w.frames, w.seed, points=True, streaming=True, restrict=STREAM_LAUNCH,
+                           cache_path=None)
+        assert cfg["block_threads"] == 256 and cfg["blocks_per_sm"] in (2, 3) and ms > 0
+        bufs = [L.alloc_points(nb) for _ in range(3)]
+        for k in range(6):
+            L.cast_into(scene, w.frames, w.seed, None, bufs[k % 3])
+        assert L.sync_status() == 0
+        for b in bufs:
+            c, p = _points_np(b)
+            assert c == c_ref
+            for f in p_ref:
+                assert np.array_equal(p[f].view(np.uint8), p_ref[f].view(np.uint8)), f
+    finally:
+        L.set_launch_config(**cfg0)
+        L.reset_schedule(0)
