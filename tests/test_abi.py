@@ -121,3 +121,16 @@ def test_cast_overlap_argument_checks(libpath):
     capi.load(libpath)
     assert capi.lidar_set_cast_overlap(None, 1) == capi.LIDAR_EINVAL
     assert capi.lidar_get_cast_overlap(None, None) == capi.LIDAR_EINVAL
+
+
+def test_header_is_plain_c():
+    """include/lidar.h is a C header: it compiles as C99 (and as C++17) with
+    warnings as errors, so C callers can use the ABI without a C++ compiler."""
+    import shutil
+    import subprocess
+    for cc, args in (("gcc", ["-std=c99", "-x", "c"]), ("g++", ["-std=c++17", "-x", "c++"])):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not available")
+        r = subprocess.run([cc, *args, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", HEADER],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
