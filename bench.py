@@ -46,8 +46,8 @@ STREAM_LAUNCH = {"traversal": (2,), "block_threads": (256,), "blocks_per_sm": (2
 # The hierarchies the benchmark walks: PLOC plus rounds of treelet
 # restructuring, with the builders' area measure weighting the boxes' top and
 # bottom faces (normal to z) less than their sides — the choices that cast
-# fastest on a GB300 (one frame each, L2 flushed; measurements in the design
-# notes)
+# fastest on a GB300 among the round counts, weights, PLOC radii and triangle
+# costs measured (one frame each, L2 flushed)
 CFG1_TREE = {"treelet_rounds": 2, "area_weight": (1.0, 1.0, 0.23)}
 CITY_TREE = {"treelet_rounds": 8, "area_weight": (1.0, 1.0, 0.35)}
 
@@ -55,6 +55,8 @@ CITY_TREE = {"treelet_rounds": 8, "area_weight": (1.0, 1.0, 0.35)}
 def tree_name(tree):
     return (f"PLOC + {tree['treelet_rounds']} treelet rounds, face weights "
             f"{'/'.join(f'{v:g}' for v in tree['area_weight'])} (x/y/z), collapsed 4-wide")
+
+
 POINT_BYTES = 12 + 4 + 4 + 12 + 2 + 4 + 4 + 4   # xyz, range, intensity, normal, material, instance, beam, frame
 
 
